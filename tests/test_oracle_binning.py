@@ -1,0 +1,44 @@
+"""Pins of the oracle's cell binning: the permutation is a stable sort of the
+particles by cell id, checked against numpy's lexsort; boundary positions
+clamp into the grid."""
+import numpy as np
+import pytest
+
+import sph_inputs
+
+
+@pytest.mark.parametrize("n,nc", [(1, (3, 3, 3)), (5000, (7, 7, 7)), (20000, (9, 5, 4))])
+def test_bin_is_stable_sort_by_cell(orc, n, nc):
+    rng = np.random.default_rng(n)
+    box = (1.0, 0.7, 2.5)
+    x = rng.uniform(0, 1, (n, 3)) * np.asarray(box)
+    cell_of, perm, start = orc.bin_cells(x, box, nc)
+    nc_ = np.asarray(nc)
+    k = np.clip(np.floor(x * (nc_.astype(np.float64) / np.asarray(box))), 0, nc_ - 1).astype(np.int64)
+    cid = k[:, 0] + nc_[0] * (k[:, 1] + nc_[1] * k[:, 2])
+    assert np.array_equal(cell_of, cid)
+    ref = np.lexsort((np.arange(n), cid))
+    assert np.array_equal(perm, ref)
+    counts = np.bincount(cid, minlength=int(np.prod(nc_)))
+    assert np.array_equal(start, np.concatenate([[0], np.cumsum(counts)]))
+
+
+def test_boundary_positions_clamp(orc):
+    box = (1.0, 1.0, 1.0)
+    top = np.nextafter(1.0, 0.0)
+    x = np.array([[0.0, 0.0, 0.0], [top, top, top], [1.0, 1.0, 1.0], [-1e-300, 0.5, 0.5],
+                  [1.0 / 3.0, 2.0 / 3.0, 0.5]])
+    cell_of, perm, start = orc.bin_cells(x, box, (3, 3, 3))
+    assert cell_of[0] == 0
+    assert cell_of[1] == 26 and cell_of[2] == 26
+    assert cell_of[3] == 0 + 3 * (1 + 3 * 1)
+    # 1/3 * 3 rounds to exactly 1.0 in FP64, 2/3 * 3 to 2.0
+    assert cell_of[4] == 1 + 3 * (2 + 3 * 1)
+
+
+def test_sod_grid_occupancy(orc):
+    wl = sph_inputs.sod(n_lattice=24, seed=1)
+    nc = orc.grid_dims(wl.box, wl.cell_edge)
+    _, perm, start = orc.bin_cells(wl.col("x"), wl.box, nc)
+    assert start[-1] == wl.n
+    assert sorted(perm.tolist()) == list(range(wl.n))

@@ -1,0 +1,109 @@
+"""Pins of the oracle's storage quantisers (Table 2 and bfloat16) and of the
+packed N-bit bitstream (Section 3.2).
+
+IEEE half and bfloat16 are checked exhaustively against numpy's and torch's
+own conversions; the truncated formats against the definition "keep sign,
+exponent and the top N mantissa bits"; the bitstream against hand-packed words.
+"""
+import numpy as np
+import pytest
+
+
+def test_half_decode_exhaustive(orc):
+    L = orc.lib()
+    codes = np.arange(65536, dtype=np.uint32)
+    ref = codes.astype(np.uint16).view(np.float16).astype(np.float32).view(np.uint32)
+    got = np.array([L.orc_f32_from_f16(int(c)) for c in codes], dtype=np.uint32)
+    nan = np.isnan(codes.astype(np.uint16).view(np.float16))
+    assert np.array_equal(got[~nan], ref[~nan])
+    assert np.all(np.isnan(got[nan].view(np.float32)))
+
+
+def test_half_encode_roundtrip_exhaustive(orc):
+    L = orc.lib()
+    codes = np.arange(65536, dtype=np.uint32)
+    f = codes.astype(np.uint16).view(np.float16)
+    finite = ~np.isnan(f)
+    fbits = f.astype(np.float32).view(np.uint32)
+    back = np.array([L.orc_f16_from_f32(int(b)) for b in fbits], dtype=np.uint32)
+    assert np.array_equal(back[finite], codes[finite])
+
+
+def test_half_encode_matches_numpy_rne(orc):
+    rng = np.random.default_rng(0)
+    # spread over half's normal, subnormal, overflow and underflow ranges
+    e = rng.uniform(-30, 17, 200_000)
+    vals = (np.sign(rng.uniform(-1, 1, e.size)) * 2.0 ** e).astype(np.float32)
+    # exact ties between neighbouring halves
+    h = rng.integers(1, 0x7BFF, 5000).astype(np.uint16).view(np.float16).astype(np.float32)
+    h2 = (h.view(np.uint32) + np.uint32(1 << 12)).view(np.float32)  # midpoints of normals
+    vals = np.concatenate([vals, h2, np.array([65504, 65519.99, 65520, 2 ** -25, 2 ** -24,
+                                               3 * 2 ** -26, 0.0, -0.0], np.float32)])
+    _, code = orc.quantize(vals.astype(np.float64), "fp16")
+    ref = vals.astype(np.float16).view(np.uint16).astype(np.uint32)
+    assert np.array_equal(code, ref)
+
+
+def test_bf16_matches_torch_rne(orc):
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(1)
+    vals = (rng.standard_normal(200_000) * 10.0 ** rng.uniform(-30, 30, 200_000)).astype(np.float32)
+    ties = (rng.integers(0, 1 << 31, 2000, dtype=np.uint32) & np.uint32(0xFFFF0000)) | np.uint32(0x8000)
+    vals = np.concatenate([vals, ties.view(np.float32)])
+    vals = vals[np.isfinite(vals)]
+    _, code = orc.quantize(vals.astype(np.float64), "bf16")
+    ref = torch.from_numpy(vals).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+    assert np.array_equal(code, ref.astype(np.uint32))
+
+
+def test_fp32_is_ieee_rounding(orc):
+    rng = np.random.default_rng(2)
+    d = rng.standard_normal(100_000) * 10.0 ** rng.uniform(-20, 20, 100_000)
+    v, code = orc.quantize(d, "fp32")
+    assert np.array_equal(code, d.astype(np.float32).view(np.uint32))
+    assert np.array_equal(v, d.astype(np.float32).astype(np.float64))
+
+
+@pytest.mark.parametrize("fmt,mant", [("m16", 16), ("m10", 10)])
+def test_truncated_formats(orc, fmt, mant):
+    rng = np.random.default_rng(3)
+    d = rng.standard_normal(100_000) * 10.0 ** rng.uniform(-10, 10, 100_000)
+    v, code = orc.quantize(d, fmt)
+    f = d.astype(np.float32)
+    # Table 2: total size 1 + 8 + N bits
+    assert orc.FMT_BITS[fmt] == 1 + 8 + mant
+    assert np.all(code < (1 << (1 + 8 + mant)))
+    # truncation toward zero: |value| <= |x|, same sign, error below one unit
+    # of the kept mantissa
+    assert np.all(np.abs(v) <= np.abs(f.astype(np.float64)))
+    assert np.all(np.sign(v) == np.sign(f))
+    ulp = 2.0 ** (np.floor(np.log2(np.abs(f.astype(np.float64)))) - mant)
+    assert np.all(np.abs(f - v) < ulp)
+    # the dropped low bits are zero and the kept bits unchanged
+    vb = v.astype(np.float32).view(np.uint32)
+    assert np.all(vb & np.uint32((1 << (23 - mant)) - 1) == 0)
+    assert np.all((vb >> np.uint32(23 - mant)) == (f.view(np.uint32) >> np.uint32(23 - mant)))
+    # specials survive
+    sv, _ = orc.quantize(np.array([np.inf, -np.inf, np.nan, 0.0]), fmt)
+    assert sv[0] == np.inf and sv[1] == -np.inf and np.isnan(sv[2]) and sv[3] == 0.0
+
+
+def test_pack_bits_hand_example(orc):
+    # codes 1, 2, 3 of 19 bits: bits 0..18 hold 1, bits 19..37 hold 2 (bit 20 set),
+    # bits 38..56 hold 3 (word 1, bits 6 and 7)
+    w = orc.pack_bits([1, 2, 3], 19)
+    assert list(w) == [0x00100001, 0x000000C0]
+    assert list(orc.unpack_bits(w, 3, 19)) == [1, 2, 3]
+
+
+@pytest.mark.parametrize("bits", [19, 25, 16, 32])
+def test_pack_unpack_roundtrip(orc, bits):
+    rng = np.random.default_rng(bits)
+    n = 1000
+    codes = rng.integers(0, 1 << bits, n, dtype=np.uint64).astype(np.uint32)
+    w = orc.pack_bits(codes, bits)
+    assert w.size == (n * bits + 31) // 32
+    assert np.array_equal(orc.unpack_bits(w, n, bits), codes)
+    # 32 consecutive codes fill exactly `bits` words
+    w32 = orc.pack_bits(codes[:32], bits)
+    assert w32.size == bits
