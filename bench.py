@@ -1,0 +1,394 @@
+"""Benchmark of the SPH hot path on GB300: one time step = bin -> AoS->SoA
+(U o N o C) -> density with 5 Newton h steps -> force -> kick/drift ->
+SoA->AoS, on the 1,072,476-particle Sod shock tube (FP64 AoS master, FP32
+SoA storage and arithmetic).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  `value` is SPH pair interactions per second (ordered
+pairs j != i inside the support, summed over every density pass and the force
+pass, counted by the kernels), whole job over all ranks.  Each step is timed
+with CUDA events on the library's stream; the L2 is flushed (a 512 MiB write)
+between steps, outside the timed intervals.  `--impl reference` times the FP64
+CPU oracle on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import sph_inputs  # noqa: E402
+
+METRIC = "SPH pair-interactions/s (density+force)"
+UNIT = "pairs/s"
+FLOPS_PER_PAIR = {"density": 29, "force": 50}   # counting convention, see the design doc
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--lattice", type=int, default=124, help="Sod lattice (124 -> 1,072,476 particles)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--prec", default="fp32", help="SoA storage of v, m, h, u (fp32|bf16|fp16|m16|m10)")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- workload
+def workload(args):
+    return sph_inputs.sod(n_lattice=args.lattice)
+
+
+def prec_of(args):
+    if args.prec == "fp32":
+        return None
+    return {"v": args.prec, "m": args.prec, "h": args.prec, "u": args.prec}
+
+
+def traffic_from_profile(kernel_src: str):
+    """DRAM bytes per launch of the density kernel from the committed ncu
+    summary, if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "k_density_sod1m.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m_src = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt)
+    m_tr = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not m_src or not m_tr:
+        return None
+    sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
+    return float(m_tr.group(1)) if sha == m_src.group(1) else None
+
+
+def fp32_peak_tflops(sm_count: int, mhz: float) -> float:
+    # 128 FP32 lanes per SM, one FMA (2 flops) per lane per clock
+    return sm_count * 128 * 2 * mhz * 1e6 / 1e12
+
+
+# ----------------------------------------------------------------- ours
+def run_ours(args, rank, world):
+    import torch
+    import paper_2512_05516_gb300 as sph
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    wl = workload(args)
+    n = wl.n
+    stream = torch.cuda.Stream(dev)
+    aos_host = torch.from_numpy(wl.aos.copy())
+    aos = aos_host.to(dev)
+    nc = [int(math.floor(b / max(wl.cell_edge, 2 * wl.h_cap))) for b in wl.box]
+    params = sph.make_params(wl.box, gamma=wl.gamma, alpha=wl.alpha_av, beta=wl.beta_av,
+                             eps=wl.eps_av, eta=wl.eta, h_max=wl.h_cap)
+    s = sph.Sph(aos, sph.layout_112(), params, int(np.prod(nc)), 0, stream=stream)
+    prec = prec_of(args)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    names = ["bin", "aos_to_soa", "density", "force", "kick_drift", "soa_to_aos"]
+
+    def step(ev=None):
+        calls = [lambda: s.bin_cells(wl.cell_edge),
+                 lambda: s.aos_to_soa(sph.FIELDS_FORCE, prec),
+                 lambda: s.density(wl.newton_steps),
+                 lambda: s.force(),
+                 lambda: s.kick_drift(wl.dt, wl.dt),
+                 lambda: s.soa_to_aos(sph.FIELDS_OUTPUT)]
+        for i, fn in enumerate(calls):
+            if ev is not None:
+                ev[i][0].record(stream)
+            fn()
+            if ev is not None:
+                ev[i][1].record(stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+        stream.synchronize()
+        s.reset_stats()
+        launches0 = s.stats()["launches"]
+        K = args.steps
+        ev_step = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        ev_k = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in names]
+                for _ in range(K)]
+        clocks = ClockSampler(dev.index)
+        clocks.start()
+        time.sleep(0.3)
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        for k in range(K):
+            flush.fill_(k & 0xFF)                    # evict the L2 between steps
+            ev_step[k][0].record(stream)
+            step(ev_k[k])
+            ev_step[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        clk = clocks.stop()
+        st = s.stats()
+        launches = st["launches"] - launches0
+        step_ms = [a.elapsed_time(b) for a, b in ev_step]
+        kern_ms = {nm: [ev_k[k][i][0].elapsed_time(ev_k[k][i][1]) for k in range(K)] for i, nm in enumerate(names)}
+
+    total_s = sum(step_ms) / 1e3
+    pairs = st["pairs_density"] + st["pairs_force"]
+    if st["error_bits"] & (sph.ERR_NONFINITE | sph.ERR_OUTSIDE):
+        raise RuntimeError(f"device error bits {st['error_bits']}")
+
+    # e2e: the same step through the C ABI with the AoS in pinned host memory,
+    # host->device and device->host copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        host = torch.empty_like(aos_host).pin_memory()
+        with torch.cuda.stream(stream):
+            sph.sph_aos_download(s.ctx, host.data_ptr(), n * 112)
+            s.reset_stats()
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            e2e_ms = 0.0
+            for k in range(max(1, K // 2)):
+                flush.fill_(k & 0xFF)
+                t0.record(stream)
+                sph._check(sph.sph_aos_upload(s.ctx, host.data_ptr(), n * 112), "upload")
+                step()
+                sph._check(sph.sph_aos_download(s.ctx, host.data_ptr(), n * 112), "download")
+                t1.record(stream)
+                t1.synchronize()
+                e2e_ms += t0.elapsed_time(t1)
+            st2 = s.stats()
+        e2e = {"value": (st2["pairs_density"] + st2["pairs_force"]) / (e2e_ms / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": n * 112, "d2h_bytes_per_step": n * 112,
+               "steps": max(1, K // 2), "ms_per_step": e2e_ms / max(1, K // 2)}
+
+    dens_pairs_per_launch = st["pairs_density"] / K
+    force_pairs_per_launch = st["pairs_force"] / K
+    t_den = statistics.mean(kern_ms["density"]) / 1e3
+    t_for = statistics.mean(kern_ms["force"]) / 1e3
+    dominant = "density" if t_den >= t_for else "force"
+    t_dom = t_den if dominant == "density" else t_for
+    flops = (dens_pairs_per_launch if dominant == "density" else force_pairs_per_launch) * FLOPS_PER_PAIR[dominant]
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = fp32_peak_tflops(sms, clk.get("sm_max_mhz") or 2070.0)
+    achieved = flops / t_dom / 1e12
+    kernel_src = os.path.join(ROOT, "paper_2512_05516_gb300", "csrc", "k_pairs.cu")
+    roofline = {"bound": "alu", "kernel": f"k_{dominant}", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic_from_profile(kernel_src) if dominant == "density" else None,
+                "peak_basis": "FP32 FMA pipe: SMs x 128 lanes x 2 flops x max SM clock",
+                "flops_per_pair": FLOPS_PER_PAIR[dominant]}
+    hbm = 6753.1
+    try:
+        hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    except Exception:
+        pass
+    bytes_pp = {"aos_to_soa": 116, "kick_drift": 100, "soa_to_aos": 124}
+    kernels = {}
+    for nm in names:
+        ms = statistics.mean(kern_ms[nm])
+        row = {"ms": ms}
+        if nm in bytes_pp:
+            gbs = bytes_pp[nm] * n / (ms / 1e3) / 1e9
+            row.update({"algorithmic_bytes_per_particle": bytes_pp[nm], "GB_s": gbs,
+                        "frac_of_measured_hbm": gbs / hbm})
+        kernels[nm] = row
+    kernels["density"]["pairs"] = dens_pairs_per_launch
+    kernels["force"]["pairs"] = force_pairs_per_launch
+    kernels["density"]["tests"] = st["tests_density"] / K
+    kernels["force"]["tests"] = st["tests_force"] / K
+    s.close()
+    return {"total_s": total_s, "pairs": pairs, "step_ms": step_ms, "clocks": clk, "e2e": e2e,
+            "roofline": roofline, "kernels": kernels, "launches": launches, "n": n}
+
+
+# ----------------------------------------------------------------- oracle
+def run_oracle_sample(n_targets: int, seed: int = 1):
+    """The FP64 oracle (as it stands) on a sample of the same workload: the
+    density with 5 Newton steps, EOS and force of `n_targets` random particles
+    (the density of every particle their forces need is evaluated too)."""
+    import oracle
+    wl = sph_inputs.sod()
+    rng = np.random.default_rng(seed)
+    targets = np.sort(rng.choice(wl.n, n_targets, replace=False))
+    oracle.lib()
+    t0 = time.perf_counter()
+    x, m = wl.col("x"), wl.col("m")
+    d = oracle.density(x, m, wl.col("h"), wl.box, wl.eta, wl.h_cap, wl.newton_steps, targets=targets)
+    P, c = oracle.eos(d["rho"], wl.col("u")[targets], wl.gamma)
+    # forces among the sampled particles use their own h, rho, P, c
+    sub_rho = np.ones(wl.n)
+    sub_h = np.array(wl.col("h"))
+    sub_P = np.zeros(wl.n)
+    sub_c = np.zeros(wl.n)
+    sub_rho[targets] = d["rho"]
+    sub_h[targets] = d["h"]
+    sub_P[targets] = P
+    sub_c[targets] = c
+    f = oracle.force(x, wl.col("v"), m, sub_h, sub_rho, sub_P, sub_c, wl.box, wl.alpha_av,
+                     wl.beta_av, wl.eps_av, targets=targets)
+    dt = time.perf_counter() - t0
+    # pairs the oracle evaluated: every Newton pass and the final pass of the
+    # density (approximated by (steps+1) x final count), plus the force pairs
+    pairs = float(np.sum(d["nngb"]) * (wl.newton_steps + 1) + np.sum(f["nngb"]))
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return pairs, dt, cores
+
+
+def cpu_baseline():
+    n_t = 20000
+    pairs, dt, cores = run_oracle_sample(n_t)
+    return {"value": pairs / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n_t} random particles of the 1,072,476-particle Sod step "
+                      f"(density with 5 Newton steps + EOS + force), {dt:.1f} s"}
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        n_t = 4000
+        times, pairs_l = [], []
+        cores = 1
+        for _ in range(args.warmup):
+            run_oracle_sample(n_t, seed=7)
+        for k in range(args.steps):
+            p, dt, cores = run_oracle_sample(n_t, seed=100 + k)
+            times.append(dt)
+            pairs_l.append(p)
+        value = sum(pairs_l) / sum(times)
+        sample = (f"{n_t} random particles per step of the 1,072,476-particle Sod step "
+                  "(density with 5 Newton steps + EOS + force)")
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "sod_1072476", "sample_particles_per_step": n_t},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }))
+        return
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+    r = run_ours(args, rank, world)
+
+    total_s, pairs = r["total_s"], r["pairs"]
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([total_s], dtype=torch.float64, device="cuda")
+        p = torch.tensor([pairs], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(p, op=dist.ReduceOp.SUM)
+        total_s, pairs = float(t.item()), float(p.item())
+        e2e_v = torch.tensor([r["e2e"]["value"] if r["e2e"] else 0.0], dtype=torch.float64, device="cuda")
+        dist.all_reduce(e2e_v, op=dist.ReduceOp.SUM)
+        if r["e2e"]:
+            r["e2e"]["value"] = float(e2e_v.item())
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+    cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline()
+    out = {
+        "metric": METRIC, "value": pairs / total_s, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "sod_1072476" if args.lattice == 124 else f"sod_lattice{args.lattice}",
+                   "particles_per_gpu": r["n"], "newton_steps": 5, "storage": args.prec,
+                   "aos_record_bytes": 112, "parallelism": f"replicas{world}",
+                   "l2": "flushed between steps (512 MiB write)"},
+        "roofline": r["roofline"], "cpu_baseline": cpu, "e2e": r["e2e"],
+        "gpu_launches": r["launches"], "clocks": r["clocks"], "kernels": r["kernels"],
+    }
+    print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

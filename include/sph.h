@@ -1,0 +1,282 @@
+/*
+ * libsph -- GB300 (sm_103a) SPH particle kernels over FP64 array-of-structs
+ * particle data, with on-device AoS->SoA conversion and reduced-precision
+ * storage (arXiv 2512.05516, "Compiler-supported reduced precision and
+ * AoS-SoA transformations for heterogeneous hardware").
+ *
+ * The paper's operator algebra (Section 4) maps onto the calls below:
+ *   N   narrowing to the fields a kernel reads     -> `fields` masks
+ *   C   AoS -> SoA layout change                    -> sph_aos_to_soa
+ *   U   unpack reduced precision / U^T pack         -> per-field `prec`
+ *   f   the compute kernel                          -> sph_density, sph_force,
+ *                                                      sph_kick_drift
+ *   C^T N^T U^T  widen and scatter back to the AoS  -> sph_soa_to_aos
+ *   M   host <-> device move                        -> sph_aos_upload/download
+ * The GPU-side variant of Eq. 12 (convert on the device, "in-place" in
+ * Section 6.3) is what one time step of these calls performs.
+ *
+ * Conventions shared by every entry point
+ *   - Pointers named d_* are CUDA device pointers; everything else is host.
+ *   - The caller owns the AoS records and one workspace buffer; the library
+ *     never allocates device memory.  The context itself is a small host
+ *     allocation freed by sph_destroy.
+ *   - Every call that launches work is asynchronous on the stream given to
+ *     sph_create and makes no host synchronisation, except sph_get_stats and
+ *     sph_aos_download, which synchronise that stream.
+ *   - Argument errors are detected on the host before any launch and return a
+ *     negative sph_status with no device work issued.  Conditions found on the
+ *     device (non-finite values, positions outside the box, h clamped) are
+ *     recorded in a sticky error word read by sph_get_stats.
+ *   - A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef SPH_H
+#define SPH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SPH_ABI_VERSION 1
+
+typedef enum {
+    SPH_OK = 0,
+    SPH_EINVAL = -1,     /* bad argument: null pointer, bad layout, unsupported format */
+    SPH_ENOSPACE = -2,   /* workspace or cell capacity too small for the request */
+    SPH_ECUDA = -3,      /* a CUDA runtime call or kernel launch failed */
+    SPH_ESTATE = -4,     /* call out of order (e.g. sph_density before sph_bin_cells) */
+    SPH_ECAPACITY = -5,  /* cell grid unusable: < 3 cells on an axis or cells < 2 h_max */
+    SPH_ETIMEOUT = -6,   /* a bounded device wait gave up (reserved; no call waits today) */
+    SPH_ENUMERIC = -7    /* the device recorded a numerical condition (see error_bits) */
+} sph_status;
+
+/* Particle fields.  Bit (1u << field) selects a field in a `fields` mask. */
+enum {
+    SPH_F_X = 0,     /* position, 3 components (AoS: FP64 absolute; SoA: cell-relative) */
+    SPH_F_V = 1,     /* velocity, 3 components */
+    SPH_F_A = 2,     /* acceleration, 3 components (written by sph_force) */
+    SPH_F_M = 3,     /* mass */
+    SPH_F_H = 4,     /* smoothing length (support radius 2h) */
+    SPH_F_RHO = 5,   /* density (written by sph_density) */
+    SPH_F_U = 6,     /* specific internal energy */
+    SPH_F_P = 7,     /* pressure (written by sph_density when u is present) */
+    SPH_F_DUDT = 8,  /* du/dt (written by sph_force) */
+    SPH_F_CS = 9,    /* sound speed (written by sph_density when u is present) */
+    SPH_NFIELDS = 10
+};
+#define SPH_BIT(f) (1u << (f))
+/* the narrowing N of each kernel (Section 6.1: "narrowing tailored to a kernel") */
+#define SPH_FIELDS_DENSITY (SPH_BIT(SPH_F_X) | SPH_BIT(SPH_F_M) | SPH_BIT(SPH_F_H) | SPH_BIT(SPH_F_U))
+#define SPH_FIELDS_FORCE   (SPH_FIELDS_DENSITY | SPH_BIT(SPH_F_V))
+#define SPH_FIELDS_KICK    (SPH_BIT(SPH_F_V) | SPH_BIT(SPH_F_U))
+#define SPH_FIELDS_OUTPUT  (SPH_BIT(SPH_F_V) | SPH_BIT(SPH_F_A) | SPH_BIT(SPH_F_H) | \
+                            SPH_BIT(SPH_F_RHO) | SPH_BIT(SPH_F_U) | SPH_BIT(SPH_F_P))
+
+/* SoA storage formats (Table 2 of the paper, plus bfloat16).  Storage only:
+ * every kernel computes in FP32 (Section 3.2, "expanded to a form supported
+ * natively by the hardware").  FP64 values are first rounded to FP32 (nearest
+ * even); the 16-bit formats round that FP32 value to nearest even; the
+ * truncated formats keep sign, 8 exponent bits and the top 16 or 10 mantissa
+ * bits and store the 25- or 19-bit codes as a packed little-endian bitstream
+ * (value k at bits [kB, (k+1)B) of 32-bit words). */
+typedef enum {
+    SPH_P_FP32 = 0,
+    SPH_P_BF16 = 1,
+    SPH_P_FP16 = 2,
+    SPH_P_FP32_M16 = 3,  /* 25-bit code */
+    SPH_P_FP32_M10 = 4   /* 19-bit code */
+} sph_prec;
+
+/* element type of a field inside the caller's AoS record */
+enum { SPH_AOS_F64 = 0, SPH_AOS_F32 = 1 };
+
+/* AoS layout descriptor: one record per particle, `record_bytes` apart.
+ * offset[f] is the byte offset of field f inside a record (-1: absent); a
+ * vector field stores its 3 components contiguously.  type[f] is SPH_AOS_F64
+ * or SPH_AOS_F32.  Positions must be present and FP64 (absolute positions are
+ * drifted in FP64).  record_bytes and every offset must be multiples of the
+ * field's element size; the AoS base pointer must be 16-byte aligned. */
+typedef struct {
+    int32_t record_bytes;
+    int32_t offset[SPH_NFIELDS];
+    int32_t type[SPH_NFIELDS];
+} sph_aos_layout;
+
+/* Physical and numerical parameters.
+ *   box       periodic box edge lengths; positions lie in [0, box)
+ *   gamma     adiabatic index of the ideal-gas EOS P = (gamma-1) rho u
+ *   alpha_av, beta_av, eps_av   Monaghan artificial viscosity
+ *   eta       h = eta (m/rho)^(1/3) at the smoothing-length fixed point;
+ *             eta = 1/2 (3 N_ngb / (4 pi))^(1/3) for N_ngb neighbours
+ *   h_max     upper clamp of h; cells are at least 2 h_max wide
+ *   flags     SPH_FLAG_* bits */
+typedef struct {
+    double box[3];
+    double gamma;
+    double alpha_av, beta_av, eps_av;
+    double eta;
+    double h_max;
+    int32_t flags;
+    int32_t reserved;
+} sph_params;
+
+#define SPH_FLAG_PLAIN_SUM 1   /* density sum without compensation (default: Neumaier) */
+
+/* workspace options */
+#define SPH_WS_REORDER 1       /* reserve room for sph_bin_cells(reorder_aos = 1) */
+
+/* Counters accumulated on the device since creation or sph_reset_stats. */
+typedef struct {
+    uint64_t pairs_density;      /* ordered pairs j != i, r < 2 h_i, over every density pass */
+    uint64_t pairs_force;        /* ordered pairs j != i, r < h_i + h_j */
+    uint64_t tests_density;      /* candidate distance tests made by the density kernel */
+    uint64_t tests_force;        /* candidate distance tests made by the force kernel */
+    uint64_t hcap_clamps;        /* particles whose h was clamped at h_max */
+    uint32_t error_bits;         /* SPH_ERR_* bits, sticky */
+    int32_t ncell[3];            /* current cell grid */
+    int64_t nitems;              /* work items of the pair kernels */
+    int64_t max_occupancy;       /* particles in the fullest cell */
+    uint64_t launches;           /* kernels this context has launched (host-side count) */
+} sph_stats;
+
+#define SPH_ERR_NONFINITE 1      /* a non-finite value was produced or read */
+#define SPH_ERR_OUTSIDE   2      /* a position lay outside [0, box) at binning */
+#define SPH_ERR_HCAP      4      /* some h was clamped at h_max */
+#define SPH_ERR_NEWTON    8      /* a Newton step met a non-positive derivative */
+
+/* Launch shapes of the pair kernels (an autotuner sets them). */
+typedef struct {
+    int32_t block_threads;       /* i-particles per work item = threads per CTA (32..512, multiple of 32) */
+    int32_t ctas_per_sm;         /* persistent CTAs per SM (0: occupancy maximum) */
+    int32_t stage_density;       /* neighbour candidates staged per chunk, density kernel */
+    int32_t stage_force;         /* neighbour candidates staged per chunk, force kernel */
+} sph_tuning;
+
+/* Where the library's arrays live inside the workspace (byte offsets from the
+ * workspace base, -1 when absent), for inspection and testing. */
+typedef struct {
+    int64_t n;
+    int32_t ncell[3];
+    double cell_edge[3];
+    int64_t off_perm;            /* int32[n]: sorted slot -> original particle index */
+    int64_t off_cell_of_slot;    /* int32[n]: sorted slot -> cell id */
+    int64_t off_cell_start;      /* int32[ncell+1] */
+    int64_t off_nngb;            /* int32[n], neighbour counts of the last density call */
+    int64_t off_nngb_force;      /* int32[n], neighbour counts of the last force call */
+    int64_t off_soa[SPH_NFIELDS][3];
+    int32_t prec[SPH_NFIELDS];   /* current storage format of each SoA field */
+    uint32_t valid;              /* fields whose SoA copy is current */
+    int32_t reserved;
+} sph_desc;
+
+typedef struct sph_ctx sph_ctx;
+
+/* Bytes of workspace a context needs for n particles and at most ncell_max
+ * cells; `ws_flags` is a mask of SPH_WS_* bits.  Returns 0 on a bad argument.
+ * Pure host function. */
+size_t sph_workspace_bytes(const sph_aos_layout *layout, int64_t n, int64_t ncell_max,
+                           uint32_t ws_flags);
+
+/* Create a context over n caller-owned AoS records at d_aos (device memory,
+ * records in `layout`), using the caller-owned device workspace d_workspace of
+ * workspace_bytes (at least sph_workspace_bytes(layout, n, ncell_max, ws_flags),
+ * 256-byte aligned).  `stream` is a cudaStream_t (NULL: the legacy default
+ * stream).  The CUDA device current at this call is used for all later calls.
+ * Errors: SPH_EINVAL (layout, params or pointers), SPH_ENOSPACE (workspace),
+ * SPH_ECUDA (device query).  On success *out receives the context. */
+sph_status sph_create(const sph_aos_layout *layout, const sph_params *params, int64_t n,
+                      int64_t ncell_max, uint32_t ws_flags, void *d_aos, void *d_workspace,
+                      size_t workspace_bytes, void *stream, sph_ctx **out);
+
+/* S1, cell binning (the paper works on 64-particle co-located buffers,
+ * Section 6; the build generalises them to a uniform grid).  Cells per axis
+ * nc_d = floor(box_d / max(cell_edge, 2 h_max)); each particle's cell is
+ * k_d = clamp(floor(x_d * (nc_d / box_d)), 0, nc_d - 1) in FP64, linear id
+ * kx + nc_x (ky + nc_y kz).  The permutation lists particles cell by cell,
+ * ascending original index inside a cell (a stable sort), and the pair-kernel
+ * work items are rebuilt.  reorder_aos = 1 also rewrites the AoS records in
+ * that order (the permutation then becomes the identity); it needs a
+ * workspace created with SPH_WS_REORDER.  Invalidates every SoA field.
+ * Errors: SPH_ECAPACITY (< 3 cells on an axis), SPH_ENOSPACE (more than
+ * ncell_max cells, or reorder without room), SPH_ECUDA. */
+sph_status sph_bin_cells(sph_ctx *ctx, double cell_edge, int32_t reorder_aos);
+
+/* S2, U o N o C (Section 4, Eq. 12): gather the fields in `fields` from the AoS
+ * in cell order, round them to their storage formats and write them as SoA.
+ * prec[f] (SPH_NFIELDS entries, NULL: FP32 everywhere) is the storage format
+ * of field f.  Positions are stored as offsets from their cell origin
+ * k_d * box_d / nc_d (computed in FP64, then rounded); they accept FP32 or
+ * FP16.  A, RHO, P, CS and DUDT accept FP32, BF16 and FP16; V, M, H and U
+ * accept every format.  Requires sph_bin_cells.  Errors: SPH_EINVAL (field
+ * absent from the layout, or format not allowed for it), SPH_ESTATE. */
+sph_status sph_aos_to_soa(sph_ctx *ctx, uint32_t fields, const int32_t *prec);
+
+/* S3+S4, density (Eq. 6, gather form rho_i = sum_j m_j W(r_ij, h_i), M4 cubic
+ * spline with support 2h, FP32 arithmetic, compensated sum) with
+ * `newton_steps` Newton steps on f(h) = rho(h) - m_i (eta/h)^3 (each step
+ * clamped to [h/2, 2h] and to h_max) and a final density sum at the last h.
+ * Writes RHO, the neighbour counts (j != i, r < 2h), H when newton_steps > 0,
+ * and P = (gamma-1) rho u and CS = sqrt(gamma P / rho) when U is current.
+ * Reads X, M, H (and U).  Requires sph_aos_to_soa of X, M, H.
+ * Errors: SPH_EINVAL (newton_steps < 0 or > 32), SPH_ESTATE, SPH_ECUDA. */
+sph_status sph_density(sph_ctx *ctx, int32_t newton_steps);
+
+/* S5, symmetric hydro force (Eq. 7 with Monaghan artificial viscosity and the
+ * matching energy equation, Eq. 5): for pairs r < h_i + h_j,
+ *   a_i    = -sum_j m_j (P_i/rho_i^2 + P_j/rho_j^2 + Pi_ij) grad_i W(r_ij, (h_i+h_j)/2)
+ *   du_i/dt =  sum_j m_j (P_i/rho_i^2 + Pi_ij/2) v_ij . grad_i W
+ * in FP32.  Reads X, V, M, H, RHO, P, CS; writes A and DUDT.
+ * Errors: SPH_ESTATE (inputs not current), SPH_ECUDA. */
+sph_status sph_force(sph_ctx *ctx);
+
+/* S6, kick/drift (the paper's linear kernels Kick and Drift, Section 6):
+ * v += a dt_kick and u += du/dt dt_kick in FP32 in the SoA, then
+ * x += v dt_drift in FP64 directly in the AoS, wrapped into [0, box).
+ * Reads A, DUDT, V, U; writes V, U (SoA) and X (AoS).  The SoA positions
+ * become stale (re-bin before the next pair kernel).
+ * Errors: SPH_ESTATE, SPH_ECUDA. */
+sph_status sph_kick_drift(sph_ctx *ctx, double dt_kick, double dt_drift);
+
+/* S7, C^T o N^T o U^T (Section 4, the write-back epilogue): widen the SoA
+ * fields in `fields` to the AoS element type and scatter them to their
+ * records.  Positions are not written (the AoS keeps them in FP64; drift
+ * updates them in place).  Errors: SPH_EINVAL (X requested or field absent
+ * from the layout), SPH_ESTATE (field not current), SPH_ECUDA. */
+sph_status sph_soa_to_aos(sph_ctx *ctx, uint32_t fields);
+
+/* Copy the device counters to *out.  Synchronises the context's stream.
+ * Returns SPH_ENUMERIC when error_bits has SPH_ERR_NONFINITE or
+ * SPH_ERR_OUTSIDE set (the counters are still filled in), else SPH_OK. */
+sph_status sph_get_stats(sph_ctx *ctx, sph_stats *out);
+
+/* Zero the device counters and the sticky error word (asynchronous). */
+sph_status sph_reset_stats(sph_ctx *ctx);
+
+/* Set launch shapes; values <= 0 keep the defaults.  Takes effect at the next
+ * pair-kernel call.  Errors: SPH_EINVAL (block_threads not a multiple of 32 in
+ * [32, 512], or stage sizes above the shared-memory limit). */
+sph_status sph_set_tuning(sph_ctx *ctx, const sph_tuning *tuning);
+sph_status sph_get_tuning(const sph_ctx *ctx, sph_tuning *out);
+
+/* Describe where the library's arrays live in the workspace. */
+sph_status sph_describe(const sph_ctx *ctx, sph_desc *out);
+
+/* M (Section 4): copy `bytes` bytes of AoS records between pinned or pageable
+ * host memory and the context's AoS on its stream.  bytes must not exceed
+ * n * record_bytes.  sph_aos_download synchronises the stream before it
+ * returns.  Errors: SPH_EINVAL, SPH_ECUDA. */
+sph_status sph_aos_upload(sph_ctx *ctx, const void *host, size_t bytes);
+sph_status sph_aos_download(sph_ctx *ctx, void *host, size_t bytes);
+
+/* Free the host-side context (the caller's buffers are untouched). */
+void sph_destroy(sph_ctx *ctx);
+
+/* Static English text for a status code. */
+const char *sph_status_str(sph_status status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPH_H */

@@ -1,0 +1,309 @@
+"""Python binding of libsph, the GB300 (sm_103a) SPH hot path over FP64
+array-of-structs particles with on-device AoS->SoA conversion and
+reduced-precision storage (arXiv 2512.05516).
+
+Argument marshalling only.  Module-level functions carry the C names
+(``sph_create``, ``sph_bin_cells``, ...); ``Sph`` bundles a context with the
+torch tensors that own its device memory.  PyTorch provides device memory and
+streams; every step of the path runs in libsph's CUDA kernels, and importing
+this package raises when the library is missing (there is no fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+from . import _capi
+from ._capi import (AOS_F32, AOS_F64, BIT, ERR_HCAP, ERR_NEWTON, ERR_NONFINITE, ERR_OUTSIDE,
+                    F_A, F_CS, F_DUDT, F_H, F_M, F_P, F_RHO, F_U, F_V, F_X, FIELD_NAMES,
+                    FIELDS_DENSITY, FIELDS_FORCE, FIELDS_KICK, FIELDS_OUTPUT, FLAG_PLAIN_SUM,
+                    NCOMP, P_BF16, P_FP16, P_FP32, P_FP32_M10, P_FP32_M16, PREC, SPH_NFIELDS,
+                    WS_REORDER, sph_aos_layout, sph_desc, sph_params, sph_stats, sph_tuning)
+
+_lib = _capi.load()
+
+
+class SphError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status} ({_lib.sph_status_str(status).decode()})")
+
+
+def _check(status: int, what: str, allow=(0,)):
+    if status not in allow:
+        raise SphError(status, what)
+    return status
+
+
+def library_path() -> str:
+    return _capi._build.LIB_PATH
+
+
+# ----------------------------------------------------------------- C names
+def sph_workspace_bytes(layout: sph_aos_layout, n: int, ncell_max: int, ws_flags: int = 0) -> int:
+    return int(_lib.sph_workspace_bytes(C.byref(layout), n, ncell_max, ws_flags))
+
+
+def sph_create(layout, params, n, ncell_max, ws_flags, d_aos, d_workspace, workspace_bytes, stream):
+    out = C.c_void_p()
+    st = _lib.sph_create(C.byref(layout), C.byref(params), n, ncell_max, ws_flags,
+                         C.c_void_p(d_aos), C.c_void_p(d_workspace), workspace_bytes,
+                         C.c_void_p(stream), C.byref(out))
+    return st, out
+
+
+def sph_bin_cells(ctx, cell_edge: float, reorder_aos: int) -> int:
+    return _lib.sph_bin_cells(ctx, float(cell_edge), int(reorder_aos))
+
+
+def sph_aos_to_soa(ctx, fields: int, prec) -> int:
+    arr = None
+    if prec is not None:
+        arr = (C.c_int32 * SPH_NFIELDS)(*prec)
+    return _lib.sph_aos_to_soa(ctx, fields, arr)
+
+
+def sph_density(ctx, newton_steps: int) -> int:
+    return _lib.sph_density(ctx, int(newton_steps))
+
+
+def sph_force(ctx) -> int:
+    return _lib.sph_force(ctx)
+
+
+def sph_kick_drift(ctx, dt_kick: float, dt_drift: float) -> int:
+    return _lib.sph_kick_drift(ctx, float(dt_kick), float(dt_drift))
+
+
+def sph_soa_to_aos(ctx, fields: int) -> int:
+    return _lib.sph_soa_to_aos(ctx, fields)
+
+
+def sph_get_stats(ctx):
+    s = sph_stats()
+    st = _lib.sph_get_stats(ctx, C.byref(s))
+    return st, s
+
+
+def sph_reset_stats(ctx) -> int:
+    return _lib.sph_reset_stats(ctx)
+
+
+def sph_set_tuning(ctx, tuning: sph_tuning) -> int:
+    return _lib.sph_set_tuning(ctx, C.byref(tuning))
+
+
+def sph_get_tuning(ctx):
+    t = sph_tuning()
+    st = _lib.sph_get_tuning(ctx, C.byref(t))
+    return st, t
+
+
+def sph_describe(ctx):
+    d = sph_desc()
+    st = _lib.sph_describe(ctx, C.byref(d))
+    return st, d
+
+
+def sph_aos_upload(ctx, host_ptr: int, nbytes: int) -> int:
+    return _lib.sph_aos_upload(ctx, C.c_void_p(host_ptr), nbytes)
+
+
+def sph_aos_download(ctx, host_ptr: int, nbytes: int) -> int:
+    return _lib.sph_aos_download(ctx, C.c_void_p(host_ptr), nbytes)
+
+
+def sph_destroy(ctx) -> None:
+    _lib.sph_destroy(ctx)
+
+
+def sph_status_str(status: int) -> str:
+    return _lib.sph_status_str(status).decode()
+
+
+# ----------------------------------------------------------------- helpers
+RECORD_112 = {"x": 0, "v": 24, "a": 48, "m": 72, "h": 80, "rho": 88, "u": 96, "P": 104}
+
+
+def make_layout(offsets: dict, record_bytes: int, f32_fields=()) -> sph_aos_layout:
+    """Layout descriptor from a field-name -> byte-offset map."""
+    L = sph_aos_layout()
+    L.record_bytes = record_bytes
+    for f in range(SPH_NFIELDS):
+        L.offset[f] = -1
+        L.type[f] = AOS_F64
+    for name, off in offsets.items():
+        f = FIELD_NAMES.index(name)
+        L.offset[f] = off
+        L.type[f] = AOS_F32 if name in f32_fields else AOS_F64
+    return L
+
+
+def layout_112() -> sph_aos_layout:
+    """The 112-byte FP64 record {x[3], v[3], a[3], m, h, rho, u, P}."""
+    return make_layout(RECORD_112, 112)
+
+
+def make_params(box, gamma=5.0 / 3.0, alpha=1.0, beta=2.0, eps=0.01, eta=1.1272516517868265,
+                h_max=0.1, flags=0) -> sph_params:
+    p = sph_params()
+    for k in range(3):
+        p.box[k] = float(box[k])
+    p.gamma, p.alpha_av, p.beta_av, p.eps_av = float(gamma), float(alpha), float(beta), float(eps)
+    p.eta, p.h_max, p.flags = float(eta), float(h_max), int(flags)
+    return p
+
+
+def prec_array(prec) -> list:
+    """Per-field storage formats from a {field name: format name} dict."""
+    out = [P_FP32] * SPH_NFIELDS
+    if prec:
+        for name, fmt in prec.items():
+            out[FIELD_NAMES.index(name)] = PREC[fmt] if isinstance(fmt, str) else int(fmt)
+    return out
+
+
+def mask(*names) -> int:
+    m = 0
+    for nm in names:
+        m |= BIT(FIELD_NAMES.index(nm))
+    return m
+
+
+class Sph:
+    """A libsph context over a torch-owned AoS on the current CUDA device.
+
+    `aos` is a CUDA tensor holding n records of `layout.record_bytes` bytes
+    (any dtype; e.g. float64 of shape (n, 14) for the 112-byte record).  The
+    workspace is a torch uint8 tensor owned by this object.  All calls run on
+    `stream` (default: torch's current stream)."""
+
+    def __init__(self, aos, layout: sph_aos_layout, params: sph_params, ncell_max: int,
+                 ws_flags: int = 0, stream=None):
+        import torch
+        if not aos.is_cuda:
+            raise ValueError("aos must be a CUDA tensor")
+        self.torch = torch
+        self.aos = aos
+        self.layout = layout
+        self.params = params
+        nbytes = aos.numel() * aos.element_size()
+        if nbytes % layout.record_bytes:
+            raise ValueError("AoS size is not a whole number of records")
+        self.n = nbytes // layout.record_bytes
+        self.stream = stream if stream is not None else torch.cuda.current_stream(aos.device)
+        self.ws_bytes = sph_workspace_bytes(layout, self.n, ncell_max, ws_flags)
+        if self.ws_bytes == 0:
+            raise SphError(-1, "sph_workspace_bytes")
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=aos.device)
+        with torch.cuda.device(aos.device):
+            st, ctx = sph_create(layout, params, self.n, ncell_max, ws_flags, aos.data_ptr(),
+                                 self.ws.data_ptr(), self.ws_bytes, self.stream.cuda_stream)
+        _check(st, "sph_create")
+        self.ctx = ctx
+
+    # --- the path
+    def bin_cells(self, cell_edge: float = 0.0, reorder: bool = False):
+        _check(sph_bin_cells(self.ctx, cell_edge, 1 if reorder else 0), "sph_bin_cells")
+
+    def aos_to_soa(self, fields: int, prec=None):
+        arr = prec if isinstance(prec, list) else (prec_array(prec) if prec is not None else None)
+        _check(sph_aos_to_soa(self.ctx, fields, arr), "sph_aos_to_soa")
+
+    def density(self, newton_steps: int = 0):
+        _check(sph_density(self.ctx, newton_steps), "sph_density")
+
+    def force(self):
+        _check(sph_force(self.ctx), "sph_force")
+
+    def kick_drift(self, dt_kick: float, dt_drift: float):
+        _check(sph_kick_drift(self.ctx, dt_kick, dt_drift), "sph_kick_drift")
+
+    def soa_to_aos(self, fields: int):
+        _check(sph_soa_to_aos(self.ctx, fields), "sph_soa_to_aos")
+
+    def step(self, dt: float, newton_steps: int = 5, prec=None, cell_edge: float = 0.0,
+             reorder: bool = False, out_fields: int = FIELDS_OUTPUT):
+        """One SPH time step: bin, convert, density (+h), force, kick/drift,
+        write back (the in-place GPU pipeline of the paper's Section 6.3)."""
+        self.bin_cells(cell_edge, reorder)
+        self.aos_to_soa(FIELDS_FORCE, prec)
+        self.density(newton_steps)
+        self.force()
+        self.kick_drift(dt, dt)
+        self.soa_to_aos(out_fields)
+
+    # --- inspection
+    def stats(self) -> dict:
+        st, s = sph_get_stats(self.ctx)
+        _check(st, "sph_get_stats", allow=(0, -7))
+        return {"pairs_density": s.pairs_density, "pairs_force": s.pairs_force,
+                "tests_density": s.tests_density, "tests_force": s.tests_force,
+                "hcap_clamps": s.hcap_clamps, "error_bits": s.error_bits,
+                "ncell": tuple(s.ncell), "nitems": s.nitems, "max_occupancy": s.max_occupancy,
+                "launches": s.launches, "status": st}
+
+    def reset_stats(self):
+        _check(sph_reset_stats(self.ctx), "sph_reset_stats")
+
+    def set_tuning(self, block_threads=0, ctas_per_sm=0, stage_density=0, stage_force=0):
+        t = sph_tuning(block_threads, ctas_per_sm, stage_density, stage_force)
+        _check(sph_set_tuning(self.ctx, t), "sph_set_tuning")
+
+    def tuning(self) -> dict:
+        st, t = sph_get_tuning(self.ctx)
+        _check(st, "sph_get_tuning")
+        return {"block_threads": t.block_threads, "ctas_per_sm": t.ctas_per_sm,
+                "stage_density": t.stage_density, "stage_force": t.stage_force}
+
+    def describe(self) -> sph_desc:
+        st, d = sph_describe(self.ctx)
+        _check(st, "sph_describe")
+        return d
+
+    def _ws_view(self, off: int, count: int, dtype):
+        torch = self.torch
+        es = torch.empty((), dtype=dtype).element_size()
+        return self.ws[off:off + count * es].view(dtype)
+
+    def perm(self):
+        d = self.describe()
+        return self._ws_view(d.off_perm, self.n, self.torch.int32)
+
+    def slot_cell(self):
+        d = self.describe()
+        return self._ws_view(d.off_cell_of_slot, self.n, self.torch.int32)
+
+    def cell_start(self):
+        d = self.describe()
+        nc = d.ncell[0] * d.ncell[1] * d.ncell[2]
+        return self._ws_view(d.off_cell_start, nc + 1, self.torch.int32)
+
+    def nngb(self, force: bool = False):
+        d = self.describe()
+        return self._ws_view(d.off_nngb_force if force else d.off_nngb, self.n, self.torch.int32)
+
+    def soa_raw(self, field: str, comp: int = 0):
+        """The stored words of one SoA component (float32, 16-bit codes, or the
+        uint32 words of a packed stream)."""
+        torch = self.torch
+        d = self.describe()
+        f = FIELD_NAMES.index(field)
+        fmt = d.prec[f]
+        off = d.off_soa[f][comp]
+        if fmt == P_FP32:
+            return self._ws_view(off, self.n, torch.float32)
+        if fmt in (P_BF16, P_FP16):
+            return self._ws_view(off, self.n, torch.int16)
+        bits = 25 if fmt == P_FP32_M16 else 19
+        return self._ws_view(off, (self.n * bits + 31) // 32, torch.int32)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            sph_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

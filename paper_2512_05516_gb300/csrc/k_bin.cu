@@ -1,0 +1,347 @@
+// S1 cell binning: FP64 cell index per particle, cell histogram, exclusive
+// scan, and a stable LSD radix sort of (cell id, particle index) pairs, so
+// that particles end up cell by cell in ascending original index.  Also
+// builds the pair-kernel work items (cell, first slot, count) and optionally
+// rewrites the AoS records in cell order.
+#include "sph_internal.cuh"
+
+namespace sph {
+namespace {
+
+// ---------------------------------------------------------------------------
+// cell id of every particle: k_d = clamp(floor(x_d * (nc_d / L_d)), 0, nc_d-1)
+// ---------------------------------------------------------------------------
+struct CellArgs {
+    const uint8_t *aos;
+    int64_t n;
+    int32_t stride, xoff;
+    double inv[3], box[3];
+    int32_t nc[3];
+    int32_t *keys, *vals, *count;
+    DevStats *st;
+};
+
+__device__ __forceinline__ int32_t cell_coord(double x, double inv, int32_t nc)
+{
+    double f = floor(__dmul_rn(x, inv));
+    if (!(f >= 0.0)) return 0;
+    if (f > (double)(nc - 1)) return nc - 1;
+    return (int32_t)f;
+}
+
+__global__ void k_cell_ids(CellArgs a)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const double *x = (const double *)(a.aos + i * a.stride + a.xoff);
+    double x0 = x[0], x1 = x[1], x2 = x[2];
+    bool outside = !(x0 >= 0.0 && x0 < a.box[0] && x1 >= 0.0 && x1 < a.box[1] &&
+                     x2 >= 0.0 && x2 < a.box[2]);
+    if (outside) set_error(a.st, SPH_ERR_OUTSIDE | ((isfinite(x0) && isfinite(x1) && isfinite(x2)) ? 0u : SPH_ERR_NONFINITE));
+    int32_t kx = cell_coord(x0, a.inv[0], a.nc[0]);
+    int32_t ky = cell_coord(x1, a.inv[1], a.nc[1]);
+    int32_t kz = cell_coord(x2, a.inv[2], a.nc[2]);
+    int32_t c = kx + a.nc[0] * (ky + a.nc[1] * kz);
+    a.keys[i] = c;
+    a.vals[i] = (int32_t)i;
+    atomicAdd(&a.count[c], 1);
+}
+
+// ---------------------------------------------------------------------------
+// device-wide exclusive scan (reduce / scan partials / downsweep)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int32_t warp_incl_scan(int32_t v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int32_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// exclusive scan of one value per thread across a 1024-thread block; returns
+// the block total in *total
+__device__ int32_t block_excl_scan(int32_t v, int32_t *smem32, int32_t *total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t inc = warp_incl_scan(v);
+    if (lane == 31) smem32[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        int32_t w = lane < (int)(blockDim.x >> 5) ? smem32[lane] : 0;
+        int32_t wi = warp_incl_scan(w);
+        smem32[lane] = wi - w;
+        if (lane == 31) smem32[32] = wi;
+    }
+    __syncthreads();
+    int32_t r = inc - v + smem32[warp];
+    *total = smem32[32];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int32_t *in, int64_t len, int32_t *part)
+{
+    __shared__ int32_t s[33];
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int32_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+        if (base + k < len) sum += in[base + k];
+    int32_t tot;
+    block_excl_scan(sum, s, &tot);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+// exclusive scan of part[0..nb) in place by one block; writes the grand total
+// to part[nb] and to out[len]
+__global__ void __launch_bounds__(kScanThreads) k_scan_partials(int32_t *part, int64_t nb, int32_t *out, int64_t len)
+{
+    __shared__ int32_t s[33];
+    int32_t carry = 0;
+    for (int64_t c0 = 0; c0 < nb; c0 += kScanThreads) {
+        int64_t i = c0 + threadIdx.x;
+        int32_t v = i < nb ? part[i] : 0;
+        int32_t tot;
+        int32_t e = block_excl_scan(v, s, &tot);
+        if (i < nb) part[i] = e + carry;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) {
+        part[nb] = carry;
+        out[len] = carry;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(const int32_t *in, int32_t *out, int64_t len, const int32_t *part)
+{
+    __shared__ int32_t s[33];
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int32_t v[kScanItems];
+    int32_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = base + k < len ? in[base + k] : 0;
+        sum += v[k];
+    }
+    int32_t tot;
+    int32_t e = block_excl_scan(sum, s, &tot) + part[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < len) out[base + k] = e;
+        e += v[k];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// stable LSD radix sort, 8-bit digits
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kRadixThreads) k_radix_hist(const int32_t *keys, int64_t n, int shift, uint32_t *ghist, int64_t nblk)
+{
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * kRadixTile;
+#pragma unroll
+    for (int r = 0; r < kRadixItems; ++r) {
+        int64_t i = base + r * kRadixThreads + threadIdx.x;
+        if (i < n) atomicAdd(&h[((uint32_t)keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    ghist[(int64_t)threadIdx.x * nblk + blockIdx.x] = h[threadIdx.x];
+}
+
+// Scatter one tile.  Keys are ranked in tile order (round by round, then
+// warp, then lane), so equal digits keep their input order: the sort is
+// stable.  ghist holds the exclusive scan over (digit, block).
+__global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(const int32_t *kin, const int32_t *vin, int32_t *kout,
+                                                                 int32_t *vout, int64_t n, int shift,
+                                                                 const uint32_t *ghist, int64_t nblk)
+{
+    constexpr int W = kRadixThreads / 32;
+    __shared__ uint32_t s_base[256];
+    __shared__ uint32_t s_run[256];
+    __shared__ uint32_t s_cnt[W][256];
+    __shared__ uint32_t s_pre[W][256];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    s_base[tid] = ghist[(int64_t)tid * nblk + blockIdx.x];
+    s_run[tid] = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) s_cnt[w][tid] = 0;
+    __syncthreads();
+    const uint32_t lt = (1u << lane) - 1u;
+    int64_t base = (int64_t)blockIdx.x * kRadixTile;
+    for (int r = 0; r < kRadixItems; ++r) {
+        int64_t i = base + r * kRadixThreads + tid;
+        bool ok = i < n;
+        int32_t key = ok ? kin[i] : 0;
+        int32_t val = ok ? vin[i] : 0;
+        uint32_t d = ok ? (((uint32_t)key >> shift) & 255u) : 256u;
+        uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t rank = __popc(peers & lt);
+        if (ok && rank == 0) s_cnt[warp][d] = __popc(peers);
+        __syncthreads();
+        {   // per digit: exclusive prefix over warps, carried across rounds
+            uint32_t run = s_run[tid];
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                uint32_t c = s_cnt[w][tid];
+                s_pre[w][tid] = run;
+                s_cnt[w][tid] = 0;
+                run += c;
+            }
+            s_run[tid] = run;
+        }
+        __syncthreads();
+        if (ok) {
+            uint32_t pos = s_base[d] + s_pre[warp][d] + rank;
+            kout[pos] = key;
+            vout[pos] = val;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// work items: each cell is split into tiles of `block` slots
+// ---------------------------------------------------------------------------
+__global__ void k_items_count(const int32_t *cell_start, int64_t ncell, int block, int32_t *tmp, DevStats *st)
+{
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    int32_t cnt = cell_start[c + 1] - cell_start[c];
+    tmp[c] = (cnt + block - 1) / block;
+    if (cnt > 0) atomicMax(&st->max_occ, cnt);
+}
+
+__global__ void k_items_fill(const int32_t *cell_start, const int32_t *item_off, int64_t ncell, int block,
+                             int32_t *icell, int32_t *ifirst, int32_t *icount, DevStats *st)
+{
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c == 0) st->nitems = item_off[ncell];
+    if (c >= ncell) return;
+    int32_t s = cell_start[c], e = cell_start[c + 1];
+    int32_t o = item_off[c];
+    for (int32_t f = s; f < e; f += block, ++o) {
+        icell[o] = (int32_t)c;
+        ifirst[o] = f;
+        icount[o] = min(block, e - f);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// optional AoS reordering
+// ---------------------------------------------------------------------------
+__global__ void k_gather_records(const uint8_t *aos, uint8_t *dst, const int32_t *perm, int64_t n, int32_t stride)
+{
+    // one warp per record, 8-byte words
+    int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    const uint64_t *src = (const uint64_t *)(aos + (int64_t)perm[warp] * stride);
+    uint64_t *d = (uint64_t *)(dst + warp * stride);
+    for (int w = lane; w < stride / 8; w += 32) d[w] = src[w];
+}
+
+__global__ void k_iota(int32_t *p, int64_t n)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = (int32_t)i;
+}
+
+inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t scan_exclusive(const int32_t *in, int32_t *out, int64_t len, int32_t *part, cudaStream_t s,
+                           uint64_t *launches)
+{
+    if (len <= 0) {
+        return cudaMemsetAsync(out, 0, sizeof(int32_t), s);
+    }
+    *launches += 3;
+    int64_t nb = (len + kScanTile - 1) / kScanTile;
+    k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(in, len, part);
+    k_scan_partials<<<1, kScanThreads, 0, s>>>(part, nb, out, len);
+    k_scan_down<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, len, part);
+    return cudaGetLastError();
+}
+
+cudaError_t run_binning(sph_ctx *c, int reorder)
+{
+    cudaStream_t s = c->stream;
+    cudaError_t e;
+    const int64_t n = c->n;
+    if ((e = cudaMemsetAsync(c->cell_count, 0, sizeof(int32_t) * c->ncell, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(&c->dstats->max_occ, 0, sizeof(int), s)) != cudaSuccess) return e;
+    c->sorted_buf = 0;
+    if (n > 0) {
+        CellArgs a;
+        a.aos = c->aos;
+        a.n = n;
+        a.stride = c->layout.record_bytes;
+        a.xoff = c->layout.offset[SPH_F_X];
+        for (int k = 0; k < 3; ++k) {
+            a.inv[k] = c->inv[k];
+            a.box[k] = c->params.box[k];
+            a.nc[k] = c->nc[k];
+        }
+        a.keys = c->keys[0];
+        a.vals = c->vals[0];
+        a.count = c->cell_count;
+        a.st = c->dstats;
+        k_cell_ids<<<blocks_for(n, 256), 256, 0, s>>>(a);
+        c->launches += 1;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if ((e = scan_exclusive(c->cell_count, c->cell_start, c->ncell, c->scan_part, s, &c->launches)) != cudaSuccess) return e;
+    if (n > 0) {
+        int bits = 0;
+        while (bits < 31 && ((int64_t)1 << bits) < c->ncell) ++bits;
+        const int64_t nblk = c->plan.nblk_radix;
+        int cur = 0;
+        for (int shift = 0; shift < bits; shift += 8) {
+            k_radix_hist<<<(unsigned)nblk, kRadixThreads, 0, s>>>(c->keys[cur], n, shift, c->ghist, nblk);
+            c->launches += 2;   // histogram and scatter
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            if ((e = scan_exclusive((const int32_t *)c->ghist, (int32_t *)c->ghist, 256 * nblk, c->scan_part, s, &c->launches)) != cudaSuccess)
+                return e;
+            k_radix_scatter<<<(unsigned)nblk, kRadixThreads, 0, s>>>(c->keys[cur], c->vals[cur], c->keys[cur ^ 1],
+                                                                     c->vals[cur ^ 1], n, shift, c->ghist, nblk);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            cur ^= 1;
+        }
+        c->sorted_buf = cur;
+        if (reorder) {
+            k_gather_records<<<blocks_for(n * 32, 256), 256, 0, s>>>(c->aos, c->aos_tmp, c->perm(), n,
+                                                                     c->layout.record_bytes);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            if ((e = cudaMemcpyAsync(c->aos, c->aos_tmp, (size_t)n * c->layout.record_bytes,
+                                     cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+                return e;
+            k_iota<<<blocks_for(n, 256), 256, 0, s>>>(c->perm(), n);
+            c->launches += 2;   // gather and iota
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
+}
+
+cudaError_t run_items(sph_ctx *c)
+{
+    cudaStream_t s = c->stream;
+    cudaError_t e;
+    const int block = c->tuning.block_threads;
+    k_items_count<<<blocks_for(c->ncell, 256), 256, 0, s>>>(c->cell_start, c->ncell, block, c->item_tmp, c->dstats);
+    c->launches += 2;   // count and fill
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = scan_exclusive(c->item_tmp, c->item_tmp, c->ncell, c->scan_part, s, &c->launches)) != cudaSuccess) return e;
+    k_items_fill<<<blocks_for(c->ncell, 256), 256, 0, s>>>(c->cell_start, c->item_tmp, c->ncell, block,
+                                                           c->item_cell, c->item_first, c->item_count, c->dstats);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    c->items_block = block;
+    return cudaSuccess;
+}
+
+}  // namespace sph

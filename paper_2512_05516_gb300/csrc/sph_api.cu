@@ -1,0 +1,400 @@
+// C-ABI entry points of libsph: argument validation, the workspace plan, and
+// dispatch to the kernels.  Every argument error is caught here, before any
+// device work is issued.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "sph_internal.cuh"
+
+using namespace sph;
+
+namespace {
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+bool layout_ok(const sph_aos_layout *L)
+{
+    if (!L || L->record_bytes <= 0 || L->record_bytes % 8 != 0) return false;
+    if (L->offset[SPH_F_X] < 0 || L->type[SPH_F_X] != SPH_AOS_F64) return false;
+    for (int f = 0; f < SPH_NFIELDS; ++f) {
+        if (L->offset[f] < 0) continue;
+        if (L->type[f] != SPH_AOS_F64 && L->type[f] != SPH_AOS_F32) return false;
+        int es = L->type[f] == SPH_AOS_F64 ? 8 : 4;
+        if (L->offset[f] % es != 0) return false;
+        if (L->offset[f] + es * ncomp(f) > L->record_bytes) return false;
+    }
+    return true;
+}
+
+bool params_ok(const sph_params *p)
+{
+    if (!p) return false;
+    for (int k = 0; k < 3; ++k)
+        if (!(p->box[k] > 0.0) || !std::isfinite(p->box[k])) return false;
+    if (!(p->gamma > 1.0) || !(p->eta > 0.0) || !(p->h_max > 0.0)) return false;
+    if (!(p->alpha_av >= 0.0) || !(p->beta_av >= 0.0) || !(p->eps_av >= 0.0)) return false;
+    return true;
+}
+
+// which storage formats each SoA field accepts
+bool fmt_allowed(int f, int fmt)
+{
+    if (fmt < SPH_P_FP32 || fmt > SPH_P_FP32_M10) return false;
+    switch (f) {
+    case SPH_F_X: return fmt == SPH_P_FP32 || fmt == SPH_P_FP16;
+    case SPH_F_V: case SPH_F_M: case SPH_F_H: case SPH_F_U: return true;
+    default: return !fmt_packed(fmt);
+    }
+}
+
+void default_tuning(sph_tuning *t)
+{
+    t->block_threads = 128;
+    t->ctas_per_sm = 0;
+    t->stage_density = 4096;
+    t->stage_force = 1536;
+}
+
+}  // namespace
+
+namespace sph {
+
+bool make_plan(const sph_aos_layout &L, int64_t n, int64_t ncell_max, uint32_t ws_flags, Plan *p)
+{
+    if (n < 0 || n > (int64_t)INT32_MAX / 2 || ncell_max < 27 || ncell_max > (int64_t)INT32_MAX / 2)
+        return false;
+    std::memset(p, 0, sizeof(*p));
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align_up(off + bytes, 256);
+        return o;
+    };
+    const size_t N = (size_t)n;
+    for (int b = 0; b < 2; ++b) {
+        p->keys[b] = take(4 * N);
+        p->vals[b] = take(4 * N);
+    }
+    p->cell_count = take(4 * (size_t)ncell_max);
+    p->cell_start = take(4 * ((size_t)ncell_max + 1));
+    p->nblk_radix = (n + kRadixTile - 1) / kRadixTile;
+    p->ghist = take(4 * (256 * (size_t)p->nblk_radix + 1));  // +1: the scan writes its total
+    int64_t scan_len = 256 * p->nblk_radix;
+    if (ncell_max + 1 > scan_len) scan_len = ncell_max + 1;
+    p->scan_part = take(4 * ((size_t)(scan_len + kScanTile - 1) / kScanTile + 2));
+    p->item_max = n / 32 + (n < ncell_max ? n : ncell_max) + 1;
+    p->item_cell = take(4 * (size_t)p->item_max);
+    p->item_first = take(4 * (size_t)p->item_max);
+    p->item_count = take(4 * (size_t)p->item_max);
+    p->item_tmp = take(4 * ((size_t)ncell_max + 1));
+    p->nngb = take(4 * N);
+    p->nngb_force = take(4 * N);
+    p->stage = take(4 * N);
+    p->aos_tmp = (ws_flags & SPH_WS_REORDER) ? take((size_t)L.record_bytes * N) : 0;
+    p->stats = take(sizeof(DevStats));
+    for (int f = 0; f < SPH_NFIELDS; ++f)
+        for (int c = 0; c < 3; ++c)
+            p->soa[f][c] = c < ncomp(f) ? take(4 * N + 64) : 0;
+    p->total = off;
+    return true;
+}
+
+int max_dynamic_smem(const sph_ctx *c) { return (int)c->smem_optin; }
+
+}  // namespace sph
+
+extern "C" {
+
+size_t sph_workspace_bytes(const sph_aos_layout *layout, int64_t n, int64_t ncell_max,
+                           uint32_t ws_flags)
+{
+    if (!layout_ok(layout)) return 0;
+    Plan p;
+    if (!make_plan(*layout, n, ncell_max, ws_flags, &p)) return 0;
+    return p.total;
+}
+
+sph_status sph_create(const sph_aos_layout *layout, const sph_params *params, int64_t n,
+                      int64_t ncell_max, uint32_t ws_flags, void *d_aos, void *d_workspace,
+                      size_t workspace_bytes, void *stream, sph_ctx **out)
+{
+    if (!out) return SPH_EINVAL;
+    *out = nullptr;
+    if (!layout_ok(layout) || !params_ok(params) || !d_aos || !d_workspace) return SPH_EINVAL;
+    if (((uintptr_t)d_aos & 15) != 0 || ((uintptr_t)d_workspace & 255) != 0) return SPH_EINVAL;
+    Plan plan;
+    if (!make_plan(*layout, n, ncell_max, ws_flags, &plan)) return SPH_EINVAL;
+    if (workspace_bytes < plan.total) return SPH_ENOSPACE;
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SPH_ECUDA;
+    int sms = 0, optin = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return SPH_ECUDA;
+
+    sph_ctx *c = new (std::nothrow) sph_ctx();
+    if (!c) return SPH_ENOSPACE;
+    c->layout = *layout;
+    c->params = *params;
+    c->n = n;
+    c->ncell_max = ncell_max;
+    c->ws_flags = ws_flags;
+    c->aos = (uint8_t *)d_aos;
+    c->ws = (uint8_t *)d_workspace;
+    c->ws_bytes = workspace_bytes;
+    c->stream = (cudaStream_t)stream;
+    c->device = dev;
+    c->sm_count = sms;
+    c->smem_optin = (size_t)optin;
+    c->plan = plan;
+    default_tuning(&c->tuning);
+    uint8_t *w = c->ws;
+    for (int b = 0; b < 2; ++b) {
+        c->keys[b] = (int32_t *)(w + plan.keys[b]);
+        c->vals[b] = (int32_t *)(w + plan.vals[b]);
+    }
+    c->cell_count = (int32_t *)(w + plan.cell_count);
+    c->cell_start = (int32_t *)(w + plan.cell_start);
+    c->scan_part = (int32_t *)(w + plan.scan_part);
+    c->ghist = (uint32_t *)(w + plan.ghist);
+    c->item_cell = (int32_t *)(w + plan.item_cell);
+    c->item_first = (int32_t *)(w + plan.item_first);
+    c->item_count = (int32_t *)(w + plan.item_count);
+    c->item_tmp = (int32_t *)(w + plan.item_tmp);
+    c->nngb = (int32_t *)(w + plan.nngb);
+    c->nngb_force = (int32_t *)(w + plan.nngb_force);
+    c->stage = (float *)(w + plan.stage);
+    c->aos_tmp = (ws_flags & SPH_WS_REORDER) ? w + plan.aos_tmp : nullptr;
+    c->dstats = (DevStats *)(w + plan.stats);
+    for (int f = 0; f < SPH_NFIELDS; ++f) {
+        c->prec[f] = SPH_P_FP32;
+        for (int k = 0; k < ncomp(f); ++k) c->soa[f][k] = w + plan.soa[f][k];
+    }
+    if (cudaMemsetAsync(c->dstats, 0, sizeof(DevStats), c->stream) != cudaSuccess) {
+        delete c;
+        return SPH_ECUDA;
+    }
+    *out = c;
+    return SPH_OK;
+}
+
+sph_status sph_bin_cells(sph_ctx *c, double cell_edge, int32_t reorder_aos)
+{
+    if (!c || !(std::isfinite(cell_edge) || cell_edge <= 0.0)) return SPH_EINVAL;
+    if (reorder_aos && !c->aos_tmp) return SPH_ENOSPACE;
+    double want = 2.0 * c->params.h_max;
+    if (cell_edge > want) want = cell_edge;
+    int32_t nc[3];
+    int64_t ncell = 1;
+    for (int k = 0; k < 3; ++k) {
+        double f = std::floor(c->params.box[k] / want);
+        if (f < 3.0) return SPH_ECAPACITY;
+        if (f > 4096.0) f = 4096.0;  // larger cells still cover 2 h_max
+        nc[k] = (int32_t)f;
+        ncell *= nc[k];
+    }
+    if (ncell > c->ncell_max) return SPH_ENOSPACE;
+    for (int k = 0; k < 3; ++k) {
+        c->nc[k] = nc[k];
+        c->inv[k] = (double)nc[k] / c->params.box[k];
+        c->edge[k] = c->params.box[k] / (double)nc[k];
+    }
+    c->ncell = ncell;
+    c->valid = 0;
+    c->binned = false;
+    if (run_binning(c, reorder_aos ? 1 : 0) != cudaSuccess) return SPH_ECUDA;
+    if (run_items(c) != cudaSuccess) return SPH_ECUDA;
+    c->binned = true;
+    return SPH_OK;
+}
+
+sph_status sph_aos_to_soa(sph_ctx *c, uint32_t fields, const int32_t *prec)
+{
+    if (!c) return SPH_EINVAL;
+    if (fields == 0 || (fields >> SPH_NFIELDS) != 0) return SPH_EINVAL;
+    for (int f = 0; f < SPH_NFIELDS; ++f) {
+        if (!(fields & SPH_BIT(f))) continue;
+        if (c->layout.offset[f] < 0) return SPH_EINVAL;
+        int fmt = prec ? prec[f] : SPH_P_FP32;
+        if (!fmt_allowed(f, fmt)) return SPH_EINVAL;
+    }
+    if (!c->binned) return SPH_ESTATE;
+    for (int f = 0; f < SPH_NFIELDS; ++f)
+        if (fields & SPH_BIT(f)) c->prec[f] = prec ? prec[f] : SPH_P_FP32;
+    if (run_aos_to_soa(c, fields) != cudaSuccess) return SPH_ECUDA;
+    c->valid |= fields;
+    return SPH_OK;
+}
+
+sph_status sph_density(sph_ctx *c, int32_t newton_steps)
+{
+    if (!c || newton_steps < 0 || newton_steps > 32) return SPH_EINVAL;
+    if (!c->binned) return SPH_ESTATE;
+    const uint32_t need = SPH_BIT(SPH_F_X) | SPH_BIT(SPH_F_M) | SPH_BIT(SPH_F_H);
+    if ((c->valid & need) != need) return SPH_ESTATE;
+    // outputs keep their current format; packed outputs are not supported for
+    // rho / P / c (fmt_allowed), h may be packed (written through the stage)
+    if (run_density(c, newton_steps) != cudaSuccess) return SPH_ECUDA;
+    c->valid |= SPH_BIT(SPH_F_RHO) | SPH_BIT(SPH_F_H);
+    if (c->valid & SPH_BIT(SPH_F_U)) c->valid |= SPH_BIT(SPH_F_P) | SPH_BIT(SPH_F_CS);
+    return SPH_OK;
+}
+
+sph_status sph_force(sph_ctx *c)
+{
+    if (!c) return SPH_EINVAL;
+    if (!c->binned) return SPH_ESTATE;
+    const uint32_t need = SPH_BIT(SPH_F_X) | SPH_BIT(SPH_F_V) | SPH_BIT(SPH_F_M) |
+                          SPH_BIT(SPH_F_H) | SPH_BIT(SPH_F_RHO) | SPH_BIT(SPH_F_P) |
+                          SPH_BIT(SPH_F_CS);
+    if ((c->valid & need) != need) return SPH_ESTATE;
+    c->prec[SPH_F_A] = SPH_P_FP32;
+    c->prec[SPH_F_DUDT] = SPH_P_FP32;
+    if (run_force(c) != cudaSuccess) return SPH_ECUDA;
+    c->valid |= SPH_BIT(SPH_F_A) | SPH_BIT(SPH_F_DUDT);
+    return SPH_OK;
+}
+
+sph_status sph_kick_drift(sph_ctx *c, double dt_kick, double dt_drift)
+{
+    if (!c || !std::isfinite(dt_kick) || !std::isfinite(dt_drift)) return SPH_EINVAL;
+    if (!c->binned) return SPH_ESTATE;
+    const uint32_t need = SPH_BIT(SPH_F_V) | SPH_BIT(SPH_F_A) | SPH_BIT(SPH_F_U) |
+                          SPH_BIT(SPH_F_DUDT);
+    if ((c->valid & need) != need) return SPH_ESTATE;
+    if (run_kick_drift(c, dt_kick, dt_drift) != cudaSuccess) return SPH_ECUDA;
+    c->valid &= ~SPH_BIT(SPH_F_X);   // SoA positions are stale after the drift
+    return SPH_OK;
+}
+
+sph_status sph_soa_to_aos(sph_ctx *c, uint32_t fields)
+{
+    if (!c) return SPH_EINVAL;
+    if (fields == 0 || (fields >> SPH_NFIELDS) != 0 || (fields & SPH_BIT(SPH_F_X))) return SPH_EINVAL;
+    for (int f = 0; f < SPH_NFIELDS; ++f)
+        if ((fields & SPH_BIT(f)) && c->layout.offset[f] < 0) return SPH_EINVAL;
+    if (!c->binned) return SPH_ESTATE;
+    if ((c->valid & fields) != fields) return SPH_ESTATE;
+    if (run_soa_to_aos(c, fields) != cudaSuccess) return SPH_ECUDA;
+    return SPH_OK;
+}
+
+sph_status sph_get_stats(sph_ctx *c, sph_stats *out)
+{
+    if (!c || !out) return SPH_EINVAL;
+    DevStats d;
+    if (cudaMemcpyAsync(&d, c->dstats, sizeof(d), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+        return SPH_ECUDA;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SPH_ECUDA;
+    std::memset(out, 0, sizeof(*out));
+    out->pairs_density = d.pairs_density;
+    out->pairs_force = d.pairs_force;
+    out->tests_density = d.tests_density;
+    out->tests_force = d.tests_force;
+    out->hcap_clamps = d.hcap_clamps;
+    out->error_bits = d.error_bits;
+    for (int k = 0; k < 3; ++k) out->ncell[k] = c->nc[k];
+    out->nitems = d.nitems;
+    out->max_occupancy = d.max_occ;
+    out->launches = c->launches;
+    if (d.error_bits & (SPH_ERR_NONFINITE | SPH_ERR_OUTSIDE)) return SPH_ENUMERIC;
+    return SPH_OK;
+}
+
+sph_status sph_reset_stats(sph_ctx *c)
+{
+    if (!c) return SPH_EINVAL;
+    // keep nitems / max_occ (they describe the current binning)
+    if (cudaMemsetAsync(c->dstats, 0, offsetof(DevStats, queue), c->stream) != cudaSuccess)
+        return SPH_ECUDA;
+    return SPH_OK;
+}
+
+sph_status sph_set_tuning(sph_ctx *c, const sph_tuning *t)
+{
+    if (!c || !t) return SPH_EINVAL;
+    sph_tuning n = c->tuning;
+    if (t->block_threads > 0) {
+        if (t->block_threads % 32 != 0 || t->block_threads < 32 || t->block_threads > kMaxBlock)
+            return SPH_EINVAL;
+        n.block_threads = t->block_threads;
+    }
+    if (t->ctas_per_sm > 0) n.ctas_per_sm = t->ctas_per_sm;
+    if (t->stage_density > 0) n.stage_density = t->stage_density;
+    if (t->stage_force > 0) n.stage_force = t->stage_force;
+    const size_t lists = (size_t)(n.block_threads / 32) * kListCap * sizeof(uint16_t);
+    if ((size_t)n.stage_density * 16 + lists + 1024 > c->smem_optin) return SPH_EINVAL;
+    if ((size_t)n.stage_force * 48 + lists + 1024 > c->smem_optin) return SPH_EINVAL;
+    if (n.stage_density > 65535 || n.stage_force > 65535) return SPH_EINVAL;
+    c->tuning = n;
+    return SPH_OK;
+}
+
+sph_status sph_get_tuning(const sph_ctx *c, sph_tuning *out)
+{
+    if (!c || !out) return SPH_EINVAL;
+    *out = c->tuning;
+    return SPH_OK;
+}
+
+sph_status sph_describe(const sph_ctx *c, sph_desc *out)
+{
+    if (!c || !out) return SPH_EINVAL;
+    std::memset(out, 0, sizeof(*out));
+    out->n = c->n;
+    for (int k = 0; k < 3; ++k) {
+        out->ncell[k] = c->nc[k];
+        out->cell_edge[k] = c->edge[k];
+    }
+    auto rel = [&](const void *p) { return p ? (int64_t)((const uint8_t *)p - c->ws) : (int64_t)-1; };
+    out->off_perm = rel(c->perm());
+    out->off_cell_of_slot = rel(c->slot_cell());
+    out->off_cell_start = rel(c->cell_start);
+    out->off_nngb = rel(c->nngb);
+    out->off_nngb_force = rel(c->nngb_force);
+    for (int f = 0; f < SPH_NFIELDS; ++f) {
+        out->prec[f] = c->prec[f];
+        for (int k = 0; k < 3; ++k) out->off_soa[f][k] = k < ncomp(f) ? rel(c->soa[f][k]) : -1;
+    }
+    out->valid = c->valid;
+    return SPH_OK;
+}
+
+sph_status sph_aos_upload(sph_ctx *c, const void *host, size_t bytes)
+{
+    if (!c || !host || bytes > (size_t)c->n * (size_t)c->layout.record_bytes) return SPH_EINVAL;
+    if (cudaMemcpyAsync(c->aos, host, bytes, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+        return SPH_ECUDA;
+    return SPH_OK;
+}
+
+sph_status sph_aos_download(sph_ctx *c, void *host, size_t bytes)
+{
+    if (!c || !host || bytes > (size_t)c->n * (size_t)c->layout.record_bytes) return SPH_EINVAL;
+    if (cudaMemcpyAsync(host, c->aos, bytes, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+        return SPH_ECUDA;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SPH_ECUDA;
+    return SPH_OK;
+}
+
+void sph_destroy(sph_ctx *c) { delete c; }
+
+const char *sph_status_str(sph_status s)
+{
+    switch (s) {
+    case SPH_OK: return "ok";
+    case SPH_EINVAL: return "invalid argument";
+    case SPH_ENOSPACE: return "workspace or cell capacity too small";
+    case SPH_ECUDA: return "CUDA error";
+    case SPH_ESTATE: return "call out of order: an input is not current";
+    case SPH_ECAPACITY: return "cell grid unusable (fewer than 3 cells on an axis)";
+    case SPH_ETIMEOUT: return "bounded device wait gave up";
+    case SPH_ENUMERIC: return "device recorded a numerical condition";
+    default: return "unknown status";
+    }
+}
+
+}  // extern "C"

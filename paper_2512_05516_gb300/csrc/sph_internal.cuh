@@ -1,0 +1,228 @@
+// Internal declarations of libsph: the context, the workspace plan, the
+// storage-format codecs used by every kernel, and the launch wrappers.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "sph.h"
+
+namespace sph {
+
+constexpr int kRadixThreads = 256;
+constexpr int kRadixItems = 8;
+constexpr int kRadixTile = kRadixThreads * kRadixItems;   // keys per block per pass
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;      // elements per scan block
+constexpr int kListCap = 512;                              // per-warp candidate list entries
+constexpr int kMaxBlock = 512;
+constexpr float kSigma = 0.318309886183790671538f;        // 1/pi, 3D M4 normalisation
+
+inline int ncomp(int f) { return (f == SPH_F_X || f == SPH_F_V || f == SPH_F_A) ? 3 : 1; }
+
+// Device-resident counters and queue heads (lives in the workspace).
+struct DevStats {
+    unsigned long long pairs_density;
+    unsigned long long pairs_force;
+    unsigned long long tests_density;
+    unsigned long long tests_force;
+    unsigned long long hcap_clamps;
+    unsigned int error_bits;
+    unsigned int queue;          // persistent work-queue head (zeroed before each launch)
+    int nitems;                  // pair-kernel work items of the current binning
+    int max_occ;                 // particles in the fullest cell
+    int pad[6];
+};
+
+// Byte offsets of every workspace array.
+struct Plan {
+    size_t keys[2], vals[2];
+    size_t cell_count, cell_start, scan_part, ghist;
+    size_t item_cell, item_first, item_count, item_tmp;
+    size_t nngb, nngb_force, stage, aos_tmp, stats;
+    size_t soa[SPH_NFIELDS][3];
+    size_t total;
+    int64_t item_max, nblk_radix;
+};
+
+bool make_plan(const sph_aos_layout &L, int64_t n, int64_t ncell_max, uint32_t ws_flags, Plan *p);
+
+// Per-field view handed to kernels.
+struct FieldRef {
+    void *p[3];
+    int fmt;
+};
+
+// ---------------------------------------------------------------------------
+// storage-format codecs (Table 2 and bfloat16).  All formats decode to FP32.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline int fmt_bits(int fmt)
+{
+    switch (fmt) {
+    case SPH_P_BF16: case SPH_P_FP16: return 16;
+    case SPH_P_FP32_M16: return 25;
+    case SPH_P_FP32_M10: return 19;
+    default: return 32;
+    }
+}
+__host__ __device__ inline bool fmt_packed(int fmt)
+{
+    return fmt == SPH_P_FP32_M16 || fmt == SPH_P_FP32_M10;
+}
+
+__device__ __forceinline__ float dec_bf16(uint16_t b) { return __uint_as_float((uint32_t)b << 16); }
+
+// round to nearest, ties to even, on the upper 16 bits; NaN stays a quiet NaN
+__device__ __forceinline__ uint16_t enc_bf16(float f)
+{
+    uint32_t u = __float_as_uint(f);
+    if ((u & 0x7F800000u) == 0x7F800000u && (u & 0x7FFFFFu)) return (uint16_t)((u >> 16) | 0x40u);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
+// truncated single: keep the top B bits (sign, exponent, B-9 mantissa bits)
+__device__ __forceinline__ uint32_t enc_trunc(float f, int B)
+{
+    uint32_t u = __float_as_uint(f);
+    if ((u & 0x7F800000u) == 0x7F800000u && (u & 0x7FFFFFu)) u |= 0x400000u;
+    return u >> (32 - B);
+}
+
+__device__ __forceinline__ float ld_packed(const uint32_t *__restrict__ w, int64_t k, int B)
+{
+    int64_t bit = k * (int64_t)B;
+    int64_t wi = bit >> 5;
+    int sh = (int)(bit & 31);
+    uint32_t lo = __ldg(w + wi);
+    uint32_t hi = (sh + B > 32) ? __ldg(w + wi + 1) : 0u;
+    uint32_t code = __funnelshift_r(lo, hi, sh) & ((1u << B) - 1u);
+    return __uint_as_float(code << (32 - B));
+}
+
+__device__ __forceinline__ float ld_val(const void *p, int fmt, int64_t k)
+{
+    switch (fmt) {
+    case SPH_P_BF16: return dec_bf16(__ldg((const unsigned short *)p + k));
+    case SPH_P_FP16: return __half2float(__ushort_as_half(__ldg((const unsigned short *)p + k)));
+    case SPH_P_FP32_M16: return ld_packed((const uint32_t *)p, k, 25);
+    case SPH_P_FP32_M10: return ld_packed((const uint32_t *)p, k, 19);
+    default: return __ldg((const float *)p + k);
+    }
+}
+
+// element store for the non-packed formats
+__device__ __forceinline__ void st_val(void *p, int fmt, int64_t k, float v)
+{
+    switch (fmt) {
+    case SPH_P_BF16: ((uint16_t *)p)[k] = enc_bf16(v); break;
+    case SPH_P_FP16: ((__half *)p)[k] = __float2half_rn(v); break;
+    default: ((float *)p)[k] = v; break;
+    }
+}
+
+// Warp-cooperative store into a packed stream.  All 32 lanes must call it
+// together with consecutive k whose warp base (k - lane) is a multiple of 32;
+// lanes with valid == false contribute zero bits.  The 32 codes of the warp
+// fill exactly B words starting at word (base/32)*B; words at or beyond
+// `nwords` are not written.
+__device__ __forceinline__ void st_packed_warp(uint32_t *w, int64_t k, float v, bool valid,
+                                               int B, int64_t nwords)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t base = k - lane;
+    uint32_t code = valid ? enc_trunc(v, B) : 0u;
+    const int j = lane;                  // word j of this warp's B-word block
+    const int v0 = (32 * j) / B;
+    const int v1 = (32 * j + 31) / B;
+    uint32_t word = 0u;
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+        int src = v0 + t;
+        uint32_t cv = __shfl_sync(0xffffffffu, code, src < 32 ? src : 31);
+        if (j < B && src <= v1 && src < 32) {
+            int pos = src * B - 32 * j;  // bit position of value src inside word j
+            word |= pos >= 0 ? (cv << pos) : (cv >> (-pos));
+        }
+    }
+    int64_t wi = (base >> 5) * B + j;
+    if (j < B && wi < nwords) w[wi] = word;
+}
+
+__device__ __forceinline__ void st_any(void *p, int fmt, int64_t k, float v, bool valid,
+                                       int64_t n)
+{
+    if (fmt_packed(fmt)) {
+        const int B = fmt_bits(fmt);
+        st_packed_warp((uint32_t *)p, k, v, valid, B, (n * B + 31) / 32);
+    } else if (valid) {
+        st_val(p, fmt, k, v);
+    }
+}
+
+__device__ __forceinline__ void set_error(DevStats *s, unsigned bits) { atomicOr(&s->error_bits, bits); }
+
+}  // namespace sph
+
+// ---------------------------------------------------------------------------
+// The context (host side).
+// ---------------------------------------------------------------------------
+struct sph_ctx {
+    sph_aos_layout layout;
+    sph_params params;
+    int64_t n = 0, ncell_max = 0;
+    uint32_t ws_flags = 0;
+    uint8_t *aos = nullptr;
+    uint8_t *ws = nullptr;
+    size_t ws_bytes = 0;
+    cudaStream_t stream = nullptr;
+    int device = 0, sm_count = 0;
+    size_t smem_optin = 0;
+    sph_tuning tuning{};
+    sph::Plan plan{};
+
+    // cell grid of the last binning
+    int32_t nc[3] = {0, 0, 0};
+    double edge[3] = {0, 0, 0};
+    double inv[3] = {0, 0, 0};
+    int64_t ncell = 0;
+    bool binned = false;
+    int items_block = 0;          // block size the work items were built for
+    int sorted_buf = 0;           // which ping-pong buffer holds the sorted keys/values
+
+    // workspace arrays
+    int32_t *keys[2] = {nullptr, nullptr};
+    int32_t *vals[2] = {nullptr, nullptr};
+    int32_t *cell_count = nullptr, *cell_start = nullptr, *scan_part = nullptr;
+    uint32_t *ghist = nullptr;
+    int32_t *item_cell = nullptr, *item_first = nullptr, *item_count = nullptr, *item_tmp = nullptr;
+    int32_t *nngb = nullptr, *nngb_force = nullptr;
+    float *stage = nullptr;
+    uint8_t *aos_tmp = nullptr;
+    sph::DevStats *dstats = nullptr;
+    void *soa[SPH_NFIELDS][3] = {};
+    int prec[SPH_NFIELDS] = {};
+    uint32_t valid = 0;
+    uint64_t launches = 0;        // kernels launched through this context
+
+    int32_t *perm() const { return vals[sorted_buf]; }
+    int32_t *slot_cell() const { return keys[sorted_buf]; }
+};
+
+namespace sph {
+// launch wrappers (each returns the first CUDA error, or cudaSuccess)
+cudaError_t run_binning(sph_ctx *c, int reorder);
+cudaError_t run_items(sph_ctx *c);
+cudaError_t run_aos_to_soa(sph_ctx *c, uint32_t fields);
+cudaError_t run_soa_to_aos(sph_ctx *c, uint32_t fields);
+cudaError_t run_density(sph_ctx *c, int newton_steps);
+cudaError_t run_force(sph_ctx *c);
+cudaError_t run_kick_drift(sph_ctx *c, double dt_kick, double dt_drift);
+cudaError_t scan_exclusive(const int32_t *in, int32_t *out, int64_t len, int32_t *part,
+                           cudaStream_t s, uint64_t *launches);
+int max_dynamic_smem(const sph_ctx *c);
+}  // namespace sph

@@ -11,6 +11,11 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: long-running CPU test")
+    # the library and the oracle are compiled in-tree (quick when up to date)
+    import __graft_entry__
+    __graft_entry__.build()
+    import oracle
+    oracle.build()
 
 
 @pytest.fixture(scope="session")

@@ -1,0 +1,95 @@
+"""S3/S4 parity: density (Eq. 6) with and without the smoothing-length
+iteration, neighbour counts, and the EOS, against the FP64 oracle.
+
+Tolerances: density and h within 1e-5 relative (FP32 arithmetic on FP32
+storage).  Neighbour counts are integers decided by an FP32 distance test
+against the FP64 one: each GPU count must lie between the oracle's counts at
+h (1 -+ delta), i.e. only pairs within delta of the support radius may differ,
+and the counts must be identical for every particle without such a pair."""
+import numpy as np
+import pytest
+
+import sph_inputs
+from gpu_util import count_band_ok, make_sph
+
+pytestmark = pytest.mark.gpu
+
+import paper_2512_05516_gb300 as sph_mod  # noqa: E402
+
+
+def _run_density(wl, newton, prec=None, tuning=None, flags=0):
+    s = make_sph(wl, flags=flags)
+    if tuning:
+        s.set_tuning(**tuning)
+    s.bin_cells(wl.cell_edge)
+    s.aos_to_soa(sph_mod.FIELDS_DENSITY, prec)
+    s.density(newton)
+    s.soa_to_aos(sph_mod.mask("rho", "h", "P"))
+    perm = s.perm().cpu().numpy()
+    counts = np.empty(wl.n, np.int32)
+    counts[perm] = s.nngb().cpu().numpy()
+    out = s.aos.cpu().numpy()
+    res = {"rho": out[:, 11].copy(), "h": out[:, 10].copy(), "P": out[:, 13].copy(),
+           "nngb": counts, "stats": s.stats()}
+    s.close()
+    return res
+
+
+def test_uniform_4096_fixed_h(orc):
+    wl = sph_inputs.uniform_density()
+    g = _run_density(wl, 0)
+    o = orc.density(wl.col("x"), wl.col("m"), wl.col("h"), wl.box, wl.eta, wl.h_cap, 0)
+    err = np.abs(g["rho"] - o["rho"]) / o["rho"]
+    assert err.max() <= 1e-5, err.max()
+    ok, lo, hi = count_band_ok(orc, wl, wl.col("h"), g["nngb"], 1e-6)
+    assert ok.all()
+    exact = lo == hi
+    assert np.array_equal(g["nngb"][exact], o["nngb"][exact])
+    assert g["stats"]["pairs_density"] == int(g["nngb"].sum())
+    assert g["stats"]["error_bits"] == 0
+
+
+@pytest.mark.parametrize("shuffle", [False, True])
+def test_sod_newton(orc, shuffle):
+    wl = sph_inputs.sod(n_lattice=24, seed=12, shuffle=shuffle)
+    g = _run_density(wl, 5)
+    o = orc.density(wl.col("x"), wl.col("m"), wl.col("h"), wl.box, wl.eta, wl.h_cap, 5)
+    assert (np.abs(g["h"] - o["h"]) / o["h"]).max() <= 1e-5
+    assert (np.abs(g["rho"] - o["rho"]) / o["rho"]).max() <= 1e-5
+    P, _ = orc.eos(o["rho"], wl.col("u"), wl.gamma)
+    assert (np.abs(g["P"] - P) / P).max() <= 1e-5
+    ok, lo, hi = count_band_ok(orc, wl, o["h"], g["nngb"], 2e-5)
+    assert ok.all()
+    # density passes: 5 Newton sums + 1 final sum, each over every particle
+    assert g["stats"]["pairs_density"] > 5 * g["nngb"].sum()
+
+
+def test_results_do_not_depend_on_launch_shape(orc):
+    # the accumulated pair set and its order are fixed by the staged candidate
+    # order, so block size, staging chunk and CTAs per SM change nothing
+    wl = sph_inputs.sod(n_lattice=20, seed=13)
+    ref = _run_density(wl, 3)
+    for tun in ({"block_threads": 32}, {"block_threads": 256, "stage_density": 200},
+                {"block_threads": 64, "ctas_per_sm": 1, "stage_density": 1000}):
+        g = _run_density(wl, 3, tuning=tun)
+        assert np.array_equal(g["rho"], ref["rho"]), tun
+        assert np.array_equal(g["h"], ref["h"]), tun
+        assert np.array_equal(g["nngb"], ref["nngb"]), tun
+
+
+def test_plain_sum_is_within_tolerance_too(orc):
+    wl = sph_inputs.uniform_density()
+    g = _run_density(wl, 0, flags=sph_mod.FLAG_PLAIN_SUM)
+    o = orc.density(wl.col("x"), wl.col("m"), wl.col("h"), wl.box, wl.eta, wl.h_cap, 0)
+    assert (np.abs(g["rho"] - o["rho"]) / o["rho"]).max() <= 1e-5
+
+
+def test_h_clamp_is_counted(orc):
+    wl = sph_inputs.sod(n_lattice=24, seed=14)
+    wl.h_cap = 0.8 * wl.meta["h_right"]          # too small for the sparse half
+    g = _run_density(wl, 5)
+    o = orc.density(wl.col("x"), wl.col("m"), wl.col("h"), wl.box, wl.eta, wl.h_cap, 5)
+    assert g["stats"]["error_bits"] & sph_mod.ERR_HCAP
+    clamped = int(np.count_nonzero(o["flags"] & orc.FLAG_HCAP))
+    assert abs(int(g["stats"]["hcap_clamps"]) - clamped) <= max(2, clamped // 100)
+    assert (np.abs(g["rho"] - o["rho"]) / o["rho"]).max() <= 1e-5
