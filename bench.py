@@ -298,15 +298,15 @@ def run_oracle_sample(n_targets: int, seed: int = 1):
     f = oracle.force(x, wl.col("v"), m, sub_h, sub_rho, sub_P, sub_c, wl.box, wl.alpha_av,
                      wl.beta_av, wl.eps_av, targets=targets)
     dt = time.perf_counter() - t0
-    # pairs the oracle evaluated: every Newton pass and the final pass of the
-    # density (approximated by (steps+1) x final count), plus the force pairs
-    pairs = float(np.sum(d["nngb"]) * (wl.newton_steps + 1) + np.sum(f["nngb"]))
+    # pairs the oracle evaluated: every Newton pass and the final density
+    # pass, plus the force pairs
+    pairs = float(np.sum(d["pairs_all"]) + np.sum(f["nngb"]))
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return pairs, dt, cores
 
 
 def cpu_baseline():
-    n_t = 20000
+    n_t = 600000
     pairs, dt, cores = run_oracle_sample(n_t)
     return {"value": pairs / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n_t} random particles of the 1,072,476-particle Sod step "
@@ -321,7 +321,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        n_t = 4000
+        n_t = 20000
         times, pairs_l = [], []
         cores = 1
         for _ in range(args.warmup):

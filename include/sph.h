@@ -148,10 +148,10 @@ typedef struct {
 
 /* Launch shapes of the pair kernels (an autotuner sets them). */
 typedef struct {
-    int32_t block_threads;       /* i-particles per work item = threads per CTA (32..512, multiple of 32) */
+    int32_t block_threads;       /* threads per CTA of the pair kernels (32..256, multiple of 32); one warp per work item */
     int32_t ctas_per_sm;         /* persistent CTAs per SM (0: occupancy maximum) */
-    int32_t stage_density;       /* neighbour candidates staged per chunk, density kernel */
-    int32_t stage_force;         /* neighbour candidates staged per chunk, force kernel */
+    int32_t stage_density;       /* neighbour candidates staged per warp, density kernel (>= 32) */
+    int32_t stage_force;         /* neighbour candidates staged per warp, force kernel (>= 32) */
 } sph_tuning;
 
 /* Where the library's arrays live inside the workspace (byte offsets from the
@@ -256,7 +256,7 @@ sph_status sph_reset_stats(sph_ctx *ctx);
 
 /* Set launch shapes; values <= 0 keep the defaults.  Takes effect at the next
  * pair-kernel call.  Errors: SPH_EINVAL (block_threads not a multiple of 32 in
- * [32, 512], or stage sizes above the shared-memory limit). */
+ * [32, 256], or stage sizes outside [32, 65535] or above the shared-memory limit). */
 sph_status sph_set_tuning(sph_ctx *ctx, const sph_tuning *tuning);
 sph_status sph_get_tuning(const sph_ctx *ctx, sph_tuning *out);
 

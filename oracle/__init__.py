@@ -74,7 +74,7 @@ def _declare(L):
     L.orc_bin.argtypes = [_i64, _p, _p, _p, _p, _p, _p]
     L.orc_density.restype = None
     L.orc_density.argtypes = [_i64, _p, _p, _p, _p, _d, _d, C.c_int, C.c_int, _i64, _p,
-                              _p, _p, _p, _p, _p]
+                              _p, _p, _p, _p, _p, _p]
     L.orc_eos.restype = None
     L.orc_eos.argtypes = [_i64, _p, _p, _d, _p, _p]
     L.orc_force.restype = None
@@ -171,10 +171,12 @@ def density(x, m, h, box, eta, h_cap, newton_steps=0, brute=False, targets=None)
     drdh = np.zeros(nt)
     nngb = np.zeros(nt, np.int32)
     flags = np.zeros(nt, np.int32)
+    pairs = np.zeros(nt, np.int64)
     lib().orc_density(n, _ptr(x), _ptr(m), _ptr(h), _ptr(_f64(box)), float(eta),
                       float(h_cap), int(newton_steps), int(bool(brute)), nt, _ptr(t),
-                      _ptr(rho), _ptr(hout), _ptr(drdh), _ptr(nngb), _ptr(flags))
-    return {"rho": rho, "h": hout, "drho_dh": drdh, "nngb": nngb, "flags": flags}
+                      _ptr(rho), _ptr(hout), _ptr(drdh), _ptr(nngb), _ptr(flags), _ptr(pairs))
+    return {"rho": rho, "h": hout, "drho_dh": drdh, "nngb": nngb, "flags": flags,
+            "pairs_all": pairs}
 
 
 def eos(rho, u, gamma):

@@ -274,7 +274,7 @@ void orc_density(int64_t n, const double *x, const double *m, const double *h_in
                  const double *box, double eta, double h_cap, int newton_steps,
                  int brute, int64_t ntarget, const int64_t *targets,
                  double *rho, double *h_out, double *drho_dh, int32_t *nngb,
-                 int32_t *flags)
+                 int32_t *flags, int64_t *pairs_all)
 {
     grid_t g;
     int use_grid = !brute && grid_build(&g, n, x, box, 2.0 * h_cap);
@@ -295,8 +295,10 @@ void orc_density(int64_t n, const double *x, const double *m, const double *h_in
             if (h > h_cap) { h = h_cap; fl |= ORC_FLAG_HCAP; }
             double r, dr;
             int32_t cnt;
+            int64_t npairs = 0;     /* neighbour pairs summed over every pass */
             for (int s = 0; s < newton_steps; ++s) {
                 density_sums(&all, &nb, m, i, h, &r, &dr, &cnt);
+                npairs += cnt;
                 /* R5: f(h) = rho(h) - m (eta/h)^3, f'(h) = drho/dh + 3 m eta^3 / h^4 */
                 double f = r - m[i] * eta3 / (h * h * h);
                 double fp = dr + 3.0 * m[i] * eta3 / (h * h * h * h);
@@ -309,12 +311,14 @@ void orc_density(int64_t n, const double *x, const double *m, const double *h_in
                 h = hn;
             }
             density_sums(&all, &nb, m, i, h, &r, &dr, &cnt);
+            npairs += cnt;
             if (!isfinite(r)) fl |= ORC_FLAG_NONFINITE;
             rho[t] = r;
             if (h_out) h_out[t] = h;
             if (drho_dh) drho_dh[t] = dr;
             if (nngb) nngb[t] = cnt;
             if (flags) flags[t] = fl;
+            if (pairs_all) pairs_all[t] = npairs;
         }
         free(all.c); free(nb.c);
     }

@@ -49,7 +49,7 @@ void orc_density(int64_t n, const double *x, const double *m, const double *h_in
                  const double *box, double eta, double h_cap, int newton_steps,
                  int brute, int64_t ntarget, const int64_t *targets,
                  double *rho, double *h_out, double *drho_dh, int32_t *nngb,
-                 int32_t *flags);
+                 int32_t *flags, int64_t *pairs_all);
 
 /* ---- ideal-gas equation of state ---- */
 void orc_eos(int64_t n, const double *rho, const double *u, double gamma,

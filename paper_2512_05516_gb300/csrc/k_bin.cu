@@ -332,16 +332,14 @@ cudaError_t run_items(sph_ctx *c)
 {
     cudaStream_t s = c->stream;
     cudaError_t e;
-    const int block = c->tuning.block_threads;
+    const int block = kItemTile;    // one warp per work item
     k_items_count<<<blocks_for(c->ncell, 256), 256, 0, s>>>(c->cell_start, c->ncell, block, c->item_tmp, c->dstats);
     c->launches += 2;   // count and fill
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = scan_exclusive(c->item_tmp, c->item_tmp, c->ncell, c->scan_part, s, &c->launches)) != cudaSuccess) return e;
     k_items_fill<<<blocks_for(c->ncell, 256), 256, 0, s>>>(c->cell_start, c->item_tmp, c->ncell, block,
                                                            c->item_cell, c->item_first, c->item_count, c->dstats);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    c->items_block = block;
-    return cudaSuccess;
+    return cudaGetLastError();
 }
 
 }  // namespace sph

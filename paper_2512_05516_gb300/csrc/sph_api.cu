@@ -51,10 +51,10 @@ bool fmt_allowed(int f, int fmt)
 
 void default_tuning(sph_tuning *t)
 {
-    t->block_threads = 128;
+    t->block_threads = 64;
     t->ctas_per_sm = 0;
-    t->stage_density = 4096;
-    t->stage_force = 1536;
+    t->stage_density = 640;
+    t->stage_force = 320;
 }
 
 }  // namespace
@@ -325,10 +325,10 @@ sph_status sph_set_tuning(sph_ctx *c, const sph_tuning *t)
     if (t->ctas_per_sm > 0) n.ctas_per_sm = t->ctas_per_sm;
     if (t->stage_density > 0) n.stage_density = t->stage_density;
     if (t->stage_force > 0) n.stage_force = t->stage_force;
-    const size_t lists = (size_t)(n.block_threads / 32) * kListCap * sizeof(uint16_t);
-    if ((size_t)n.stage_density * 16 + lists + 1024 > c->smem_optin) return SPH_EINVAL;
-    if ((size_t)n.stage_force * 48 + lists + 1024 > c->smem_optin) return SPH_EINVAL;
+    if (n.stage_density < 32 || n.stage_force < 32) return SPH_EINVAL;
     if (n.stage_density > 65535 || n.stage_force > 65535) return SPH_EINVAL;
+    if (density_smem_bytes(n.block_threads, n.stage_density) > c->smem_optin) return SPH_EINVAL;
+    if (force_smem_bytes(n.block_threads, n.stage_force) > c->smem_optin) return SPH_EINVAL;
     c->tuning = n;
     return SPH_OK;
 }

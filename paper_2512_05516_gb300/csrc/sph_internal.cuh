@@ -18,8 +18,8 @@ constexpr int kRadixTile = kRadixThreads * kRadixItems;   // keys per block per 
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
 constexpr int kScanTile = kScanThreads * kScanItems;      // elements per scan block
-constexpr int kListCap = 512;                              // per-warp candidate list entries
-constexpr int kMaxBlock = 512;
+constexpr int kItemTile = 32;                              // i-particles per pair-kernel work item (one warp)
+constexpr int kMaxBlock = 256;
 constexpr float kSigma = 0.318309886183790671538f;        // 1/pi, 3D M4 normalisation
 
 inline int ncomp(int f) { return (f == SPH_F_X || f == SPH_F_V || f == SPH_F_A) ? 3 : 1; }
@@ -50,6 +50,15 @@ struct Plan {
 };
 
 bool make_plan(const sph_aos_layout &L, int64_t n, int64_t ncell_max, uint32_t ws_flags, Plan *p);
+
+// Launch shape of a persistent kernel, computed once per tuning so that no
+// attribute or occupancy query runs while a stream is being captured.
+struct LaunchCache {
+    size_t smem = 0;
+    int block = 0;
+    int per_sm_req = -1;
+    int grid = 0;
+};
 
 // Per-field view handed to kernels.
 struct FieldRef {
@@ -191,8 +200,8 @@ struct sph_ctx {
     double inv[3] = {0, 0, 0};
     int64_t ncell = 0;
     bool binned = false;
-    int items_block = 0;          // block size the work items were built for
-    int sorted_buf = 0;           // which ping-pong buffer holds the sorted keys/values
+    sph::LaunchCache lc_density, lc_force;
+    int sorted_buf = 0;          // which ping-pong buffer holds the sorted keys/values
 
     // workspace arrays
     int32_t *keys[2] = {nullptr, nullptr};
@@ -225,4 +234,6 @@ cudaError_t run_kick_drift(sph_ctx *c, double dt_kick, double dt_drift);
 cudaError_t scan_exclusive(const int32_t *in, int32_t *out, int64_t len, int32_t *part,
                            cudaStream_t s, uint64_t *launches);
 int max_dynamic_smem(const sph_ctx *c);
+size_t density_smem_bytes(int block_threads, int stage_cap);
+size_t force_smem_bytes(int block_threads, int stage_cap);
 }  // namespace sph
