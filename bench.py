@@ -117,15 +117,15 @@ def prec_of(args):
     return {"v": args.prec, "m": args.prec, "h": args.prec, "u": args.prec}
 
 
-def traffic_from_profile(kernel_src: str):
-    """DRAM bytes per launch of the density kernel from the committed ncu
-    summary, if it was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "k_density_sod1m.md")
+def traffic_from_profile(kernel_src: str, kernel: str):
+    """DRAM bytes per launch of a pair kernel from the committed ncu summary,
+    if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "k_pairs_sod1m.md")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
     m_src = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt)
-    m_tr = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    m_tr = re.search(re.escape(kernel) + r"\.dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
     if not m_src or not m_tr:
         return None
     sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
@@ -245,7 +245,7 @@ def run_ours(args, rank, world):
     kernel_src = os.path.join(ROOT, "paper_2512_05516_gb300", "csrc", "k_pairs.cu")
     roofline = {"bound": "alu", "kernel": f"k_{dominant}", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic_from_profile(kernel_src) if dominant == "density" else None,
+                "traffic": traffic_from_profile(kernel_src, f"k_{dominant}"),
                 "peak_basis": "FP32 FMA pipe: SMs x 128 lanes x 2 flops x max SM clock",
                 "flops_per_pair": FLOPS_PER_PAIR[dominant]}
     hbm = 6753.1
