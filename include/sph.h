@@ -270,6 +270,41 @@ sph_status sph_describe(const sph_ctx *ctx, sph_desc *out);
 sph_status sph_aos_upload(sph_ctx *ctx, const void *host, size_t bytes);
 sph_status sph_aos_download(sph_ctx *ctx, void *host, size_t bytes);
 
+/* Allocation-free cell binning.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory at all, such
+ * as a plugin running inside a host application that owns the whole device
+ * memory pool and offers plugins no allocation hook, or a latency-critical
+ * path where cudaMalloc's implicit device-wide synchronisation is not
+ * acceptable.  It computes exactly what sph_bin_cells computes (same cell
+ * rule, same stable order) without a context or a workspace: its scratch
+ * memory is a fixed array of SPH_NOALLOC_SCRATCH_BYTES inside libsph, which
+ * every device that loads the library holds until the process exits.
+ *
+ *   d_aos           n device records in `layout` (positions FP64, 8-byte aligned)
+ *   box, nc         host arrays of 3: box edges and cells per axis (each >= 1)
+ *   d_perm          device int32[n]: sorted slot -> original particle index
+ *   d_cell_of_slot  device int32[n]: sorted slot -> cell id kx + nc_x (ky + nc_y kz)
+ *   d_cell_start    device int32[nc_x nc_y nc_z + 1]: first slot of each cell
+ *   stream          cudaStream_t (NULL: legacy default stream)
+ *
+ * The call is asynchronous and allocates nothing: no cudaMalloc, cudaFree or
+ * allocating library routine.  The first call on a device (the device current
+ * at the call) looks up the array's device address once; make that first
+ * call before any stream capture.  All calls on a device share the one
+ * array, which keeps the last call's contents (every call clears what must
+ * start at zero), so calls that overlap on the GPU -- on different streams,
+ * or from different threads -- race and must be serialised by the caller.
+ * Positions outside [0, box) are clamped into the edge cells; no error word
+ * is kept.  Errors: SPH_ENOSPACE when n > SPH_NOALLOC_MAX_PARTICLES or the
+ * grid has more than SPH_NOALLOC_MAX_CELLS cells (nothing is launched),
+ * SPH_EINVAL for bad arguments, SPH_ECUDA for a failed CUDA call. */
+#define SPH_NOALLOC_MAX_PARTICLES 262144
+#define SPH_NOALLOC_MAX_CELLS 262144
+#define SPH_NOALLOC_SCRATCH_BYTES 5636096
+sph_status sph_bin_cells_noalloc(const void *d_aos, const sph_aos_layout *layout, int64_t n,
+                                 const double *box, const int32_t *nc, int32_t *d_perm,
+                                 int32_t *d_cell_of_slot, int32_t *d_cell_start, void *stream);
+
 /* Free the host-side context (the caller's buffers are untouched). */
 void sph_destroy(sph_ctx *ctx);
 

@@ -112,6 +112,21 @@ def sph_aos_download(ctx, host_ptr: int, nbytes: int) -> int:
     return _lib.sph_aos_download(ctx, C.c_void_p(host_ptr), nbytes)
 
 
+NOALLOC_MAX_PARTICLES = 262144
+NOALLOC_MAX_CELLS = 262144
+
+
+def sph_bin_cells_noalloc(d_aos: int, layout: sph_aos_layout, n: int, box, nc, d_perm: int,
+                          d_cell_of_slot: int, d_cell_start: int, stream: int) -> int:
+    """Cell binning for callers that cannot allocate device memory: scratch
+    lives in a fixed array inside libsph (see include/sph.h)."""
+    b = (C.c_double * 3)(*[float(v) for v in box])
+    g = (C.c_int32 * 3)(*[int(v) for v in nc])
+    return _lib.sph_bin_cells_noalloc(C.c_void_p(d_aos), C.byref(layout), int(n), b, g,
+                                      C.c_void_p(d_perm), C.c_void_p(d_cell_of_slot),
+                                      C.c_void_p(d_cell_start), C.c_void_p(stream))
+
+
 def sph_destroy(ctx) -> None:
     _lib.sph_destroy(ctx)
 

@@ -86,6 +86,8 @@ PROTOTYPES = {
     "sph_describe": (C.c_int, [_P, C.POINTER(sph_desc)]),
     "sph_aos_upload": (C.c_int, [_P, _P, C.c_size_t]),
     "sph_aos_download": (C.c_int, [_P, _P, C.c_size_t]),
+    "sph_bin_cells_noalloc": (C.c_int, [_P, C.POINTER(sph_aos_layout), C.c_int64, C.POINTER(C.c_double),
+                                        C.POINTER(C.c_int32), _P, _P, _P, _P]),
     "sph_destroy": (None, [_P]),
     "sph_status_str": (C.c_char_p, [C.c_int]),
 }

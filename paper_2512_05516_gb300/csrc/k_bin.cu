@@ -328,6 +328,55 @@ cudaError_t run_binning(sph_ctx *c, int reorder)
     return cudaSuccess;
 }
 
+// Binning over caller-supplied buffers (no context): the same kernels as
+// run_binning, driven with explicit pointers.  Results go to out_perm,
+// out_cell and out_start.
+cudaError_t bin_raw(const BinRaw &b, cudaStream_t s)
+{
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(b.count, 0, sizeof(int32_t) * (size_t)b.ncell, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(b.st, 0, sizeof(DevStats), s)) != cudaSuccess) return e;
+    uint64_t launches = 0;
+    if (b.n > 0) {
+        CellArgs a;
+        a.aos = b.aos;
+        a.n = b.n;
+        a.stride = b.stride;
+        a.xoff = b.xoff;
+        for (int k = 0; k < 3; ++k) {
+            a.inv[k] = b.inv[k];
+            a.box[k] = b.box[k];
+            a.nc[k] = b.nc[k];
+        }
+        a.keys = b.keys[0];
+        a.vals = b.vals[0];
+        a.count = b.count;
+        a.st = b.st;
+        k_cell_ids<<<blocks_for(b.n, 256), 256, 0, s>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if ((e = scan_exclusive(b.count, b.out_start, b.ncell, b.scan_part, s, &launches)) != cudaSuccess) return e;
+    if (b.n == 0) return cudaSuccess;
+    int bits = 0;
+    while (bits < 31 && ((int64_t)1 << bits) < b.ncell) ++bits;
+    const int64_t nblk = (b.n + kRadixTile - 1) / kRadixTile;
+    int cur = 0;
+    for (int shift = 0; shift < bits; shift += 8) {
+        k_radix_hist<<<(unsigned)nblk, kRadixThreads, 0, s>>>(b.keys[cur], b.n, shift, b.ghist, nblk);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = scan_exclusive((const int32_t *)b.ghist, (int32_t *)b.ghist, 256 * nblk, b.scan_part, s,
+                                &launches)) != cudaSuccess)
+            return e;
+        k_radix_scatter<<<(unsigned)nblk, kRadixThreads, 0, s>>>(b.keys[cur], b.vals[cur], b.keys[cur ^ 1],
+                                                                 b.vals[cur ^ 1], b.n, shift, b.ghist, nblk);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        cur ^= 1;
+    }
+    const size_t bytes = sizeof(int32_t) * (size_t)b.n;
+    if ((e = cudaMemcpyAsync(b.out_perm, b.vals[cur], bytes, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
+    return cudaMemcpyAsync(b.out_cell, b.keys[cur], bytes, cudaMemcpyDeviceToDevice, s);
+}
+
 cudaError_t run_items(sph_ctx *c)
 {
     cudaStream_t s = c->stream;

@@ -234,6 +234,21 @@ cudaError_t run_kick_drift(sph_ctx *c, double dt_kick, double dt_drift);
 cudaError_t scan_exclusive(const int32_t *in, int32_t *out, int64_t len, int32_t *part,
                            cudaStream_t s, uint64_t *launches);
 int max_dynamic_smem(const sph_ctx *c);
+// binning over explicit buffers (used by the allocation-free entry point)
+struct BinRaw {
+    const uint8_t *aos;
+    int64_t n;
+    int32_t stride, xoff;
+    double inv[3], box[3];
+    int32_t nc[3];
+    int64_t ncell;
+    int32_t *keys[2], *vals[2];
+    int32_t *count, *scan_part;
+    uint32_t *ghist;
+    DevStats *st;
+    int32_t *out_perm, *out_cell, *out_start;
+};
+cudaError_t bin_raw(const BinRaw &b, cudaStream_t s);
 size_t density_smem_bytes(int block_threads, int stage_cap);
 size_t force_smem_bytes(int block_threads, int stage_cap);
 }  // namespace sph
