@@ -152,6 +152,8 @@ typedef struct {
     int32_t ctas_per_sm;         /* persistent CTAs per SM (0: occupancy maximum) */
     int32_t stage_density;       /* neighbour candidates staged per warp, density kernel (>= 32) */
     int32_t stage_force;         /* neighbour candidates staged per warp, force kernel (>= 32) */
+    int32_t subcells;            /* sub-cells per cell edge used to order particles, 1 or 2
+                                    (default 2); takes effect at the next sph_bin_cells */
 } sph_tuning;
 
 /* Where the library's arrays live inside the workspace (byte offsets from the
@@ -161,14 +163,14 @@ typedef struct {
     int32_t ncell[3];
     double cell_edge[3];
     int64_t off_perm;            /* int32[n]: sorted slot -> original particle index */
-    int64_t off_cell_of_slot;    /* int32[n]: sorted slot -> cell id */
-    int64_t off_cell_start;      /* int32[ncell+1] */
+    int64_t off_cell_of_slot;    /* int32[n]: sorted slot -> key = cell * s^3 + sub-cell */
+    int64_t off_cell_start;      /* int32[ncell s^3 + 1]: first slot of each key */
     int64_t off_nngb;            /* int32[n], neighbour counts of the last density call */
     int64_t off_nngb_force;      /* int32[n], neighbour counts of the last force call */
     int64_t off_soa[SPH_NFIELDS][3];
     int32_t prec[SPH_NFIELDS];   /* current storage format of each SoA field */
     uint32_t valid;              /* fields whose SoA copy is current */
-    int32_t reserved;
+    int32_t subcells;            /* s: sub-cells per cell edge of the last binning */
 } sph_desc;
 
 typedef struct sph_ctx sph_ctx;
@@ -194,9 +196,13 @@ sph_status sph_create(const sph_aos_layout *layout, const sph_params *params, in
  * Section 6; the build generalises them to a uniform grid).  Cells per axis
  * nc_d = floor(box_d / max(cell_edge, 2 h_max)); each particle's cell is
  * k_d = clamp(floor(x_d * (nc_d / box_d)), 0, nc_d - 1) in FP64, linear id
- * kx + nc_x (ky + nc_y kz).  The permutation lists particles cell by cell,
- * ascending original index inside a cell (a stable sort), and the pair-kernel
- * work items are rebuilt.  reorder_aos = 1 also rewrites the AoS records in
+ * kx + nc_x (ky + nc_y kz).  Each cell is split into s^3 sub-cells
+ * (s = tuning.subcells): fine coordinate f_d = clamp(floor(x_d * (s nc_d /
+ * box_d)), 0, s nc_d - 1), cell f_d / s, sub-cell f_d % s, key
+ * cell s^3 + (s_x + s (s_y + s s_z)).  The permutation lists particles by key,
+ * ascending original index among equal keys (a stable sort), so every cell
+ * stays contiguous and spatially compact inside; the pair-kernel work items
+ * are rebuilt.  reorder_aos = 1 also rewrites the AoS records in
  * that order (the permutation then becomes the identity); it needs a
  * workspace created with SPH_WS_REORDER.  Invalidates every SoA field.
  * Errors: SPH_ECAPACITY (< 3 cells on an axis), SPH_ENOSPACE (more than
@@ -275,8 +281,9 @@ sph_status sph_aos_download(sph_ctx *ctx, void *host, size_t bytes);
  * as a plugin running inside a host application that owns the whole device
  * memory pool and offers plugins no allocation hook, or a latency-critical
  * path where cudaMalloc's implicit device-wide synchronisation is not
- * acceptable.  It computes exactly what sph_bin_cells computes (same cell
- * rule, same stable order) without a context or a workspace: its scratch
+ * acceptable.  It computes exactly what sph_bin_cells computes with one
+ * sub-cell per cell (tuning.subcells = 1: same cell rule, same stable order)
+ * without a context or a workspace: its scratch
  * memory is a fixed array of SPH_NOALLOC_SCRATCH_BYTES inside libsph, which
  * every device that loads the library holds until the process exits.
  *

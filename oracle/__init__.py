@@ -72,6 +72,8 @@ def _declare(L):
         getattr(L, name).argtypes = [_d, _d]
     L.orc_bin.restype = C.c_int
     L.orc_bin.argtypes = [_i64, _p, _p, _p, _p, _p, _p]
+    L.orc_bin_sub.restype = C.c_int
+    L.orc_bin_sub.argtypes = [_i64, _p, _p, _p, C.c_int32, _p, _p, _p]
     L.orc_density.restype = None
     L.orc_density.argtypes = [_i64, _p, _p, _p, _p, _d, _d, C.c_int, C.c_int, _i64, _p,
                               _p, _p, _p, _p, _p, _p]
@@ -136,18 +138,19 @@ def dWdh(r, h):
 
 
 # ---------------------------------------------------------------- binning
-def bin_cells(x, box, nc):
-    """Stable cell binning.  Returns (cell_of[n] int32, perm[n] int64,
-    cell_start[ncell+1] int64)."""
+def bin_cells(x, box, nc, sub=1):
+    """Stable binning into cells split into sub^3 sub-cells.  Returns
+    (key[n] int32, perm[n] int64, start[ncell sub^3 + 1] int64) where key is
+    cell * sub^3 + sub-cell."""
     x = _f64(x, (-1, 3))
     n = x.shape[0]
     nc = np.ascontiguousarray(nc, dtype=np.int32)
-    ncell = int(np.prod(nc.astype(np.int64)))
+    ncell = int(np.prod(nc.astype(np.int64))) * sub ** 3
     cell_of = np.zeros(n, np.int32)
     perm = np.zeros(n, np.int64)
     start = np.zeros(ncell + 1, np.int64)
-    rc = lib().orc_bin(n, _ptr(x), _ptr(_f64(box)), _ptr(nc), _ptr(cell_of), _ptr(perm),
-                       _ptr(start))
+    rc = lib().orc_bin_sub(n, _ptr(x), _ptr(_f64(box)), _ptr(nc), int(sub), _ptr(cell_of),
+                           _ptr(perm), _ptr(start))
     if rc != 0:
         raise ValueError("orc_bin failed")
     return cell_of, perm, start

@@ -124,24 +124,37 @@ static int32_t cell_coord(double x, double inv, int32_t nc)
 /* ------------------------------------------------------------------------- */
 
 /*
- * Cell of particle i: k_d = clamp(floor(x_d * (nc_d / L_d)), 0, nc_d - 1),
- * linear id kx + nc_x (ky + nc_y kz).  perm lists the particles cell by cell,
- * ascending original index inside a cell; cell_start[c] is the first slot of
- * cell c, cell_start[ncell] = n.  Returns 0, or -1 on a bad grid.
+ * Cells with sub-cells: each of the nc_x nc_y nc_z cells is split into
+ * sub^3 sub-cells.  Fine coordinate f_d = clamp(floor(x_d * (sub nc_d / L_d)),
+ * 0, sub nc_d - 1); cell k_d = f_d / sub, sub-cell s_d = f_d % sub; key
+ * (kx + nc_x (ky + nc_y kz)) sub^3 + (s_x + sub (s_y + sub s_z)).  perm lists
+ * the particles by key, ascending original index among equal keys;
+ * cell_start[key] is the first slot of that sub-cell, cell_start[ncell sub^3]
+ * = n.  With sub = 1 this is the plain cell list.  Returns 0, or -1 on a bad
+ * grid.
  */
-int orc_bin(int64_t n, const double *x, const double *box, const int32_t *nc,
-            int32_t *cell_of, int64_t *perm, int64_t *cell_start)
+int orc_bin_sub(int64_t n, const double *x, const double *box, const int32_t *nc, int32_t sub,
+                int32_t *cell_of, int64_t *perm, int64_t *cell_start)
 {
-    if (nc[0] < 1 || nc[1] < 1 || nc[2] < 1) return -1;
-    int64_t ncell = (int64_t)nc[0] * nc[1] * nc[2];
+    if (nc[0] < 1 || nc[1] < 1 || nc[2] < 1 || sub < 1) return -1;
+    const int64_t s3 = (int64_t)sub * sub * sub;
+    int64_t ncell = (int64_t)nc[0] * nc[1] * nc[2] * s3;
     double inv[3];
-    for (int k = 0; k < 3; ++k) inv[k] = (double)nc[k] / box[k];
+    int32_t nf[3];
+    for (int k = 0; k < 3; ++k) {
+        nf[k] = nc[k] * sub;
+        inv[k] = (double)nf[k] / box[k];
+    }
     for (int64_t c = 0; c <= ncell; ++c) cell_start[c] = 0;
     for (int64_t i = 0; i < n; ++i) {
-        int32_t kx = cell_coord(x[3 * i + 0], inv[0], nc[0]);
-        int32_t ky = cell_coord(x[3 * i + 1], inv[1], nc[1]);
-        int32_t kz = cell_coord(x[3 * i + 2], inv[2], nc[2]);
-        int32_t c = kx + nc[0] * (ky + nc[1] * kz);
+        int32_t f[3], k[3], s[3];
+        for (int a = 0; a < 3; ++a) {
+            f[a] = cell_coord(x[3 * i + a], inv[a], nf[a]);
+            k[a] = f[a] / sub;
+            s[a] = f[a] % sub;
+        }
+        int64_t cell = k[0] + (int64_t)nc[0] * (k[1] + (int64_t)nc[1] * k[2]);
+        int32_t c = (int32_t)(cell * s3 + (s[0] + sub * (s[1] + sub * s[2])));
         cell_of[i] = c;
         cell_start[c + 1] += 1;
     }
@@ -152,6 +165,13 @@ int orc_bin(int64_t n, const double *x, const double *box, const int32_t *nc,
     for (int64_t i = 0; i < n; ++i) perm[fill[cell_of[i]]++] = i;
     free(fill);
     return 0;
+}
+
+/* plain cell list: one sub-cell per cell */
+int orc_bin(int64_t n, const double *x, const double *box, const int32_t *nc,
+            int32_t *cell_of, int64_t *perm, int64_t *cell_start)
+{
+    return orc_bin_sub(n, x, box, nc, 1, cell_of, perm, cell_start);
 }
 
 /* ------------------------------------------------------------------------- */

@@ -41,6 +41,8 @@ double orc_dWdr(double r, double h);
 double orc_dWdh(double r, double h);
 
 /* ---- cell binning: FP64 cell index, stable counting sort ---- */
+int orc_bin_sub(int64_t n, const double *x, const double *box, const int32_t *nc, int32_t sub,
+                int32_t *cell_of, int64_t *perm, int64_t *cell_start);
 int orc_bin(int64_t n, const double *x, const double *box, const int32_t *nc,
             int32_t *cell_of, int64_t *perm, int64_t *cell_start);
 

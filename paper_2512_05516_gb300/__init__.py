@@ -260,15 +260,17 @@ class Sph:
     def reset_stats(self):
         _check(sph_reset_stats(self.ctx), "sph_reset_stats")
 
-    def set_tuning(self, block_threads=0, ctas_per_sm=0, stage_density=0, stage_force=0):
-        t = sph_tuning(block_threads, ctas_per_sm, stage_density, stage_force)
+    def set_tuning(self, block_threads=0, ctas_per_sm=0, stage_density=0, stage_force=0,
+                   subcells=0):
+        t = sph_tuning(block_threads, ctas_per_sm, stage_density, stage_force, subcells)
         _check(sph_set_tuning(self.ctx, t), "sph_set_tuning")
 
     def tuning(self) -> dict:
         st, t = sph_get_tuning(self.ctx)
         _check(st, "sph_get_tuning")
         return {"block_threads": t.block_threads, "ctas_per_sm": t.ctas_per_sm,
-                "stage_density": t.stage_density, "stage_force": t.stage_force}
+                "stage_density": t.stage_density, "stage_force": t.stage_force,
+                "subcells": t.subcells}
 
     def describe(self) -> sph_desc:
         st, d = sph_describe(self.ctx)
@@ -290,7 +292,7 @@ class Sph:
 
     def cell_start(self):
         d = self.describe()
-        nc = d.ncell[0] * d.ncell[1] * d.ncell[2]
+        nc = d.ncell[0] * d.ncell[1] * d.ncell[2] * d.subcells ** 3
         return self._ws_view(d.off_cell_start, nc + 1, self.torch.int32)
 
     def nngb(self, force: bool = False):

@@ -56,7 +56,7 @@ class sph_stats(C.Structure):
 
 class sph_tuning(C.Structure):
     _fields_ = [("block_threads", C.c_int32), ("ctas_per_sm", C.c_int32),
-                ("stage_density", C.c_int32), ("stage_force", C.c_int32)]
+                ("stage_density", C.c_int32), ("stage_force", C.c_int32), ("subcells", C.c_int32)]
 
 
 class sph_desc(C.Structure):
@@ -64,7 +64,7 @@ class sph_desc(C.Structure):
                 ("off_perm", C.c_int64), ("off_cell_of_slot", C.c_int64),
                 ("off_cell_start", C.c_int64), ("off_nngb", C.c_int64),
                 ("off_nngb_force", C.c_int64), ("off_soa", (C.c_int64 * 3) * SPH_NFIELDS),
-                ("prec", C.c_int32 * SPH_NFIELDS), ("valid", C.c_uint32), ("reserved", C.c_int32)]
+                ("prec", C.c_int32 * SPH_NFIELDS), ("valid", C.c_uint32), ("subcells", C.c_int32)]
 
 
 # every symbol the header declares, with its prototype

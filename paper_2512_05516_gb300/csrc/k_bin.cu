@@ -17,6 +17,7 @@ struct CellArgs {
     int32_t stride, xoff;
     double inv[3], box[3];
     int32_t nc[3];
+    int32_t sub;                 // sub-cells per cell edge
     int32_t *keys, *vals, *count;
     DevStats *st;
 };
@@ -38,10 +39,14 @@ __global__ void k_cell_ids(CellArgs a)
     bool outside = !(x0 >= 0.0 && x0 < a.box[0] && x1 >= 0.0 && x1 < a.box[1] &&
                      x2 >= 0.0 && x2 < a.box[2]);
     if (outside) set_error(a.st, SPH_ERR_OUTSIDE | ((isfinite(x0) && isfinite(x1) && isfinite(x2)) ? 0u : SPH_ERR_NONFINITE));
-    int32_t kx = cell_coord(x0, a.inv[0], a.nc[0]);
-    int32_t ky = cell_coord(x1, a.inv[1], a.nc[1]);
-    int32_t kz = cell_coord(x2, a.inv[2], a.nc[2]);
-    int32_t c = kx + a.nc[0] * (ky + a.nc[1] * kz);
+    // fine coordinates on the grid of sub-cells (inv = sub * nc / L); the cell
+    // is f / sub, the sub-cell f % sub
+    const int32_t S = a.sub;
+    int32_t fx = cell_coord(x0, a.inv[0], a.nc[0] * S);
+    int32_t fy = cell_coord(x1, a.inv[1], a.nc[1] * S);
+    int32_t fz = cell_coord(x2, a.inv[2], a.nc[2] * S);
+    int32_t cell = fx / S + a.nc[0] * (fy / S + a.nc[1] * (fz / S));
+    int32_t c = cell * S * S * S + (fx % S + S * (fy % S + S * (fz % S)));
     a.keys[i] = c;
     a.vals[i] = (int32_t)i;
     atomicAdd(&a.count[c], 1);
@@ -206,22 +211,24 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(const int32_t *
 // ---------------------------------------------------------------------------
 // work items: each cell is split into tiles of `block` slots
 // ---------------------------------------------------------------------------
-__global__ void k_items_count(const int32_t *cell_start, int64_t ncell, int block, int32_t *tmp, DevStats *st)
+// cell_start is indexed by sub-cell key; cell c spans keys [c s3, (c+1) s3)
+__global__ void k_items_count(const int32_t *cell_start, int64_t ncell, int s3, int block, int32_t *tmp,
+                              DevStats *st)
 {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
-    int32_t cnt = cell_start[c + 1] - cell_start[c];
+    int32_t cnt = cell_start[(c + 1) * s3] - cell_start[c * s3];
     tmp[c] = (cnt + block - 1) / block;
     if (cnt > 0) atomicMax(&st->max_occ, cnt);
 }
 
-__global__ void k_items_fill(const int32_t *cell_start, const int32_t *item_off, int64_t ncell, int block,
+__global__ void k_items_fill(const int32_t *cell_start, const int32_t *item_off, int64_t ncell, int s3, int block,
                              int32_t *icell, int32_t *ifirst, int32_t *icount, DevStats *st)
 {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c == 0) st->nitems = item_off[ncell];
     if (c >= ncell) return;
-    int32_t s = cell_start[c], e = cell_start[c + 1];
+    int32_t s = cell_start[c * s3], e = cell_start[(c + 1) * s3];
     int32_t o = item_off[c];
     for (int32_t f = s; f < e; f += block, ++o) {
         icell[o] = (int32_t)c;
@@ -273,7 +280,9 @@ cudaError_t run_binning(sph_ctx *c, int reorder)
     cudaStream_t s = c->stream;
     cudaError_t e;
     const int64_t n = c->n;
-    if ((e = cudaMemsetAsync(c->cell_count, 0, sizeof(int32_t) * c->ncell, s)) != cudaSuccess) return e;
+    const int S = c->sub;
+    const int64_t nkeys = c->ncell * S * S * S;     // sub-cells
+    if ((e = cudaMemsetAsync(c->cell_count, 0, sizeof(int32_t) * nkeys, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(&c->dstats->max_occ, 0, sizeof(int), s)) != cudaSuccess) return e;
     c->sorted_buf = 0;
     if (n > 0) {
@@ -282,8 +291,9 @@ cudaError_t run_binning(sph_ctx *c, int reorder)
         a.n = n;
         a.stride = c->layout.record_bytes;
         a.xoff = c->layout.offset[SPH_F_X];
+        a.sub = S;
         for (int k = 0; k < 3; ++k) {
-            a.inv[k] = c->inv[k];
+            a.inv[k] = (double)(c->nc[k] * S) / c->params.box[k];
             a.box[k] = c->params.box[k];
             a.nc[k] = c->nc[k];
         }
@@ -295,10 +305,10 @@ cudaError_t run_binning(sph_ctx *c, int reorder)
         c->launches += 1;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    if ((e = scan_exclusive(c->cell_count, c->cell_start, c->ncell, c->scan_part, s, &c->launches)) != cudaSuccess) return e;
+    if ((e = scan_exclusive(c->cell_count, c->cell_start, nkeys, c->scan_part, s, &c->launches)) != cudaSuccess) return e;
     if (n > 0) {
         int bits = 0;
-        while (bits < 31 && ((int64_t)1 << bits) < c->ncell) ++bits;
+        while (bits < 31 && ((int64_t)1 << bits) < nkeys) ++bits;
         const int64_t nblk = c->plan.nblk_radix;
         int cur = 0;
         for (int shift = 0; shift < bits; shift += 8) {
@@ -343,6 +353,7 @@ cudaError_t bin_raw(const BinRaw &b, cudaStream_t s)
         a.n = b.n;
         a.stride = b.stride;
         a.xoff = b.xoff;
+        a.sub = 1;                   // plain cells: b.ncell keys
         for (int k = 0; k < 3; ++k) {
             a.inv[k] = b.inv[k];
             a.box[k] = b.box[k];
@@ -382,11 +393,13 @@ cudaError_t run_items(sph_ctx *c)
     cudaStream_t s = c->stream;
     cudaError_t e;
     const int block = kItemTile;    // one warp per work item
-    k_items_count<<<blocks_for(c->ncell, 256), 256, 0, s>>>(c->cell_start, c->ncell, block, c->item_tmp, c->dstats);
+    const int s3 = c->sub * c->sub * c->sub;
+    k_items_count<<<blocks_for(c->ncell, 256), 256, 0, s>>>(c->cell_start, c->ncell, s3, block, c->item_tmp,
+                                                            c->dstats);
     c->launches += 2;   // count and fill
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = scan_exclusive(c->item_tmp, c->item_tmp, c->ncell, c->scan_part, s, &c->launches)) != cudaSuccess) return e;
-    k_items_fill<<<blocks_for(c->ncell, 256), 256, 0, s>>>(c->cell_start, c->item_tmp, c->ncell, block,
+    k_items_fill<<<blocks_for(c->ncell, 256), 256, 0, s>>>(c->cell_start, c->item_tmp, c->ncell, s3, block,
                                                            c->item_cell, c->item_first, c->item_count, c->dstats);
     return cudaGetLastError();
 }

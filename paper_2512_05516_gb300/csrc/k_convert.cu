@@ -17,6 +17,7 @@ struct ConvArgs {
     const int32_t *perm;
     const int32_t *slot_cell;
     int32_t nc[3];
+    int32_t s3;                  // sub-cells per cell
     double edge[3];
     int nf;
     int fid[SPH_NFIELDS];
@@ -38,7 +39,7 @@ __global__ void __launch_bounds__(256) k_aos_to_soa(ConvArgs a)
         double org[3] = {0.0, 0.0, 0.0};
         if (f == SPH_F_X && ok) {
             // cell-relative positions: offset from k_d * (L_d / nc_d), in FP64
-            int32_t cid = a.slot_cell[k];
+            int32_t cid = a.slot_cell[k] / a.s3;   // key = cell * s^3 + sub-cell
             int32_t kx = cid % a.nc[0];
             int32_t t = cid / a.nc[0];
             int32_t ky = t % a.nc[1];
@@ -89,6 +90,7 @@ ConvArgs make_args(sph_ctx *c, uint32_t fields)
     a.stride = c->layout.record_bytes;
     a.perm = c->perm();
     a.slot_cell = c->slot_cell();
+    a.s3 = c->sub * c->sub * c->sub;
     for (int k = 0; k < 3; ++k) {
         a.nc[k] = c->nc[k];
         a.edge[k] = c->edge[k];

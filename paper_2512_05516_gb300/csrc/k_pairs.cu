@@ -2,29 +2,33 @@
 // as persistent CUDA-core kernels over a work queue of warp-sized items.
 //
 // Work item = (cell, first slot, count <= 32): a tile of one cell, one lane
-// per i-particle.  Warps are independent: each pops its own item, stages into
-// its own shared-memory region only those particles of the 27 neighbour cells
-// (periodic) that can reach the bounding box of its lanes, converted to FP32
-// and shifted into the cell's frame (positions are cell-relative, so the
-// shift is the neighbour's cell offset times the cell edge), then runs the
-// pair loop.  No block-wide barrier is ever taken.  When a neighbourhood does
-// not fit the stage, it is streamed through it in chunks.
+// per i-particle.  Inside a cell the particles are ordered by sub-cell, so a
+// tile is spatially compact.  Warps are independent: each pops its own item,
+// lists the sub-cells of the 27 neighbour cells (periodic) whose box comes
+// within reach of the bounding box of its lanes, stages the particles of
+// those sub-cells that are themselves within reach into its own shared-memory
+// region (converted to FP32 and shifted into the cell's frame: positions are
+// cell-relative, so the shift is the neighbour's cell offset times the cell
+// edge), and runs the pair loop.  No block-wide barrier is ever taken.  A
+// neighbourhood that does not fit the stage is streamed through it in chunks.
 //
 // Density (Eq. 6, gather form): rho_i = sum_j m_j W(r_ij, h_i), M4 cubic
-// spline W = sigma/h^3 w(r/h), support 2h, compensated FP32 sum (TwoSum);
+// spline W = sigma/h^3 w(r/h), support 2h, compensated FP32 sum (Kahan);
 // `newton_steps` Newton steps on f(h) = rho(h) - m_i (eta/h)^3 clamped to
 // [h/2, 2h] and h_max, then a final sum; EOS P = (gamma-1) rho u,
-// c = sqrt(gamma P / rho).  Pass 0 also builds, per lane, the list of staged
-// candidates within 2 h (1 + skin); later passes walk only that list and
-// rebuild it when h outgrows the skin.
+// c = sqrt(gamma P / rho).  Each lane keeps the list of staged candidates
+// within 2 h (1 + skin); the passes walk only that list, and it is rebuilt
+// when h outgrows the skin.
 //
 // Force (Eq. 7 + Monaghan viscosity, Eq. 5 for du/dt), pairs r < h_i + h_j:
 //   a_i    -= m_j (P_i/rho_i^2 + P_j/rho_j^2 + Pi_ij) gradW(r_ij, hbar)
 //   du_i/dt += m_j (P_i/rho_i^2 + Pi_ij/2) v_ij . gradW
+// Each lane first lists its pairs among the staged candidates, then
+// evaluates them with every lane busy.
 //
-// Summation order: every lane accumulates its pairs in staged order (cell of
-// the stencil, then slot), whatever the chunking, list or launch shape, so
-// results do not depend on the tuning.
+// Summation order: every lane accumulates its pairs in staged order
+// (stencil cell, sub-cell, slot), whatever the chunking, list or launch
+// shape, so results do not depend on the tuning.
 #include "sph_internal.cuh"
 
 namespace sph {
@@ -33,14 +37,19 @@ cudaError_t run_pack(sph_ctx *c, const float *src, int f);
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int kLaneCap = 96;        // per-lane neighbour list entries (density)
-constexpr float kSkin = 0.12f;      // list / stage radius = 2 h (1 + skin)
+constexpr int kLaneCap = 96;                                 // per-lane pair list entries
+constexpr float kSkin = 0.12f;                               // list / stage radius = 2 h (1 + skin)
+constexpr int kMaxEnt = 27 * kMaxSub * kMaxSub * kMaxSub;    // stencil sub-cells
+constexpr int kEntPerLane = (kMaxEnt + 31) / 32;
+constexpr int kStageUnroll = 4;                              // 32-candidate batches in flight
 
 struct Common {
     int64_t n;
     int32_t nc[3];
     float edge[3];
-    const int32_t *cell_start;
+    int sub, s3;                     // sub-cells per cell edge, per cell
+    int lg_sub, lg_s3;               // their base-2 logarithms (sub is 1 or 2)
+    const int32_t *cell_start;       // indexed by key = cell * s3 + sub-cell
     const int32_t *icell, *ifirst, *icount;
     DevStats *st;
     FieldRef x, m, h;
@@ -65,38 +74,20 @@ struct DensityArgs {
 struct ForceArgs {
     Common c;
     FieldRef v, rho, P, cs;
-    float alpha, beta, eps;
+    float alpha, beta, eps, h_cap;
     float *a[3];
     float *dudt;
     int32_t *nngb;
 };
 
-// the 27 neighbour cells of an item, one per lane (lanes 27..31 hold empty cells)
-struct Stencil {
-    int start, count;
-    float sx, sy, sz;
+// The candidate stream of one warp: the kept stencil sub-cells, in stencil
+// order (neighbour cell t, then sub-cell), as prefix sums in shared memory.
+// Stream position g lies in the first entry e with incl[e] > g, at slot
+// base[e] + g.
+struct Tab {
+    int incl[kMaxEnt];
+    int base[kMaxEnt];
 };
-
-__device__ __forceinline__ Stencil stencil_lane(const Common &c, int cell, int lane)
-{
-    Stencil s{0, 0, 0.f, 0.f, 0.f};
-    if (lane < 27) {
-        const int kx = cell % c.nc[0];
-        const int ky = (cell / c.nc[0]) % c.nc[1];
-        const int kz = cell / (c.nc[0] * c.nc[1]);
-        const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
-        const int nx = (kx + dx + c.nc[0]) % c.nc[0];
-        const int ny = (ky + dy + c.nc[1]) % c.nc[1];
-        const int nz = (kz + dz + c.nc[2]) % c.nc[2];
-        const int nb = nx + c.nc[0] * (ny + c.nc[1] * nz);
-        s.start = c.cell_start[nb];
-        s.count = c.cell_start[nb + 1] - s.start;
-        s.sx = (float)dx * c.edge[0];
-        s.sy = (float)dy * c.edge[1];
-        s.sz = (float)dz * c.edge[2];
-    }
-    return s;
-}
 
 __device__ __forceinline__ int pop_item(DevStats *st, int lane)
 {
@@ -146,6 +137,89 @@ __device__ __forceinline__ float box_dist2(const Box &b, float x, float y, float
     return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
 }
 
+// offset of stencil cell t (0..26) in the item cell's frame
+__device__ __forceinline__ void stencil_shift(const Common &c, int t, float &sx, float &sy, float &sz)
+{
+    sx = (float)(t % 3 - 1) * c.edge[0];
+    sy = (float)((t / 3) % 3 - 1) * c.edge[1];
+    sz = (float)(t / 9 - 1) * c.edge[2];
+}
+
+// List the stencil sub-cells of `cell` whose box comes within sqrt(R2) of the
+// warp box (every particle of a sub-cell sits inside its box: positions are
+// cell-relative offsets, widened here by a rounding margin).  Returns the
+// number of candidates in the stream (warp-uniform).
+__device__ int build_stream(const Common &c, int cell, const Box &box, float R2, Tab &tab, int lane)
+{
+    const int nent = 27 * c.s3;
+    const int E = (nent + 31) / 32;            // entries per lane, lane-blocked
+    const int kx = cell % c.nc[0];
+    const int ky = (cell / c.nc[0]) % c.nc[1];
+    const int kz = cell / (c.nc[0] * c.nc[1]);
+    int cnt[kEntPerLane], st[kEntPerLane];
+    int local = 0;
+#pragma unroll
+    for (int i = 0; i < kEntPerLane; ++i) {
+        cnt[i] = 0;
+        st[i] = 0;
+        const int e = lane * E + i;
+        if (i < E && e < nent) {
+            const int t = e >> c.lg_s3, q = e & (c.s3 - 1);
+            const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+            int nx = kx + dx, ny = ky + dy, nz = kz + dz;      // periodic wrap, |d| <= 1
+            nx += nx < 0 ? c.nc[0] : (nx >= c.nc[0] ? -c.nc[0] : 0);
+            ny += ny < 0 ? c.nc[1] : (ny >= c.nc[1] ? -c.nc[1] : 0);
+            nz += nz < 0 ? c.nc[2] : (nz >= c.nc[2] ? -c.nc[2] : 0);
+            const int key = ((nx + c.nc[0] * (ny + c.nc[1] * nz)) << c.lg_s3) + q;
+            const int s0 = c.cell_start[key];
+            const int n0 = c.cell_start[key + 1] - s0;
+            st[i] = s0;
+            if (n0 > 0) {
+                const int m1 = c.sub - 1;
+                const int qa[3] = {q & m1, (q >> c.lg_sub) & m1, q >> (2 * c.lg_sub)};
+                const int da[3] = {dx, dy, dz};
+                float d2 = 0.0f;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const float se = c.edge[a] / (float)c.sub;
+                    const float margin = c.edge[a] * (1.0f / 512.0f);
+                    const float lo = (float)da[a] * c.edge[a] + (float)qa[a] * se - margin;
+                    const float hi = lo + se + 2.0f * margin;
+                    const float g = fmaxf(0.0f, fmaxf(lo - box.hi[a], box.lo[a] - hi));
+                    d2 = fmaf(g, g, d2);
+                }
+                if (d2 < R2) cnt[i] = n0;
+            }
+        }
+        local += cnt[i];
+    }
+    int inc = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += v;
+    }
+    int run = inc - local;
+#pragma unroll
+    for (int i = 0; i < kEntPerLane; ++i) {
+        const int e = lane * E + i;
+        if (i < E && e < nent) {
+            run += cnt[i];
+            tab.incl[e] = run;
+            tab.base[e] = st[i] - (run - cnt[i]);
+        }
+    }
+    __syncwarp();
+    return __shfl_sync(FULL, inc, 31);
+}
+
+// Walk forward from entry e to the entry holding stream position g (g < total).
+__device__ __forceinline__ int advance(const Tab &tab, int nent, int e, int g)
+{
+    while (e < nent - 1 && tab.incl[e] <= g) ++e;
+    return e;
+}
+
 // M4 spline w(q) and w'(q), branch-free
 __device__ __forceinline__ void spline(float q, float &w, float &dw)
 {
@@ -158,13 +232,13 @@ __device__ __forceinline__ void spline(float q, float &w, float &dw)
     dw = inner ? dw_in : -0.75f * t2;
 }
 
-// compensated accumulation: s + c carries the running sum (Knuth's TwoSum)
-__device__ __forceinline__ void two_sum_add(float &s, float &c, float x)
+// Kahan compensated accumulation: s - c carries the running sum; c holds the
+// low-order part lost by the last addition (the terms are non-negative)
+__device__ __forceinline__ void kahan_add(float &s, float &c, float x)
 {
-    const float t = __fadd_rn(s, x);
-    const float bp = __fsub_rn(t, s);
-    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp));
-    c = __fadd_rn(c, err);
+    const float y = __fsub_rn(x, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
     s = t;
 }
 
@@ -174,12 +248,13 @@ __device__ __forceinline__ void two_sum_add(float &s, float &c, float x)
 
 // density pass accumulators of one lane
 struct DAcc {
-    float s, c, d;   // compensated sum of m w, and sum of m (3w + q w')
+    float s, c, d;   // compensated sum of m w (s - c), and sum of m (3w + q w')
     int n;           // pairs with r < 2h (self included)
 };
 
+// one candidate of a density pass; `deriv` adds the dh term (Newton passes)
 __device__ __forceinline__ void dens_pair(DAcc &a, float xi, float yi, float zi, float h2x4,
-                                          float hinv, bool plain, const float4 q)
+                                          float hinv, bool plain, bool deriv, const float4 q)
 {
     const float dx = xi - q.x, dy = yi - q.y, dz = zi - q.z;
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
@@ -190,51 +265,68 @@ __device__ __forceinline__ void dens_pair(DAcc &a, float xi, float yi, float zi,
     spline(qq, w, dw);
     const float mw = in ? q.w * w : 0.0f;
     if (plain) a.s += mw;
-    else two_sum_add(a.s, a.c, mw);
-    a.d = fmaf(in ? q.w : 0.0f, fmaf(qq, dw, 3.0f * w), a.d);
+    else kahan_add(a.s, a.c, mw);
+    if (deriv) a.d = fmaf(in ? q.w : 0.0f, fmaf(qq, dw, 3.0f * w), a.d);
     a.n += in ? 1 : 0;
 }
 
-// Stage the candidates of the 27 cells within distance sqrt(R2) of the warp
-// box, in stencil order, from stream position `skip` on (chunked streaming).
-// Writes at most `cap` entries; returns how many candidates were found from
-// `skip` on (may exceed cap).
-__device__ int stage_density(const Common &c, const Stencil &st, const Box &box, float R2,
-                             float4 *sj, int cap, int skip, int lane)
+// A position in the candidate stream and the table entry holding it.
+struct Cursor {
+    int g, e;
+};
+
+// Stage the stream's candidates within distance sqrt(R2) of the warp box, in
+// stream order, starting at `cur`, until the stage is full or the stream ends.
+// Returns how many were staged (<= cap) and moves `cur` to the first batch
+// not staged (cur.g == total when the stream is exhausted).  A chunk always
+// stages at least one batch, since a batch holds at most 32 <= cap.
+__device__ int stage_density(const Common &c, const Tab &tab, int total, const Box &box, float R2,
+                             float4 *sj, int cap, Cursor &cur, int lane)
 {
     const unsigned lt = (1u << lane) - 1u;
+    const int nent = 27 * c.s3;
     int found = 0;
-    for (int t = 0; t < 27; ++t) {
-        const int start = __shfl_sync(FULL, st.start, t);
-        const int cnt = __shfl_sync(FULL, st.count, t);
-        const float sx = __shfl_sync(FULL, st.sx, t);
-        const float sy = __shfl_sync(FULL, st.sy, t);
-        const float sz = __shfl_sync(FULL, st.sz, t);
-        for (int p0 = 0; p0 < cnt; p0 += 32) {
-            const int p = p0 + lane;
-            bool keep = false;
-            float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-            int64_t j = 0;
-            if (p < cnt) {
-                j = (int64_t)start + p;
-                q.x = ld_val(c.x.p[0], c.x.fmt, j) + sx;
-                q.y = ld_val(c.x.p[1], c.x.fmt, j) + sy;
-                q.z = ld_val(c.x.p[2], c.x.fmt, j) + sz;
-                keep = box_dist2(box, q.x, q.y, q.z) < R2;
+    int ecur = cur.e;
+    for (int g0 = cur.g; g0 < total; g0 += 32 * kStageUnroll) {
+        float4 q[kStageUnroll];
+        int eu[kStageUnroll];
+        int e = ecur;
+#pragma unroll
+        for (int u = 0; u < kStageUnroll; ++u) {
+            const int g = g0 + u * 32 + lane;
+            q[u] = make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.0f);
+            if (g < total) {
+                e = advance(tab, nent, e, g);
+                const int64_t j = (int64_t)tab.base[e] + g;
+                float sx, sy, sz;
+                stencil_shift(c, e >> c.lg_s3, sx, sy, sz);
+                q[u].x = ld_val(c.x.p[0], c.x.fmt, j) + sx;
+                q[u].y = ld_val(c.x.p[1], c.x.fmt, j) + sy;
+                q[u].z = ld_val(c.x.p[2], c.x.fmt, j) + sz;
+                q[u].w = ld_val(c.m.p[0], c.m.fmt, j);
             }
-            const unsigned b = __ballot_sync(FULL, keep);
-            if (keep) {
-                const int pos = found + __popc(b & lt) - skip;
-                if (pos >= 0 && pos < cap) {
-                    q.w = ld_val(c.m.p[0], c.m.fmt, j);
-                    sj[pos] = q;
-                }
-            }
-            found += __popc(b);
+            eu[u] = e;
         }
+#pragma unroll
+        for (int u = 0; u < kStageUnroll; ++u) {
+            const bool keep = box_dist2(box, q[u].x, q[u].y, q[u].z) < R2;
+            const unsigned b = __ballot_sync(FULL, keep);
+            const int nb = __popc(b);
+            if (found + nb > cap) {     // stage full: resume at this batch
+                cur.g = g0 + u * 32;
+                cur.e = __shfl_sync(FULL, eu[u], 0);
+                __syncwarp();
+                return found;
+            }
+            if (keep) sj[found + __popc(b & lt)] = q[u];
+            found += nb;
+        }
+        ecur = __shfl_sync(FULL, e, 31);
     }
+    cur.g = total;
+    cur.e = ecur;
     __syncwarp();
-    return found - skip;
+    return found;
 }
 
 __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
@@ -242,9 +334,10 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
     extern __shared__ __align__(16) unsigned char smem[];
     const Common &c = a.c;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const size_t per_warp = (size_t)c.cap * sizeof(float4) + (size_t)32 * kLaneCap * sizeof(uint16_t);
+    const size_t per_warp = (size_t)c.cap * sizeof(float4) + (size_t)32 * kLaneCap * sizeof(uint16_t) + sizeof(Tab);
     float4 *sj = reinterpret_cast<float4 *>(smem + warp * per_warp);
     uint16_t *lst = reinterpret_cast<uint16_t *>(sj + c.cap);
+    Tab &tab = *reinterpret_cast<Tab *>(lst + 32 * kLaneCap);
 
     unsigned long long my_pairs = 0, my_tests = 0;
     unsigned my_err = 0;
@@ -268,15 +361,16 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
             if (!(hi > 0.0f) || !isfinite(hi)) { hi = a.h_cap; my_err |= SPH_ERR_NONFINITE; }
             if (hi > a.h_cap) { hi = a.h_cap; clamped = true; }
         }
-        const Stencil st = stencil_lane(c, cell, lane);
         const Box box = warp_box(ok, xi, yi, zi);
 
         // stage everything within 2 h_stage of the box, h_stage = max h (1 + skin)
         float h_stage = fminf(warp_max(ok ? hi : 0.0f) * (1.0f + kSkin), a.h_cap);
-        int T = stage_density(c, st, box, 4.0f * h_stage * h_stage, sj, c.cap, 0, lane);
-        bool fits = T <= c.cap;
-        bool lists_ok = false;     // this lane's list holds every staged candidate within 2 h_list
-        float h_list = 0.0f;
+        float R2s = 4.0f * h_stage * h_stage;
+        int total = build_stream(c, cell, box, R2s, tab, lane);
+        Cursor cur{0, 0};
+        int T = stage_density(c, tab, total, box, R2s, sj, c.cap, cur, lane);
+        bool fits = cur.g >= total;
+        float h_list = 0.0f;       // this lane's list holds every staged candidate within 2 h_list
         int nlist = 0;
 
         float rho = 0.f, drdh = 0.f;
@@ -284,19 +378,21 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
         for (int pass = 0; pass < a.npass; ++pass) {
             const float h2x4 = 4.0f * hi * hi;
             const float hinv = 1.0f / hi;
+            const bool deriv = pass + 1 < a.npass;     // the last pass needs no dh term
             DAcc acc{0.f, 0.f, 0.f, 0};
             if (fits && __any_sync(FULL, ok && hi > h_stage)) {
                 // h outgrew the stage: re-stage with the current h
                 h_stage = fminf(warp_max(ok ? hi : 0.0f) * (1.0f + kSkin), a.h_cap);
-                T = stage_density(c, st, box, 4.0f * h_stage * h_stage, sj, c.cap, 0, lane);
-                fits = T <= c.cap;
+                R2s = 4.0f * h_stage * h_stage;
+                total = build_stream(c, cell, box, R2s, tab, lane);
+                Cursor rc{0, 0};
+                T = stage_density(c, tab, total, box, R2s, sj, c.cap, rc, lane);
+                fits = rc.g >= total;
                 h_list = 0.0f;
             }
             if (fits) {
                 // rebuild when some lane's h outgrew its list radius (always on pass 0)
-                const bool rebuild = __any_sync(FULL, ok && hi > h_list);
-                if (rebuild) {
-                    // walk every staged candidate and rebuild this lane's list
+                if (__any_sync(FULL, ok && hi > h_list)) {
                     h_list = fminf(hi * (1.0f + kSkin), h_stage);
                     const float R2l = 4.0f * h_list * h_list;
                     nlist = 0;
@@ -309,42 +405,40 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
                             if (r2 < R2l) {
                                 if (nlist < kLaneCap) lst[nlist * 32 + lane] = (uint16_t)e;
                                 ++nlist;
-                                dens_pair(acc, xi, yi, zi, h2x4, hinv, a.plain_sum, q);
                             }
                         }
                     }
-                    lists_ok = nlist <= kLaneCap;
                     __syncwarp();
-                } else if (ok) {
-                    if (lists_ok) {
-                        my_tests += (unsigned long long)nlist;
+                }
+                if (ok) {
+                    my_tests += (unsigned long long)(nlist <= kLaneCap ? nlist : T);
+                    if (nlist <= kLaneCap) {
 #pragma unroll 4
                         for (int e = 0; e < nlist; ++e)
-                            dens_pair(acc, xi, yi, zi, h2x4, hinv, a.plain_sum, sj[lst[e * 32 + lane]]);
+                            dens_pair(acc, xi, yi, zi, h2x4, hinv, a.plain_sum, deriv, sj[lst[e * 32 + lane]]);
                     } else {
                         // this lane's list overflowed: walk the whole stage
-                        my_tests += (unsigned long long)T;
-                        for (int e = 0; e < T; ++e) dens_pair(acc, xi, yi, zi, h2x4, hinv, a.plain_sum, sj[e]);
+                        for (int e = 0; e < T; ++e) dens_pair(acc, xi, yi, zi, h2x4, hinv, a.plain_sum, deriv, sj[e]);
                     }
                 }
             } else {
                 // the neighbourhood does not fit: stream it through the stage
                 const float hw = warp_max(ok ? hi : 0.0f);
                 const float R2 = 4.0f * hw * hw;
-                for (int skip = 0;; skip += c.cap) {
-                    const int got = stage_density(c, st, box, R2, sj, c.cap, skip, lane);
-                    const int len = min(got, c.cap);
+                const int tot = build_stream(c, cell, box, R2, tab, lane);
+                Cursor sc{0, 0};
+                do {
+                    const int len = stage_density(c, tab, tot, box, R2, sj, c.cap, sc, lane);
                     if (ok) {
                         my_tests += (unsigned long long)len;
-                        for (int e = 0; e < len; ++e) dens_pair(acc, xi, yi, zi, h2x4, hinv, a.plain_sum, sj[e]);
+                        for (int e = 0; e < len; ++e) dens_pair(acc, xi, yi, zi, h2x4, hinv, a.plain_sum, deriv, sj[e]);
                     }
                     __syncwarp();
-                    if (got <= c.cap) break;
-                }
+                } while (sc.g < tot);
             }
             if (ok) {
                 const float h3inv = hinv * hinv * hinv;
-                rho = kSigma * h3inv * (acc.s + acc.c);
+                rho = kSigma * h3inv * (acc.s - acc.c);
                 drdh = -kSigma * h3inv * hinv * acc.d;
                 cnt = acc.n - 1;           // the self term is in rho, not in the count
                 my_pairs += (unsigned long long)cnt;
@@ -391,51 +485,85 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
 // ---------------------------------------------------------------------------
 
 // Stage the force candidates (those within h_max(warp) + h_j of the warp box)
-// from stream position `skip` on; returns how many were found (may exceed cap).
-__device__ int stage_force(const ForceArgs &a, const Stencil &st, const Box &box, float hw,
-                           float4 *sA, float4 *sB, float4 *sC, int cap, int skip, int lane)
+// from `cur` on, until the stage is full or the stream ends; returns how many
+// were staged and moves `cur` (as stage_density).  The loads a kept
+// candidate needs beyond x and h are issued for all batches in flight before
+// anything is stored.  The stream's sub-cells were chosen with h_j <= h_max
+// (the 27-cell grid covers pairs up to 2 h_max only); a candidate with a
+// larger h sets the h-cap error bit.
+__device__ int stage_force(const ForceArgs &a, const Tab &tab, int total, const Box &box, float hw,
+                           float4 *sA, float4 *sB, float4 *sC, int cap, Cursor &cur, int lane,
+                           unsigned &err)
 {
     const Common &c = a.c;
     const unsigned lt = (1u << lane) - 1u;
+    const int nent = 27 * c.s3;
     int found = 0;
-    for (int t = 0; t < 27; ++t) {
-        const int start = __shfl_sync(FULL, st.start, t);
-        const int cnt = __shfl_sync(FULL, st.count, t);
-        const float sx = __shfl_sync(FULL, st.sx, t);
-        const float sy = __shfl_sync(FULL, st.sy, t);
-        const float sz = __shfl_sync(FULL, st.sz, t);
-        for (int p0 = 0; p0 < cnt; p0 += 32) {
-            const int p = p0 + lane;
-            bool keep = false;
-            float4 qa = make_float4(0.f, 0.f, 0.f, 0.f);
-            int64_t j = 0;
-            if (p < cnt) {
-                j = (int64_t)start + p;
-                qa.x = ld_val(c.x.p[0], c.x.fmt, j) + sx;
-                qa.y = ld_val(c.x.p[1], c.x.fmt, j) + sy;
-                qa.z = ld_val(c.x.p[2], c.x.fmt, j) + sz;
-                qa.w = ld_val(c.h.p[0], c.h.fmt, j);
-                const float rr = hw + qa.w;
-                keep = box_dist2(box, qa.x, qa.y, qa.z) < rr * rr;
+    int ecur = cur.e;
+    for (int g0 = cur.g; g0 < total; g0 += 32 * kStageUnroll) {
+        float4 qa[kStageUnroll], qb[kStageUnroll], qc[kStageUnroll];
+        int64_t jj[kStageUnroll];
+        int eu[kStageUnroll];
+        bool keep[kStageUnroll];
+        int e = ecur;
+#pragma unroll
+        for (int u = 0; u < kStageUnroll; ++u) {
+            const int g = g0 + u * 32 + lane;
+            qa[u] = make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.0f);
+            jj[u] = 0;
+            if (g < total) {
+                e = advance(tab, nent, e, g);
+                const int64_t j = (int64_t)tab.base[e] + g;
+                jj[u] = j;
+                float sx, sy, sz;
+                stencil_shift(c, e >> c.lg_s3, sx, sy, sz);
+                qa[u].x = ld_val(c.x.p[0], c.x.fmt, j) + sx;
+                qa[u].y = ld_val(c.x.p[1], c.x.fmt, j) + sy;
+                qa[u].z = ld_val(c.x.p[2], c.x.fmt, j) + sz;
+                qa[u].w = ld_val(c.h.p[0], c.h.fmt, j);
             }
-            const unsigned b = __ballot_sync(FULL, keep);
-            if (keep) {
-                const int pos = found + __popc(b & lt) - skip;
-                if (pos >= 0 && pos < cap) {
-                    const float rj = ld_val(a.rho.p[0], a.rho.fmt, j);
-                    const float Pj = ld_val(a.P.p[0], a.P.fmt, j);
-                    sA[pos] = qa;
-                    sB[pos] = make_float4(ld_val(a.v.p[0], a.v.fmt, j), ld_val(a.v.p[1], a.v.fmt, j),
-                                          ld_val(a.v.p[2], a.v.fmt, j), ld_val(c.m.p[0], c.m.fmt, j));
-                    sC[pos] = make_float4(Pj / (rj * rj), rj, ld_val(a.cs.p[0], a.cs.fmt, j),
-                                          __int_as_float((int)j));
-                }
-            }
-            found += __popc(b);
+            eu[u] = e;
         }
+#pragma unroll
+        for (int u = 0; u < kStageUnroll; ++u) {
+            if (qa[u].w > a.h_cap) err |= SPH_ERR_HCAP;
+            const float rr = hw + qa[u].w;
+            keep[u] = box_dist2(box, qa[u].x, qa[u].y, qa[u].z) < rr * rr;
+            qb[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            qc[u] = make_float4(0.f, 1.f, 0.f, 0.f);
+            if (keep[u]) {
+                const int64_t j = jj[u];
+                qb[u] = make_float4(ld_val(a.v.p[0], a.v.fmt, j), ld_val(a.v.p[1], a.v.fmt, j),
+                                    ld_val(a.v.p[2], a.v.fmt, j), ld_val(c.m.p[0], c.m.fmt, j));
+                qc[u] = make_float4(ld_val(a.P.p[0], a.P.fmt, j), ld_val(a.rho.p[0], a.rho.fmt, j),
+                                    ld_val(a.cs.p[0], a.cs.fmt, j), __int_as_float((int)j));
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kStageUnroll; ++u) {
+            const unsigned b = __ballot_sync(FULL, keep[u]);
+            const int nb = __popc(b);
+            if (found + nb > cap) {     // stage full: resume at this batch
+                cur.g = g0 + u * 32;
+                cur.e = __shfl_sync(FULL, eu[u], 0);
+                __syncwarp();
+                return found;
+            }
+            if (keep[u]) {
+                const int pos = found + __popc(b & lt);
+                const float rj = qc[u].y;
+                sA[pos] = qa[u];
+                sB[pos] = qb[u];
+                sC[pos] = make_float4(qc[u].x / (rj * rj), rj, qc[u].z, qc[u].w);
+            }
+            found += nb;
+        }
+        ecur = __shfl_sync(FULL, e, 31);
     }
+    cur.g = total;
+    cur.e = ecur;
     __syncwarp();
-    return found - skip;
+    return found;
 }
 
 __global__ void __launch_bounds__(kMaxBlock, 1) k_force(ForceArgs a)
@@ -443,9 +571,12 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_force(ForceArgs a)
     extern __shared__ __align__(16) unsigned char smem[];
     const Common &c = a.c;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float4 *sA = reinterpret_cast<float4 *>(smem) + (size_t)warp * 3 * c.cap;   // x, y, z, h
+    const size_t per_warp = (size_t)c.cap * 3 * sizeof(float4) + (size_t)32 * kLaneCap * sizeof(uint16_t) + sizeof(Tab);
+    float4 *sA = reinterpret_cast<float4 *>(smem + warp * per_warp);         // x, y, z, h
     float4 *sB = sA + c.cap;                                                  // vx, vy, vz, m
     float4 *sC = sB + c.cap;                                                  // P/rho^2, rho, c, slot
+    uint16_t *lst = reinterpret_cast<uint16_t *>(sC + c.cap);                 // per-lane pair lists
+    Tab &tab = *reinterpret_cast<Tab *>(lst + 32 * kLaneCap);
     unsigned long long my_pairs = 0, my_tests = 0;
     unsigned my_err = 0;
     const int nitems = c.st->nitems;
@@ -471,28 +602,47 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_force(ForceArgs a)
             Pr2i = Pi / (rhoi * rhoi);
             ci = ld_val(a.cs.p[0], a.cs.fmt, k);
         }
-        const Stencil st = stencil_lane(c, cell, lane);
         const Box box = warp_box(ok, xi, yi, zi);
         const float hw = warp_max(ok ? hi : 0.0f);
+        const float rc = hw + a.h_cap;
+        const int total = build_stream(c, cell, box, rc * rc, tab, lane);
         const int kself = (int)k;
         float ax = 0.f, ay = 0.f, az = 0.f, du = 0.f;
         int cnt = 0;
-        for (int skip = 0;; skip += c.cap) {
-            const int got = stage_force(a, st, box, hw, sA, sB, sC, c.cap, skip, lane);
-            const int len = min(got, c.cap);
+        if (hi > a.h_cap) my_err |= SPH_ERR_HCAP;
+        Cursor cur{0, 0};
+        do {
+            const int len = stage_force(a, tab, total, box, hw, sA, sB, sC, c.cap, cur, lane, my_err);
             if (ok) {
                 my_tests += (unsigned long long)len;
-                for (int e = 0; e < len; ++e) {
-                    const float4 q = sA[e];
-                    const float dx = xi - q.x, dy = yi - q.y, dz = zi - q.z;
-                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    const float hs = hi + q.w;
-                    if (r2 < hs * hs) {
-                        const float4 qc = sC[e];
+                // phase 1 collects this lane's pairs into its list, phase 2
+                // evaluates them with every lane busy; a full list is drained
+                // and the scan resumes where it stopped
+                int e = 0;
+                for (;;) {
+                    int nl = 0;
+                    for (; e < len; ++e) {
+                        const float4 q = sA[e];
+                        const float dx = xi - q.x, dy = yi - q.y, dz = zi - q.z;
+                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        const float hs = hi + q.w;
+                        if (r2 < hs * hs) {
+                            if (nl == kLaneCap) break;
+                            lst[nl * 32 + lane] = (uint16_t)e;
+                            ++nl;
+                        }
+                    }
+                    for (int l = 0; l < nl; ++l) {
+                        const int p = lst[l * 32 + lane];
+                        const float4 q = sA[p];
+                        const float dx = xi - q.x, dy = yi - q.y, dz = zi - q.z;
+                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        const float hs = hi + q.w;
+                        const float4 qc = sC[p];
                         if (__float_as_int(qc.w) != kself) {
                             ++cnt;
                             if (r2 > 0.0f) {
-                                const float4 qb = sB[e];
+                                const float4 qb = sB[p];
                                 const float rinv = rsqrtf(r2);
                                 const float r = r2 * rinv;
                                 const float hb = 0.5f * hs;
@@ -519,11 +669,11 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_force(ForceArgs a)
                             }
                         }
                     }
+                    if (e >= len) break;   // every staged candidate scanned
                 }
             }
             __syncwarp();
-            if (got <= c.cap) break;
-        }
+        } while (cur.g < total);
         if (ok) {
             if (!isfinite(ax) || !isfinite(ay) || !isfinite(az) || !isfinite(du)) my_err |= SPH_ERR_NONFINITE;
             a.a[0][k] = ax;
@@ -551,6 +701,10 @@ Common make_common(sph_ctx *c, int cap)
         m.nc[k] = c->nc[k];
         m.edge[k] = (float)c->edge[k];
     }
+    m.sub = c->sub;
+    m.s3 = c->sub * c->sub * c->sub;
+    m.lg_sub = c->sub == 2 ? 1 : 0;
+    m.lg_s3 = 3 * m.lg_sub;
     m.cell_start = c->cell_start;
     m.icell = c->item_cell;
     m.ifirst = c->item_first;
@@ -598,12 +752,14 @@ cudaError_t launch_persistent(sph_ctx *c, K kernel, const A &args, size_t smem, 
 
 size_t density_smem_bytes(int block_threads, int cap)
 {
-    return (size_t)(block_threads / 32) * ((size_t)cap * sizeof(float4) + (size_t)32 * kLaneCap * sizeof(uint16_t));
+    return (size_t)(block_threads / 32) *
+           ((size_t)cap * sizeof(float4) + (size_t)32 * kLaneCap * sizeof(uint16_t) + sizeof(Tab));
 }
 
 size_t force_smem_bytes(int block_threads, int cap)
 {
-    return (size_t)(block_threads / 32) * (size_t)cap * 3 * sizeof(float4);
+    return (size_t)(block_threads / 32) *
+           ((size_t)cap * 3 * sizeof(float4) + (size_t)32 * kLaneCap * sizeof(uint16_t) + sizeof(Tab));
 }
 
 cudaError_t run_density(sph_ctx *c, int newton_steps)
@@ -657,6 +813,7 @@ cudaError_t run_force(sph_ctx *c)
     a.alpha = (float)c->params.alpha_av;
     a.beta = (float)c->params.beta_av;
     a.eps = (float)c->params.eps_av;
+    a.h_cap = (float)c->params.h_max;
     for (int k = 0; k < 3; ++k) a.a[k] = (float *)c->soa[SPH_F_A][k];
     a.dudt = (float *)c->soa[SPH_F_DUDT][0];
     a.nngb = c->nngb_force;

@@ -51,10 +51,13 @@ bool fmt_allowed(int f, int fmt)
 
 void default_tuning(sph_tuning *t)
 {
-    t->block_threads = 64;
+    // measured best on the 1M-particle Sod step (GB300): density prefers a
+    // stage that holds a whole neighbourhood, force more resident warps
+    t->block_threads = 128;
     t->ctas_per_sm = 0;
-    t->stage_density = 640;
-    t->stage_force = 320;
+    t->stage_density = 1024;
+    t->stage_force = 128;
+    t->subcells = 2;
 }
 
 }  // namespace
@@ -77,12 +80,13 @@ bool make_plan(const sph_aos_layout &L, int64_t n, int64_t ncell_max, uint32_t w
         p->keys[b] = take(4 * N);
         p->vals[b] = take(4 * N);
     }
-    p->cell_count = take(4 * (size_t)ncell_max);
-    p->cell_start = take(4 * ((size_t)ncell_max + 1));
+    const int64_t nkeys = ncell_max * kMaxSub * kMaxSub * kMaxSub;   // sub-cells
+    p->cell_count = take(4 * (size_t)nkeys);
+    p->cell_start = take(4 * ((size_t)nkeys + 1));
     p->nblk_radix = (n + kRadixTile - 1) / kRadixTile;
     p->ghist = take(4 * (256 * (size_t)p->nblk_radix + 1));  // +1: the scan writes its total
     int64_t scan_len = 256 * p->nblk_radix;
-    if (ncell_max + 1 > scan_len) scan_len = ncell_max + 1;
+    if (nkeys + 1 > scan_len) scan_len = nkeys + 1;
     p->scan_part = take(4 * ((size_t)(scan_len + kScanTile - 1) / kScanTile + 2));
     p->item_max = n / 32 + (n < ncell_max ? n : ncell_max) + 1;
     p->item_cell = take(4 * (size_t)p->item_max);
@@ -203,6 +207,7 @@ sph_status sph_bin_cells(sph_ctx *c, double cell_edge, int32_t reorder_aos)
         c->edge[k] = c->params.box[k] / (double)nc[k];
     }
     c->ncell = ncell;
+    c->sub = c->tuning.subcells;
     c->valid = 0;
     c->binned = false;
     if (run_binning(c, reorder_aos ? 1 : 0) != cudaSuccess) return SPH_ECUDA;
@@ -325,6 +330,10 @@ sph_status sph_set_tuning(sph_ctx *c, const sph_tuning *t)
     if (t->ctas_per_sm > 0) n.ctas_per_sm = t->ctas_per_sm;
     if (t->stage_density > 0) n.stage_density = t->stage_density;
     if (t->stage_force > 0) n.stage_force = t->stage_force;
+    if (t->subcells > 0) {
+        if (t->subcells > kMaxSub) return SPH_EINVAL;
+        n.subcells = t->subcells;
+    }
     if (n.stage_density < 32 || n.stage_force < 32) return SPH_EINVAL;
     if (n.stage_density > 65535 || n.stage_force > 65535) return SPH_EINVAL;
     if (density_smem_bytes(n.block_threads, n.stage_density) > c->smem_optin) return SPH_EINVAL;
@@ -360,6 +369,7 @@ sph_status sph_describe(const sph_ctx *c, sph_desc *out)
         for (int k = 0; k < 3; ++k) out->off_soa[f][k] = k < ncomp(f) ? rel(c->soa[f][k]) : -1;
     }
     out->valid = c->valid;
+    out->subcells = c->sub;
     return SPH_OK;
 }
 

@@ -19,6 +19,7 @@ constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
 constexpr int kScanTile = kScanThreads * kScanItems;      // elements per scan block
 constexpr int kItemTile = 32;                              // i-particles per pair-kernel work item (one warp)
+constexpr int kMaxSub = 2;                                 // sub-cells per cell edge, at most
 constexpr int kMaxBlock = 256;
 constexpr float kSigma = 0.318309886183790671538f;        // 1/pi, 3D M4 normalisation
 
@@ -199,6 +200,7 @@ struct sph_ctx {
     double edge[3] = {0, 0, 0};
     double inv[3] = {0, 0, 0};
     int64_t ncell = 0;
+    int sub = 1;                  // sub-cells per cell edge of the last binning
     bool binned = false;
     sph::LaunchCache lc_density, lc_force;
     int sorted_buf = 0;          // which ping-pong buffer holds the sorted keys/values

@@ -9,13 +9,15 @@ from gpu_util import make_sph
 pytestmark = pytest.mark.gpu
 
 
-def _check(orc, wl, reorder=False):
+def _check(orc, wl, reorder=False, sub=2):
     s = make_sph(wl, ws_flags=1 if reorder else 0)
+    s.set_tuning(subcells=sub)
     x0 = wl.col("x").copy()
     s.bin_cells(wl.cell_edge, reorder)
-    cell_of, perm, start = orc.bin_cells(x0, wl.box, s.nc)
+    cell_of, perm, start = orc.bin_cells(x0, wl.box, s.nc, sub=sub)
     d = s.describe()
     assert list(d.ncell) == list(s.nc)
+    assert d.subcells == sub
     assert np.array_equal(s.cell_start().cpu().numpy(), start.astype(np.int32))
     if reorder:
         # records now in cell order; the permutation is the identity
@@ -26,14 +28,15 @@ def _check(orc, wl, reorder=False):
         assert np.array_equal(s.perm().cpu().numpy(), perm.astype(np.int32))
     assert np.array_equal(s.slot_cell().cpu().numpy(), cell_of[perm].astype(np.int32))
     st = s.stats()
-    assert st["max_occupancy"] == int(np.max(np.diff(start)))
+    assert st["max_occupancy"] == int(np.max(np.diff(start[::sub ** 3])))
     assert st["error_bits"] == 0
     return s
 
 
+@pytest.mark.parametrize("sub", [1, 2])
 @pytest.mark.parametrize("shuffle", [False, True])
-def test_uniform_4096(orc, shuffle):
-    _check(orc, sph_inputs.uniform_density(shuffle=shuffle))
+def test_uniform_4096(orc, shuffle, sub):
+    _check(orc, sph_inputs.uniform_density(shuffle=shuffle), sub=sub)
 
 
 def test_sod_small_and_reorder(orc):

@@ -23,6 +23,27 @@ def test_bin_is_stable_sort_by_cell(orc, n, nc):
     assert np.array_equal(start, np.concatenate([[0], np.cumsum(counts)]))
 
 
+@pytest.mark.parametrize("sub", [2, 4])
+def test_subcell_order_refines_the_cell_order(orc, sub):
+    # sorting by (cell, sub-cell, index): cells stay contiguous, in the same
+    # order as the plain cell list; inside a cell the slots are grouped by
+    # sub-cell, found independently as floor(x * sub * nc / L) mod sub
+    rng = np.random.default_rng(sub)
+    n, nc, box = 20000, np.array([5, 6, 4]), np.array([1.0, 1.3, 0.8])
+    x = rng.uniform(0, 1, (n, 3)) * box
+    key, perm, start = orc.bin_cells(x, box, nc, sub=sub)
+    cell_of, perm1, start1 = orc.bin_cells(x, box, nc)
+    s3 = sub ** 3
+    assert np.array_equal(start[::s3], start1)
+    assert np.array_equal(key // s3, cell_of)
+    f = np.clip(np.floor(x * (sub * nc / box)), 0, sub * nc - 1).astype(np.int64)
+    assert np.array_equal(f // sub, np.clip(np.floor(x * (nc / box)), 0, nc - 1))
+    s = f % sub
+    want = cell_of.astype(np.int64) * s3 + s[:, 0] + sub * (s[:, 1] + sub * s[:, 2])
+    assert np.array_equal(key, want)
+    assert np.array_equal(perm, np.lexsort((np.arange(n), want)))
+
+
 def test_boundary_positions_clamp(orc):
     box = (1.0, 1.0, 1.0)
     top = np.nextafter(1.0, 0.0)

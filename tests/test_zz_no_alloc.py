@@ -16,6 +16,7 @@ pytestmark = pytest.mark.gpu
 def _regular(wl, nc_expect):
     from gpu_util import make_sph
     s = make_sph(wl)
+    s.set_tuning(subcells=1)       # the allocation-free binning uses plain cells
     s.bin_cells(wl.cell_edge)
     assert list(s.nc) == list(nc_expect)
     out = (s.perm().clone(), s.slot_cell().clone(), s.cell_start().clone())
