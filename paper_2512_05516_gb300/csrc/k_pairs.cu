@@ -74,6 +74,7 @@ struct DensityArgs {
 struct ForceArgs {
     Common c;
     FieldRef v, rho, P, cs;
+    const float *key_hmax;           // largest h of every sub-cell
     float alpha, beta, eps, h_cap;
     float *a[3];
     float *dudt;
@@ -145,11 +146,13 @@ __device__ __forceinline__ void stencil_shift(const Common &c, int t, float &sx,
     sz = (float)(t / 9 - 1) * c.edge[2];
 }
 
-// List the stencil sub-cells of `cell` whose box comes within sqrt(R2) of the
+// List the stencil sub-cells of `cell` whose box comes within reach of the
 // warp box (every particle of a sub-cell sits inside its box: positions are
-// cell-relative offsets, widened here by a rounding margin).  Returns the
-// number of candidates in the stream (warp-uniform).
-__device__ int build_stream(const Common &c, int cell, const Box &box, float R2, Tab &tab, int lane)
+// cell-relative offsets, widened here by a rounding margin).  The reach is
+// sqrt(R2), or, with `key_hmax`, hw + the largest h of the sub-cell.  Returns
+// the number of candidates in the stream (warp-uniform).
+__device__ int build_stream(const Common &c, int cell, const Box &box, float R2, Tab &tab, int lane,
+                            const float *key_hmax = nullptr, float hw = 0.0f)
 {
     const int nent = 27 * c.s3;
     const int E = (nent + 31) / 32;            // entries per lane, lane-blocked
@@ -188,7 +191,12 @@ __device__ int build_stream(const Common &c, int cell, const Box &box, float R2,
                     const float g = fmaxf(0.0f, fmaxf(lo - box.hi[a], box.lo[a] - hi));
                     d2 = fmaf(g, g, d2);
                 }
-                if (d2 < R2) cnt[i] = n0;
+                float reach2 = R2;
+                if (key_hmax) {
+                    const float rr = hw + key_hmax[key];
+                    reach2 = rr * rr;
+                }
+                if (d2 < reach2) cnt[i] = n0;
             }
         }
         local += cnt[i];
@@ -484,13 +492,29 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
 // Force
 // ---------------------------------------------------------------------------
 
+// Largest h of every sub-cell: slots are sorted by key, so the lanes of a
+// warp share few keys; each key group reduces in the warp and its leader
+// does one atomic max (h > 0, so the float order is the unsigned order).
+__global__ void __launch_bounds__(256) k_key_hmax(FieldRef h, const int32_t *slot_key, int64_t n, float h_cap,
+                                                  float *key_hmax)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool ok = k < n;
+    const int key = ok ? slot_key[k] : -1;
+    float hv = ok ? ld_val(h.p[0], h.fmt, k) : 0.0f;
+    if (ok && !(hv > 0.0f && hv <= 3.0e38f)) hv = h_cap;       // NaN / non-positive: assume h_max
+    const unsigned peers = __match_any_sync(FULL, key);
+    const unsigned mx = __reduce_max_sync(peers, __float_as_uint(hv));
+    if (ok && (threadIdx.x & 31) == __ffs(peers) - 1)
+        atomicMax(reinterpret_cast<unsigned *>(key_hmax) + key, mx);
+}
+
 // Stage the force candidates (those within h_max(warp) + h_j of the warp box)
 // from `cur` on, until the stage is full or the stream ends; returns how many
 // were staged and moves `cur` (as stage_density).  The loads a kept
 // candidate needs beyond x and h are issued for all batches in flight before
-// anything is stored.  The stream's sub-cells were chosen with h_j <= h_max
-// (the 27-cell grid covers pairs up to 2 h_max only); a candidate with a
-// larger h sets the h-cap error bit.
+// anything is stored.  The 27-cell grid covers pairs up to 2 h_max only; a
+// candidate with a larger h sets the h-cap error bit.
 __device__ int stage_force(const ForceArgs &a, const Tab &tab, int total, const Box &box, float hw,
                            float4 *sA, float4 *sB, float4 *sC, int cap, Cursor &cur, int lane,
                            unsigned &err)
@@ -604,8 +628,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_force(ForceArgs a)
         }
         const Box box = warp_box(ok, xi, yi, zi);
         const float hw = warp_max(ok ? hi : 0.0f);
-        const float rc = hw + a.h_cap;
-        const int total = build_stream(c, cell, box, rc * rc, tab, lane);
+        const int total = build_stream(c, cell, box, 0.0f, tab, lane, a.key_hmax, hw);
         const int kself = (int)k;
         float ax = 0.f, ay = 0.f, az = 0.f, du = 0.f;
         int cnt = 0;
@@ -817,6 +840,15 @@ cudaError_t run_force(sph_ctx *c)
     for (int k = 0; k < 3; ++k) a.a[k] = (float *)c->soa[SPH_F_A][k];
     a.dudt = (float *)c->soa[SPH_F_DUDT][0];
     a.nngb = c->nngb_force;
+    // the reach of every sub-cell, from the h the force will read
+    cudaError_t e;
+    const int64_t nkeys = c->ncell * c->sub * c->sub * c->sub;
+    if ((e = cudaMemsetAsync(c->key_hmax, 0, sizeof(float) * nkeys, c->stream)) != cudaSuccess) return e;
+    k_key_hmax<<<(unsigned)((c->n + 255) / 256), 256, 0, c->stream>>>(a.c.h, c->slot_cell(), c->n, a.h_cap,
+                                                                     c->key_hmax);
+    c->launches += 1;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    a.key_hmax = c->key_hmax;
     return launch_persistent(c, k_force, a, force_smem_bytes(c->tuning.block_threads, a.c.cap), c->lc_force);
 }
 

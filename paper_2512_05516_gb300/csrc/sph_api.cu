@@ -96,6 +96,7 @@ bool make_plan(const sph_aos_layout &L, int64_t n, int64_t ncell_max, uint32_t w
     p->nngb = take(4 * N);
     p->nngb_force = take(4 * N);
     p->stage = take(4 * N);
+    p->key_hmax = take(4 * (size_t)nkeys);
     p->aos_tmp = (ws_flags & SPH_WS_REORDER) ? take((size_t)L.record_bytes * N) : 0;
     p->stats = take(sizeof(DevStats));
     for (int f = 0; f < SPH_NFIELDS; ++f)
@@ -171,6 +172,7 @@ sph_status sph_create(const sph_aos_layout *layout, const sph_params *params, in
     c->nngb = (int32_t *)(w + plan.nngb);
     c->nngb_force = (int32_t *)(w + plan.nngb_force);
     c->stage = (float *)(w + plan.stage);
+    c->key_hmax = (float *)(w + plan.key_hmax);
     c->aos_tmp = (ws_flags & SPH_WS_REORDER) ? w + plan.aos_tmp : nullptr;
     c->dstats = (DevStats *)(w + plan.stats);
     for (int f = 0; f < SPH_NFIELDS; ++f) {

@@ -44,7 +44,7 @@ struct Plan {
     size_t keys[2], vals[2];
     size_t cell_count, cell_start, scan_part, ghist;
     size_t item_cell, item_first, item_count, item_tmp;
-    size_t nngb, nngb_force, stage, aos_tmp, stats;
+    size_t nngb, nngb_force, stage, aos_tmp, stats, key_hmax;
     size_t soa[SPH_NFIELDS][3];
     size_t total;
     int64_t item_max, nblk_radix;
@@ -213,6 +213,7 @@ struct sph_ctx {
     int32_t *item_cell = nullptr, *item_first = nullptr, *item_count = nullptr, *item_tmp = nullptr;
     int32_t *nngb = nullptr, *nngb_force = nullptr;
     float *stage = nullptr;
+    float *key_hmax = nullptr;    // largest h of every sub-cell (force pruning)
     uint8_t *aos_tmp = nullptr;
     sph::DevStats *dstats = nullptr;
     void *soa[SPH_NFIELDS][3] = {};
