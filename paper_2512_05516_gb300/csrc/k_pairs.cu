@@ -283,11 +283,22 @@ struct Cursor {
     int g, e;
 };
 
+// Staging load: F32 kernels (every field they read stored as FP32) use plain
+// loads, which keeps the unrolled staging loops small; the others decode
+// whatever storage format the field has.
+template <bool F32>
+__device__ __forceinline__ float ldv(const void *p, int fmt, int64_t k)
+{
+    if (F32) return __ldg((const float *)p + k);
+    return ld_val(p, fmt, k);
+}
+
 // Stage the stream's candidates within distance sqrt(R2) of the warp box, in
 // stream order, starting at `cur`, until the stage is full or the stream ends.
 // Returns how many were staged (<= cap) and moves `cur` to the first batch
 // not staged (cur.g == total when the stream is exhausted).  A chunk always
 // stages at least one batch, since a batch holds at most 32 <= cap.
+template <bool F32>
 __device__ int stage_density(const Common &c, const Tab &tab, int total, const Box &box, float R2,
                              float4 *sj, int cap, Cursor &cur, int lane)
 {
@@ -308,10 +319,10 @@ __device__ int stage_density(const Common &c, const Tab &tab, int total, const B
                 const int64_t j = (int64_t)tab.base[e] + g;
                 float sx, sy, sz;
                 stencil_shift(c, e >> c.lg_s3, sx, sy, sz);
-                q[u].x = ld_val(c.x.p[0], c.x.fmt, j) + sx;
-                q[u].y = ld_val(c.x.p[1], c.x.fmt, j) + sy;
-                q[u].z = ld_val(c.x.p[2], c.x.fmt, j) + sz;
-                q[u].w = ld_val(c.m.p[0], c.m.fmt, j);
+                q[u].x = ldv<F32>(c.x.p[0], c.x.fmt, j) + sx;
+                q[u].y = ldv<F32>(c.x.p[1], c.x.fmt, j) + sy;
+                q[u].z = ldv<F32>(c.x.p[2], c.x.fmt, j) + sz;
+                q[u].w = ldv<F32>(c.m.p[0], c.m.fmt, j);
             }
             eu[u] = e;
         }
@@ -337,6 +348,7 @@ __device__ int stage_density(const Common &c, const Tab &tab, int total, const B
     return found;
 }
 
+template <bool F32>
 __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -376,7 +388,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
         float R2s = 4.0f * h_stage * h_stage;
         int total = build_stream(c, cell, box, R2s, tab, lane);
         Cursor cur{0, 0};
-        int T = stage_density(c, tab, total, box, R2s, sj, c.cap, cur, lane);
+        int T = stage_density<F32>(c, tab, total, box, R2s, sj, c.cap, cur, lane);
         bool fits = cur.g >= total;
         float h_list = 0.0f;       // this lane's list holds every staged candidate within 2 h_list
         int nlist = 0;
@@ -394,7 +406,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
                 R2s = 4.0f * h_stage * h_stage;
                 total = build_stream(c, cell, box, R2s, tab, lane);
                 Cursor rc{0, 0};
-                T = stage_density(c, tab, total, box, R2s, sj, c.cap, rc, lane);
+                T = stage_density<F32>(c, tab, total, box, R2s, sj, c.cap, rc, lane);
                 fits = rc.g >= total;
                 h_list = 0.0f;
             }
@@ -436,7 +448,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
                 const int tot = build_stream(c, cell, box, R2, tab, lane);
                 Cursor sc{0, 0};
                 do {
-                    const int len = stage_density(c, tab, tot, box, R2, sj, c.cap, sc, lane);
+                    const int len = stage_density<F32>(c, tab, tot, box, R2, sj, c.cap, sc, lane);
                     if (ok) {
                         my_tests += (unsigned long long)len;
                         for (int e = 0; e < len; ++e) dens_pair(acc, xi, yi, zi, h2x4, hinv, a.plain_sum, deriv, sj[e]);
@@ -515,6 +527,7 @@ __global__ void __launch_bounds__(256) k_key_hmax(FieldRef h, const int32_t *slo
 // candidate needs beyond x and h are issued for all batches in flight before
 // anything is stored.  The 27-cell grid covers pairs up to 2 h_max only; a
 // candidate with a larger h sets the h-cap error bit.
+template <bool F32>
 __device__ int stage_force(const ForceArgs &a, const Tab &tab, int total, const Box &box, float hw,
                            float4 *sA, float4 *sB, float4 *sC, int cap, Cursor &cur, int lane,
                            unsigned &err)
@@ -541,10 +554,10 @@ __device__ int stage_force(const ForceArgs &a, const Tab &tab, int total, const 
                 jj[u] = j;
                 float sx, sy, sz;
                 stencil_shift(c, e >> c.lg_s3, sx, sy, sz);
-                qa[u].x = ld_val(c.x.p[0], c.x.fmt, j) + sx;
-                qa[u].y = ld_val(c.x.p[1], c.x.fmt, j) + sy;
-                qa[u].z = ld_val(c.x.p[2], c.x.fmt, j) + sz;
-                qa[u].w = ld_val(c.h.p[0], c.h.fmt, j);
+                qa[u].x = ldv<F32>(c.x.p[0], c.x.fmt, j) + sx;
+                qa[u].y = ldv<F32>(c.x.p[1], c.x.fmt, j) + sy;
+                qa[u].z = ldv<F32>(c.x.p[2], c.x.fmt, j) + sz;
+                qa[u].w = ldv<F32>(c.h.p[0], c.h.fmt, j);
             }
             eu[u] = e;
         }
@@ -557,10 +570,10 @@ __device__ int stage_force(const ForceArgs &a, const Tab &tab, int total, const 
             qc[u] = make_float4(0.f, 1.f, 0.f, 0.f);
             if (keep[u]) {
                 const int64_t j = jj[u];
-                qb[u] = make_float4(ld_val(a.v.p[0], a.v.fmt, j), ld_val(a.v.p[1], a.v.fmt, j),
-                                    ld_val(a.v.p[2], a.v.fmt, j), ld_val(c.m.p[0], c.m.fmt, j));
-                qc[u] = make_float4(ld_val(a.P.p[0], a.P.fmt, j), ld_val(a.rho.p[0], a.rho.fmt, j),
-                                    ld_val(a.cs.p[0], a.cs.fmt, j), __int_as_float((int)j));
+                qb[u] = make_float4(ldv<F32>(a.v.p[0], a.v.fmt, j), ldv<F32>(a.v.p[1], a.v.fmt, j),
+                                    ldv<F32>(a.v.p[2], a.v.fmt, j), ldv<F32>(c.m.p[0], c.m.fmt, j));
+                qc[u] = make_float4(ldv<F32>(a.P.p[0], a.P.fmt, j), ldv<F32>(a.rho.p[0], a.rho.fmt, j),
+                                    ldv<F32>(a.cs.p[0], a.cs.fmt, j), __int_as_float((int)j));
             }
         }
 #pragma unroll
@@ -590,6 +603,7 @@ __device__ int stage_force(const ForceArgs &a, const Tab &tab, int total, const 
     return found;
 }
 
+template <bool F32>
 __global__ void __launch_bounds__(kMaxBlock, 1) k_force(ForceArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -635,7 +649,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_force(ForceArgs a)
         if (hi > a.h_cap) my_err |= SPH_ERR_HCAP;
         Cursor cur{0, 0};
         do {
-            const int len = stage_force(a, tab, total, box, hw, sA, sB, sC, c.cap, cur, lane, my_err);
+            const int len = stage_force<F32>(a, tab, total, box, hw, sA, sB, sC, c.cap, cur, lane, my_err);
             if (ok) {
                 my_tests += (unsigned long long)len;
                 // phase 1 collects this lane's pairs into its list, phase 2
@@ -811,8 +825,10 @@ cudaError_t run_density(sph_ctx *c, int newton_steps)
     a.cs_out = c->soa[SPH_F_CS][0];
     a.cs_fmt = c->prec[SPH_F_CS];
     a.nngb = c->nngb;
-    cudaError_t e = launch_persistent(c, k_density, a, density_smem_bytes(c->tuning.block_threads, a.c.cap),
-                                      c->lc_density);
+    const size_t smem = density_smem_bytes(c->tuning.block_threads, a.c.cap);
+    const bool f32 = a.c.x.fmt == SPH_P_FP32 && a.c.m.fmt == SPH_P_FP32;   // what staging loads
+    cudaError_t e = f32 ? launch_persistent(c, k_density<true>, a, smem, c->lc_density[1])
+                        : launch_persistent(c, k_density<false>, a, smem, c->lc_density[0]);
     if (e != cudaSuccess) return e;
     if (a.write_h && h_packed) return run_pack(c, c->stage, SPH_F_H);
     return cudaSuccess;
@@ -849,7 +865,12 @@ cudaError_t run_force(sph_ctx *c)
     c->launches += 1;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     a.key_hmax = c->key_hmax;
-    return launch_persistent(c, k_force, a, force_smem_bytes(c->tuning.block_threads, a.c.cap), c->lc_force);
+    const size_t smem = force_smem_bytes(c->tuning.block_threads, a.c.cap);
+    const bool f32 = a.c.x.fmt == SPH_P_FP32 && a.c.h.fmt == SPH_P_FP32 && a.c.m.fmt == SPH_P_FP32 &&
+                     a.v.fmt == SPH_P_FP32 && a.rho.fmt == SPH_P_FP32 && a.P.fmt == SPH_P_FP32 &&
+                     a.cs.fmt == SPH_P_FP32;
+    return f32 ? launch_persistent(c, k_force<true>, a, smem, c->lc_force[1])
+               : launch_persistent(c, k_force<false>, a, smem, c->lc_force[0]);
 }
 
 }  // namespace sph

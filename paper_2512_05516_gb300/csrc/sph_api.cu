@@ -53,7 +53,7 @@ void default_tuning(sph_tuning *t)
 {
     // measured best on the 1M-particle Sod step (GB300): density prefers a
     // stage that holds a whole neighbourhood, force more resident warps
-    t->block_threads = 128;
+    t->block_threads = 32;
     t->ctas_per_sm = 0;
     t->stage_density = 1024;
     t->stage_force = 128;

@@ -202,7 +202,7 @@ struct sph_ctx {
     int64_t ncell = 0;
     int sub = 1;                  // sub-cells per cell edge of the last binning
     bool binned = false;
-    sph::LaunchCache lc_density, lc_force;
+    sph::LaunchCache lc_density[2], lc_force[2];   // [generic formats, all FP32]
     int sorted_buf = 0;          // which ping-pong buffer holds the sorted keys/values
 
     // workspace arrays
