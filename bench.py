@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--prec", default="fp32", help="SoA storage of v, m, h, u (fp32|bf16|fp16|m16|m10)")
+    ap.add_argument("--no-long-run", action="store_true", help="skip the 33.5M-particle memory-bound rows")
     return ap.parse_args()
 
 
@@ -272,6 +273,91 @@ def run_ours(args, rank, world):
             "roofline": roofline, "kernels": kernels, "launches": launches, "n": n}
 
 
+# ----------------------------------------------------------------- long run (HBM-bound rows)
+def algorithmic_bytes(prec_bytes: int, pos_bytes: int):
+    """Minimum bytes per particle of the memory-bound calls (112-byte FP64
+    record; v, m, h, u stored in `prec_bytes`, positions in `pos_bytes`;
+    a and du/dt FP32; 4-byte permutation and key per slot)."""
+    conv = (72 + 8) + 3 * pos_bytes + 3 * prec_bytes + 3 * prec_bytes
+    kick = (24 + 3 * prec_bytes + 12 + prec_bytes + 4 + 4) + (24 + 3 * prec_bytes + prec_bytes)
+    back = (3 * prec_bytes + 12 + prec_bytes + 4 + prec_bytes + 4 + 4) + 80
+    return {"aos_to_soa": conv, "kick_drift": kick, "soa_to_aos": back}
+
+
+def run_long_run(steps: int = 3, graph_steps: int = 10):
+    """Memory-bound rows on the 33,554,432-particle long-run lattice (box
+    2x1x1, FP64 AoS master, FP16 storage of x, v, m, h, u): per-call CUDA-event
+    times of the conversion, kick/drift and write-back kernels against the
+    HBM peak, and whole steps replayed from a CUDA graph."""
+    import torch
+    import paper_2512_05516_gb300 as sph
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    wl = sph_inputs.long_run()
+    n = wl.n
+    stream = torch.cuda.Stream(dev)
+    aos = torch.from_numpy(wl.aos).to(dev)
+    del wl.aos
+    nc = [int(math.floor(b / max(wl.cell_edge, 2 * wl.h_cap))) for b in wl.box]
+    params = sph.make_params(wl.box, gamma=wl.gamma, alpha=wl.alpha_av, beta=wl.beta_av,
+                             eps=wl.eps_av, eta=wl.eta, h_max=wl.h_cap)
+    s = sph.Sph(aos, sph.layout_112(), params, int(np.prod(nc)), sph.WS_REORDER, stream=stream)
+    prec = {"x": "fp16", "v": "fp16", "m": "fp16", "h": "fp16", "u": "fp16"}
+    names = ["bin", "aos_to_soa", "density", "force", "kick_drift", "soa_to_aos"]
+    calls = [lambda: s.bin_cells(wl.cell_edge), lambda: s.aos_to_soa(sph.FIELDS_FORCE, prec),
+             lambda: s.density(0), lambda: s.force(), lambda: s.kick_drift(wl.dt, wl.dt),
+             lambda: s.soa_to_aos(sph.FIELDS_OUTPUT)]
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in names]
+          for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        # warm-up step; its binning also sorts the AoS records into cell order
+        # once, so later steps see an almost sequential permutation
+        s.bin_cells(wl.cell_edge, reorder=True)
+        for fn in calls[1:]:
+            fn()
+        for k in range(steps):
+            for i, fn in enumerate(calls):
+                ev[k][i][0].record(stream)
+                fn()
+                ev[k][i][1].record(stream)
+        stream.synchronize()
+        ms = {nm: statistics.mean(ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(steps))
+              for i, nm in enumerate(names)}
+        # whole steps as one CUDA graph
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            for _ in range(graph_steps):
+                for fn in calls:
+                    fn()
+        s.reset_stats()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.replay()
+        e1.record(stream)
+        e1.synchronize()
+        graph_ms = e0.elapsed_time(e1) / graph_steps
+    st = s.stats()
+    if st["error_bits"] & (sph.ERR_NONFINITE | sph.ERR_OUTSIDE):
+        raise RuntimeError(f"long run: device error bits {st['error_bits']}")
+    hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6753.1
+    bpp = algorithmic_bytes(2, 2)
+    kern = {}
+    for nm in names:
+        row = {"ms": ms[nm]}
+        if nm in bpp:
+            gbs = bpp[nm] * n / (ms[nm] / 1e3) / 1e9
+            row.update({"algorithmic_bytes_per_particle": bpp[nm], "GB_s": gbs,
+                        "frac_of_measured_hbm": gbs / hbm})
+        kern[nm] = row
+    pairs = (st["pairs_density"] + st["pairs_force"]) / graph_steps
+    s.close()
+    del aos
+    torch.cuda.empty_cache()
+    return {"workload": "long_run_33554432", "particles": n, "storage": "fp16 (x, v, m, h, u)",
+            "ms_per_step_graph": graph_ms, "pairs_per_s": pairs / (graph_ms / 1e3),
+            "kernels": kern, "hbm_peak_gbs": hbm}
+
+
 # ----------------------------------------------------------------- oracle
 def run_oracle_sample(n_targets: int, seed: int = 1):
     """The FP64 oracle (as it stands) on a sample of the same workload: the
@@ -372,6 +458,7 @@ def main():
             dist.destroy_process_group()
         return
     cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline()
+    long = None if args.no_long_run or world > 1 else run_long_run()
     out = {
         "metric": METRIC, "value": pairs / total_s, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
@@ -383,6 +470,7 @@ def main():
                    "l2": "flushed between steps (512 MiB write)"},
         "roofline": r["roofline"], "cpu_baseline": cpu, "e2e": r["e2e"],
         "gpu_launches": r["launches"], "clocks": r["clocks"], "kernels": r["kernels"],
+        "memory_bound_rows": long,
     }
     print(json.dumps(out))
     if world > 1:

@@ -96,8 +96,9 @@ enum { SPH_AOS_F64 = 0, SPH_AOS_F32 = 1 };
  * offset[f] is the byte offset of field f inside a record (-1: absent); a
  * vector field stores its 3 components contiguously.  type[f] is SPH_AOS_F64
  * or SPH_AOS_F32.  Positions must be present and FP64 (absolute positions are
- * drifted in FP64).  record_bytes and every offset must be multiples of the
- * field's element size; the AoS base pointer must be 16-byte aligned. */
+ * drifted in FP64).  record_bytes must be a multiple of 8 and at most 512;
+ * every offset a multiple of the field's element size; the AoS base pointer
+ * 16-byte aligned. */
 typedef struct {
     int32_t record_bytes;
     int32_t offset[SPH_NFIELDS];

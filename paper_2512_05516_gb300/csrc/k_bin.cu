@@ -22,12 +22,22 @@ struct CellArgs {
     DevStats *st;
 };
 
+// floor(x * inv) clamped to [0, nc-1]: one FP64 multiply (the product must
+// round exactly as the definition says) and one round-down conversion, which
+// maps NaN to INT_MIN and overflows to INT_MAX, so the integer clamp gives
+// 0 for NaN and negatives and nc-1 above the grid.
 __device__ __forceinline__ int32_t cell_coord(double x, double inv, int32_t nc)
 {
-    double f = floor(__dmul_rn(x, inv));
-    if (!(f >= 0.0)) return 0;
-    if (f > (double)(nc - 1)) return nc - 1;
-    return (int32_t)f;
+    const int f = __double2int_rd(__dmul_rn(x, inv));
+    return min(max(f, 0), nc - 1);
+}
+
+// x in [0, L) compared on bit patterns (FP64 compares are slow on this GPU):
+// non-negative doubles order like their bits; -0 counts as inside
+__device__ __forceinline__ bool in_box(double x, double L)
+{
+    const long long b = __double_as_longlong(x);
+    return (b >= 0 && b < __double_as_longlong(L)) || b == (long long)0x8000000000000000ull;
 }
 
 __global__ void k_cell_ids(CellArgs a)
@@ -36,8 +46,7 @@ __global__ void k_cell_ids(CellArgs a)
     if (i >= a.n) return;
     const double *x = (const double *)(a.aos + i * a.stride + a.xoff);
     double x0 = x[0], x1 = x[1], x2 = x[2];
-    bool outside = !(x0 >= 0.0 && x0 < a.box[0] && x1 >= 0.0 && x1 < a.box[1] &&
-                     x2 >= 0.0 && x2 < a.box[2]);
+    const bool outside = !(in_box(x0, a.box[0]) && in_box(x1, a.box[1]) && in_box(x2, a.box[2]));
     if (outside) set_error(a.st, SPH_ERR_OUTSIDE | ((isfinite(x0) && isfinite(x1) && isfinite(x2)) ? 0u : SPH_ERR_NONFINITE));
     // fine coordinates on the grid of sub-cells (inv = sub * nc / L); the cell
     // is f / sub, the sub-cell f % sub

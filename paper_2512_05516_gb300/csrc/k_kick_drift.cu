@@ -2,16 +2,22 @@
 //   v += a dt_kick, u += du/dt dt_kick       FP32, in the SoA (storage format
 //                                            of v and u applied on the store)
 //   x += v dt_drift, wrapped into [0, L)      FP64, in place in the AoS record
-// One thread per sorted slot; warps stay whole for packed v/u stores.
+// One thread per sorted slot; warps stay whole for packed v/u stores.  The
+// three FP64 position words of the warp's 32 records are loaded and stored
+// lane-contiguously through shared memory.
 #include "sph_internal.cuh"
 
 namespace sph {
 namespace {
 
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int kKDThreads = 256;
+
 struct KDArgs {
     uint8_t *aos;
     int64_t n;
-    int32_t stride, xoff;
+    int32_t W;                   // record words
+    int32_t xw;                  // first position word in the record
     const int32_t *perm;
     double box[3];
     float dtk;
@@ -25,26 +31,63 @@ struct KDArgs {
     DevStats *st;
 };
 
-__global__ void __launch_bounds__(256) k_kick_drift(KDArgs a)
+__global__ void __launch_bounds__(kKDThreads) k_kick_drift(KDArgs a)
 {
+    __shared__ double sx[kKDThreads / 32][32 * 3 + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double *xs = sx[warp];
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool ok = k < a.n;
+    const int64_t o = ok ? a.perm[k] : -1;
+    // kick first: its loads do not wait for the permutation
     float vn[3] = {0.f, 0.f, 0.f};
     float un = 0.f;
     if (ok) {
         for (int c = 0; c < 3; ++c) vn[c] = fmaf(a.a[c][k], a.dtk, ld_val(a.v[c], a.vfmt, k));
         un = fmaf(a.dudt[k], a.dtk, ld_val(a.u, a.ufmt, k));
-        const int64_t o = a.perm[k];
-        double *x = (double *)(a.aos + o * a.stride + a.xoff);
+    }
+    double *aos64 = (double *)a.aos;
+    // lane l moves word l % 3 of record l / 3 (then +32, +64)
+    double xw[3];
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+        const int idx = lane + 32 * t;
+        const int r = idx / 3, w = idx - 3 * r;
+        const int64_t orr = __shfl_sync(FULL, o, r);
+        xw[t] = orr >= 0 ? aos64[orr * a.W + a.xw + w] : 0.0;
+    }
+#pragma unroll
+    for (int t = 0; t < 3; ++t) xs[lane + 32 * t] = xw[t];
+    __syncwarp();
+    if (ok) {
         bool bad = false;
         for (int c = 0; c < 3; ++c) {
-            double y = __dadd_rn(x[c], __dmul_rn((double)vn[c], a.dtd));
-            y = __dsub_rn(y, __dmul_rn(a.box[c], floor(y / a.box[c])));
-            if (y >= a.box[c]) y = 0.0;
-            bad |= !isfinite(y);
-            x[c] = y;
+            // x += v dt in FP64 (one FMA, the FP64 arithmetic the step
+            // needs); a position already in [0, L) -- tested on the bit
+            // patterns, since non-negative doubles order like their bits --
+            // needs no wrap; the few that left the box take the periodic
+            // wrap x - L floor(x / L)
+            double y = fma(f2d_bits(vn[c]), a.dtd, xs[3 * lane + c]);
+            const long long yb = __double_as_longlong(y);
+            if (yb < 0 || yb >= __double_as_longlong(a.box[c])) {
+                if ((yb & 0x7FF0000000000000ll) == 0x7FF0000000000000ll) {
+                    bad = true;                        // inf or nan
+                } else {
+                    y = __dsub_rn(y, __dmul_rn(a.box[c], floor(y / a.box[c])));
+                    if (y >= a.box[c]) y = 0.0;        // rounding onto L
+                }
+            }
+            xs[3 * lane + c] = y;
         }
         if (bad || !isfinite(un)) set_error(a.st, SPH_ERR_NONFINITE);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+        const int idx = lane + 32 * t;
+        const int r = idx / 3, w = idx - 3 * r;
+        const int64_t orr = __shfl_sync(FULL, o, r);
+        if (orr >= 0) aos64[orr * a.W + a.xw + w] = xs[idx];
     }
     for (int c = 0; c < 3; ++c) st_any(a.v[c], a.vfmt, k, vn[c], ok, a.n);
     st_any(a.u, a.ufmt, k, un, ok, a.n);
@@ -58,8 +101,8 @@ cudaError_t run_kick_drift(sph_ctx *c, double dt_kick, double dt_drift)
     KDArgs a;
     a.aos = c->aos;
     a.n = c->n;
-    a.stride = c->layout.record_bytes;
-    a.xoff = c->layout.offset[SPH_F_X];
+    a.W = c->layout.record_bytes / 8;
+    a.xw = c->layout.offset[SPH_F_X] / 8;
     a.perm = c->perm();
     for (int k = 0; k < 3; ++k) {
         a.box[k] = c->params.box[k];
@@ -73,7 +116,7 @@ cudaError_t run_kick_drift(sph_ctx *c, double dt_kick, double dt_drift)
     a.ufmt = c->prec[SPH_F_U];
     a.dudt = (const float *)c->soa[SPH_F_DUDT][0];
     a.st = c->dstats;
-    k_kick_drift<<<(unsigned)((c->n + 255) / 256), 256, 0, c->stream>>>(a);
+    k_kick_drift<<<(unsigned)((c->n + kKDThreads - 1) / kKDThreads), kKDThreads, 0, c->stream>>>(a);
     c->launches += 1;
     return cudaGetLastError();
 }

@@ -283,22 +283,32 @@ struct Cursor {
     int g, e;
 };
 
-// Staging load: F32 kernels (every field they read stored as FP32) use plain
-// loads, which keeps the unrolled staging loops small; the others decode
-// whatever storage format the field has.
-template <bool F32>
-__device__ __forceinline__ float ldv(const void *p, int fmt, int64_t k)
+// Staging loads.  The pair kernels are compiled for fixed storage formats of
+// the positions (FX) and of the particle fields (FV: v, m, h); those decode
+// with one load each, which keeps the unrolled staging loops small (the
+// kernels are instruction-cache bound otherwise).  kAnyFmt decodes whatever
+// format the field has at run time (mixed or packed formats).
+constexpr int kAnyFmt = -1;
+
+template <int F>
+__device__ __forceinline__ float ldf(const void *p, int fmt, int64_t k)
 {
-    if (F32) return __ldg((const float *)p + k);
-    return ld_val(p, fmt, k);
+    if constexpr (F == SPH_P_FP32) return __ldg((const float *)p + k);
+    else if constexpr (F == SPH_P_FP16) return __half2float(__ushort_as_half(__ldg((const unsigned short *)p + k)));
+    else if constexpr (F == SPH_P_BF16) return dec_bf16(__ldg((const unsigned short *)p + k));
+    else return ld_val(p, fmt, k);
 }
+
+// derived fields (rho, P, c) are FP32 in the fixed-format kernels
+template <int FX>
+__host__ __device__ constexpr int derived_fmt() { return FX == kAnyFmt ? kAnyFmt : (int)SPH_P_FP32; }
 
 // Stage the stream's candidates within distance sqrt(R2) of the warp box, in
 // stream order, starting at `cur`, until the stage is full or the stream ends.
 // Returns how many were staged (<= cap) and moves `cur` to the first batch
 // not staged (cur.g == total when the stream is exhausted).  A chunk always
 // stages at least one batch, since a batch holds at most 32 <= cap.
-template <bool F32>
+template <int FX, int FV>
 __device__ int stage_density(const Common &c, const Tab &tab, int total, const Box &box, float R2,
                              float4 *sj, int cap, Cursor &cur, int lane)
 {
@@ -319,10 +329,10 @@ __device__ int stage_density(const Common &c, const Tab &tab, int total, const B
                 const int64_t j = (int64_t)tab.base[e] + g;
                 float sx, sy, sz;
                 stencil_shift(c, e >> c.lg_s3, sx, sy, sz);
-                q[u].x = ldv<F32>(c.x.p[0], c.x.fmt, j) + sx;
-                q[u].y = ldv<F32>(c.x.p[1], c.x.fmt, j) + sy;
-                q[u].z = ldv<F32>(c.x.p[2], c.x.fmt, j) + sz;
-                q[u].w = ldv<F32>(c.m.p[0], c.m.fmt, j);
+                q[u].x = ldf<FX>(c.x.p[0], c.x.fmt, j) + sx;
+                q[u].y = ldf<FX>(c.x.p[1], c.x.fmt, j) + sy;
+                q[u].z = ldf<FX>(c.x.p[2], c.x.fmt, j) + sz;
+                q[u].w = ldf<FV>(c.m.p[0], c.m.fmt, j);
             }
             eu[u] = e;
         }
@@ -348,7 +358,7 @@ __device__ int stage_density(const Common &c, const Tab &tab, int total, const B
     return found;
 }
 
-template <bool F32>
+template <int FX, int FV>
 __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -388,7 +398,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
         float R2s = 4.0f * h_stage * h_stage;
         int total = build_stream(c, cell, box, R2s, tab, lane);
         Cursor cur{0, 0};
-        int T = stage_density<F32>(c, tab, total, box, R2s, sj, c.cap, cur, lane);
+        int T = stage_density<FX, FV>(c, tab, total, box, R2s, sj, c.cap, cur, lane);
         bool fits = cur.g >= total;
         float h_list = 0.0f;       // this lane's list holds every staged candidate within 2 h_list
         int nlist = 0;
@@ -406,7 +416,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
                 R2s = 4.0f * h_stage * h_stage;
                 total = build_stream(c, cell, box, R2s, tab, lane);
                 Cursor rc{0, 0};
-                T = stage_density<F32>(c, tab, total, box, R2s, sj, c.cap, rc, lane);
+                T = stage_density<FX, FV>(c, tab, total, box, R2s, sj, c.cap, rc, lane);
                 fits = rc.g >= total;
                 h_list = 0.0f;
             }
@@ -448,7 +458,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
                 const int tot = build_stream(c, cell, box, R2, tab, lane);
                 Cursor sc{0, 0};
                 do {
-                    const int len = stage_density<F32>(c, tab, tot, box, R2, sj, c.cap, sc, lane);
+                    const int len = stage_density<FX, FV>(c, tab, tot, box, R2, sj, c.cap, sc, lane);
                     if (ok) {
                         my_tests += (unsigned long long)len;
                         for (int e = 0; e < len; ++e) dens_pair(acc, xi, yi, zi, h2x4, hinv, a.plain_sum, deriv, sj[e]);
@@ -527,7 +537,7 @@ __global__ void __launch_bounds__(256) k_key_hmax(FieldRef h, const int32_t *slo
 // candidate needs beyond x and h are issued for all batches in flight before
 // anything is stored.  The 27-cell grid covers pairs up to 2 h_max only; a
 // candidate with a larger h sets the h-cap error bit.
-template <bool F32>
+template <int FX, int FV>
 __device__ int stage_force(const ForceArgs &a, const Tab &tab, int total, const Box &box, float hw,
                            float4 *sA, float4 *sB, float4 *sC, int cap, Cursor &cur, int lane,
                            unsigned &err)
@@ -554,10 +564,10 @@ __device__ int stage_force(const ForceArgs &a, const Tab &tab, int total, const 
                 jj[u] = j;
                 float sx, sy, sz;
                 stencil_shift(c, e >> c.lg_s3, sx, sy, sz);
-                qa[u].x = ldv<F32>(c.x.p[0], c.x.fmt, j) + sx;
-                qa[u].y = ldv<F32>(c.x.p[1], c.x.fmt, j) + sy;
-                qa[u].z = ldv<F32>(c.x.p[2], c.x.fmt, j) + sz;
-                qa[u].w = ldv<F32>(c.h.p[0], c.h.fmt, j);
+                qa[u].x = ldf<FX>(c.x.p[0], c.x.fmt, j) + sx;
+                qa[u].y = ldf<FX>(c.x.p[1], c.x.fmt, j) + sy;
+                qa[u].z = ldf<FX>(c.x.p[2], c.x.fmt, j) + sz;
+                qa[u].w = ldf<FV>(c.h.p[0], c.h.fmt, j);
             }
             eu[u] = e;
         }
@@ -570,10 +580,11 @@ __device__ int stage_force(const ForceArgs &a, const Tab &tab, int total, const 
             qc[u] = make_float4(0.f, 1.f, 0.f, 0.f);
             if (keep[u]) {
                 const int64_t j = jj[u];
-                qb[u] = make_float4(ldv<F32>(a.v.p[0], a.v.fmt, j), ldv<F32>(a.v.p[1], a.v.fmt, j),
-                                    ldv<F32>(a.v.p[2], a.v.fmt, j), ldv<F32>(c.m.p[0], c.m.fmt, j));
-                qc[u] = make_float4(ldv<F32>(a.P.p[0], a.P.fmt, j), ldv<F32>(a.rho.p[0], a.rho.fmt, j),
-                                    ldv<F32>(a.cs.p[0], a.cs.fmt, j), __int_as_float((int)j));
+                constexpr int FR = derived_fmt<FX>();
+                qb[u] = make_float4(ldf<FV>(a.v.p[0], a.v.fmt, j), ldf<FV>(a.v.p[1], a.v.fmt, j),
+                                    ldf<FV>(a.v.p[2], a.v.fmt, j), ldf<FV>(c.m.p[0], c.m.fmt, j));
+                qc[u] = make_float4(ldf<FR>(a.P.p[0], a.P.fmt, j), ldf<FR>(a.rho.p[0], a.rho.fmt, j),
+                                    ldf<FR>(a.cs.p[0], a.cs.fmt, j), __int_as_float((int)j));
             }
         }
 #pragma unroll
@@ -603,7 +614,7 @@ __device__ int stage_force(const ForceArgs &a, const Tab &tab, int total, const 
     return found;
 }
 
-template <bool F32>
+template <int FX, int FV>
 __global__ void __launch_bounds__(kMaxBlock, 1) k_force(ForceArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -649,7 +660,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_force(ForceArgs a)
         if (hi > a.h_cap) my_err |= SPH_ERR_HCAP;
         Cursor cur{0, 0};
         do {
-            const int len = stage_force<F32>(a, tab, total, box, hw, sA, sB, sC, c.cap, cur, lane, my_err);
+            const int len = stage_force<FX, FV>(a, tab, total, box, hw, sA, sB, sC, c.cap, cur, lane, my_err);
             if (ok) {
                 my_tests += (unsigned long long)len;
                 // phase 1 collects this lane's pairs into its list, phase 2
@@ -785,6 +796,16 @@ cudaError_t launch_persistent(sph_ctx *c, K kernel, const A &args, size_t smem, 
     return cudaGetLastError();
 }
 
+// Which fixed-format instantiation serves positions in fx and fields in fv:
+// 1..6 for (FP32 | FP16) x (FP32 | BF16 | FP16), 0 for the run-time decoder.
+int fmt_variant(int fx, int fv)
+{
+    const int ix = fx == SPH_P_FP32 ? 0 : (fx == SPH_P_FP16 ? 1 : -1);
+    const int iv = fv == SPH_P_FP32 ? 0 : (fv == SPH_P_BF16 ? 1 : (fv == SPH_P_FP16 ? 2 : -1));
+    if (ix < 0 || iv < 0) return 0;
+    return 1 + 3 * ix + iv;
+}
+
 }  // namespace
 
 size_t density_smem_bytes(int block_threads, int cap)
@@ -826,9 +847,16 @@ cudaError_t run_density(sph_ctx *c, int newton_steps)
     a.cs_fmt = c->prec[SPH_F_CS];
     a.nngb = c->nngb;
     const size_t smem = density_smem_bytes(c->tuning.block_threads, a.c.cap);
-    const bool f32 = a.c.x.fmt == SPH_P_FP32 && a.c.m.fmt == SPH_P_FP32;   // what staging loads
-    cudaError_t e = f32 ? launch_persistent(c, k_density<true>, a, smem, c->lc_density[1])
-                        : launch_persistent(c, k_density<false>, a, smem, c->lc_density[0]);
+    cudaError_t e;
+    switch (fmt_variant(a.c.x.fmt, a.c.m.fmt)) {    // what the staging loads
+    case 1: e = launch_persistent(c, k_density<SPH_P_FP32, SPH_P_FP32>, a, smem, c->lc_density[1]); break;
+    case 2: e = launch_persistent(c, k_density<SPH_P_FP32, SPH_P_BF16>, a, smem, c->lc_density[2]); break;
+    case 3: e = launch_persistent(c, k_density<SPH_P_FP32, SPH_P_FP16>, a, smem, c->lc_density[3]); break;
+    case 4: e = launch_persistent(c, k_density<SPH_P_FP16, SPH_P_FP32>, a, smem, c->lc_density[4]); break;
+    case 5: e = launch_persistent(c, k_density<SPH_P_FP16, SPH_P_BF16>, a, smem, c->lc_density[5]); break;
+    case 6: e = launch_persistent(c, k_density<SPH_P_FP16, SPH_P_FP16>, a, smem, c->lc_density[6]); break;
+    default: e = launch_persistent(c, k_density<kAnyFmt, kAnyFmt>, a, smem, c->lc_density[0]); break;
+    }
     if (e != cudaSuccess) return e;
     if (a.write_h && h_packed) return run_pack(c, c->stage, SPH_F_H);
     return cudaSuccess;
@@ -866,11 +894,20 @@ cudaError_t run_force(sph_ctx *c)
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     a.key_hmax = c->key_hmax;
     const size_t smem = force_smem_bytes(c->tuning.block_threads, a.c.cap);
-    const bool f32 = a.c.x.fmt == SPH_P_FP32 && a.c.h.fmt == SPH_P_FP32 && a.c.m.fmt == SPH_P_FP32 &&
-                     a.v.fmt == SPH_P_FP32 && a.rho.fmt == SPH_P_FP32 && a.P.fmt == SPH_P_FP32 &&
-                     a.cs.fmt == SPH_P_FP32;
-    return f32 ? launch_persistent(c, k_force<true>, a, smem, c->lc_force[1])
-               : launch_persistent(c, k_force<false>, a, smem, c->lc_force[0]);
+    // fixed-format kernels: v, m, h share one format; rho, P, c are FP32
+    int v = 0;
+    if (a.c.h.fmt == a.c.m.fmt && a.v.fmt == a.c.m.fmt && a.rho.fmt == SPH_P_FP32 &&
+        a.P.fmt == SPH_P_FP32 && a.cs.fmt == SPH_P_FP32)
+        v = fmt_variant(a.c.x.fmt, a.c.m.fmt);
+    switch (v) {
+    case 1: return launch_persistent(c, k_force<SPH_P_FP32, SPH_P_FP32>, a, smem, c->lc_force[1]);
+    case 2: return launch_persistent(c, k_force<SPH_P_FP32, SPH_P_BF16>, a, smem, c->lc_force[2]);
+    case 3: return launch_persistent(c, k_force<SPH_P_FP32, SPH_P_FP16>, a, smem, c->lc_force[3]);
+    case 4: return launch_persistent(c, k_force<SPH_P_FP16, SPH_P_FP32>, a, smem, c->lc_force[4]);
+    case 5: return launch_persistent(c, k_force<SPH_P_FP16, SPH_P_BF16>, a, smem, c->lc_force[5]);
+    case 6: return launch_persistent(c, k_force<SPH_P_FP16, SPH_P_FP16>, a, smem, c->lc_force[6]);
+    default: return launch_persistent(c, k_force<kAnyFmt, kAnyFmt>, a, smem, c->lc_force[0]);
+    }
 }
 
 }  // namespace sph

@@ -16,7 +16,7 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 bool layout_ok(const sph_aos_layout *L)
 {
-    if (!L || L->record_bytes <= 0 || L->record_bytes % 8 != 0) return false;
+    if (!L || L->record_bytes <= 0 || L->record_bytes % 8 != 0 || L->record_bytes > 512) return false;
     if (L->offset[SPH_F_X] < 0 || L->type[SPH_F_X] != SPH_AOS_F64) return false;
     for (int f = 0; f < SPH_NFIELDS; ++f) {
         if (L->offset[f] < 0) continue;

@@ -176,6 +176,43 @@ __device__ __forceinline__ void st_any(void *p, int fmt, int64_t k, float v, boo
 
 __device__ __forceinline__ void set_error(DevStats *s, unsigned bits) { atomicOr(&s->error_bits, bits); }
 
+// ---------------------------------------------------------------------------
+// FP64 <-> FP32 conversions on the integer pipes.  On this GPU FP64
+// instructions (conversions included) issue at a small fraction of the FP32
+// rate, and the memory-bound kernels would be bound by them.  These follow
+// the IEEE 754 definitions: binary32 -> binary64 is exact (re-bias the
+// exponent, widen the mantissa); binary64 -> binary32 rounds to nearest,
+// ties to even.  Values outside the normal binary32 range (zeros excepted)
+// take the hardware conversion: they are rare.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double f2d_bits(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xFFu;
+    const uint64_t s = (uint64_t)(u >> 31) << 63;
+    if ((u & 0x7FFFFFFFu) == 0u) return __longlong_as_double((long long)s);          // +-0
+    if (e == 0u) return (double)f;                                                   // subnormal
+    const uint64_t m = (uint64_t)(u & 0x7FFFFFu) << 29;
+    const uint64_t E = e == 0xFFu ? 0x7FFull : (uint64_t)(e + (1023 - 127));          // inf / nan keep all-ones
+    return __longlong_as_double((long long)(s | (E << 52) | m));
+}
+
+__device__ __forceinline__ float d2f_bits_rn(double d)
+{
+    const uint64_t u = (uint64_t)__double_as_longlong(d);
+    const uint32_t s = (uint32_t)(u >> 63) << 31;
+    if ((u << 1) == 0u) return __uint_as_float(s);                                    // +-0
+    const int e = (int)((u >> 52) & 0x7FFu);
+    if (e < 1023 - 126 || e > 1023 + 127) return __double2float_rn(d);              // not a normal float
+    const uint64_t m = u & 0xFFFFFFFFFFFFFull;
+    const uint32_t top = (uint32_t)(m >> 29);                                         // kept 23 bits
+    const uint32_t rem = (uint32_t)(m & 0x1FFFFFFFull);                               // dropped 29 bits
+    uint32_t bits = ((uint32_t)(e - (1023 - 127)) << 23) | top;
+    // round half to even; a carry moves into the exponent (up to infinity)
+    bits += (rem > 0x10000000u || (rem == 0x10000000u && (top & 1u))) ? 1u : 0u;
+    return __uint_as_float(s | bits);
+}
+
 }  // namespace sph
 
 // ---------------------------------------------------------------------------
@@ -202,7 +239,7 @@ struct sph_ctx {
     int64_t ncell = 0;
     int sub = 1;                  // sub-cells per cell edge of the last binning
     bool binned = false;
-    sph::LaunchCache lc_density[2], lc_force[2];   // [generic formats, all FP32]
+    sph::LaunchCache lc_density[8], lc_force[8];   // one per storage-format instantiation
     int sorted_buf = 0;          // which ping-pong buffer holds the sorted keys/values
 
     // workspace arrays
