@@ -338,6 +338,31 @@ def run_long_run(steps: int = 3, graph_steps: int = 10):
     st = s.stats()
     if st["error_bits"] & (sph.ERR_NONFINITE | sph.ERR_OUTSIDE):
         raise RuntimeError(f"long run: device error bits {st['error_bits']}")
+    pairs = (st["pairs_density"] + st["pairs_force"]) / graph_steps
+    # the comparison: an FP32 SoA kept across steps needs no conversion or
+    # write-back; its step is binning + density + force + kick/drift on FP32
+    # storage (timed per call; the FP32 conversion that refreshes the SoA
+    # here between those calls is not counted)
+    names32 = ["bin", "density", "force", "kick_drift"]
+    ev32 = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in names32]
+            for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        for k in range(steps + 1):
+            for i, fn in enumerate([lambda: s.bin_cells(wl.cell_edge), None, lambda: s.density(0),
+                                    lambda: s.force(), lambda: s.kick_drift(wl.dt, wl.dt)]):
+                if fn is None:
+                    s.aos_to_soa(sph.FIELDS_FORCE)          # FP32, untimed
+                    continue
+                j = i if i == 0 else i - 1
+                if k > 0:
+                    ev32[k - 1][j][0].record(stream)
+                fn()
+                if k > 0:
+                    ev32[k - 1][j][1].record(stream)
+            s.soa_to_aos(sph.FIELDS_OUTPUT)                  # keeps the AoS state current, untimed
+        stream.synchronize()
+    ms32 = {nm: statistics.mean(ev32[k][i][0].elapsed_time(ev32[k][i][1]) for k in range(steps))
+            for i, nm in enumerate(names32)}
     hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6753.1
     bpp = algorithmic_bytes(2, 2)
@@ -349,13 +374,17 @@ def run_long_run(steps: int = 3, graph_steps: int = 10):
             row.update({"algorithmic_bytes_per_particle": bpp[nm], "GB_s": gbs,
                         "frac_of_measured_hbm": gbs / hbm})
         kern[nm] = row
-    pairs = (st["pairs_density"] + st["pairs_force"]) / graph_steps
     s.close()
     del aos
     torch.cuda.empty_cache()
+    fp16_step = sum(ms.values())
+    fp32_step = sum(ms32.values())
     return {"workload": "long_run_33554432", "particles": n, "storage": "fp16 (x, v, m, h, u)",
             "ms_per_step_graph": graph_ms, "pairs_per_s": pairs / (graph_ms / 1e3),
-            "kernels": kern, "hbm_peak_gbs": hbm}
+            "kernels": kern, "hbm_peak_gbs": hbm,
+            "vs_fp32_soa": {"fp16_with_conversion_ms": fp16_step,
+                            "fp32_soa_no_conversion_ms": fp32_step,
+                            "fp32_kernels_ms": ms32, "speedup": fp32_step / fp16_step}}
 
 
 # ----------------------------------------------------------------- oracle
@@ -397,6 +426,19 @@ def cpu_baseline():
     return {"value": pairs / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n_t} random particles of the 1,072,476-particle Sod step "
                       f"(density with 5 Newton steps + EOS + force), {dt:.1f} s"}
+
+
+def combine_ranks(total_s: float, pairs: float, e2e_value: float, device: str):
+    """Whole-job figures of N independent replicas (the path has no exchange
+    step): the slowest rank's timed seconds, the pairs all ranks processed,
+    and the sum of the ranks' end-to-end rates.  Every rank calls it."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([total_s], dtype=torch.float64, device=device)
+    p = torch.tensor([pairs, e2e_value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(p, op=dist.ReduceOp.SUM)
+    return float(t[0].item()), float(p[0].item()), float(p[1].item())
 
 
 def main():
@@ -441,17 +483,10 @@ def main():
 
     total_s, pairs = r["total_s"], r["pairs"]
     if world > 1:
-        import torch
-        import torch.distributed as dist
-        t = torch.tensor([total_s], dtype=torch.float64, device="cuda")
-        p = torch.tensor([pairs], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(p, op=dist.ReduceOp.SUM)
-        total_s, pairs = float(t.item()), float(p.item())
-        e2e_v = torch.tensor([r["e2e"]["value"] if r["e2e"] else 0.0], dtype=torch.float64, device="cuda")
-        dist.all_reduce(e2e_v, op=dist.ReduceOp.SUM)
+        e2e_in = r["e2e"]["value"] if r["e2e"] else 0.0
+        total_s, pairs, e2e_v = combine_ranks(total_s, pairs, e2e_in, "cuda")
         if r["e2e"]:
-            r["e2e"]["value"] = float(e2e_v.item())
+            r["e2e"]["value"] = e2e_v
     if rank != 0:
         if world > 1:
             import torch.distributed as dist

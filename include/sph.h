@@ -215,10 +215,32 @@ sph_status sph_bin_cells(sph_ctx *ctx, double cell_edge, int32_t reorder_aos);
  * prec[f] (SPH_NFIELDS entries, NULL: FP32 everywhere) is the storage format
  * of field f.  Positions are stored as offsets from their cell origin
  * k_d * box_d / nc_d (computed in FP64, then rounded); they accept FP32 or
- * FP16.  A, RHO, P, CS and DUDT accept FP32, BF16 and FP16; V, M, H and U
- * accept every format.  Requires sph_bin_cells.  Errors: SPH_EINVAL (field
- * absent from the layout, or format not allowed for it), SPH_ESTATE. */
+ * FP16.  RHO, P and CS accept FP32, BF16 and FP16; A and DUDT (written by
+ * the force, read by kick/drift) FP32 only; V, M, H and U accept every
+ * format.  Each value is multiplied by its field's storage scale 2^e
+ * (sph_set_field_scale) before rounding.  Requires sph_bin_cells.  Errors:
+ * SPH_EINVAL (field absent from the layout, or format not allowed for it),
+ * SPH_ESTATE. */
 sph_status sph_aos_to_soa(sph_ctx *ctx, uint32_t fields, const int32_t *prec);
+
+/* Exact power-of-two storage scale per field (a reading of the paper's
+ * storage formats, Section 3 and Table 2, which fix the bit layout but not the
+ * range: the paper's own values stay inside FP32's).  A 16-bit format covers
+ * a fixed window -- FP16 keeps 11 significant bits only for magnitudes in
+ * [2^-14, 65504] -- so a particle mass of 5e-7 would be stored as a
+ * subnormal with 4 significant bits.  With exp2[f] = e, field f is stored as
+ * the code of value * 2^e and read back as decode(code) * 2^-e everywhere
+ * (conversion, kernel outputs, kick/drift, write-back).  Multiplying by a
+ * power of two is exact while the product stays a normal FP32 number, so the
+ * scale moves the window without adding rounding: the stored value is the
+ * unscaled format's rounding of value * 2^e.  exp2 holds SPH_NFIELDS entries
+ * in [-SPH_SCALE_MAX_EXP, SPH_SCALE_MAX_EXP]; A and DUDT are always FP32
+ * and take 0 only.  All scales are 0 after sph_create.  A field whose scale
+ * changes loses its SoA contents (convert it again).  Host-only, no device
+ * work.  Errors: SPH_EINVAL. */
+#define SPH_SCALE_MAX_EXP 64
+sph_status sph_set_field_scale(sph_ctx *ctx, const int32_t *exp2);
+sph_status sph_get_field_scale(const sph_ctx *ctx, int32_t *exp2_out);
 
 /* S3+S4, density (Eq. 6, gather form rho_i = sum_j m_j W(r_ij, h_i), M4 cubic
  * spline with support 2h, FP32 arithmetic, compensated sum) with

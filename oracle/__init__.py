@@ -226,13 +226,16 @@ def ball_mark(x, box, radius, targets):
 
 
 # ---------------------------------------------------------------- quantisers
-def quantize(values, fmt):
-    """Returns (value as FP64, integer code) of each input in storage format `fmt`."""
-    v = _f64(values).ravel()
+def quantize(values, fmt, exp2=0):
+    """Returns (value as FP64, integer code) of each input in storage format
+    `fmt`.  With a storage scale 2^exp2 the code is that of value * 2^exp2 and
+    the value returned is the decoded code times 2^-exp2 (powers of two scale
+    exactly in FP64)."""
+    v = np.ldexp(_f64(values).ravel(), int(exp2))
     out = np.zeros_like(v)
     code = np.zeros(v.shape, np.uint32)
     lib().orc_quantize(v.shape[0], _ptr(v), FMT[fmt], _ptr(out), _ptr(code))
-    return out, code
+    return np.ldexp(out, -int(exp2)), code
 
 
 def pack_bits(codes, bits):
@@ -249,10 +252,11 @@ def unpack_bits(words, n, bits):
     return out
 
 
-def cell_relative(x, box, nc, fmt="fp32"):
+def cell_relative(x, box, nc, fmt="fp32", exp2=0):
     """Positions as the library stores them: the offset from the particle's cell
-    origin (k * L/nc, k from the binning rule) rounded to `fmt`, added back to
-    the origin in FP64.  Returns (positions, offsets-as-stored)."""
+    origin (k * L/nc, k from the binning rule) rounded to `fmt` (under the
+    storage scale 2^exp2), added back to the origin in FP64.  Returns
+    (positions, offsets-as-stored)."""
     x = _f64(x, (-1, 3))
     box = _f64(box)
     nc = np.asarray(nc, dtype=np.int64)
@@ -262,7 +266,7 @@ def cell_relative(x, box, nc, fmt="fp32"):
     edge = box / nc.astype(np.float64)
     origin = k * edge
     off = x - origin
-    q, _ = quantize(off.ravel(), fmt)
+    q, _ = quantize(off.ravel(), fmt, exp2)
     q = q.reshape(off.shape)
     return origin + q, q
 

@@ -78,6 +78,17 @@ def sph_soa_to_aos(ctx, fields: int) -> int:
     return _lib.sph_soa_to_aos(ctx, fields)
 
 
+def sph_set_field_scale(ctx, exp2) -> int:
+    arr = (C.c_int32 * SPH_NFIELDS)(*[int(e) for e in exp2])
+    return _lib.sph_set_field_scale(ctx, arr)
+
+
+def sph_get_field_scale(ctx):
+    arr = (C.c_int32 * SPH_NFIELDS)()
+    st = _lib.sph_get_field_scale(ctx, arr)
+    return st, list(arr)
+
+
 def sph_get_stats(ctx):
     s = sph_stats()
     st = _lib.sph_get_stats(ctx, C.byref(s))
@@ -177,6 +188,31 @@ def prec_array(prec) -> list:
     return out
 
 
+SCALE_MAX_EXP = 64
+
+
+def scale_array(scale) -> list:
+    """Per-field storage-scale exponents from a {field name: e} dict."""
+    out = [0] * SPH_NFIELDS
+    if scale:
+        for name, e in scale.items():
+            out[FIELD_NAMES.index(name)] = int(e)
+    return out
+
+
+def suggest_scale(max_abs: float, fmt, headroom_bits: int = 4) -> int:
+    """Storage-scale exponent e for a field whose magnitudes reach `max_abs`:
+    FP16 gets the largest value 2^headroom_bits below its top binade (room
+    for growth during a run); the other formats keep FP32's exponent range
+    and need no scale (0)."""
+    import math
+    f = PREC[fmt] if isinstance(fmt, str) else int(fmt)
+    if f != P_FP16 or not (max_abs > 0.0) or not math.isfinite(max_abs):
+        return 0
+    e = (15 - headroom_bits) - math.floor(math.log2(max_abs))
+    return max(-SCALE_MAX_EXP, min(SCALE_MAX_EXP, e))
+
+
 def mask(*names) -> int:
     m = 0
     for nm in names:
@@ -223,6 +259,16 @@ class Sph:
     def aos_to_soa(self, fields: int, prec=None):
         arr = prec if isinstance(prec, list) else (prec_array(prec) if prec is not None else None)
         _check(sph_aos_to_soa(self.ctx, fields, arr), "sph_aos_to_soa")
+
+    def set_scale(self, scale):
+        """Power-of-two storage scales, {field name: e} or a list per field."""
+        arr = scale if isinstance(scale, list) else scale_array(scale)
+        _check(sph_set_field_scale(self.ctx, arr), "sph_set_field_scale")
+
+    def scale(self) -> dict:
+        st, arr = sph_get_field_scale(self.ctx)
+        _check(st, "sph_get_field_scale")
+        return {FIELD_NAMES[f]: arr[f] for f in range(SPH_NFIELDS)}
 
     def density(self, newton_steps: int = 0):
         _check(sph_density(self.ctx, newton_steps), "sph_density")

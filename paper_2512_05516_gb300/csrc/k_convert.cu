@@ -34,6 +34,7 @@ struct ConvArgs {
     int off[SPH_NFIELDS];
     int type[SPH_NFIELDS];
     int fmt[SPH_NFIELDS];
+    float scl[SPH_NFIELDS];      // storage scale: 2^e on the way in, 2^-e on the way out
     int nco[SPH_NFIELDS];
     void *soa[SPH_NFIELDS][3];
 };
@@ -121,7 +122,7 @@ __global__ void __launch_bounds__(kConvThreads) k_aos_to_soa(ConvArgs a)
                     v = *(const float *)(mine + a.off[j] + 4 * c);
                 }
             }
-            st_any(a.soa[j][c], a.fmt[j], k, v, ok, a.n);
+            st_any(a.soa[j][c], a.fmt[j], k, v * a.scl[j], ok, a.n);
         }
     }
 }
@@ -138,7 +139,7 @@ __global__ void __launch_bounds__(kConvThreads) k_soa_to_aos(ConvArgs a)
     if (ok) {
         for (int j = 0; j < a.nf; ++j) {
             for (int c = 0; c < a.nco[j]; ++c) {
-                const float v = ld_val(a.soa[j][c], a.fmt[j], k);
+                const float v = ld_val(a.soa[j][c], a.fmt[j], k) * a.scl[j];
                 if (a.type[j] == SPH_AOS_F64) *(double *)(mine + a.off[j] + 8 * c) = f2d_bits(v);
                 else *(float *)(mine + a.off[j] + 4 * c) = v;
             }
@@ -154,7 +155,7 @@ __global__ void __launch_bounds__(256) k_pack(const float *src, void *dst, int f
     st_any(dst, fmt, k, ok ? src[k] : 0.0f, ok, n);
 }
 
-ConvArgs make_args(sph_ctx *c, uint32_t fields)
+ConvArgs make_args(sph_ctx *c, uint32_t fields, bool to_soa)
 {
     ConvArgs a;
     a.aos = c->aos;
@@ -178,6 +179,7 @@ ConvArgs make_args(sph_ctx *c, uint32_t fields)
         a.off[j] = c->layout.offset[f];
         a.type[j] = c->layout.type[f];
         a.fmt[j] = c->prec[f];
+        a.scl[j] = to_soa ? c->enc(f) : c->dec(f);
         a.nco[j] = ncomp(f);
         for (int k = 0; k < 3; ++k) a.soa[j][k] = c->soa[f][k];
         const int es = a.type[j] == SPH_AOS_F64 ? 8 : 4;
@@ -197,7 +199,7 @@ inline size_t conv_smem(const ConvArgs &a) { return (size_t)(kConvThreads / 32) 
 cudaError_t run_aos_to_soa(sph_ctx *c, uint32_t fields)
 {
     if (c->n == 0) return cudaSuccess;
-    ConvArgs a = make_args(c, fields);
+    ConvArgs a = make_args(c, fields, true);
     const size_t smem = conv_smem(a);
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_aos_to_soa, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
@@ -210,7 +212,7 @@ cudaError_t run_aos_to_soa(sph_ctx *c, uint32_t fields)
 cudaError_t run_soa_to_aos(sph_ctx *c, uint32_t fields)
 {
     if (c->n == 0) return cudaSuccess;
-    ConvArgs a = make_args(c, fields);
+    ConvArgs a = make_args(c, fields, false);
     const size_t smem = conv_smem(a);
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_soa_to_aos, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)

@@ -24,9 +24,11 @@ struct KDArgs {
     double dtd;
     void *v[3];
     int vfmt;
+    float vdec, venc;            // storage scale of v: stored = v * venc
     const float *a[3];
     void *u;
     int ufmt;
+    float udec, uenc;
     const float *dudt;
     DevStats *st;
 };
@@ -43,8 +45,8 @@ __global__ void __launch_bounds__(kKDThreads) k_kick_drift(KDArgs a)
     float vn[3] = {0.f, 0.f, 0.f};
     float un = 0.f;
     if (ok) {
-        for (int c = 0; c < 3; ++c) vn[c] = fmaf(a.a[c][k], a.dtk, ld_val(a.v[c], a.vfmt, k));
-        un = fmaf(a.dudt[k], a.dtk, ld_val(a.u, a.ufmt, k));
+        for (int c = 0; c < 3; ++c) vn[c] = fmaf(a.a[c][k], a.dtk, ld_val(a.v[c], a.vfmt, k) * a.vdec);
+        un = fmaf(a.dudt[k], a.dtk, ld_val(a.u, a.ufmt, k) * a.udec);
     }
     double *aos64 = (double *)a.aos;
     // lane l moves word l % 3 of record l / 3 (then +32, +64)
@@ -89,8 +91,8 @@ __global__ void __launch_bounds__(kKDThreads) k_kick_drift(KDArgs a)
         const int64_t orr = __shfl_sync(FULL, o, r);
         if (orr >= 0) aos64[orr * a.W + a.xw + w] = xs[idx];
     }
-    for (int c = 0; c < 3; ++c) st_any(a.v[c], a.vfmt, k, vn[c], ok, a.n);
-    st_any(a.u, a.ufmt, k, un, ok, a.n);
+    for (int c = 0; c < 3; ++c) st_any(a.v[c], a.vfmt, k, vn[c] * a.venc, ok, a.n);
+    st_any(a.u, a.ufmt, k, un * a.uenc, ok, a.n);
 }
 
 }  // namespace
@@ -112,8 +114,12 @@ cudaError_t run_kick_drift(sph_ctx *c, double dt_kick, double dt_drift)
     a.dtk = (float)dt_kick;
     a.dtd = dt_drift;
     a.vfmt = c->prec[SPH_F_V];
+    a.vdec = c->dec(SPH_F_V);
+    a.venc = c->enc(SPH_F_V);
     a.u = c->soa[SPH_F_U][0];
     a.ufmt = c->prec[SPH_F_U];
+    a.udec = c->dec(SPH_F_U);
+    a.uenc = c->enc(SPH_F_U);
     a.dudt = (const float *)c->soa[SPH_F_DUDT][0];
     a.st = c->dstats;
     k_kick_drift<<<(unsigned)((c->n + kKDThreads - 1) / kKDThreads), kKDThreads, 0, c->stream>>>(a);

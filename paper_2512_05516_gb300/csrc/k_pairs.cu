@@ -68,6 +68,7 @@ struct DensityArgs {
     bool write_h;
     void *P_out; int P_fmt;
     void *cs_out; int cs_fmt;
+    float rho_enc, h_enc, P_enc, cs_enc;   // storage scales of the outputs
     int32_t *nngb;
 };
 
@@ -329,10 +330,10 @@ __device__ int stage_density(const Common &c, const Tab &tab, int total, const B
                 const int64_t j = (int64_t)tab.base[e] + g;
                 float sx, sy, sz;
                 stencil_shift(c, e >> c.lg_s3, sx, sy, sz);
-                q[u].x = ldf<FX>(c.x.p[0], c.x.fmt, j) + sx;
-                q[u].y = ldf<FX>(c.x.p[1], c.x.fmt, j) + sy;
-                q[u].z = ldf<FX>(c.x.p[2], c.x.fmt, j) + sz;
-                q[u].w = ldf<FV>(c.m.p[0], c.m.fmt, j);
+                q[u].x = fmaf(ldf<FX>(c.x.p[0], c.x.fmt, j), c.x.dec, sx);
+                q[u].y = fmaf(ldf<FX>(c.x.p[1], c.x.fmt, j), c.x.dec, sy);
+                q[u].z = fmaf(ldf<FX>(c.x.p[2], c.x.fmt, j), c.x.dec, sz);
+                q[u].w = ldf<FV>(c.m.p[0], c.m.fmt, j) * c.m.dec;
             }
             eu[u] = e;
         }
@@ -382,12 +383,12 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
         bool clamped = false;
         float xi = 0.f, yi = 0.f, zi = 0.f, mi = 0.f, hi = 0.f, ui = 0.f;
         if (ok) {
-            xi = ld_val(c.x.p[0], c.x.fmt, k);
-            yi = ld_val(c.x.p[1], c.x.fmt, k);
-            zi = ld_val(c.x.p[2], c.x.fmt, k);
-            mi = ld_val(c.m.p[0], c.m.fmt, k);
-            hi = ld_val(c.h.p[0], c.h.fmt, k);
-            if (a.has_u) ui = ld_val(a.u.p[0], a.u.fmt, k);
+            xi = ld_val(c.x.p[0], c.x.fmt, k) * c.x.dec;
+            yi = ld_val(c.x.p[1], c.x.fmt, k) * c.x.dec;
+            zi = ld_val(c.x.p[2], c.x.fmt, k) * c.x.dec;
+            mi = ld_val(c.m.p[0], c.m.fmt, k) * c.m.dec;
+            hi = ld_val(c.h.p[0], c.h.fmt, k) * c.h.dec;
+            if (a.has_u) ui = ld_val(a.u.p[0], a.u.fmt, k) * a.u.dec;
             if (!(hi > 0.0f) || !isfinite(hi)) { hi = a.h_cap; my_err |= SPH_ERR_NONFINITE; }
             if (hi > a.h_cap) { hi = a.h_cap; clamped = true; }
         }
@@ -487,13 +488,13 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
         }
         if (ok) {
             if (!isfinite(rho)) my_err |= SPH_ERR_NONFINITE;
-            st_val(a.rho_out, a.rho_fmt, k, rho);
-            if (a.write_h) st_val(a.h_out, a.h_fmt, k, hi);
+            st_val(a.rho_out, a.rho_fmt, k, rho * a.rho_enc);
+            if (a.write_h) st_val(a.h_out, a.h_fmt, k, hi * a.h_enc);
             a.nngb[k] = cnt;
             if (a.has_u) {
                 const float P = a.gm1 * rho * ui;
-                st_val(a.P_out, a.P_fmt, k, P);
-                st_val(a.cs_out, a.cs_fmt, k, __fsqrt_rn(a.gamma * P / rho));
+                st_val(a.P_out, a.P_fmt, k, P * a.P_enc);
+                st_val(a.cs_out, a.cs_fmt, k, __fsqrt_rn(a.gamma * P / rho) * a.cs_enc);
             }
             if (clamped) {   // each clamped particle counted once per call
                 atomicAdd(&c.st->hcap_clamps, 1ull);
@@ -523,7 +524,7 @@ __global__ void __launch_bounds__(256) k_key_hmax(FieldRef h, const int32_t *slo
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool ok = k < n;
     const int key = ok ? slot_key[k] : -1;
-    float hv = ok ? ld_val(h.p[0], h.fmt, k) : 0.0f;
+    float hv = ok ? ld_val(h.p[0], h.fmt, k) * h.dec : 0.0f;
     if (ok && !(hv > 0.0f && hv <= 3.0e38f)) hv = h_cap;       // NaN / non-positive: assume h_max
     const unsigned peers = __match_any_sync(FULL, key);
     const unsigned mx = __reduce_max_sync(peers, __float_as_uint(hv));
@@ -564,10 +565,10 @@ __device__ int stage_force(const ForceArgs &a, const Tab &tab, int total, const 
                 jj[u] = j;
                 float sx, sy, sz;
                 stencil_shift(c, e >> c.lg_s3, sx, sy, sz);
-                qa[u].x = ldf<FX>(c.x.p[0], c.x.fmt, j) + sx;
-                qa[u].y = ldf<FX>(c.x.p[1], c.x.fmt, j) + sy;
-                qa[u].z = ldf<FX>(c.x.p[2], c.x.fmt, j) + sz;
-                qa[u].w = ldf<FV>(c.h.p[0], c.h.fmt, j);
+                qa[u].x = fmaf(ldf<FX>(c.x.p[0], c.x.fmt, j), c.x.dec, sx);
+                qa[u].y = fmaf(ldf<FX>(c.x.p[1], c.x.fmt, j), c.x.dec, sy);
+                qa[u].z = fmaf(ldf<FX>(c.x.p[2], c.x.fmt, j), c.x.dec, sz);
+                qa[u].w = ldf<FV>(c.h.p[0], c.h.fmt, j) * c.h.dec;
             }
             eu[u] = e;
         }
@@ -581,10 +582,10 @@ __device__ int stage_force(const ForceArgs &a, const Tab &tab, int total, const 
             if (keep[u]) {
                 const int64_t j = jj[u];
                 constexpr int FR = derived_fmt<FX>();
-                qb[u] = make_float4(ldf<FV>(a.v.p[0], a.v.fmt, j), ldf<FV>(a.v.p[1], a.v.fmt, j),
-                                    ldf<FV>(a.v.p[2], a.v.fmt, j), ldf<FV>(c.m.p[0], c.m.fmt, j));
-                qc[u] = make_float4(ldf<FR>(a.P.p[0], a.P.fmt, j), ldf<FR>(a.rho.p[0], a.rho.fmt, j),
-                                    ldf<FR>(a.cs.p[0], a.cs.fmt, j), __int_as_float((int)j));
+                qb[u] = make_float4(ldf<FV>(a.v.p[0], a.v.fmt, j) * a.v.dec, ldf<FV>(a.v.p[1], a.v.fmt, j) * a.v.dec,
+                                    ldf<FV>(a.v.p[2], a.v.fmt, j) * a.v.dec, ldf<FV>(c.m.p[0], c.m.fmt, j) * c.m.dec);
+                qc[u] = make_float4(ldf<FR>(a.P.p[0], a.P.fmt, j) * a.P.dec, ldf<FR>(a.rho.p[0], a.rho.fmt, j) * a.rho.dec,
+                                    ldf<FR>(a.cs.p[0], a.cs.fmt, j) * a.cs.dec, __int_as_float((int)j));
             }
         }
 #pragma unroll
@@ -639,17 +640,17 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_force(ForceArgs a)
         float xi = 0.f, yi = 0.f, zi = 0.f, hi = 0.f, vxi = 0.f, vyi = 0.f, vzi = 0.f;
         float rhoi = 1.f, Pr2i = 0.f, ci = 0.f;
         if (ok) {
-            xi = ld_val(c.x.p[0], c.x.fmt, k);
-            yi = ld_val(c.x.p[1], c.x.fmt, k);
-            zi = ld_val(c.x.p[2], c.x.fmt, k);
-            hi = ld_val(c.h.p[0], c.h.fmt, k);
-            vxi = ld_val(a.v.p[0], a.v.fmt, k);
-            vyi = ld_val(a.v.p[1], a.v.fmt, k);
-            vzi = ld_val(a.v.p[2], a.v.fmt, k);
-            rhoi = ld_val(a.rho.p[0], a.rho.fmt, k);
-            const float Pi = ld_val(a.P.p[0], a.P.fmt, k);
+            xi = ld_val(c.x.p[0], c.x.fmt, k) * c.x.dec;
+            yi = ld_val(c.x.p[1], c.x.fmt, k) * c.x.dec;
+            zi = ld_val(c.x.p[2], c.x.fmt, k) * c.x.dec;
+            hi = ld_val(c.h.p[0], c.h.fmt, k) * c.h.dec;
+            vxi = ld_val(a.v.p[0], a.v.fmt, k) * a.v.dec;
+            vyi = ld_val(a.v.p[1], a.v.fmt, k) * a.v.dec;
+            vzi = ld_val(a.v.p[2], a.v.fmt, k) * a.v.dec;
+            rhoi = ld_val(a.rho.p[0], a.rho.fmt, k) * a.rho.dec;
+            const float Pi = ld_val(a.P.p[0], a.P.fmt, k) * a.P.dec;
             Pr2i = Pi / (rhoi * rhoi);
-            ci = ld_val(a.cs.p[0], a.cs.fmt, k);
+            ci = ld_val(a.cs.p[0], a.cs.fmt, k) * a.cs.dec;
         }
         const Box box = warp_box(ok, xi, yi, zi);
         const float hw = warp_max(ok ? hi : 0.0f);
@@ -762,6 +763,7 @@ Common make_common(sph_ctx *c, int cap)
         FieldRef r;
         for (int k = 0; k < 3; ++k) r.p[k] = c->soa[f][k];
         r.fmt = c->prec[f];
+        r.dec = c->dec(f);
         return r;
     };
     m.x = ref(SPH_F_X);
@@ -828,6 +830,7 @@ cudaError_t run_density(sph_ctx *c, int newton_steps)
     a.has_u = (c->valid & SPH_BIT(SPH_F_U)) != 0;
     for (int k = 0; k < 3; ++k) a.u.p[k] = c->soa[SPH_F_U][0];
     a.u.fmt = c->prec[SPH_F_U];
+    a.u.dec = c->dec(SPH_F_U);
     a.npass = newton_steps + 1;
     const double eta = c->params.eta;
     a.eta3 = (float)(eta * eta * eta);
@@ -845,6 +848,10 @@ cudaError_t run_density(sph_ctx *c, int newton_steps)
     a.P_fmt = c->prec[SPH_F_P];
     a.cs_out = c->soa[SPH_F_CS][0];
     a.cs_fmt = c->prec[SPH_F_CS];
+    a.rho_enc = c->enc(SPH_F_RHO);
+    a.h_enc = c->enc(SPH_F_H);
+    a.P_enc = c->enc(SPH_F_P);
+    a.cs_enc = c->enc(SPH_F_CS);
     a.nngb = c->nngb;
     const size_t smem = density_smem_bytes(c->tuning.block_threads, a.c.cap);
     cudaError_t e;
@@ -871,6 +878,7 @@ cudaError_t run_force(sph_ctx *c)
         FieldRef r;
         for (int k = 0; k < 3; ++k) r.p[k] = c->soa[f][k];
         r.fmt = c->prec[f];
+        r.dec = c->dec(f);
         return r;
     };
     a.v = ref(SPH_F_V);

@@ -45,6 +45,7 @@ bool fmt_allowed(int f, int fmt)
     switch (f) {
     case SPH_F_X: return fmt == SPH_P_FP32 || fmt == SPH_P_FP16;
     case SPH_F_V: case SPH_F_M: case SPH_F_H: case SPH_F_U: return true;
+    case SPH_F_A: case SPH_F_DUDT: return fmt == SPH_P_FP32;    // the force writes, kick/drift reads, FP32
     default: return !fmt_packed(fmt);
     }
 }
@@ -233,6 +234,27 @@ sph_status sph_aos_to_soa(sph_ctx *c, uint32_t fields, const int32_t *prec)
         if (fields & SPH_BIT(f)) c->prec[f] = prec ? prec[f] : SPH_P_FP32;
     if (run_aos_to_soa(c, fields) != cudaSuccess) return SPH_ECUDA;
     c->valid |= fields;
+    return SPH_OK;
+}
+
+sph_status sph_set_field_scale(sph_ctx *c, const int32_t *exp2)
+{
+    if (!c || !exp2) return SPH_EINVAL;
+    for (int f = 0; f < SPH_NFIELDS; ++f) {
+        if (exp2[f] < -SPH_SCALE_MAX_EXP || exp2[f] > SPH_SCALE_MAX_EXP) return SPH_EINVAL;
+        if ((f == SPH_F_A || f == SPH_F_DUDT) && exp2[f] != 0) return SPH_EINVAL;
+    }
+    for (int f = 0; f < SPH_NFIELDS; ++f) {
+        if (c->scale_exp[f] != exp2[f]) c->valid &= ~SPH_BIT(f);   // stored under the old scale
+        c->scale_exp[f] = exp2[f];
+    }
+    return SPH_OK;
+}
+
+sph_status sph_get_field_scale(const sph_ctx *c, int32_t *exp2_out)
+{
+    if (!c || !exp2_out) return SPH_EINVAL;
+    for (int f = 0; f < SPH_NFIELDS; ++f) exp2_out[f] = c->scale_exp[f];
     return SPH_OK;
 }
 

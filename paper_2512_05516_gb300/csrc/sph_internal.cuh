@@ -5,6 +5,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstddef>
 #include <cstdint>
 
@@ -61,10 +62,12 @@ struct LaunchCache {
     int grid = 0;
 };
 
-// Per-field view handed to kernels.
+// Per-field view handed to kernels: the SoA arrays, the storage format and
+// the decode factor 2^-e of the field's power-of-two storage scale.
 struct FieldRef {
     void *p[3];
     int fmt;
+    float dec;
 };
 
 // ---------------------------------------------------------------------------
@@ -255,10 +258,13 @@ struct sph_ctx {
     sph::DevStats *dstats = nullptr;
     void *soa[SPH_NFIELDS][3] = {};
     int prec[SPH_NFIELDS] = {};
+    int32_t scale_exp[SPH_NFIELDS] = {};   // storage scale 2^e of every field
     uint32_t valid = 0;
     uint64_t launches = 0;        // kernels launched through this context
 
     int32_t *perm() const { return vals[sorted_buf]; }
+    float enc(int f) const { return ldexpf(1.0f, scale_exp[f]); }     // value -> stored
+    float dec(int f) const { return ldexpf(1.0f, -scale_exp[f]); }    // stored -> value
     int32_t *slot_cell() const { return keys[sorted_buf]; }
 };
 

@@ -200,7 +200,11 @@ def sedov(nx: int = 256, ny: int = 256, nz: int = 128, seed: int = SEED_BASE + 3
     # h may double in the rarefied centre; the cell edge leaves that room
     ncell = int(math.floor(nz * s / (2.0 * headroom * h0)))
     cell = (nz * s) / ncell
-    return Workload("sedov", aos, box, h_cap=0.5 * cell, cell_edge=cell, newton_steps=5,
+    # fixed step: a quarter of the smoothing length over the hot particles'
+    # sound speed c = sqrt(gamma (gamma - 1) u)  (2.0e-6 at 256 x 256 x 128)
+    gamma = 5.0 / 3.0
+    dt = 0.25 * h0 / math.sqrt(gamma * (gamma - 1.0) * float(u.max()))
+    return Workload("sedov", aos, box, h_cap=0.5 * cell, cell_edge=cell, dt=dt, newton_steps=5,
                     meta={"m": m, "hot": hot, "h0": h0})
 
 

@@ -120,5 +120,21 @@ def test_calls_on_null_context_fail_cleanly(sph):
     assert sph.sph_get_stats(null)[0] == sph._capi.EINVAL
     assert sph.sph_set_tuning(null, sph.sph_tuning()) == sph._capi.EINVAL
     assert sph.sph_describe(null)[0] == sph._capi.EINVAL
+    assert sph.sph_set_field_scale(null, [0] * sph.SPH_NFIELDS) == sph._capi.EINVAL
+    assert sph.sph_get_field_scale(null)[0] == sph._capi.EINVAL
     sph.sph_destroy(null)
     assert sph.sph_status_str(-5).startswith("cell grid")
+
+
+def test_suggest_scale_puts_fp16_values_in_range(sph):
+    # the Sod particle mass (1/124)^3 is subnormal in FP16; the suggested
+    # exponent moves it 4 binades below FP16's top binade
+    m = (1.0 / 124.0) ** 3
+    e = sph.suggest_scale(m, "fp16")
+    assert 2.0 ** 11 <= m * 2.0 ** e < 2.0 ** 12
+    assert sph.suggest_scale(262144.0, "fp16") == 11 - 18
+    for fmt in ("fp32", "bf16", "m16", "m10"):
+        assert sph.suggest_scale(m, fmt) == 0
+    assert sph.suggest_scale(0.0, "fp16") == 0
+    assert sph.suggest_scale(1e-300, "fp16") == sph.SCALE_MAX_EXP
+    assert sph.scale_array({"m": 5, "u": -3}) == [0, 0, 0, 5, 0, 0, -3, 0, 0, 0]

@@ -115,3 +115,79 @@ def test_fp16_positions_relative_to_cell(orc):
     xq, _ = orc.cell_relative(wl.col("x"), wl.box, s.nc, "fp16")
     o = orc.density(xq, wl.col("m"), wl.col("h"), wl.box, wl.eta, wl.h_cap, 5)
     assert (np.abs(out[:, 11] - o["rho"]) / o["rho"]).max() <= 1e-5
+
+
+def test_fp16_storage_scale_on_a_subnormal_mass(orc):
+    # lattice 48: m = 1/48^3 = 9.0e-6, an FP16 subnormal.  Unscaled, the
+    # stored mass loses ~0.3 %; with the power-of-two storage scale the
+    # codes are the oracle's codes of m 2^e, the density matches the
+    # oracle on those inputs (mode Q) to FP32 accuracy, and against FP64
+    # (mode T) it stays within 1e-3.
+    wl = sph_inputs.sod(n_lattice=48, seed=44)
+    m, h = wl.col("m"), wl.col("h")
+    e = sph_mod.suggest_scale(float(m.max()), "fp16")
+    assert e > 0
+    s = make_sph(wl)
+    s.bin_cells(wl.cell_edge)
+    t = orc.density(wl.col("x"), m, h, wl.box, wl.eta, wl.h_cap, 5)
+    res = {}
+    for scaled in (False, True):
+        s.set_scale({"m": e if scaled else 0})
+        assert s.scale()["m"] == (e if scaled else 0)
+        s.aos_to_soa(sph_mod.FIELDS_DENSITY, {"m": "fp16"})
+        perm = s.perm().cpu().numpy()
+        raw = s.soa_raw("m").cpu().numpy().view(np.uint16).astype(np.uint32)
+        mq, code = orc.quantize(m, "fp16", e if scaled else 0)
+        assert np.array_equal(raw, code[perm])
+        s.density(5)
+        s.soa_to_aos(sph_mod.mask("rho", "h"))
+        out = s.aos.cpu().numpy()
+        o = orc.density(wl.col("x"), mq, h, wl.box, wl.eta, wl.h_cap, 5)
+        assert (np.abs(out[:, 11] - o["rho"]) / o["rho"]).max() <= 1e-5
+        res[scaled] = (np.abs(out[:, 11] - t["rho"]) / t["rho"]).max()
+        s.aos.copy_(torch.from_numpy(np.ascontiguousarray(wl.aos)).cuda())
+    assert res[False] > 1e-3
+    assert res[True] <= 1e-3
+
+
+def test_storage_scale_in_kick_drift_and_write_back(orc):
+    # scaled v and u: kick/drift decodes, updates and re-encodes under the
+    # scale, and the write-back decodes again; u reaches 3e5, above FP16's
+    # largest finite 65504, and stays finite only through the scale
+    wl = sph_inputs.random_cloud(4000, seed=45, vel=2.0)
+    wl.h_cap = 0.05
+    rng = np.random.default_rng(5)
+    wl.col("u")[:] = rng.uniform(1e3, 3e5, wl.n)
+    wl.col("a")[:] = rng.uniform(-10, 10, (wl.n, 3))
+    rec = np.zeros((wl.n, 16))
+    rec[:, :14] = wl.aos
+    rec[:, 14] = rng.uniform(-1e4, 1e4, wl.n)               # du/dt, at byte 112
+    layout = sph_mod.make_layout({**sph_mod.RECORD_112, "dudt": 112}, 128)
+    s = make_sph(wl, aos=torch.from_numpy(rec).cuda(), layout=layout)
+    s.bin_cells(wl.cell_edge)
+    eu = sph_mod.suggest_scale(float(wl.col("u").max()), "fp16")
+    ev = sph_mod.suggest_scale(float(np.abs(wl.col("v")).max()), "fp16")
+    assert eu < 0 < ev
+    s.set_scale({"u": eu, "v": ev})
+    s.aos_to_soa(sph_mod.mask("x", "v", "a", "u", "dudt"), {"v": "fp16", "u": "fp16"})
+    dt = 1e-3
+    s.kick_drift(dt, dt)
+    s.soa_to_aos(sph_mod.mask("v", "u"))
+    out = s.aos.cpu().numpy()
+    st = s.stats()
+    assert st["error_bits"] == 0
+    vq = _qs(orc, wl.col("v"), "fp16", ev)
+    uq = _qs(orc, wl.col("u"), "fp16", eu)
+    a32 = wl.col("a").astype(np.float32).astype(np.float64)
+    du32 = rec[:, 14].astype(np.float32).astype(np.float64)
+    v_new = _qs(orc, vq + np.float32(dt) * a32, "fp16", ev)
+    u_new = _qs(orc, uq + np.float32(dt) * du32, "fp16", eu)
+    # within one FP16 unit of the scaled format (the FP32 update may round
+    # differently from the FP64 one at a tie)
+    assert np.all(np.isfinite(out[:, 12]))
+    assert np.all(np.abs(out[:, 3:6] - v_new) <= 2.0 ** -10 * np.abs(v_new))
+    assert np.all(np.abs(out[:, 12] - u_new) <= 2.0 ** -10 * np.abs(u_new))
+
+
+def _qs(orc, vals, fmt, e):
+    return orc.quantize(np.asarray(vals, dtype=np.float64).ravel(), fmt, e)[0].reshape(np.shape(vals))

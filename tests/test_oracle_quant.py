@@ -107,3 +107,23 @@ def test_pack_unpack_roundtrip(orc, bits):
     # 32 consecutive codes fill exactly `bits` words
     w32 = orc.pack_bits(codes[:32], bits)
     assert w32.size == bits
+
+
+def test_scaled_half_keeps_eleven_bits_of_a_subnormal_mass(orc):
+    # Sod's particle mass (1/124)^3 = 5.2e-7 is an FP16 subnormal (spacing
+    # 2^-24): stored unscaled it keeps 4 significant bits; under the storage
+    # scale 2^20 it is a normal half with 11.  The code is numpy's half of
+    # the scaled FP32 value, and the decoded value is within half an ulp.
+    m = (1.0 / 124.0) ** 3
+    q0, _ = orc.quantize([m], "fp16")
+    assert abs(q0[0] - m) / m > 1e-2                      # the unscaled damage
+    assert q0[0] == round(m / 2.0 ** -24) * 2.0 ** -24    # nearest subnormal
+    q, code = orc.quantize([m], "fp16", exp2=20)
+    ref = np.float32(m * 2.0 ** 20).astype(np.float16)
+    assert code[0] == int(ref.view(np.uint16))
+    assert q[0] == float(ref) * 2.0 ** -20
+    assert abs(q[0] - m) <= 2.0 ** -11 * 2.0 ** np.floor(np.log2(m))
+    # a negative exponent brings Sedov's peak energy 262144 under 65504
+    q, _ = orc.quantize([262144.0, 1e-6], "fp16", exp2=-7)
+    assert q[0] == 262144.0
+    assert q[1] == 0.0                                    # 1e-6 * 2^-7 underflows
