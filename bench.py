@@ -156,15 +156,14 @@ def run_ours(args, rank, world):
     s = sph.Sph(aos, sph.layout_112(), params, int(np.prod(nc)), 0, stream=stream)
     prec = prec_of(args)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    names = ["bin", "aos_to_soa", "density", "force", "kick_drift", "soa_to_aos"]
+    names = ["bin", "aos_to_soa", "density", "force", "kick_drift_writeback"]
 
     def step(ev=None):
         calls = [lambda: s.bin_cells(wl.cell_edge),
                  lambda: s.aos_to_soa(sph.FIELDS_FORCE, prec),
                  lambda: s.density(wl.newton_steps),
                  lambda: s.force(),
-                 lambda: s.kick_drift(wl.dt, wl.dt),
-                 lambda: s.soa_to_aos(sph.FIELDS_OUTPUT)]
+                 lambda: s.kick_drift_writeback(wl.dt, wl.dt, sph.FIELDS_OUTPUT)]
         for i, fn in enumerate(calls):
             if ev is not None:
                 ev[i][0].record(stream)
@@ -254,7 +253,8 @@ def run_ours(args, rank, world):
         hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
     except Exception:
         pass
-    bytes_pp = {"aos_to_soa": 116, "kick_drift": 100, "soa_to_aos": 124}
+    pb = PREC_BYTES[args.prec]
+    bytes_pp = algorithmic_bytes(pb, 4)
     kernels = {}
     for nm in names:
         ms = statistics.mean(kern_ms[nm])
@@ -274,14 +274,24 @@ def run_ours(args, rank, world):
 
 
 # ----------------------------------------------------------------- long run (HBM-bound rows)
-def algorithmic_bytes(prec_bytes: int, pos_bytes: int):
+PREC_BYTES = {"fp32": 4, "bf16": 2, "fp16": 2, "m16": 25 / 8, "m10": 19 / 8}
+
+
+def algorithmic_bytes(prec_bytes: float, pos_bytes: float):
     """Minimum bytes per particle of the memory-bound calls (112-byte FP64
     record; v, m, h, u stored in `prec_bytes`, positions in `pos_bytes`;
-    a and du/dt FP32; 4-byte permutation and key per slot)."""
-    conv = (72 + 8) + 3 * pos_bytes + 3 * prec_bytes + 3 * prec_bytes
-    kick = (24 + 3 * prec_bytes + 12 + prec_bytes + 4 + 4) + (24 + 3 * prec_bytes + prec_bytes)
-    back = (3 * prec_bytes + 12 + prec_bytes + 4 + prec_bytes + 4 + 4) + 80
-    return {"aos_to_soa": conv, "kick_drift": kick, "soa_to_aos": back}
+    a, du/dt, rho, P FP32; 4-byte permutation and 4-byte key per slot).
+      aos_to_soa            read x, v, m, h, u (72 B) + perm, key; write the SoA
+      kick_drift            read x (AoS), v, a, u, du/dt, perm; write x, v, u
+      soa_to_aos            read v, a, h, rho, u, P, perm; write them (80 B)
+      kick_drift_writeback  read x, v, a, u, du/dt, h, rho, P, perm; write x,
+                            v, a, h, rho, u, P (104 B) to the AoS"""
+    p = prec_bytes
+    conv = (72 + 8) + 3 * pos_bytes + 3 * p + 3 * p
+    kick = (24 + 3 * p + 12 + p + 4 + 4) + (24 + 3 * p + p)
+    back = (3 * p + 12 + p + 4 + p + 4 + 4) + 80
+    fused = (24 + 3 * p + 12 + p + 4 + p + 4 + 4 + 4) + 104
+    return {"aos_to_soa": conv, "kick_drift": kick, "soa_to_aos": back, "kick_drift_writeback": fused}
 
 
 def run_long_run(steps: int = 3, graph_steps: int = 10):
@@ -302,10 +312,10 @@ def run_long_run(steps: int = 3, graph_steps: int = 10):
                              eps=wl.eps_av, eta=wl.eta, h_max=wl.h_cap)
     s = sph.Sph(aos, sph.layout_112(), params, int(np.prod(nc)), sph.WS_REORDER, stream=stream)
     prec = {"x": "fp16", "v": "fp16", "m": "fp16", "h": "fp16", "u": "fp16"}
-    names = ["bin", "aos_to_soa", "density", "force", "kick_drift", "soa_to_aos"]
+    names = ["bin", "aos_to_soa", "density", "force", "kick_drift_writeback"]
     calls = [lambda: s.bin_cells(wl.cell_edge), lambda: s.aos_to_soa(sph.FIELDS_FORCE, prec),
-             lambda: s.density(0), lambda: s.force(), lambda: s.kick_drift(wl.dt, wl.dt),
-             lambda: s.soa_to_aos(sph.FIELDS_OUTPUT)]
+             lambda: s.density(0), lambda: s.force(),
+             lambda: s.kick_drift_writeback(wl.dt, wl.dt, sph.FIELDS_OUTPUT)]
     ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in names]
           for _ in range(steps)]
     with torch.cuda.stream(stream):
@@ -339,6 +349,21 @@ def run_long_run(steps: int = 3, graph_steps: int = 10):
     if st["error_bits"] & (sph.ERR_NONFINITE | sph.ERR_OUTSIDE):
         raise RuntimeError(f"long run: device error bits {st['error_bits']}")
     pairs = (st["pairs_density"] + st["pairs_force"]) / graph_steps
+    # S6 and S7 as separate calls (kick/drift alone, then the write-back)
+    sep = ["kick_drift", "soa_to_aos"]
+    ev_sep = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in sep]
+              for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        for k in range(steps):
+            for fn in calls[:4]:
+                fn()
+            for i, fn in enumerate([lambda: s.kick_drift(wl.dt, wl.dt), lambda: s.soa_to_aos(sph.FIELDS_OUTPUT)]):
+                ev_sep[k][i][0].record(stream)
+                fn()
+                ev_sep[k][i][1].record(stream)
+        stream.synchronize()
+    for i, nm in enumerate(sep):
+        ms[nm] = statistics.mean(ev_sep[k][i][0].elapsed_time(ev_sep[k][i][1]) for k in range(steps))
     # the comparison: an FP32 SoA kept across steps needs no conversion or
     # write-back; its step is binning + density + force + kick/drift on FP32
     # storage (timed per call; the FP32 conversion that refreshes the SoA
@@ -367,7 +392,7 @@ def run_long_run(steps: int = 3, graph_steps: int = 10):
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6753.1
     bpp = algorithmic_bytes(2, 2)
     kern = {}
-    for nm in names:
+    for nm in names + sep:
         row = {"ms": ms[nm]}
         if nm in bpp:
             gbs = bpp[nm] * n / (ms[nm] / 1e3) / 1e9
@@ -377,7 +402,7 @@ def run_long_run(steps: int = 3, graph_steps: int = 10):
     s.close()
     del aos
     torch.cuda.empty_cache()
-    fp16_step = sum(ms.values())
+    fp16_step = sum(ms[nm] for nm in names)
     fp32_step = sum(ms32.values())
     return {"workload": "long_run_33554432", "particles": n, "storage": "fp16 (x, v, m, h, u)",
             "ms_per_step_graph": graph_ms, "pairs_per_s": pairs / (graph_ms / 1e3),

@@ -10,7 +10,9 @@
  *   U   unpack reduced precision / U^T pack         -> per-field `prec`
  *   f   the compute kernel                          -> sph_density, sph_force,
  *                                                      sph_kick_drift
- *   C^T N^T U^T  widen and scatter back to the AoS  -> sph_soa_to_aos
+ *   C^T N^T U^T  widen and scatter back to the AoS  -> sph_soa_to_aos (or fused
+ *                                                      with the kick/drift:
+ *                                                      sph_kick_drift_writeback)
  *   M   host <-> device move                        -> sph_aos_upload/download
  * The GPU-side variant of Eq. 12 (convert on the device, "in-place" in
  * Section 6.3) is what one time step of these calls performs.
@@ -274,6 +276,18 @@ sph_status sph_kick_drift(sph_ctx *ctx, double dt_kick, double dt_drift);
  * updates them in place).  Errors: SPH_EINVAL (X requested or field absent
  * from the layout), SPH_ESTATE (field not current), SPH_ECUDA. */
 sph_status sph_soa_to_aos(sph_ctx *ctx, uint32_t fields);
+
+/* S6 + S7 in one pass over the records: the same results in the AoS as
+ * sph_kick_drift(dt_kick, dt_drift) followed by sph_soa_to_aos(fields) --
+ * bit for bit, v and u written as their storage format holds them after the
+ * kick -- but each record is visited once, so the sectors that x and the
+ * written fields share are written whole.  The kicked v and u go to the AoS
+ * only: afterwards the SoA copies of X, V and U are stale (convert again
+ * before reading them on the device).  `fields` as for sph_soa_to_aos.
+ * Errors: SPH_EINVAL (fields empty, X requested or a field absent from the
+ * layout, non-finite dt), SPH_ESTATE (A, DUDT, V, U or a requested field
+ * not current), SPH_ECUDA. */
+sph_status sph_kick_drift_writeback(sph_ctx *ctx, double dt_kick, double dt_drift, uint32_t fields);
 
 /* Copy the device counters to *out.  Synchronises the context's stream.
  * Returns SPH_ENUMERIC when error_bits has SPH_ERR_NONFINITE or

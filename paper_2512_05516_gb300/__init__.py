@@ -78,6 +78,10 @@ def sph_soa_to_aos(ctx, fields: int) -> int:
     return _lib.sph_soa_to_aos(ctx, fields)
 
 
+def sph_kick_drift_writeback(ctx, dt_kick: float, dt_drift: float, fields: int) -> int:
+    return _lib.sph_kick_drift_writeback(ctx, float(dt_kick), float(dt_drift), fields)
+
+
 def sph_set_field_scale(ctx, exp2) -> int:
     arr = (C.c_int32 * SPH_NFIELDS)(*[int(e) for e in exp2])
     return _lib.sph_set_field_scale(ctx, arr)
@@ -282,16 +286,19 @@ class Sph:
     def soa_to_aos(self, fields: int):
         _check(sph_soa_to_aos(self.ctx, fields), "sph_soa_to_aos")
 
+    def kick_drift_writeback(self, dt_kick: float, dt_drift: float, fields: int = FIELDS_OUTPUT):
+        _check(sph_kick_drift_writeback(self.ctx, dt_kick, dt_drift, fields), "sph_kick_drift_writeback")
+
     def step(self, dt: float, newton_steps: int = 5, prec=None, cell_edge: float = 0.0,
              reorder: bool = False, out_fields: int = FIELDS_OUTPUT):
-        """One SPH time step: bin, convert, density (+h), force, kick/drift,
-        write back (the in-place GPU pipeline of the paper's Section 6.3)."""
+        """One SPH time step: bin, convert, density (+h), force, kick/drift
+        fused with the write-back (the in-place GPU pipeline of the paper's
+        Section 6.3)."""
         self.bin_cells(cell_edge, reorder)
         self.aos_to_soa(FIELDS_FORCE, prec)
         self.density(newton_steps)
         self.force()
-        self.kick_drift(dt, dt)
-        self.soa_to_aos(out_fields)
+        self.kick_drift_writeback(dt, dt, out_fields)
 
     # --- inspection
     def stats(self) -> dict:

@@ -79,6 +79,7 @@ PROTOTYPES = {
     "sph_force": (C.c_int, [_P]),
     "sph_kick_drift": (C.c_int, [_P, C.c_double, C.c_double]),
     "sph_soa_to_aos": (C.c_int, [_P, C.c_uint32]),
+    "sph_kick_drift_writeback": (C.c_int, [_P, C.c_double, C.c_double, C.c_uint32]),
     "sph_set_field_scale": (C.c_int, [_P, C.POINTER(C.c_int32)]),
     "sph_get_field_scale": (C.c_int, [_P, C.POINTER(C.c_int32)]),
     "sph_get_stats": (C.c_int, [_P, C.POINTER(sph_stats)]),

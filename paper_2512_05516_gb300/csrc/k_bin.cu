@@ -260,6 +260,17 @@ __global__ void k_gather_records(const uint8_t *aos, uint8_t *dst, const int32_t
     for (int w = lane; w < stride / 8; w += 32) d[w] = src[w];
 }
 
+// cell origins k * edge_d per axis (FP64 product, as the conversion's
+// cell-relative offsets define them), kMaxCellsPerAxis entries per axis
+__global__ void k_origins(double *origin, int3 nc, double3 edge)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= kMaxCellsPerAxis) return;
+    origin[k] = k < nc.x ? __dmul_rn((double)k, edge.x) : 0.0;
+    origin[kMaxCellsPerAxis + k] = k < nc.y ? __dmul_rn((double)k, edge.y) : 0.0;
+    origin[2 * kMaxCellsPerAxis + k] = k < nc.z ? __dmul_rn((double)k, edge.z) : 0.0;
+}
+
 __global__ void k_iota(int32_t *p, int64_t n)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -294,6 +305,10 @@ cudaError_t run_binning(sph_ctx *c, int reorder)
     if ((e = cudaMemsetAsync(c->cell_count, 0, sizeof(int32_t) * nkeys, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(&c->dstats->max_occ, 0, sizeof(int), s)) != cudaSuccess) return e;
     c->sorted_buf = 0;
+    k_origins<<<kMaxCellsPerAxis / 256, 256, 0, s>>>(c->origin, make_int3(c->nc[0], c->nc[1], c->nc[2]),
+                                                     make_double3(c->edge[0], c->edge[1], c->edge[2]));
+    c->launches += 1;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (n > 0) {
         CellArgs a;
         a.aos = c->aos;

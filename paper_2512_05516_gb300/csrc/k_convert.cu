@@ -4,148 +4,114 @@
 //   C^T N^T U^T    decode SoA values, widen to the AoS element type, scatter
 //                  to the particle's record
 // One thread per sorted slot.  A warp moves the records of its 32 slots
-// through shared memory: lane-contiguous loads (or stores) of the 8-byte
-// words (4-byte units) a call touches, so each instruction covers whole
-// records instead of one word of 32 records; each lane then reads (or
-// writes) its own record's fields there.  All 32 lanes stay alive so that
-// packed formats can be written warp-cooperatively.
-#include "sph_internal.cuh"
+// through shared memory in 16-byte chunks (8-byte ones when the record size
+// is not a multiple of 16), lane-contiguous, so each load or store
+// instruction covers whole records; each lane then reads (or writes) its own
+// record's fields there.  The fields a call moves are unrolled on the host
+// into a table of scalar components.  All 32 lanes stay alive so that packed
+// formats can be written warp-cooperatively.  No FP64 arithmetic: widening
+// and narrowing work on the bit patterns, and the cell-relative offsets of
+// the positions are formed exactly in integer arithmetic.
+#include <cstring>
+
+#include "k_records.cuh"
 
 namespace sph {
 namespace {
 
-constexpr unsigned FULL = 0xffffffffu;
 constexpr int kConvThreads = 128;
+constexpr int kMaxComp = 3 * SPH_NFIELDS;
+
+// one scalar component a call moves
+struct Comp {
+    int32_t off;                 // byte offset in the record
+    int32_t kind;                // 0: FP64 value, 1: FP32 value, 2 + a: FP64 position, axis a
+    int32_t fmt;                 // storage format
+    float scl;                   // 2^e on the way in, 2^-e on the way out
+    void *soa;
+};
 
 struct ConvArgs {
     uint8_t *aos;
     int64_t n;
-    int32_t W;                   // record words (record_bytes / 8)
-    int32_t Wp;                  // words per record in shared memory (odd: fewer bank conflicts)
-    uint64_t wmask;              // record words the call reads
-    uint64_t umask[2];           // 4-byte units the call writes (write-back)
+    RecGeom g;
+    ChunkRun run;                // chunks the gather reads / the write-back writes
+    uint64_t umask[2];           // 4-byte units the write-back writes
     const int32_t *perm;
-    const int32_t *slot_cell;
-    int32_t nc[3];
-    int32_t s3;                  // sub-cells per cell
-    double edge[3];
-    int nf;
-    int fid[SPH_NFIELDS];
-    int off[SPH_NFIELDS];
-    int type[SPH_NFIELDS];
-    int fmt[SPH_NFIELDS];
-    float scl[SPH_NFIELDS];      // storage scale: 2^e on the way in, 2^-e on the way out
-    int nco[SPH_NFIELDS];
-    void *soa[SPH_NFIELDS][3];
+    const int32_t *slot_cell;    // key = cell * s^3 + sub-cell
+    int32_t lg_s3;
+    uint64_t m_nc0, m_nc1;       // magic divisors for nc_x, nc_y
+    int32_t nc0, nc1;
+    const double *origin[3];     // cell origin k * (L / nc) per axis
+    bool has_x;
+    int ncomp;
+    Comp comp[kMaxComp];
 };
 
-constexpr int kLoadBatch = 8;    // record words in flight per lane
-
-// Copy the words in `wmask` of the warp's 32 records (record index o of each
-// lane, -1 for none) into rec[r * Wp + w], kLoadBatch loads in flight per lane.
-__device__ __forceinline__ void load_records(const uint64_t *aos64, uint64_t *rec, int64_t o, int W, int Wp,
-                                             uint64_t wmask, int lane)
+template <typename T>
+__global__ void __launch_bounds__(kConvThreads, 12) k_aos_to_soa(ConvArgs a)
 {
-    int r = 0, w = lane;
-    while (w >= W) { w -= W; ++r; }
-    for (int idx0 = 0; idx0 < 32 * W; idx0 += 32 * kLoadBatch) {
-        uint64_t buf[kLoadBatch];
-        int dst[kLoadBatch];
-#pragma unroll
-        for (int b = 0; b < kLoadBatch; ++b) {
-            const int idx = idx0 + 32 * b + lane;
-            dst[b] = -1;
-            const int64_t orr = __shfl_sync(FULL, o, r < 32 ? r : 31);
-            if (idx < 32 * W && orr >= 0 && ((wmask >> w) & 1ull)) {
-                buf[b] = aos64[orr * W + w];
-                dst[b] = r * Wp + w;
-            }
-            w += 32;
-            while (w >= W) { w -= W; ++r; }
-        }
-#pragma unroll
-        for (int b = 0; b < kLoadBatch; ++b)
-            if (dst[b] >= 0) rec[dst[b]] = buf[b];
-    }
-    __syncwarp();
-}
-
-// Store the 4-byte units in `umask` of the warp's 32 records from shared memory.
-__device__ __forceinline__ void store_records(uint32_t *aos32, const uint32_t *rec32, int64_t o, int W, int Wp,
-                                              const uint64_t umask[2], int lane)
-{
-    __syncwarp();
-    const int U = 2 * W, Up = 2 * Wp;
-    int r = 0, u = lane;
-    while (u >= U) { u -= U; ++r; }
-    for (int idx = lane; idx < 32 * U; idx += 32) {
-        const int64_t orr = __shfl_sync(FULL, o, r);
-        if (orr >= 0 && ((umask[u >> 6] >> (u & 63)) & 1ull)) aos32[orr * U + u] = rec32[r * Up + u];
-        u += 32;
-        while (u >= U) { u -= U; ++r; }
-    }
-}
-
-__global__ void __launch_bounds__(kConvThreads) k_aos_to_soa(ConvArgs a)
-{
-    extern __shared__ uint64_t smem[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *smem = reinterpret_cast<T *>(smem_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint64_t *rec = smem + (size_t)warp * 32 * a.Wp;
+    T *rec = smem + (size_t)warp * 32 * a.g.Up;
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool ok = k < a.n;
     const int64_t o = ok ? a.perm[k] : -1;
-    const int32_t key = ok ? a.slot_cell[k] : 0;     // issued before the record loads
-    load_records((const uint64_t *)a.aos, rec, o, a.W, a.Wp, a.wmask, lane);
-    const uint8_t *mine = (const uint8_t *)(rec + lane * a.Wp);
-    for (int j = 0; j < a.nf; ++j) {
-        const int f = a.fid[j];
-        double org[3] = {0.0, 0.0, 0.0};
-        if (f == SPH_F_X && ok) {
-            // cell-relative positions: offset from k_d * (L_d / nc_d), in FP64
-            int32_t cid = key / a.s3;                // key = cell * s^3 + sub-cell
-            int32_t kx = cid % a.nc[0];
-            int32_t t = cid / a.nc[0];
-            int32_t ky = t % a.nc[1];
-            int32_t kz = t / a.nc[1];
-            org[0] = (double)kx * a.edge[0];
-            org[1] = (double)ky * a.edge[1];
-            org[2] = (double)kz * a.edge[2];
-        }
-        for (int c = 0; c < a.nco[j]; ++c) {
-            float v = 0.0f;
-            if (ok) {
-                if (a.type[j] == SPH_AOS_F64) {
-                    double d = *(const double *)(mine + a.off[j] + 8 * c);
-                    if (f == SPH_F_X) d = __dsub_rn(d, org[c]);     // the only FP64 arithmetic here
-                    v = d2f_bits_rn(d);
+    double org0 = 0.0, org1 = 0.0, org2 = 0.0;
+    if (a.has_x && ok) {
+        // the cell's coordinates from its key, then its origin (tables)
+        const uint32_t cell = (uint32_t)a.slot_cell[k] >> a.lg_s3;
+        const uint32_t t = div_magic(cell, a.m_nc0);
+        const uint32_t kx = cell - t * (uint32_t)a.nc0;
+        const uint32_t kz = div_magic(t, a.m_nc1);
+        const uint32_t ky = t - kz * (uint32_t)a.nc1;
+        org0 = __ldg(a.origin[0] + kx);
+        org1 = __ldg(a.origin[1] + ky);
+        org2 = __ldg(a.origin[2] + kz);
+    }
+    load_chunks<T>(reinterpret_cast<const T *>(a.aos), rec, o, a.g, a.run, lane);
+    const unsigned char *mine = reinterpret_cast<const unsigned char *>(rec + lane * a.g.Up);
+    for (int i = 0; i < a.ncomp; ++i) {
+        const Comp cp = a.comp[i];
+        float v = 0.0f;
+        if (ok) {
+            if (cp.kind == 1) {
+                v = *reinterpret_cast<const float *>(mine + cp.off);
+            } else {
+                const double d = *reinterpret_cast<const double *>(mine + cp.off);
+                if (cp.kind >= 2) {
+                    const double og = cp.kind == 2 ? org0 : (cp.kind == 3 ? org1 : org2);
+                    v = cell_offset_f32(d, og);
                 } else {
-                    v = *(const float *)(mine + a.off[j] + 4 * c);
+                    v = d2f_bits_rn(d);
                 }
             }
-            st_any(a.soa[j][c], a.fmt[j], k, v * a.scl[j], ok, a.n);
         }
+        st_any(cp.soa, cp.fmt, k, v * cp.scl, ok, a.n);
     }
 }
 
-__global__ void __launch_bounds__(kConvThreads) k_soa_to_aos(ConvArgs a)
+template <typename T>
+__global__ void __launch_bounds__(kConvThreads, 12) k_soa_to_aos(ConvArgs a)
 {
-    extern __shared__ uint64_t smem[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *smem = reinterpret_cast<T *>(smem_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint64_t *rec = smem + (size_t)warp * 32 * a.Wp;
+    T *rec = smem + (size_t)warp * 32 * a.g.Up;
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool ok = k < a.n;
     const int64_t o = ok ? a.perm[k] : -1;
-    uint8_t *mine = (uint8_t *)(rec + lane * a.Wp);
+    unsigned char *mine = reinterpret_cast<unsigned char *>(rec + lane * a.g.Up);
     if (ok) {
-        for (int j = 0; j < a.nf; ++j) {
-            for (int c = 0; c < a.nco[j]; ++c) {
-                const float v = ld_val(a.soa[j][c], a.fmt[j], k) * a.scl[j];
-                if (a.type[j] == SPH_AOS_F64) *(double *)(mine + a.off[j] + 8 * c) = f2d_bits(v);
-                else *(float *)(mine + a.off[j] + 4 * c) = v;
-            }
+        for (int i = 0; i < a.ncomp; ++i) {
+            const Comp cp = a.comp[i];
+            const float v = ld_val(cp.soa, cp.fmt, k) * cp.scl;
+            if (cp.kind == 1) *reinterpret_cast<float *>(mine + cp.off) = v;
+            else *reinterpret_cast<double *>(mine + cp.off) = f2d_bits(v);
         }
     }
-    store_records((uint32_t *)a.aos, (const uint32_t *)rec, o, a.W, a.Wp, a.umask, lane);
+    store_chunks<T>(reinterpret_cast<T *>(a.aos), rec, o, a.g, a.run, a.umask, lane);
 }
 
 __global__ void __launch_bounds__(256) k_pack(const float *src, void *dst, int fmt, int64_t n)
@@ -158,68 +124,74 @@ __global__ void __launch_bounds__(256) k_pack(const float *src, void *dst, int f
 ConvArgs make_args(sph_ctx *c, uint32_t fields, bool to_soa)
 {
     ConvArgs a;
+    std::memset(&a, 0, sizeof(a));
     a.aos = c->aos;
     a.n = c->n;
-    a.W = c->layout.record_bytes / 8;
-    a.Wp = a.W | 1;
-    a.wmask = 0;
-    a.umask[0] = a.umask[1] = 0;
+    const int cb = record_chunk_bytes(c->layout.record_bytes);
+    a.g = rec_geom(c->layout.record_bytes, cb);
     a.perm = c->perm();
     a.slot_cell = c->slot_cell();
-    a.s3 = c->sub * c->sub * c->sub;
-    for (int k = 0; k < 3; ++k) {
-        a.nc[k] = c->nc[k];
-        a.edge[k] = c->edge[k];
-    }
-    a.nf = 0;
+    a.lg_s3 = c->sub == 2 ? 3 : 0;
+    a.nc0 = c->nc[0];
+    a.nc1 = c->nc[1];
+    a.m_nc0 = magic64((uint32_t)c->nc[0]);
+    a.m_nc1 = magic64((uint32_t)c->nc[1]);
+    for (int d = 0; d < 3; ++d) a.origin[d] = c->origin + d * kMaxCellsPerAxis;
+    a.has_x = false;
+    a.ncomp = 0;
+    uint64_t cmask = 0;
     for (int f = 0; f < SPH_NFIELDS; ++f) {
         if (!(fields & SPH_BIT(f))) continue;
-        int j = a.nf++;
-        a.fid[j] = f;
-        a.off[j] = c->layout.offset[f];
-        a.type[j] = c->layout.type[f];
-        a.fmt[j] = c->prec[f];
-        a.scl[j] = to_soa ? c->enc(f) : c->dec(f);
-        a.nco[j] = ncomp(f);
-        for (int k = 0; k < 3; ++k) a.soa[j][k] = c->soa[f][k];
-        const int es = a.type[j] == SPH_AOS_F64 ? 8 : 4;
-        const int b0 = a.off[j], b1 = a.off[j] + es * a.nco[j];     // byte range [b0, b1)
-        for (int w = b0 / 8; w <= (b1 - 1) / 8; ++w) a.wmask |= 1ull << w;
+        const bool f64 = c->layout.type[f] == SPH_AOS_F64;
+        const int es = f64 ? 8 : 4;
+        for (int comp = 0; comp < ncomp(f); ++comp) {
+            Comp &cp = a.comp[a.ncomp++];
+            cp.off = c->layout.offset[f] + es * comp;
+            cp.kind = !f64 ? 1 : (f == SPH_F_X ? 2 + comp : 0);
+            cp.fmt = c->prec[f];
+            cp.scl = to_soa ? c->enc(f) : c->dec(f);
+            cp.soa = c->soa[f][comp];
+        }
+        if (f == SPH_F_X) a.has_x = true;
+        const int b0 = c->layout.offset[f], b1 = b0 + es * ncomp(f);     // byte range [b0, b1)
+        for (int q = b0 / cb; q <= (b1 - 1) / cb; ++q) cmask |= 1ull << q;
         for (int u = b0 / 4; u <= (b1 - 1) / 4; ++u) a.umask[u >> 6] |= 1ull << (u & 63);
     }
+    a.run = chunk_run(to_soa ? cmask : chunks_of_units(a.umask, cb));
     return a;
 }
 
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-inline size_t conv_smem(const ConvArgs &a) { return (size_t)(kConvThreads / 32) * 32 * a.Wp * sizeof(uint64_t); }
+template <typename T>
+cudaError_t launch_conv(sph_ctx *c, const ConvArgs &a, bool to_soa)
+{
+    const size_t smem = (size_t)(kConvThreads / 32) * 32 * a.g.Up * sizeof(T);
+    cudaError_t e;
+    auto kern = to_soa ? k_aos_to_soa<T> : k_soa_to_aos<T>;
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+        return e;
+    kern<<<blocks_for(c->n, kConvThreads), kConvThreads, smem, c->stream>>>(a);
+    c->launches += 1;
+    return cudaGetLastError();
+}
 
 }  // namespace
 
 cudaError_t run_aos_to_soa(sph_ctx *c, uint32_t fields)
 {
     if (c->n == 0) return cudaSuccess;
-    ConvArgs a = make_args(c, fields, true);
-    const size_t smem = conv_smem(a);
-    cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_aos_to_soa, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-        return e;
-    k_aos_to_soa<<<blocks_for(c->n, kConvThreads), kConvThreads, smem, c->stream>>>(a);
-    c->launches += 1;
-    return cudaGetLastError();
+    const ConvArgs a = make_args(c, fields, true);
+    return record_chunk_bytes(c->layout.record_bytes) == 16 ? launch_conv<uint4>(c, a, true)
+                                                            : launch_conv<uint2>(c, a, true);
 }
 
 cudaError_t run_soa_to_aos(sph_ctx *c, uint32_t fields)
 {
     if (c->n == 0) return cudaSuccess;
-    ConvArgs a = make_args(c, fields, false);
-    const size_t smem = conv_smem(a);
-    cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_soa_to_aos, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-        return e;
-    k_soa_to_aos<<<blocks_for(c->n, kConvThreads), kConvThreads, smem, c->stream>>>(a);
-    c->launches += 1;
-    return cudaGetLastError();
+    const ConvArgs a = make_args(c, fields, false);
+    return record_chunk_bytes(c->layout.record_bytes) == 16 ? launch_conv<uint4>(c, a, false)
+                                                            : launch_conv<uint2>(c, a, false);
 }
 
 // pack an FP32 staging array into field f's packed stream

@@ -1,23 +1,42 @@
-// S6: the paper's linear kernels Kick and Drift (Section 6), fused.
-//   v += a dt_kick, u += du/dt dt_kick       FP32, in the SoA (storage format
-//                                            of v and u applied on the store)
-//   x += v dt_drift, wrapped into [0, L)      FP64, in place in the AoS record
-// One thread per sorted slot; warps stay whole for packed v/u stores.  The
-// three FP64 position words of the warp's 32 records are loaded and stored
-// lane-contiguously through shared memory.
-#include "sph_internal.cuh"
+// S6: the paper's linear kernels Kick and Drift (Section 6), fused, and
+// optionally fused with S7, the write-back of the step's results.
+//   v += a dt_kick, u += du/dt dt_kick       FP32 (storage format of v and u
+//                                            applied to the result)
+//   x += v dt_drift, wrapped into [0, L)      FP64, in the AoS record
+// One thread per sorted slot.  The warp's 32 records move through shared
+// memory in 16-byte chunks (k_records.cuh): the chunks holding x are loaded,
+// the new x (and, with a write-back, every written field) is placed in the
+// record image, and the written 4-byte units go back lane-contiguously.
+// With the write-back, x and the fields share one pass over the records, so
+// the sectors they cover are written whole instead of being merged twice.
+#include <cstring>
+
+#include "k_records.cuh"
 
 namespace sph {
 namespace {
 
-constexpr unsigned FULL = 0xffffffffu;
-constexpr int kKDThreads = 256;
+constexpr int kKDThreads = 128;
+constexpr int kMaxWb = 3 * SPH_NFIELDS;
+
+// one written-back scalar component
+struct WbComp {
+    int32_t off;                 // byte offset in the record
+    int32_t f64;                 // AoS element is FP64
+    int32_t src;                 // 0: the SoA value; 1 + c: kicked v_c; 4: kicked u
+    int32_t fmt;                 // storage format of the SoA value
+    float dec;                   // 2^-e
+    const void *soa;
+};
 
 struct KDArgs {
     uint8_t *aos;
     int64_t n;
-    int32_t W;                   // record words
-    int32_t xw;                  // first position word in the record
+    RecGeom g;
+    ChunkRun xrun;               // the chunks holding x
+    ChunkRun wrun;               // the chunks holding any written unit
+    int32_t xoff;                // byte offset of x in the record
+    uint64_t umask[2];           // units written: x, plus the write-back fields
     const int32_t *perm;
     double box[3];
     float dtk;
@@ -30,14 +49,31 @@ struct KDArgs {
     int ufmt;
     float udec, uenc;
     const float *dudt;
+    bool write_soa;              // store the kicked v, u in the SoA
+    int nwb;
+    WbComp wb[kMaxWb];
     DevStats *st;
 };
 
-__global__ void __launch_bounds__(kKDThreads) k_kick_drift(KDArgs a)
+// the value a store in `fmt` followed by a load returns
+__device__ __forceinline__ float quantize_fmt(float x, int fmt)
 {
-    __shared__ double sx[kKDThreads / 32][32 * 3 + 1];
+    switch (fmt) {
+    case SPH_P_BF16: return dec_bf16(enc_bf16(x));
+    case SPH_P_FP16: return __half2float(__float2half_rn(x));
+    case SPH_P_FP32_M16: return __uint_as_float(enc_trunc(x, 25) << 7);
+    case SPH_P_FP32_M10: return __uint_as_float(enc_trunc(x, 19) << 13);
+    default: return x;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kKDThreads, 10) k_kick_drift(KDArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *smem = reinterpret_cast<T *>(smem_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double *xs = sx[warp];
+    T *rec = smem + (size_t)warp * 32 * a.g.Up;
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool ok = k < a.n;
     const int64_t o = ok ? a.perm[k] : -1;
@@ -48,20 +84,10 @@ __global__ void __launch_bounds__(kKDThreads) k_kick_drift(KDArgs a)
         for (int c = 0; c < 3; ++c) vn[c] = fmaf(a.a[c][k], a.dtk, ld_val(a.v[c], a.vfmt, k) * a.vdec);
         un = fmaf(a.dudt[k], a.dtk, ld_val(a.u, a.ufmt, k) * a.udec);
     }
-    double *aos64 = (double *)a.aos;
-    // lane l moves word l % 3 of record l / 3 (then +32, +64)
-    double xw[3];
-#pragma unroll
-    for (int t = 0; t < 3; ++t) {
-        const int idx = lane + 32 * t;
-        const int r = idx / 3, w = idx - 3 * r;
-        const int64_t orr = __shfl_sync(FULL, o, r);
-        xw[t] = orr >= 0 ? aos64[orr * a.W + a.xw + w] : 0.0;
-    }
-#pragma unroll
-    for (int t = 0; t < 3; ++t) xs[lane + 32 * t] = xw[t];
-    __syncwarp();
+    load_chunks<T>(reinterpret_cast<const T *>(a.aos), rec, o, a.g, a.xrun, lane);
+    unsigned char *mine = reinterpret_cast<unsigned char *>(rec + lane * a.g.Up);
     if (ok) {
+        double *xs = reinterpret_cast<double *>(mine + a.xoff);
         bool bad = false;
         for (int c = 0; c < 3; ++c) {
             // x += v dt in FP64 (one FMA, the FP64 arithmetic the step
@@ -69,7 +95,7 @@ __global__ void __launch_bounds__(kKDThreads) k_kick_drift(KDArgs a)
             // patterns, since non-negative doubles order like their bits --
             // needs no wrap; the few that left the box take the periodic
             // wrap x - L floor(x / L)
-            double y = fma(f2d_bits(vn[c]), a.dtd, xs[3 * lane + c]);
+            double y = fma(f2d_bits(vn[c]), a.dtd, xs[c]);
             const long long yb = __double_as_longlong(y);
             if (yb < 0 || yb >= __double_as_longlong(a.box[c])) {
                 if ((yb & 0x7FF0000000000000ll) == 0x7FF0000000000000ll) {
@@ -79,32 +105,65 @@ __global__ void __launch_bounds__(kKDThreads) k_kick_drift(KDArgs a)
                     if (y >= a.box[c]) y = 0.0;        // rounding onto L
                 }
             }
-            xs[3 * lane + c] = y;
+            xs[c] = y;
         }
         if (bad || !isfinite(un)) set_error(a.st, SPH_ERR_NONFINITE);
+        // the write-back: v and u as the storage format holds them after the
+        // kick, the other fields as stored
+        for (int i = 0; i < a.nwb; ++i) {
+            const WbComp w = a.wb[i];
+            float val;
+            if (w.src == 0) val = ld_val(w.soa, w.fmt, k) * w.dec;
+            else if (w.src == 4) val = quantize_fmt(un * a.uenc, a.ufmt) * a.udec;
+            else val = quantize_fmt((w.src == 1 ? vn[0] : (w.src == 2 ? vn[1] : vn[2])) * a.venc, a.vfmt) * a.vdec;
+            if (w.f64) *reinterpret_cast<double *>(mine + w.off) = f2d_bits(val);
+            else *reinterpret_cast<float *>(mine + w.off) = val;
+        }
     }
-    __syncwarp();
-#pragma unroll
-    for (int t = 0; t < 3; ++t) {
-        const int idx = lane + 32 * t;
-        const int r = idx / 3, w = idx - 3 * r;
-        const int64_t orr = __shfl_sync(FULL, o, r);
-        if (orr >= 0) aos64[orr * a.W + a.xw + w] = xs[idx];
+    store_chunks<T>(reinterpret_cast<T *>(a.aos), rec, o, a.g, a.wrun, a.umask, lane);
+    if (a.write_soa) {
+        for (int c = 0; c < 3; ++c) st_any(a.v[c], a.vfmt, k, vn[c] * a.venc, ok, a.n);
+        st_any(a.u, a.ufmt, k, un * a.uenc, ok, a.n);
     }
-    for (int c = 0; c < 3; ++c) st_any(a.v[c], a.vfmt, k, vn[c] * a.venc, ok, a.n);
-    st_any(a.u, a.ufmt, k, un * a.uenc, ok, a.n);
+}
+
+inline void add_units(uint64_t umask[2], int b0, int b1)
+{
+    for (int u = b0 / 4; u <= (b1 - 1) / 4; ++u) umask[u >> 6] |= 1ull << (u & 63);
+}
+
+template <typename T>
+cudaError_t launch_kd(sph_ctx *c, const KDArgs &a)
+{
+    const size_t smem = (size_t)(kKDThreads / 32) * 32 * a.g.Up * sizeof(T);
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_kick_drift<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+        cudaSuccess)
+        return e;
+    const unsigned grid = (unsigned)((c->n + kKDThreads - 1) / kKDThreads);
+    k_kick_drift<T><<<grid, kKDThreads, smem, c->stream>>>(a);
+    c->launches += 1;
+    return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t run_kick_drift(sph_ctx *c, double dt_kick, double dt_drift)
+// wb_fields == 0: kick/drift alone (v, u stored back in the SoA); otherwise
+// kick/drift fused with the write-back of wb_fields (v, u not stored in SoA)
+cudaError_t run_kick_drift(sph_ctx *c, double dt_kick, double dt_drift, uint32_t wb_fields)
 {
     if (c->n == 0) return cudaSuccess;
     KDArgs a;
+    std::memset(&a, 0, sizeof(a));
     a.aos = c->aos;
     a.n = c->n;
-    a.W = c->layout.record_bytes / 8;
-    a.xw = c->layout.offset[SPH_F_X] / 8;
+    const int cb = record_chunk_bytes(c->layout.record_bytes);
+    a.g = rec_geom(c->layout.record_bytes, cb);
+    a.xoff = c->layout.offset[SPH_F_X];
+    uint64_t xm = 0;
+    for (int q = a.xoff / cb; q <= (a.xoff + 23) / cb; ++q) xm |= 1ull << q;
+    a.xrun = chunk_run(xm);
+    add_units(a.umask, a.xoff, a.xoff + 24);
     a.perm = c->perm();
     for (int k = 0; k < 3; ++k) {
         a.box[k] = c->params.box[k];
@@ -121,10 +180,26 @@ cudaError_t run_kick_drift(sph_ctx *c, double dt_kick, double dt_drift)
     a.udec = c->dec(SPH_F_U);
     a.uenc = c->enc(SPH_F_U);
     a.dudt = (const float *)c->soa[SPH_F_DUDT][0];
+    a.write_soa = wb_fields == 0;
+    a.nwb = 0;
+    for (int f = 0; f < SPH_NFIELDS; ++f) {
+        if (!(wb_fields & SPH_BIT(f))) continue;
+        const bool f64 = c->layout.type[f] == SPH_AOS_F64;
+        const int es = f64 ? 8 : 4;
+        for (int comp = 0; comp < ncomp(f); ++comp) {
+            WbComp &w = a.wb[a.nwb++];
+            w.off = c->layout.offset[f] + es * comp;
+            w.f64 = f64 ? 1 : 0;
+            w.src = f == SPH_F_V ? 1 + comp : (f == SPH_F_U ? 4 : 0);
+            w.fmt = c->prec[f];
+            w.dec = c->dec(f);
+            w.soa = c->soa[f][comp];
+        }
+        add_units(a.umask, c->layout.offset[f], c->layout.offset[f] + es * ncomp(f));
+    }
+    a.wrun = chunk_run(chunks_of_units(a.umask, cb));
     a.st = c->dstats;
-    k_kick_drift<<<(unsigned)((c->n + kKDThreads - 1) / kKDThreads), kKDThreads, 0, c->stream>>>(a);
-    c->launches += 1;
-    return cudaGetLastError();
+    return cb == 16 ? launch_kd<uint4>(c, a) : launch_kd<uint2>(c, a);
 }
 
 }  // namespace sph

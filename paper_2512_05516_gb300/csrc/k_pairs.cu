@@ -297,6 +297,8 @@ __device__ __forceinline__ float ldf(const void *p, int fmt, int64_t k)
     if constexpr (F == SPH_P_FP32) return __ldg((const float *)p + k);
     else if constexpr (F == SPH_P_FP16) return __half2float(__ushort_as_half(__ldg((const unsigned short *)p + k)));
     else if constexpr (F == SPH_P_BF16) return dec_bf16(__ldg((const unsigned short *)p + k));
+    else if constexpr (F == SPH_P_FP32_M16) return ld_packed((const uint32_t *)p, k, 25);
+    else if constexpr (F == SPH_P_FP32_M10) return ld_packed((const uint32_t *)p, k, 19);
     else return ld_val(p, fmt, k);
 }
 
@@ -799,14 +801,56 @@ cudaError_t launch_persistent(sph_ctx *c, K kernel, const A &args, size_t smem, 
 }
 
 // Which fixed-format instantiation serves positions in fx and fields in fv:
-// 1..6 for (FP32 | FP16) x (FP32 | BF16 | FP16), 0 for the run-time decoder.
+// 1..10 for (FP32 | FP16) x (FP32 | BF16 | FP16 | FP32-m16 | FP32-m10), 0 for
+// the run-time decoder.
+constexpr int kVariants = 11;
 int fmt_variant(int fx, int fv)
 {
     const int ix = fx == SPH_P_FP32 ? 0 : (fx == SPH_P_FP16 ? 1 : -1);
-    const int iv = fv == SPH_P_FP32 ? 0 : (fv == SPH_P_BF16 ? 1 : (fv == SPH_P_FP16 ? 2 : -1));
+    int iv = -1;
+    switch (fv) {
+    case SPH_P_FP32: iv = 0; break;
+    case SPH_P_BF16: iv = 1; break;
+    case SPH_P_FP16: iv = 2; break;
+    case SPH_P_FP32_M16: iv = 3; break;
+    case SPH_P_FP32_M10: iv = 4; break;
+    default: break;
+    }
     if (ix < 0 || iv < 0) return 0;
-    return 1 + 3 * ix + iv;
+    return 1 + 5 * ix + iv;
 }
+
+// One launch table per kernel family, indexed by fmt_variant.
+template <template <int, int> class K>
+struct Variants {
+    template <typename A>
+    static cudaError_t launch(sph_ctx *c, int v, const A &a, size_t smem, LaunchCache *lc)
+    {
+        constexpr int P32 = SPH_P_FP32, P16 = SPH_P_FP16, B16 = SPH_P_BF16, M16 = SPH_P_FP32_M16,
+                      M10 = SPH_P_FP32_M10;
+        switch (v) {
+        case 1: return launch_persistent(c, K<P32, P32>::fn, a, smem, lc[1]);
+        case 2: return launch_persistent(c, K<P32, B16>::fn, a, smem, lc[2]);
+        case 3: return launch_persistent(c, K<P32, P16>::fn, a, smem, lc[3]);
+        case 4: return launch_persistent(c, K<P32, M16>::fn, a, smem, lc[4]);
+        case 5: return launch_persistent(c, K<P32, M10>::fn, a, smem, lc[5]);
+        case 6: return launch_persistent(c, K<P16, P32>::fn, a, smem, lc[6]);
+        case 7: return launch_persistent(c, K<P16, B16>::fn, a, smem, lc[7]);
+        case 8: return launch_persistent(c, K<P16, P16>::fn, a, smem, lc[8]);
+        case 9: return launch_persistent(c, K<P16, M16>::fn, a, smem, lc[9]);
+        case 10: return launch_persistent(c, K<P16, M10>::fn, a, smem, lc[10]);
+        default: return launch_persistent(c, K<kAnyFmt, kAnyFmt>::fn, a, smem, lc[0]);
+        }
+    }
+};
+template <int FX, int FV>
+struct DensityK {
+    static constexpr auto fn = k_density<FX, FV>;
+};
+template <int FX, int FV>
+struct ForceK {
+    static constexpr auto fn = k_force<FX, FV>;
+};
 
 }  // namespace
 
@@ -854,16 +898,8 @@ cudaError_t run_density(sph_ctx *c, int newton_steps)
     a.cs_enc = c->enc(SPH_F_CS);
     a.nngb = c->nngb;
     const size_t smem = density_smem_bytes(c->tuning.block_threads, a.c.cap);
-    cudaError_t e;
-    switch (fmt_variant(a.c.x.fmt, a.c.m.fmt)) {    // what the staging loads
-    case 1: e = launch_persistent(c, k_density<SPH_P_FP32, SPH_P_FP32>, a, smem, c->lc_density[1]); break;
-    case 2: e = launch_persistent(c, k_density<SPH_P_FP32, SPH_P_BF16>, a, smem, c->lc_density[2]); break;
-    case 3: e = launch_persistent(c, k_density<SPH_P_FP32, SPH_P_FP16>, a, smem, c->lc_density[3]); break;
-    case 4: e = launch_persistent(c, k_density<SPH_P_FP16, SPH_P_FP32>, a, smem, c->lc_density[4]); break;
-    case 5: e = launch_persistent(c, k_density<SPH_P_FP16, SPH_P_BF16>, a, smem, c->lc_density[5]); break;
-    case 6: e = launch_persistent(c, k_density<SPH_P_FP16, SPH_P_FP16>, a, smem, c->lc_density[6]); break;
-    default: e = launch_persistent(c, k_density<kAnyFmt, kAnyFmt>, a, smem, c->lc_density[0]); break;
-    }
+    // what the staging loads decides the instantiation
+    cudaError_t e = Variants<DensityK>::launch(c, fmt_variant(a.c.x.fmt, a.c.m.fmt), a, smem, c->lc_density);
     if (e != cudaSuccess) return e;
     if (a.write_h && h_packed) return run_pack(c, c->stage, SPH_F_H);
     return cudaSuccess;
@@ -907,15 +943,7 @@ cudaError_t run_force(sph_ctx *c)
     if (a.c.h.fmt == a.c.m.fmt && a.v.fmt == a.c.m.fmt && a.rho.fmt == SPH_P_FP32 &&
         a.P.fmt == SPH_P_FP32 && a.cs.fmt == SPH_P_FP32)
         v = fmt_variant(a.c.x.fmt, a.c.m.fmt);
-    switch (v) {
-    case 1: return launch_persistent(c, k_force<SPH_P_FP32, SPH_P_FP32>, a, smem, c->lc_force[1]);
-    case 2: return launch_persistent(c, k_force<SPH_P_FP32, SPH_P_BF16>, a, smem, c->lc_force[2]);
-    case 3: return launch_persistent(c, k_force<SPH_P_FP32, SPH_P_FP16>, a, smem, c->lc_force[3]);
-    case 4: return launch_persistent(c, k_force<SPH_P_FP16, SPH_P_FP32>, a, smem, c->lc_force[4]);
-    case 5: return launch_persistent(c, k_force<SPH_P_FP16, SPH_P_BF16>, a, smem, c->lc_force[5]);
-    case 6: return launch_persistent(c, k_force<SPH_P_FP16, SPH_P_FP16>, a, smem, c->lc_force[6]);
-    default: return launch_persistent(c, k_force<kAnyFmt, kAnyFmt>, a, smem, c->lc_force[0]);
-    }
+    return Variants<ForceK>::launch(c, v, a, smem, c->lc_force);
 }
 
 }  // namespace sph

@@ -98,6 +98,7 @@ bool make_plan(const sph_aos_layout &L, int64_t n, int64_t ncell_max, uint32_t w
     p->nngb_force = take(4 * N);
     p->stage = take(4 * N);
     p->key_hmax = take(4 * (size_t)nkeys);
+    p->origin = take(sizeof(double) * 3 * kMaxCellsPerAxis);
     p->aos_tmp = (ws_flags & SPH_WS_REORDER) ? take((size_t)L.record_bytes * N) : 0;
     p->stats = take(sizeof(DevStats));
     for (int f = 0; f < SPH_NFIELDS; ++f)
@@ -174,6 +175,7 @@ sph_status sph_create(const sph_aos_layout *layout, const sph_params *params, in
     c->nngb_force = (int32_t *)(w + plan.nngb_force);
     c->stage = (float *)(w + plan.stage);
     c->key_hmax = (float *)(w + plan.key_hmax);
+    c->origin = (double *)(w + plan.origin);
     c->aos_tmp = (ws_flags & SPH_WS_REORDER) ? w + plan.aos_tmp : nullptr;
     c->dstats = (DevStats *)(w + plan.stats);
     for (int f = 0; f < SPH_NFIELDS; ++f) {
@@ -199,7 +201,7 @@ sph_status sph_bin_cells(sph_ctx *c, double cell_edge, int32_t reorder_aos)
     for (int k = 0; k < 3; ++k) {
         double f = std::floor(c->params.box[k] / want);
         if (f < 3.0) return SPH_ECAPACITY;
-        if (f > 4096.0) f = 4096.0;  // larger cells still cover 2 h_max
+        if (f > (double)kMaxCellsPerAxis) f = kMaxCellsPerAxis;  // larger cells still cover 2 h_max
         nc[k] = (int32_t)f;
         ncell *= nc[k];
     }
@@ -294,8 +296,22 @@ sph_status sph_kick_drift(sph_ctx *c, double dt_kick, double dt_drift)
     const uint32_t need = SPH_BIT(SPH_F_V) | SPH_BIT(SPH_F_A) | SPH_BIT(SPH_F_U) |
                           SPH_BIT(SPH_F_DUDT);
     if ((c->valid & need) != need) return SPH_ESTATE;
-    if (run_kick_drift(c, dt_kick, dt_drift) != cudaSuccess) return SPH_ECUDA;
+    if (run_kick_drift(c, dt_kick, dt_drift, 0) != cudaSuccess) return SPH_ECUDA;
     c->valid &= ~SPH_BIT(SPH_F_X);   // SoA positions are stale after the drift
+    return SPH_OK;
+}
+
+sph_status sph_kick_drift_writeback(sph_ctx *c, double dt_kick, double dt_drift, uint32_t fields)
+{
+    if (!c || !std::isfinite(dt_kick) || !std::isfinite(dt_drift)) return SPH_EINVAL;
+    if (fields == 0 || (fields >> SPH_NFIELDS) != 0 || (fields & SPH_BIT(SPH_F_X))) return SPH_EINVAL;
+    for (int f = 0; f < SPH_NFIELDS; ++f)
+        if ((fields & SPH_BIT(f)) && c->layout.offset[f] < 0) return SPH_EINVAL;
+    if (!c->binned) return SPH_ESTATE;
+    const uint32_t need = SPH_BIT(SPH_F_V) | SPH_BIT(SPH_F_A) | SPH_BIT(SPH_F_U) | SPH_BIT(SPH_F_DUDT) | fields;
+    if ((c->valid & need) != need) return SPH_ESTATE;
+    if (run_kick_drift(c, dt_kick, dt_drift, fields) != cudaSuccess) return SPH_ECUDA;
+    c->valid &= ~(SPH_BIT(SPH_F_X) | SPH_BIT(SPH_F_V) | SPH_BIT(SPH_F_U));   // kicked values went to the AoS only
     return SPH_OK;
 }
 

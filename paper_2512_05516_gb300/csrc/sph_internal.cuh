@@ -22,6 +22,7 @@ constexpr int kScanTile = kScanThreads * kScanItems;      // elements per scan b
 constexpr int kItemTile = 32;                              // i-particles per pair-kernel work item (one warp)
 constexpr int kMaxSub = 2;                                 // sub-cells per cell edge, at most
 constexpr int kMaxBlock = 256;
+constexpr int kMaxCellsPerAxis = 4096;                     // the binning caps n_c per axis here
 constexpr float kSigma = 0.318309886183790671538f;        // 1/pi, 3D M4 normalisation
 
 inline int ncomp(int f) { return (f == SPH_F_X || f == SPH_F_V || f == SPH_F_A) ? 3 : 1; }
@@ -45,7 +46,7 @@ struct Plan {
     size_t keys[2], vals[2];
     size_t cell_count, cell_start, scan_part, ghist;
     size_t item_cell, item_first, item_count, item_tmp;
-    size_t nngb, nngb_force, stage, aos_tmp, stats, key_hmax;
+    size_t nngb, nngb_force, stage, aos_tmp, stats, key_hmax, origin;
     size_t soa[SPH_NFIELDS][3];
     size_t total;
     int64_t item_max, nblk_radix;
@@ -242,7 +243,7 @@ struct sph_ctx {
     int64_t ncell = 0;
     int sub = 1;                  // sub-cells per cell edge of the last binning
     bool binned = false;
-    sph::LaunchCache lc_density[8], lc_force[8];   // one per storage-format instantiation
+    sph::LaunchCache lc_density[12], lc_force[12];   // one per storage-format instantiation
     int sorted_buf = 0;          // which ping-pong buffer holds the sorted keys/values
 
     // workspace arrays
@@ -254,6 +255,7 @@ struct sph_ctx {
     int32_t *nngb = nullptr, *nngb_force = nullptr;
     float *stage = nullptr;
     float *key_hmax = nullptr;    // largest h of every sub-cell (force pruning)
+    double *origin = nullptr;     // cell origins k * (L_d / nc_d), kMaxCellsPerAxis per axis
     uint8_t *aos_tmp = nullptr;
     sph::DevStats *dstats = nullptr;
     void *soa[SPH_NFIELDS][3] = {};
@@ -276,7 +278,7 @@ cudaError_t run_aos_to_soa(sph_ctx *c, uint32_t fields);
 cudaError_t run_soa_to_aos(sph_ctx *c, uint32_t fields);
 cudaError_t run_density(sph_ctx *c, int newton_steps);
 cudaError_t run_force(sph_ctx *c);
-cudaError_t run_kick_drift(sph_ctx *c, double dt_kick, double dt_drift);
+cudaError_t run_kick_drift(sph_ctx *c, double dt_kick, double dt_drift, uint32_t wb_fields);
 cudaError_t scan_exclusive(const int32_t *in, int32_t *out, int64_t len, int32_t *part,
                            cudaStream_t s, uint64_t *launches);
 int max_dynamic_smem(const sph_ctx *c);

@@ -117,6 +117,7 @@ def test_calls_on_null_context_fail_cleanly(sph):
     assert sph.sph_force(null) == sph._capi.EINVAL
     assert sph.sph_kick_drift(null, 0.1, 0.1) == sph._capi.EINVAL
     assert sph.sph_soa_to_aos(null, 2) == sph._capi.EINVAL
+    assert sph.sph_kick_drift_writeback(null, 0.1, 0.1, 2) == sph._capi.EINVAL
     assert sph.sph_get_stats(null)[0] == sph._capi.EINVAL
     assert sph.sph_set_tuning(null, sph.sph_tuning()) == sph._capi.EINVAL
     assert sph.sph_describe(null)[0] == sph._capi.EINVAL

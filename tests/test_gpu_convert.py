@@ -57,10 +57,13 @@ def sph_inputs_col(aos, name):
     return aos[:, c0:c0 + nc] if nc > 1 else aos[:, c0]
 
 
+@pytest.mark.parametrize("case", ["sod24", "long_run_box2"])
 @pytest.mark.parametrize("fmt", ["fp32", "fp16"])
-def test_cell_relative_positions(orc, fmt):
+def test_cell_relative_positions(orc, fmt, case):
+    # the offsets are x - k L/nc rounded once; the box 2 x 1 x 1 case has
+    # different cell counts per axis (the cell coordinates come from the key)
     import paper_2512_05516_gb300 as sph
-    wl = sph_inputs.sod(n_lattice=24, seed=8)
+    wl = sph_inputs.sod(n_lattice=24, seed=8) if case == "sod24" else sph_inputs.long_run(nx=96, ny=48, nz=48)
     s = make_sph(wl)
     s.bin_cells(wl.cell_edge)
     perm = s.perm().cpu().numpy()
@@ -117,3 +120,32 @@ def test_format_rules_rejected_on_host():
         with pytest.raises(sph.SphError) as e:
             s.aos_to_soa(sph.mask(field), {field: fmt})
         assert e.value.status == -1
+
+
+@pytest.mark.parametrize("name", ["v", "m", "h", "rho", "u", "P"])
+def test_one_field_at_a_time(orc, name):
+    # a call that touches a single field moves one or two chunks of each
+    # record; the gather and the write-back must pick exactly those
+    import paper_2512_05516_gb300 as sph
+    wl = sph_inputs.random_cloud(3000, seed=11, vel=2.0)
+    wl.cell_edge = 2.0 * wl.h_cap
+    rng = np.random.default_rng(12)
+    for f in ("rho", "P"):
+        wl.col(f)[:] = rng.uniform(0.1, 5.0, wl.n)
+    s = make_sph(wl)
+    s.bin_cells(wl.cell_edge)
+    perm = s.perm().cpu().numpy()
+    s.aos_to_soa(sph.mask(name), {name: "bf16"})
+    col = wl.col(name)
+    for c in range(3 if name == "v" else 1):
+        vals = (col[:, c] if name == "v" else col)[perm]
+        assert np.array_equal(s.soa_raw(name, c).cpu().numpy(), _codes(orc, vals, "bf16")), c
+    before = s.aos.cpu().numpy().copy()
+    s.soa_to_aos(sph.mask(name))
+    after = s.aos.cpu().numpy()
+    off, ncomp = sph_inputs.RECORD_112[name]
+    cols = list(range(off // 8, off // 8 + ncomp))
+    q, _ = orc.quantize(before[:, cols].ravel(), "bf16")
+    assert np.array_equal(after[:, cols].ravel(), q)
+    others = [j for j in range(14) if j not in cols]
+    assert np.array_equal(after[:, others], before[:, others])
