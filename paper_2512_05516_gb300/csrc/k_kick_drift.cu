@@ -9,6 +9,7 @@
 // record image, and the written 4-byte units go back lane-contiguously.
 // With the write-back, x and the fields share one pass over the records, so
 // the sectors they cover are written whole instead of being merged twice.
+#include <algorithm>
 #include <cstring>
 
 #include "k_records.cuh"
@@ -84,6 +85,13 @@ __global__ void __launch_bounds__(kKDThreads, 10) k_kick_drift(KDArgs a)
         for (int c = 0; c < 3; ++c) vn[c] = fmaf(a.a[c][k], a.dtk, ld_val(a.v[c], a.vfmt, k) * a.vdec);
         un = fmaf(a.dudt[k], a.dtk, ld_val(a.u, a.ufmt, k) * a.udec);
     }
+    // the write-back values read from the SoA: issued before the record
+    // loads (a fixed unrolled window keeps them in flight together)
+    constexpr int W = 8;
+    float pre[W];
+#pragma unroll
+    for (int i = 0; i < W; ++i)
+        if (ok && i < a.nwb && a.wb[i].src == 0) pre[i] = ld_val(a.wb[i].soa, a.wb[i].fmt, k);
     load_chunks<T>(reinterpret_cast<const T *>(a.aos), rec, o, a.g, a.xrun, lane);
     unsigned char *mine = reinterpret_cast<unsigned char *>(rec + lane * a.g.Up);
     if (ok) {
@@ -110,7 +118,18 @@ __global__ void __launch_bounds__(kKDThreads, 10) k_kick_drift(KDArgs a)
         if (bad || !isfinite(un)) set_error(a.st, SPH_ERR_NONFINITE);
         // the write-back: v and u as the storage format holds them after the
         // kick, the other fields as stored
-        for (int i = 0; i < a.nwb; ++i) {
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            if (i >= a.nwb) break;
+            const WbComp w = a.wb[i];
+            float val;
+            if (w.src == 0) val = pre[i] * w.dec;
+            else if (w.src == 4) val = quantize_fmt(un * a.uenc, a.ufmt) * a.udec;
+            else val = quantize_fmt((w.src == 1 ? vn[0] : (w.src == 2 ? vn[1] : vn[2])) * a.venc, a.vfmt) * a.vdec;
+            if (w.f64) *reinterpret_cast<double *>(mine + w.off) = f2d_bits(val);
+            else *reinterpret_cast<float *>(mine + w.off) = val;
+        }
+        for (int i = W; i < a.nwb; ++i) {
             const WbComp w = a.wb[i];
             float val;
             if (w.src == 0) val = ld_val(w.soa, w.fmt, k) * w.dec;
@@ -197,6 +216,8 @@ cudaError_t run_kick_drift(sph_ctx *c, double dt_kick, double dt_drift, uint32_t
         }
         add_units(a.umask, c->layout.offset[f], c->layout.offset[f] + es * ncomp(f));
     }
+    // SoA-sourced components first: the kernel preloads the first ones
+    std::stable_partition(a.wb, a.wb + a.nwb, [](const WbComp &w) { return w.src == 0; });
     a.wrun = chunk_run(chunks_of_units(a.umask, cb));
     a.st = c->dstats;
     return cb == 16 ? launch_kd<uint4>(c, a) : launch_kd<uint2>(c, a);

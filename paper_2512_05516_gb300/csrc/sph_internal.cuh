@@ -193,28 +193,34 @@ __device__ __forceinline__ double f2d_bits(float f)
 {
     const uint32_t u = __float_as_uint(f);
     const uint32_t e = (u >> 23) & 0xFFu;
-    const uint64_t s = (uint64_t)(u >> 31) << 63;
-    if ((u & 0x7FFFFFFFu) == 0u) return __longlong_as_double((long long)s);          // +-0
-    if (e == 0u) return (double)f;                                                   // subnormal
-    const uint64_t m = (uint64_t)(u & 0x7FFFFFu) << 29;
-    const uint64_t E = e == 0xFFu ? 0x7FFull : (uint64_t)(e + (1023 - 127));          // inf / nan keep all-ones
-    return __longlong_as_double((long long)(s | (E << 52) | m));
+    const uint32_t s = u & 0x80000000u;
+    if (e - 1u > 253u) {                                   // zero, subnormal, inf, nan
+        if ((u & 0x7FFFFFFFu) == 0u) return __hiloint2double((int)s, 0);
+        if (e == 0u) return (double)f;                     // subnormal: rare
+        return __hiloint2double((int)(s | 0x7FF00000u | ((u & 0x7FFFFFu) >> 3)), (int)(u << 29));
+    }
+    // re-bias the exponent (+896) and widen the mantissa: 32-bit halves only
+    const uint32_t hi = s | (((u & 0x7FFFFFFFu) >> 3) + (896u << 20));
+    return __hiloint2double((int)hi, (int)(u << 29));
 }
 
 __device__ __forceinline__ float d2f_bits_rn(double d)
 {
-    const uint64_t u = (uint64_t)__double_as_longlong(d);
-    const uint32_t s = (uint32_t)(u >> 63) << 31;
-    if ((u << 1) == 0u) return __uint_as_float(s);                                    // +-0
-    const int e = (int)((u >> 52) & 0x7FFu);
-    if (e < 1023 - 126 || e > 1023 + 127) return __double2float_rn(d);              // not a normal float
-    const uint64_t m = u & 0xFFFFFFFFFFFFFull;
-    const uint32_t top = (uint32_t)(m >> 29);                                         // kept 23 bits
-    const uint32_t rem = (uint32_t)(m & 0x1FFFFFFFull);                               // dropped 29 bits
-    uint32_t bits = ((uint32_t)(e - (1023 - 127)) << 23) | top;
-    // round half to even; a carry moves into the exponent (up to infinity)
-    bits += (rem > 0x10000000u || (rem == 0x10000000u && (top & 1u))) ? 1u : 0u;
-    return __uint_as_float(s | bits);
+    const uint32_t lo = (uint32_t)__double2loint(d);
+    const uint32_t hi = (uint32_t)__double2hiint(d);
+    const uint32_t e = (hi >> 20) & 0x7FFu;
+    if (e - 897u > 253u) {                                 // not a normal float
+        if (((hi & 0x7FFFFFFFu) | lo) == 0u) return __uint_as_float(hi & 0x80000000u);     // +-0
+        return __double2float_rn(d);                       // rare
+    }
+    // bits 31..23 of w: the exponent's low 9 bits; 22..0: the top 23 mantissa
+    // bits; e - 896 = (low 9 bits - 0x180) mod 512 lies in [1, 254]
+    const uint32_t w = __funnelshift_l(lo, hi, 3);
+    uint32_t r = (w - (0x180u << 23)) | (hi & 0x80000000u);
+    // round half to even on the 29 dropped bits; a carry moves into the
+    // exponent (up to infinity)
+    r += ((lo & 0x1FFFFFFFu) + 0x0FFFFFFFu + (r & 1u)) >> 29;
+    return __uint_as_float(r);
 }
 
 }  // namespace sph
