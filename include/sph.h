@@ -157,6 +157,13 @@ typedef struct {
     int32_t stage_force;         /* neighbour candidates staged per warp, force kernel (>= 32) */
     int32_t subcells;            /* sub-cells per cell edge used to order particles, 1 or 2
                                     (default 2); takes effect at the next sph_bin_cells */
+    int32_t item_order;          /* order of the pair-kernel work queue, set at sph_bin_cells:
+                                    0 cell order, 1 costliest first (items grouped by
+                                    the power-of-two class of count x stencil occupancy,
+                                    classes in descending order); -1 keeps the current */
+    int32_t class_launches;      /* 1: one pair-kernel launch per cost class (needs
+                                    item_order 1), 0: one persistent launch over the
+                                    whole queue; -1 keeps the current */
 } sph_tuning;
 
 /* Where the library's arrays live inside the workspace (byte offsets from the

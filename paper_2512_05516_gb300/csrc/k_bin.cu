@@ -247,6 +247,63 @@ __global__ void k_items_fill(const int32_t *cell_start, const int32_t *item_off,
 }
 
 // ---------------------------------------------------------------------------
+// optional queue order: work items grouped by cost class, costliest first
+// ---------------------------------------------------------------------------
+
+// class key of every item: the power of two of (its particle count x the
+// particles of the 27 cells around its cell), stored as
+// kItemClasses - 1 - log2 so that ascending keys put the costliest first
+__global__ void k_item_class(const int32_t *cell_start, const int32_t *icell, const int32_t *icount, int3 nc,
+                             int s3, const DevStats *st, int32_t *key, int32_t *hist)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= st->nitems) return;
+    const int cell = icell[i];
+    const int kx = cell % nc.x, t = cell / nc.x, ky = t % nc.y, kz = t / nc.y;
+    long long occ = 0;
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int x = (kx + dx + nc.x) % nc.x, y = (ky + dy + nc.y) % nc.y, z = (kz + dz + nc.z) % nc.z;
+                const long long cid = x + (long long)nc.x * (y + (long long)nc.y * z);
+                occ += cell_start[(cid + 1) * s3] - cell_start[cid * s3];
+            }
+    const long long cost = (long long)icount[i] * occ;
+    const int lg = cost > 0 ? min(63 - __clzll(cost), kItemClasses - 1) : 0;
+    key[i] = kItemClasses - 1 - lg;
+    atomicAdd(&hist[key[i]], 1);
+}
+
+// one warp: class starts (kItemClasses + 1 entries) and scatter cursors
+__global__ void k_class_scan(int32_t *hist)
+{
+    const int lane = threadIdx.x;
+    const int32_t v = hist[lane];
+    int32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    int32_t *start = hist + kItemClasses, *cursor = hist + 2 * kItemClasses + 1;
+    start[lane] = inc - v;
+    cursor[lane] = inc - v;
+    if (lane == 31) start[kItemClasses] = inc;
+}
+
+__global__ void k_item_scatter(const int32_t *icell, const int32_t *ifirst, const int32_t *icount,
+                               const int32_t *key, int32_t *cursor, int32_t *sorted, int64_t item_max,
+                               const DevStats *st)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= st->nitems) return;
+    const int pos = atomicAdd(&cursor[key[i]], 1);
+    sorted[pos] = icell[i];
+    sorted[item_max + pos] = ifirst[i];
+    sorted[2 * item_max + pos] = icount[i];
+}
+
+// ---------------------------------------------------------------------------
 // optional AoS reordering
 // ---------------------------------------------------------------------------
 __global__ void k_gather_records(const uint8_t *aos, uint8_t *dst, const int32_t *perm, int64_t n, int32_t stride)
@@ -425,7 +482,28 @@ cudaError_t run_items(sph_ctx *c)
     if ((e = scan_exclusive(c->item_tmp, c->item_tmp, c->ncell, c->scan_part, s, &c->launches)) != cudaSuccess) return e;
     k_items_fill<<<blocks_for(c->ncell, 256), 256, 0, s>>>(c->cell_start, c->item_tmp, c->ncell, s3, block,
                                                            c->item_cell, c->item_first, c->item_count, c->dstats);
-    return cudaGetLastError();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    c->items_by_class = false;
+    if (c->tuning.item_order == 1) {
+        const int64_t im = c->plan.item_max;
+        const unsigned g = blocks_for(im, 256);
+        if ((e = cudaMemsetAsync(c->class_hist, 0, sizeof(int32_t) * kItemClasses, s)) != cudaSuccess) return e;
+        k_item_class<<<g, 256, 0, s>>>(c->cell_start, c->item_cell, c->item_count,
+                                       make_int3(c->nc[0], c->nc[1], c->nc[2]), s3, c->dstats, c->item_class,
+                                       c->class_hist);
+        k_class_scan<<<1, 32, 0, s>>>(c->class_hist);
+        k_item_scatter<<<g, 256, 0, s>>>(c->item_cell, c->item_first, c->item_count, c->item_class,
+                                         c->class_hist + 2 * kItemClasses + 1, c->item_sorted, im, c->dstats);
+        c->launches += 3;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        int32_t *dst[3] = {c->item_cell, c->item_first, c->item_count};
+        for (int a = 0; a < 3; ++a)
+            if ((e = cudaMemcpyAsync(dst[a], c->item_sorted + a * im, sizeof(int32_t) * im, cudaMemcpyDeviceToDevice,
+                                     s)) != cudaSuccess)
+                return e;
+        c->items_by_class = true;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace sph

@@ -51,6 +51,7 @@ struct Common {
     int lg_sub, lg_s3;               // their base-2 logarithms (sub is 1 or 2)
     const int32_t *cell_start;       // indexed by key = cell * s3 + sub-cell
     const int32_t *icell, *ifirst, *icount;
+    const int32_t *range;            // [first, last) item of this launch in device memory, or null: all
     DevStats *st;
     FieldRef x, m, h;
     int cap;                         // staged candidates per warp
@@ -374,9 +375,10 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
 
     unsigned long long my_pairs = 0, my_tests = 0;
     unsigned my_err = 0;
-    const int nitems = c.st->nitems;
+    const int lo = c.range ? c.range[0] : 0;
+    const int hi = c.range ? c.range[1] : c.st->nitems;
 
-    for (int it = pop_item(c.st, lane); it < nitems; it = pop_item(c.st, lane)) {
+    for (int it = lo + pop_item(c.st, lane); it < hi; it = lo + pop_item(c.st, lane)) {
         const int cell = c.icell[it];
         const int first = c.ifirst[it];
         const int count = c.icount[it];
@@ -631,9 +633,10 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_force(ForceArgs a)
     Tab &tab = *reinterpret_cast<Tab *>(lst + 32 * kLaneCap);
     unsigned long long my_pairs = 0, my_tests = 0;
     unsigned my_err = 0;
-    const int nitems = c.st->nitems;
+    const int lo = c.range ? c.range[0] : 0;
+    const int hi = c.range ? c.range[1] : c.st->nitems;
 
-    for (int it = pop_item(c.st, lane); it < nitems; it = pop_item(c.st, lane)) {
+    for (int it = lo + pop_item(c.st, lane); it < hi; it = lo + pop_item(c.st, lane)) {
         const int cell = c.icell[it];
         const int first = c.ifirst[it];
         const int count = c.icount[it];
@@ -760,6 +763,7 @@ Common make_common(sph_ctx *c, int cap)
     m.icell = c->item_cell;
     m.ifirst = c->item_first;
     m.icount = c->item_count;
+    m.range = nullptr;
     m.st = c->dstats;
     auto ref = [&](int f) {
         FieldRef r;
@@ -793,6 +797,19 @@ cudaError_t launch_persistent(sph_ctx *c, K kernel, const A &args, size_t smem, 
         lc.block = block;
         lc.per_sm_req = c->tuning.ctas_per_sm;
         lc.grid = c->sm_count * per_sm;
+    }
+    if (c->tuning.class_launches && c->items_by_class) {
+        // one launch per cost class, over that class's items
+        const int32_t *start = c->class_hist + kItemClasses;
+        for (int k = 0; k < kItemClasses; ++k) {
+            A per = args;
+            per.c.range = start + k;
+            if ((e = cudaMemsetAsync(&c->dstats->queue, 0, sizeof(unsigned), c->stream)) != cudaSuccess) return e;
+            kernel<<<(unsigned)lc.grid, block, smem, c->stream>>>(per);
+            c->launches += 1;
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+        return cudaSuccess;
     }
     if ((e = cudaMemsetAsync(&c->dstats->queue, 0, sizeof(unsigned), c->stream)) != cudaSuccess) return e;
     kernel<<<(unsigned)lc.grid, block, smem, c->stream>>>(args);

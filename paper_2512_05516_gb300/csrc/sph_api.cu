@@ -59,6 +59,8 @@ void default_tuning(sph_tuning *t)
     t->stage_density = 1024;
     t->stage_force = 128;
     t->subcells = 2;
+    t->item_order = 0;
+    t->class_launches = 0;
 }
 
 }  // namespace
@@ -94,6 +96,9 @@ bool make_plan(const sph_aos_layout &L, int64_t n, int64_t ncell_max, uint32_t w
     p->item_first = take(4 * (size_t)p->item_max);
     p->item_count = take(4 * (size_t)p->item_max);
     p->item_tmp = take(4 * ((size_t)ncell_max + 1));
+    p->item_sorted = take(4 * 3 * (size_t)p->item_max);
+    p->item_class = take(4 * (size_t)p->item_max);
+    p->class_hist = take(4 * 3 * (kItemClasses + 1));
     p->nngb = take(4 * N);
     p->nngb_force = take(4 * N);
     p->stage = take(4 * N);
@@ -171,6 +176,9 @@ sph_status sph_create(const sph_aos_layout *layout, const sph_params *params, in
     c->item_first = (int32_t *)(w + plan.item_first);
     c->item_count = (int32_t *)(w + plan.item_count);
     c->item_tmp = (int32_t *)(w + plan.item_tmp);
+    c->item_sorted = (int32_t *)(w + plan.item_sorted);
+    c->item_class = (int32_t *)(w + plan.item_class);
+    c->class_hist = (int32_t *)(w + plan.class_hist);
     c->nngb = (int32_t *)(w + plan.nngb);
     c->nngb_force = (int32_t *)(w + plan.nngb_force);
     c->stage = (float *)(w + plan.stage);
@@ -373,6 +381,14 @@ sph_status sph_set_tuning(sph_ctx *c, const sph_tuning *t)
     if (t->subcells > 0) {
         if (t->subcells > kMaxSub) return SPH_EINVAL;
         n.subcells = t->subcells;
+    }
+    if (t->item_order >= 0) {
+        if (t->item_order > 1) return SPH_EINVAL;
+        n.item_order = t->item_order;
+    }
+    if (t->class_launches >= 0) {
+        if (t->class_launches > 1) return SPH_EINVAL;
+        n.class_launches = t->class_launches;
     }
     if (n.stage_density < 32 || n.stage_force < 32) return SPH_EINVAL;
     if (n.stage_density > 65535 || n.stage_force > 65535) return SPH_EINVAL;

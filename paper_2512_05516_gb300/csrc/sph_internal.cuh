@@ -22,6 +22,7 @@ constexpr int kScanTile = kScanThreads * kScanItems;      // elements per scan b
 constexpr int kItemTile = 32;                              // i-particles per pair-kernel work item (one warp)
 constexpr int kMaxSub = 2;                                 // sub-cells per cell edge, at most
 constexpr int kMaxBlock = 256;
+constexpr int kItemClasses = 32;                           // power-of-two cost classes of work items
 constexpr int kMaxCellsPerAxis = 4096;                     // the binning caps n_c per axis here
 constexpr float kSigma = 0.318309886183790671538f;        // 1/pi, 3D M4 normalisation
 
@@ -45,7 +46,7 @@ struct DevStats {
 struct Plan {
     size_t keys[2], vals[2];
     size_t cell_count, cell_start, scan_part, ghist;
-    size_t item_cell, item_first, item_count, item_tmp;
+    size_t item_cell, item_first, item_count, item_tmp, item_sorted, item_class, class_hist;
     size_t nngb, nngb_force, stage, aos_tmp, stats, key_hmax, origin;
     size_t soa[SPH_NFIELDS][3];
     size_t total;
@@ -258,6 +259,10 @@ struct sph_ctx {
     int32_t *cell_count = nullptr, *cell_start = nullptr, *scan_part = nullptr;
     uint32_t *ghist = nullptr;
     int32_t *item_cell = nullptr, *item_first = nullptr, *item_count = nullptr, *item_tmp = nullptr;
+    int32_t *item_sorted = nullptr;   // 3 x item_max: the items in queue order, while sorting
+    int32_t *item_class = nullptr;    // cost class of every item
+    int32_t *class_hist = nullptr;    // per class: count, start (kItemClasses + 1), cursor
+    bool items_by_class = false;      // the last binning grouped the items by cost class
     int32_t *nngb = nullptr, *nngb_force = nullptr;
     float *stage = nullptr;
     float *key_hmax = nullptr;    // largest h of every sub-cell (force pruning)

@@ -208,17 +208,14 @@ def sedov(nx: int = 256, ny: int = 256, nz: int = 128, seed: int = SEED_BASE + 3
                     meta={"m": m, "hot": hot, "h0": h0})
 
 
-def _maxwell_cdf(a):
-    """P(|d| < R) for d ~ N(0, s^2 I_3), a = R / s."""
-    return math.erf(a / math.sqrt(2.0)) - math.sqrt(2.0 / math.pi) * a * math.exp(-0.5 * a * a)
-
-
 def gaussian_mixture(n: int = 16_777_216, seed: int = SEED_BASE + 4, n_blob: int = 8,
                      background: float = 0.2) -> Workload:
     """Clustered set: a `background` fraction uniform in the unit cube and the
     rest split equally over `n_blob` isotropic Gaussians with centres uniform in
-    the cube and sigma_k = 0.01 * 10^(k/7), wrapped periodically.  One global h
-    is chosen so that the mean neighbour count (pairs within 2h) is 48."""
+    the cube and sigma_k = 0.01 * 10^(k/7), wrapped periodically.  One global h,
+    set like the uniform set's: (4 pi / 3) (2h)^3 N = 48, i.e. 48 neighbours at
+    the mean density (2h = 0.0088 and 113 cells per axis at N = 2^24); the
+    clusters then hold up to ~10^5 particles within 2h."""
     rng = np.random.Generator(np.random.PCG64(seed))
     sig = np.array([0.01 * 10.0 ** (k / 7.0) for k in range(n_blob)])
     centres = rng.uniform(0.0, 1.0, size=(n_blob, 3))
@@ -231,32 +228,7 @@ def gaussian_mixture(n: int = 16_777_216, seed: int = SEED_BASE + 4, n_blob: int
         parts.append(centres[k] + sig[k] * rng.standard_normal(size=(counts[k], 3)))
     pos = _wrap(np.concatenate(parts), (1.0, 1.0, 1.0))
     pos = pos[rng.permutation(n)]
-    w_bg = n_bg / n
-    w = np.array(counts) / n
-
-    def mean_ngb(R):
-        vr = 4.0 / 3.0 * math.pi * R ** 3
-        e = w_bg * w_bg * vr + 2.0 * w_bg * (1.0 - w_bg) * vr
-        for k in range(n_blob):
-            e += w[k] ** 2 * _maxwell_cdf(R / (math.sqrt(2.0) * sig[k]))
-            for l in range(n_blob):
-                if l == k:
-                    continue
-                d = centres[k] - centres[l]
-                d -= np.round(d)
-                s2 = sig[k] ** 2 + sig[l] ** 2
-                g = math.exp(-0.5 * float(d @ d) / s2) / (2.0 * math.pi * s2) ** 1.5
-                e += w[k] * w[l] * g * vr
-        return e * n
-
-    lo, hi = 1e-5, 0.5
-    for _ in range(200):
-        mid = 0.5 * (lo + hi)
-        if mean_ngb(mid) < N_NGB:
-            lo = mid
-        else:
-            hi = mid
-    h = 0.25 * (lo + hi)
+    h = 0.5 * (3.0 * N_NGB / (4.0 * math.pi * n)) ** (1.0 / 3.0)
     aos = _empty(n)
     _set(aos, "x", pos)
     _set(aos, "m", 1.0 / n)
