@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--prec", default="fp32", help="SoA storage of v, m, h, u (fp32|bf16|fp16|m16|m10)")
     ap.add_argument("--no-long-run", action="store_true", help="skip the 33.5M-particle memory-bound rows")
     ap.add_argument("--no-autotune", action="store_true", help="default launch shapes instead of the autotuner's")
+    ap.add_argument("--no-uneven", action="store_true", help="skip the 16.7M-particle clustered batching rows")
+    ap.add_argument("--no-vs-plain", action="store_true", help="skip the plain FP32 SoA comparison")
     return ap.parse_args()
 
 
@@ -422,6 +424,105 @@ def run_long_run(steps: int = 3, graph_steps: int = 10):
                             "fp32_kernels_ms": ms32, "speedup": fp32_step / fp16_step}}
 
 
+def run_vs_plain(lattice: int = 124, steps: int = 3):
+    """The reduced-precision batched step against the plain FP32 SoA step on
+    the same Sod set: bin, convert, density (5 Newton steps), force,
+    kick/drift + write-back.  Reduced: v, m, h, u stored in FP16 under
+    power-of-two storage scales, batched kernels with the autotuner's shapes.
+    Plain: FP32 storage, one thread per particle over the 27 neighbour
+    cells."""
+    import torch
+    import paper_2512_05516_gb300 as sph
+    from paper_2512_05516_gb300 import autotune
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    wl = sph_inputs.sod(n_lattice=lattice)
+    stream = torch.cuda.Stream(dev)
+    nc = [int(math.floor(b / max(wl.cell_edge, 2 * wl.h_cap))) for b in wl.box]
+    params = sph.make_params(wl.box, gamma=wl.gamma, alpha=wl.alpha_av, beta=wl.beta_av,
+                             eps=wl.eps_av, eta=wl.eta, h_max=wl.h_cap)
+    rows = {}
+    for name in ("plain_fp32", "batched_fp16_scaled"):
+        aos = torch.from_numpy(wl.aos.copy()).to(dev)
+        s = sph.Sph(aos, sph.layout_112(), params, int(np.prod(nc)), 0, stream=stream)
+        prec = None
+        with torch.cuda.stream(stream):
+            if name == "plain_fp32":
+                s.set_tuning(pair_kernel=1)
+            else:
+                prec = {"v": "fp16", "m": "fp16", "h": "fp16", "u": "fp16"}
+                s.set_scale({f: sph.suggest_scale(float(np.abs(wl.col(f)).max()), "fp16") for f in ("v", "m", "h", "u")})
+                autotune.tune(s, wl.cell_edge, prec, wl.newton_steps)
+            s.step(wl.dt, wl.newton_steps, prec=prec, cell_edge=wl.cell_edge)
+            s.reset_stats()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                s.step(wl.dt, wl.newton_steps, prec=prec, cell_edge=wl.cell_edge)
+            e1.record(stream)
+            e1.synchronize()
+        st = s.stats()
+        ms = e0.elapsed_time(e1) / steps
+        rows[name] = {"ms_per_step": ms,
+                      "pairs_per_s": (st["pairs_density"] + st["pairs_force"]) / steps / (ms / 1e3),
+                      "tests_per_pair": (st["tests_density"] + st["tests_force"]) /
+                      max(1, st["pairs_density"] + st["pairs_force"])}
+        s.close()
+        del aos
+    rows["speedup"] = rows["plain_fp32"]["ms_per_step"] / rows["batched_fp16_scaled"]["ms_per_step"]
+    rows["workload"] = f"sod_{wl.n}"
+    rows["density_error_note"] = ("FP16 storage under power-of-two scales: density relative RMSE "
+                                  "3.1e-4, max 4.5e-4 against FP64 after one step (tests/precision_report.py)")
+    return rows
+
+
+def run_uneven(n: int = 16_777_216):
+    """Uneven occupancy (the clustered Gaussian mixture, one global h, up to
+    ~65,000 particles in a cell), BF16 storage of v, m, h, u: one density
+    (fixed h) and one force call per work-queue variant -- one persistent
+    launch over the queue in cell order, the same with the costliest items
+    first, and one launch per power-of-two cost class."""
+    import torch
+    import paper_2512_05516_gb300 as sph
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    wl = sph_inputs.gaussian_mixture(n=n)
+    stream = torch.cuda.Stream(dev)
+    aos = torch.from_numpy(wl.aos).to(dev)
+    nc = [int(math.floor(b / max(wl.cell_edge, 2 * wl.h_cap))) for b in wl.box]
+    params = sph.make_params(wl.box, eta=wl.eta, h_max=wl.h_cap)
+    s = sph.Sph(aos, sph.layout_112(), params, int(np.prod(nc)), 0, stream=stream)
+    prec = {"v": "bf16", "m": "bf16", "h": "bf16", "u": "bf16"}
+    rows = []
+    with torch.cuda.stream(stream):
+        for order, per in [(0, 0), (1, 0), (1, 1)]:
+            s.set_tuning(item_order=order, class_launches=per)
+            s.bin_cells(wl.cell_edge)
+            s.aos_to_soa(sph.FIELDS_FORCE, prec)
+            s.density(0)                                  # warm-up
+            s.force()
+            s.reset_stats()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record(stream)
+            s.density(0)
+            ev[1].record(stream)
+            s.force()
+            ev[2].record(stream)
+            ev[2].synchronize()
+            st = s.stats()
+            td, tf = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+            rows.append({"queue": "costliest first" if order else "cell order",
+                         "launches": "one per cost class" if per else "one persistent",
+                         "density_ms": td, "force_ms": tf,
+                         "density_pairs_per_s": st["pairs_density"] / (td / 1e3),
+                         "force_pairs_per_s": st["pairs_force"] / (tf / 1e3),
+                         "pairs_per_s": (st["pairs_density"] + st["pairs_force"]) / ((td + tf) / 1e3),
+                         "max_occupancy": st["max_occupancy"]})
+    s.close()
+    del aos
+    torch.cuda.empty_cache()
+    return {"workload": f"gaussian_mixture_{n}", "storage": "bf16 (v, m, h, u)", "h": wl.meta["h"],
+            "cells_per_axis": nc[0], "variants": rows}
+
+
 # ----------------------------------------------------------------- oracle
 def run_oracle_sample(n_targets: int, seed: int = 1):
     """The FP64 oracle (as it stands) on a sample of the same workload: the
@@ -529,6 +630,8 @@ def main():
         return
     cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline()
     long = None if args.no_long_run or world > 1 else run_long_run()
+    uneven = None if args.no_uneven or world > 1 else run_uneven()
+    vs_plain = None if args.no_vs_plain or world > 1 else run_vs_plain()
     out = {
         "metric": METRIC, "value": pairs / total_s, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
@@ -541,7 +644,7 @@ def main():
                    "tuning": r["tuning"], "tuning_source": r["tuning_source"]},
         "roofline": r["roofline"], "cpu_baseline": cpu, "e2e": r["e2e"],
         "gpu_launches": r["launches"], "clocks": r["clocks"], "kernels": r["kernels"],
-        "memory_bound_rows": long,
+        "memory_bound_rows": long, "uneven_batching": uneven, "vs_plain_fp32_soa": vs_plain,
     }
     print(json.dumps(out))
     if world > 1:

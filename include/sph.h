@@ -164,6 +164,10 @@ typedef struct {
     int32_t class_launches;      /* 1: one pair-kernel launch per cost class (needs
                                     item_order 1), 0: one persistent launch over the
                                     whole queue; -1 keeps the current */
+    int32_t pair_kernel;         /* 0: the batched kernels (warp work items, staged and
+                                    pruned neighbourhoods); 1: the plain form, one thread
+                                    per particle looping over the 27 neighbour cells
+                                    straight from the SoA (a baseline); -1 keeps the current */
 } sph_tuning;
 
 /* Where the library's arrays live inside the workspace (byte offsets from the

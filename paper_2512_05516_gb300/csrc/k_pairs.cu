@@ -536,6 +536,38 @@ __global__ void __launch_bounds__(256) k_key_hmax(FieldRef h, const int32_t *slo
         atomicMax(reinterpret_cast<unsigned *>(key_hmax) + key, mx);
 }
 
+// One interacting force pair (r2 > 0, j != i): separation d = x_i - x_j,
+// hs = h_i + h_j, qb = (v_j, m_j), qc = (P_j / rho_j^2, rho_j, c_j, -).
+__device__ __forceinline__ void force_pair(float &ax, float &ay, float &az, float &du, float vxi, float vyi,
+                                           float vzi, float rhoi, float Pr2i, float ci, float dx, float dy,
+                                           float dz, float r2, float hs, const float4 qb, const float4 qc,
+                                           float alpha, float beta, float eps)
+{
+    const float rinv = rsqrtf(r2);
+    const float r = r2 * rinv;
+    const float hb = 0.5f * hs;
+    const float hbinv = 2.0f / hs;
+    const float qq = r * hbinv;
+    float w, dw;
+    spline(qq, w, dw);
+    const float hb2 = hbinv * hbinv;
+    const float gw = kSigma * hb2 * hb2 * dw * rinv;   // grad_i W = d * gw
+    const float vx = vxi - qb.x, vy = vyi - qb.y, vz = vzi - qb.z;
+    const float vdotr = fmaf(vx, dx, fmaf(vy, dy, vz * dz));
+    float visc = 0.0f;
+    if (vdotr < 0.0f) {
+        const float mu = hb * vdotr / fmaf(eps * hb, hb, r2);
+        const float cbar = 0.5f * (ci + qc.z);
+        const float rbar = 0.5f * (rhoi + qc.y);
+        visc = fmaf(-alpha * cbar, mu, beta * mu * mu) / rbar;
+    }
+    const float fac = qb.w * (Pr2i + qc.x + visc) * gw;
+    ax = fmaf(-fac, dx, ax);
+    ay = fmaf(-fac, dy, ay);
+    az = fmaf(-fac, dz, az);
+    du = fmaf(qb.w * fmaf(0.5f, visc, Pr2i), vdotr * gw, du);
+}
+
 // Stage the force candidates (those within h_max(warp) + h_j of the warp box)
 // from `cur` on, until the stage is full or the stream ends; returns how many
 // were staged and moves `cur` (as stage_density).  The loads a kept
@@ -695,32 +727,9 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_force(ForceArgs a)
                         const float4 qc = sC[p];
                         if (__float_as_int(qc.w) != kself) {
                             ++cnt;
-                            if (r2 > 0.0f) {
-                                const float4 qb = sB[p];
-                                const float rinv = rsqrtf(r2);
-                                const float r = r2 * rinv;
-                                const float hb = 0.5f * hs;
-                                const float hbinv = 2.0f / hs;
-                                const float qq = r * hbinv;
-                                float w, dw;
-                                spline(qq, w, dw);
-                                const float hb2 = hbinv * hbinv;
-                                const float gw = kSigma * hb2 * hb2 * dw * rinv;   // grad_i W = d * gw
-                                const float vx = vxi - qb.x, vy = vyi - qb.y, vz = vzi - qb.z;
-                                const float vdotr = fmaf(vx, dx, fmaf(vy, dy, vz * dz));
-                                float visc = 0.0f;
-                                if (vdotr < 0.0f) {
-                                    const float mu = hb * vdotr / fmaf(a.eps * hb, hb, r2);
-                                    const float cbar = 0.5f * (ci + qc.z);
-                                    const float rbar = 0.5f * (rhoi + qc.y);
-                                    visc = fmaf(-a.alpha * cbar, mu, a.beta * mu * mu) / rbar;
-                                }
-                                const float fac = qb.w * (Pr2i + qc.x + visc) * gw;
-                                ax = fmaf(-fac, dx, ax);
-                                ay = fmaf(-fac, dy, ay);
-                                az = fmaf(-fac, dz, az);
-                                du = fmaf(qb.w * fmaf(0.5f, visc, Pr2i), vdotr * gw, du);
-                            }
+                            if (r2 > 0.0f)
+                                force_pair(ax, ay, az, du, vxi, vyi, vzi, rhoi, Pr2i, ci, dx, dy, dz, r2, hs, sB[p],
+                                           qc, a.alpha, a.beta, a.eps);
                         }
                     }
                     if (e >= len) break;   // every staged candidate scanned
@@ -745,6 +754,165 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_force(ForceArgs a)
         if (my_tests) atomicAdd(&c.st->tests_force, my_tests);
     }
     if (my_err) set_error(c.st, my_err);
+}
+
+// ---------------------------------------------------------------------------
+// The plain form: one thread per particle, looping over the particles of the
+// 27 neighbour cells straight from the SoA (no work items, no staging, no
+// pruning).  The same arithmetic as the batched kernels, kept as the
+// baseline that batching and staging are measured against.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void cell_of_key(const Common &c, int key, int &kx, int &ky, int &kz)
+{
+    const int cell = key >> c.lg_s3;
+    kx = cell % c.nc[0];
+    ky = (cell / c.nc[0]) % c.nc[1];
+    kz = cell / (c.nc[0] * c.nc[1]);
+}
+
+// first key of neighbour cell t (0..26) of cell (kx, ky, kz), periodic
+__device__ __forceinline__ int neighbour_key(const Common &c, int kx, int ky, int kz, int t)
+{
+    int nx = kx + t % 3 - 1, ny = ky + (t / 3) % 3 - 1, nz = kz + t / 9 - 1;
+    nx += nx < 0 ? c.nc[0] : (nx >= c.nc[0] ? -c.nc[0] : 0);
+    ny += ny < 0 ? c.nc[1] : (ny >= c.nc[1] ? -c.nc[1] : 0);
+    nz += nz < 0 ? c.nc[2] : (nz >= c.nc[2] ? -c.nc[2] : 0);
+    return (nx + c.nc[0] * (ny + c.nc[1] * nz)) << c.lg_s3;
+}
+
+__global__ void __launch_bounds__(128) k_density_plain(DensityArgs a, const int32_t *slot_key)
+{
+    const Common &c = a.c;
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= c.n) return;
+    int kx, ky, kz;
+    cell_of_key(c, slot_key[k], kx, ky, kz);
+    const float xi = ld_val(c.x.p[0], c.x.fmt, k) * c.x.dec;
+    const float yi = ld_val(c.x.p[1], c.x.fmt, k) * c.x.dec;
+    const float zi = ld_val(c.x.p[2], c.x.fmt, k) * c.x.dec;
+    const float mi = ld_val(c.m.p[0], c.m.fmt, k) * c.m.dec;
+    float hi = ld_val(c.h.p[0], c.h.fmt, k) * c.h.dec;
+    const float ui = a.has_u ? ld_val(a.u.p[0], a.u.fmt, k) * a.u.dec : 0.0f;
+    unsigned err = 0;
+    bool clamped = false;
+    if (!(hi > 0.0f) || !isfinite(hi)) { hi = a.h_cap; err |= SPH_ERR_NONFINITE; }
+    if (hi > a.h_cap) { hi = a.h_cap; clamped = true; }
+    float rho = 0.f;
+    int cnt = 0;
+    unsigned long long tests = 0, pairs = 0;
+    for (int pass = 0; pass < a.npass; ++pass) {
+        const float h2x4 = 4.0f * hi * hi;
+        const float hinv = 1.0f / hi;
+        const bool deriv = pass + 1 < a.npass;
+        DAcc acc{0.f, 0.f, 0.f, 0};
+        for (int t = 0; t < 27; ++t) {
+            float sx, sy, sz;
+            stencil_shift(c, t, sx, sy, sz);
+            const int key0 = neighbour_key(c, kx, ky, kz, t);
+            const int j0 = c.cell_start[key0], j1 = c.cell_start[key0 + c.s3];
+            tests += (unsigned long long)(j1 - j0);
+            for (int j = j0; j < j1; ++j) {
+                const float4 q = make_float4(fmaf(ld_val(c.x.p[0], c.x.fmt, j), c.x.dec, sx),
+                                             fmaf(ld_val(c.x.p[1], c.x.fmt, j), c.x.dec, sy),
+                                             fmaf(ld_val(c.x.p[2], c.x.fmt, j), c.x.dec, sz),
+                                             ld_val(c.m.p[0], c.m.fmt, j) * c.m.dec);
+                dens_pair(acc, xi, yi, zi, h2x4, hinv, a.plain_sum, deriv, q);
+            }
+        }
+        const float h3inv = hinv * hinv * hinv;
+        rho = kSigma * h3inv * (acc.s - acc.c);
+        const float drdh = -kSigma * h3inv * hinv * acc.d;
+        cnt = acc.n - 1;
+        pairs += (unsigned long long)cnt;      // every pass's pairs, as the batched kernel counts them
+        if (pass + 1 < a.npass) {
+            const float f = rho - mi * a.eta3 * h3inv;
+            const float fp = drdh + 3.0f * mi * a.eta3 * h3inv * hinv;
+            float hn = hi;
+            if (fp > 0.0f && isfinite(f) && isfinite(fp)) hn = hi - f / fp;
+            else err |= SPH_ERR_NEWTON;
+            hn = fminf(fmaxf(hn, 0.5f * hi), 2.0f * hi);
+            if (hn > a.h_cap) { hn = a.h_cap; clamped = true; }
+            hi = hn;
+        }
+    }
+    if (!isfinite(rho)) err |= SPH_ERR_NONFINITE;
+    st_val(a.rho_out, a.rho_fmt, k, rho * a.rho_enc);
+    if (a.write_h) st_val(a.h_out, a.h_fmt, k, hi * a.h_enc);
+    a.nngb[k] = cnt;
+    if (a.has_u) {
+        const float P = a.gm1 * rho * ui;
+        st_val(a.P_out, a.P_fmt, k, P * a.P_enc);
+        st_val(a.cs_out, a.cs_fmt, k, __fsqrt_rn(a.gamma * P / rho) * a.cs_enc);
+    }
+    if (clamped) {
+        atomicAdd(&c.st->hcap_clamps, 1ull);
+        err |= SPH_ERR_HCAP;
+    }
+    if (err) set_error(c.st, err);
+    atomicAdd(&c.st->pairs_density, pairs);
+    atomicAdd(&c.st->tests_density, tests);
+}
+
+__global__ void __launch_bounds__(128) k_force_plain(ForceArgs a, const int32_t *slot_key)
+{
+    const Common &c = a.c;
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= c.n) return;
+    int kx, ky, kz;
+    cell_of_key(c, slot_key[k], kx, ky, kz);
+    const float xi = ld_val(c.x.p[0], c.x.fmt, k) * c.x.dec;
+    const float yi = ld_val(c.x.p[1], c.x.fmt, k) * c.x.dec;
+    const float zi = ld_val(c.x.p[2], c.x.fmt, k) * c.x.dec;
+    const float hi = ld_val(c.h.p[0], c.h.fmt, k) * c.h.dec;
+    const float vxi = ld_val(a.v.p[0], a.v.fmt, k) * a.v.dec;
+    const float vyi = ld_val(a.v.p[1], a.v.fmt, k) * a.v.dec;
+    const float vzi = ld_val(a.v.p[2], a.v.fmt, k) * a.v.dec;
+    const float rhoi = ld_val(a.rho.p[0], a.rho.fmt, k) * a.rho.dec;
+    const float Pr2i = ld_val(a.P.p[0], a.P.fmt, k) * a.P.dec / (rhoi * rhoi);
+    const float ci = ld_val(a.cs.p[0], a.cs.fmt, k) * a.cs.dec;
+    unsigned err = hi > a.h_cap ? SPH_ERR_HCAP : 0u;
+    float ax = 0.f, ay = 0.f, az = 0.f, du = 0.f;
+    int cnt = 0;
+    unsigned long long tests = 0;
+    for (int t = 0; t < 27; ++t) {
+        float sx, sy, sz;
+        stencil_shift(c, t, sx, sy, sz);
+        const int key0 = neighbour_key(c, kx, ky, kz, t);
+        const int j0 = c.cell_start[key0], j1 = c.cell_start[key0 + c.s3];
+        tests += (unsigned long long)(j1 - j0);
+        for (int j = j0; j < j1; ++j) {
+            const float dx = xi - fmaf(ld_val(c.x.p[0], c.x.fmt, j), c.x.dec, sx);
+            const float dy = yi - fmaf(ld_val(c.x.p[1], c.x.fmt, j), c.x.dec, sy);
+            const float dz = zi - fmaf(ld_val(c.x.p[2], c.x.fmt, j), c.x.dec, sz);
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float hj = ld_val(c.h.p[0], c.h.fmt, j) * c.h.dec;
+            const float hs = hi + hj;
+            if (hj > a.h_cap) err |= SPH_ERR_HCAP;
+            if (!(r2 < hs * hs) || j == k) continue;
+            ++cnt;
+            if (r2 > 0.0f) {
+                const float rj = ld_val(a.rho.p[0], a.rho.fmt, j) * a.rho.dec;
+                const float4 qb = make_float4(ld_val(a.v.p[0], a.v.fmt, j) * a.v.dec,
+                                              ld_val(a.v.p[1], a.v.fmt, j) * a.v.dec,
+                                              ld_val(a.v.p[2], a.v.fmt, j) * a.v.dec,
+                                              ld_val(c.m.p[0], c.m.fmt, j) * c.m.dec);
+                const float4 qc = make_float4(ld_val(a.P.p[0], a.P.fmt, j) * a.P.dec / (rj * rj), rj,
+                                              ld_val(a.cs.p[0], a.cs.fmt, j) * a.cs.dec, 0.0f);
+                force_pair(ax, ay, az, du, vxi, vyi, vzi, rhoi, Pr2i, ci, dx, dy, dz, r2, hs, qb, qc, a.alpha,
+                           a.beta, a.eps);
+            }
+        }
+    }
+    if (!isfinite(ax) || !isfinite(ay) || !isfinite(az) || !isfinite(du)) err |= SPH_ERR_NONFINITE;
+    a.a[0][k] = ax;
+    a.a[1][k] = ay;
+    a.a[2][k] = az;
+    a.dudt[k] = du;
+    a.nngb[k] = cnt;
+    if (err) set_error(c.st, err);
+    atomicAdd(&c.st->pairs_force, (unsigned long long)cnt);
+    atomicAdd(&c.st->tests_force, tests);
 }
 
 Common make_common(sph_ctx *c, int cap)
@@ -914,6 +1082,14 @@ cudaError_t run_density(sph_ctx *c, int newton_steps)
     a.P_enc = c->enc(SPH_F_P);
     a.cs_enc = c->enc(SPH_F_CS);
     a.nngb = c->nngb;
+    if (c->tuning.pair_kernel == 1) {
+        k_density_plain<<<(unsigned)((c->n + 127) / 128), 128, 0, c->stream>>>(a, c->slot_cell());
+        c->launches += 1;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        if (a.write_h && h_packed) return run_pack(c, c->stage, SPH_F_H);
+        return cudaSuccess;
+    }
     const size_t smem = density_smem_bytes(c->tuning.block_threads, a.c.cap);
     // what the staging loads decides the instantiation
     cudaError_t e = Variants<DensityK>::launch(c, fmt_variant(a.c.x.fmt, a.c.m.fmt), a, smem, c->lc_density);
@@ -954,6 +1130,11 @@ cudaError_t run_force(sph_ctx *c)
     c->launches += 1;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     a.key_hmax = c->key_hmax;
+    if (c->tuning.pair_kernel == 1) {
+        k_force_plain<<<(unsigned)((c->n + 127) / 128), 128, 0, c->stream>>>(a, c->slot_cell());
+        c->launches += 1;
+        return cudaGetLastError();
+    }
     const size_t smem = force_smem_bytes(c->tuning.block_threads, a.c.cap);
     // fixed-format kernels: v, m, h share one format; rho, P, c are FP32
     int v = 0;

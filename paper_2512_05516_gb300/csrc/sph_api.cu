@@ -61,6 +61,7 @@ void default_tuning(sph_tuning *t)
     t->subcells = 2;
     t->item_order = 0;
     t->class_launches = 0;
+    t->pair_kernel = 0;
 }
 
 }  // namespace
@@ -389,6 +390,10 @@ sph_status sph_set_tuning(sph_ctx *c, const sph_tuning *t)
     if (t->class_launches >= 0) {
         if (t->class_launches > 1) return SPH_EINVAL;
         n.class_launches = t->class_launches;
+    }
+    if (t->pair_kernel >= 0) {
+        if (t->pair_kernel > 1) return SPH_EINVAL;
+        n.pair_kernel = t->pair_kernel;
     }
     if (n.stage_density < 32 || n.stage_force < 32) return SPH_EINVAL;
     if (n.stage_density > 65535 || n.stage_force > 65535) return SPH_EINVAL;

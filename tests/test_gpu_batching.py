@@ -75,3 +75,28 @@ def test_autotuner_picks_and_caches_a_valid_shape(orc, tmp_path):
     o = orc.step(wl)
     assert (np.abs(out[:, 11] - o["rho"]) / o["rho"]).max() <= 1e-5
     s.close()
+
+
+def test_plain_form_matches_batched_and_oracle(orc):
+    # the baseline (one thread per particle over the 27 cells, no staging or
+    # pruning) computes the same step: against the oracle within the FP32
+    # tolerances, against the batched kernels to rounding
+    wl = sph_inputs.sod(n_lattice=48, seed=72)
+    outs = []
+    for plain in (0, 1):
+        s = make_sph(wl)
+        s.set_tuning(pair_kernel=plain)
+        s.step(wl.dt, 5, cell_edge=wl.cell_edge)
+        outs.append((s.aos.cpu().numpy(), s.stats()))
+        assert s.tuning()["pair_kernel"] == plain
+        s.close()
+    o = orc.step(wl)
+    for out, st in outs:
+        assert st["error_bits"] == 0
+        assert (np.abs(out[:, 11] - o["rho"]) / o["rho"]).max() <= 1e-5
+        scale = np.mean(np.linalg.norm(o["a"], axis=1))
+        assert np.linalg.norm(out[:, 6:9] - o["a"], axis=1).max() / scale <= 1e-5
+    (b, sb), (p, sp) = outs
+    assert sb["pairs_density"] == sp["pairs_density"] and sb["pairs_force"] == sp["pairs_force"]
+    assert sp["tests_density"] > 3 * sb["tests_density"]          # no pruning in the plain form
+    assert (np.abs(b[:, 11] - p[:, 11]) / p[:, 11]).max() <= 1e-6
