@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="default launch shapes instead of the autotuner's")
     ap.add_argument("--no-uneven", action="store_true", help="skip the 16.7M-particle clustered batching rows")
     ap.add_argument("--no-vs-plain", action="store_true", help="skip the plain FP32 SoA comparison")
+    ap.add_argument("--profile-case", choices=["pairs", "memory"], default=None,
+                    help="run one small fixed workload for an ncu capture and exit")
     return ap.parse_args()
 
 
@@ -577,8 +579,50 @@ def combine_ranks(total_s: float, pairs: float, e2e_value: float, device: str):
     return float(t[0].item()), float(p[0].item()), float(p[1].item())
 
 
+def profile_case(which: str):
+    """Small fixed workloads for ncu captures (profiles/ summaries name the
+    command).  'pairs': the 1,072,476-particle Sod step twice (the second is
+    the one to capture), default launch shapes.  'memory': the long-run
+    lattice at 256 x 128 x 128 (4,194,304 particles, AoS 470 MB > L2), FP16
+    storage, cell-ordered records; step 1 with separate kick/drift and
+    write-back, step 2 with the fused call."""
+    import torch
+    import paper_2512_05516_gb300 as sph
+    if which == "pairs":
+        wl = sph_inputs.sod()
+        prec, ws, steps = None, 0, 2
+    else:
+        wl = sph_inputs.long_run(nx=256, ny=128, nz=128)
+        prec, ws, steps = {"x": "fp16", "v": "fp16", "m": "fp16", "h": "fp16", "u": "fp16"}, sph.WS_REORDER, 2
+    aos = torch.from_numpy(wl.aos).cuda()
+    nc = [int(math.floor(b / max(wl.cell_edge, 2 * wl.h_cap))) for b in wl.box]
+    params = sph.make_params(wl.box, gamma=wl.gamma, alpha=wl.alpha_av, beta=wl.beta_av,
+                             eps=wl.eps_av, eta=wl.eta, h_max=wl.h_cap)
+    s = sph.Sph(aos, sph.layout_112(), params, int(np.prod(nc)), ws)
+    ns = wl.newton_steps if which == "pairs" else 0
+    for k in range(steps):
+        s.bin_cells(wl.cell_edge, reorder=(which == "memory" and k == 0))
+        s.aos_to_soa(sph.FIELDS_FORCE, prec)
+        s.density(ns)
+        s.force()
+        if which == "memory" and k == 0:
+            s.kick_drift(wl.dt, wl.dt)
+            s.soa_to_aos(sph.FIELDS_OUTPUT)
+        else:
+            s.kick_drift_writeback(wl.dt, wl.dt, sph.FIELDS_OUTPUT)
+    torch.cuda.synchronize()
+    st = s.stats()
+    print(json.dumps({"profile_case": which, "n": wl.n, "error_bits": st["error_bits"],
+                      "tuning": s.tuning()}))
+    if st["error_bits"] & (sph.ERR_NONFINITE | sph.ERR_OUTSIDE):
+        raise SystemExit(1)
+
+
 def main():
     args = parse()
+    if args.profile_case:
+        profile_case(args.profile_case)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
 

@@ -149,7 +149,9 @@ typedef struct {
 #define SPH_ERR_HCAP      4      /* some h was clamped at h_max */
 #define SPH_ERR_NEWTON    8      /* a Newton step met a non-positive derivative */
 
-/* Launch shapes of the pair kernels (an autotuner sets them). */
+/* Launch shapes of the pair kernels (an autotuner sets them; the defaults
+ * after sph_create are block_threads 32, ctas_per_sm 0, stage_density 1024,
+ * stage_force 96, subcells 2, item_order 1, class_launches 0, pair_kernel 0). */
 typedef struct {
     int32_t block_threads;       /* threads per CTA of the pair kernels (32..256, multiple of 32); one warp per work item */
     int32_t ctas_per_sm;         /* persistent CTAs per SM (0: occupancy maximum) */

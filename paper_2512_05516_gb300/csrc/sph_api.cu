@@ -52,14 +52,15 @@ bool fmt_allowed(int f, int fmt)
 
 void default_tuning(sph_tuning *t)
 {
-    // measured best on the 1M-particle Sod step (GB300): density prefers a
-    // stage that holds a whole neighbourhood, force more resident warps
+    // the autotuner's choice on the 1M-particle Sod step (GB300): density
+    // prefers a stage that holds a whole neighbourhood, force more resident
+    // warps, and the costliest work items go first
     t->block_threads = 32;
     t->ctas_per_sm = 0;
     t->stage_density = 1024;
-    t->stage_force = 128;
+    t->stage_force = 96;
     t->subcells = 2;
-    t->item_order = 0;
+    t->item_order = 1;
     t->class_launches = 0;
     t->pair_kernel = 0;
 }
