@@ -39,6 +39,7 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kLaneCap = 96;                                 // per-lane pair list entries
 constexpr float kSkin = 0.12f;                               // list / stage radius = 2 h (1 + skin)
+constexpr float kSkinTight = 0.02f;                          // list skin of a lane whose list overflowed
 constexpr int kMaxEnt = 27 * kMaxSub * kMaxSub * kMaxSub;    // stencil sub-cells
 constexpr int kEntPerLane = (kMaxEnt + 31) / 32;
 constexpr int kStageUnroll = 4;                              // 32-candidate batches in flight
@@ -83,14 +84,21 @@ struct ForceArgs {
     int32_t *nngb;
 };
 
-// The candidate stream of one warp: the kept stencil sub-cells, in stencil
-// order (neighbour cell t, then sub-cell), as prefix sums in shared memory.
-// Stream position g lies in the first entry e with incl[e] > g, at slot
-// base[e] + g.
-struct Tab {
+// The candidate stream of one warp: the kept (non-empty, within reach)
+// stencil sub-cells, compacted in stencil order (neighbour cell t, then
+// sub-cell), as prefix sums in shared memory.  Stream position g lies in the
+// first entry e with incl[e] > g, at slot base[e] + g; t[e] is the entry's
+// neighbour cell (for the shift into the item's cell frame).
+struct __align__(16) Tab {
     int incl[kMaxEnt];
     int base[kMaxEnt];
+    uint8_t t[kMaxEnt];
+    int nk;                          // kept entries
 };
+// Each warp's shared-memory region is stage | lists | table; the next warp's
+// float4 stage starts right after, so every part keeps 16-byte multiples.
+static_assert(sizeof(Tab) % 16 == 0, "stencil table size must keep 16-byte alignment");
+static_assert((32 * kLaneCap * sizeof(uint16_t)) % 16 == 0, "list size must keep 16-byte alignment");
 
 __device__ __forceinline__ int pop_item(DevStats *st, int lane)
 {
@@ -203,30 +211,42 @@ __device__ int build_stream(const Common &c, int cell, const Box &box, float R2,
         }
         local += cnt[i];
     }
-    int inc = local;
+    // prefix sums over the lanes: candidates, and kept entries (compaction)
+    int kept = 0;
+#pragma unroll
+    for (int i = 0; i < kEntPerLane; ++i) kept += cnt[i] > 0 ? 1 : 0;
+    int inc = local, kinc = kept;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const int v = __shfl_up_sync(FULL, inc, o);
-        if (lane >= o) inc += v;
+        const int w = __shfl_up_sync(FULL, kinc, o);
+        if (lane >= o) {
+            inc += v;
+            kinc += w;
+        }
     }
-    int run = inc - local;
+    int run = inc - local, pos = kinc - kept;
 #pragma unroll
     for (int i = 0; i < kEntPerLane; ++i) {
         const int e = lane * E + i;
-        if (i < E && e < nent) {
+        if (i < E && e < nent && cnt[i] > 0) {
             run += cnt[i];
-            tab.incl[e] = run;
-            tab.base[e] = st[i] - (run - cnt[i]);
+            tab.incl[pos] = run;
+            tab.base[pos] = st[i] - (run - cnt[i]);
+            tab.t[pos] = (uint8_t)(e >> c.lg_s3);
+            ++pos;
         }
     }
+    if (lane == 31) tab.nk = kinc;
     __syncwarp();
     return __shfl_sync(FULL, inc, 31);
 }
 
-// Walk forward from entry e to the entry holding stream position g (g < total).
-__device__ __forceinline__ int advance(const Tab &tab, int nent, int e, int g)
+// Walk forward from kept entry e to the entry holding stream position g
+// (g < total).
+__device__ __forceinline__ int advance(const Tab &tab, int nk, int e, int g)
 {
-    while (e < nent - 1 && tab.incl[e] <= g) ++e;
+    while (e < nk - 1 && tab.incl[e] <= g) ++e;
     return e;
 }
 
@@ -280,6 +300,34 @@ __device__ __forceinline__ void dens_pair(DAcc &a, float xi, float yi, float zi,
     a.n += in ? 1 : 0;
 }
 
+// This lane's list of the staged candidates with r^2 < R2 (indices into the
+// stage, at lst[l * 32 + lane]); returns how many there are (only the first
+// kLaneCap are stored).  Candidates go in batches whose shared-memory loads
+// are all issued before the batch's list stores.
+__device__ __forceinline__ int build_list(const float4 *sj, int T, float xi, float yi, float zi, float R2,
+                                          uint16_t *lst, int lane)
+{
+    constexpr int LB = 8;
+    int n = 0;
+    for (int e0 = 0; e0 < T; e0 += LB) {
+        float r2[LB];
+#pragma unroll
+        for (int u = 0; u < LB; ++u) {
+            const float4 q = sj[min(e0 + u, T - 1)];
+            const float dx = xi - q.x, dy = yi - q.y, dz = zi - q.z;
+            r2[u] = e0 + u < T ? fmaf(dx, dx, fmaf(dy, dy, dz * dz)) : R2;
+        }
+#pragma unroll
+        for (int u = 0; u < LB; ++u) {
+            if (r2[u] < R2) {
+                if (n < kLaneCap) lst[n * 32 + lane] = (uint16_t)(e0 + u);
+                ++n;
+            }
+        }
+    }
+    return n;
+}
+
 // A position in the candidate stream and the table entry holding it.
 struct Cursor {
     int g, e;
@@ -317,7 +365,7 @@ __device__ int stage_density(const Common &c, const Tab &tab, int total, const B
                              float4 *sj, int cap, Cursor &cur, int lane)
 {
     const unsigned lt = (1u << lane) - 1u;
-    const int nent = 27 * c.s3;
+    const int nk = tab.nk;
     int found = 0;
     int ecur = cur.e;
     for (int g0 = cur.g; g0 < total; g0 += 32 * kStageUnroll) {
@@ -329,10 +377,10 @@ __device__ int stage_density(const Common &c, const Tab &tab, int total, const B
             const int g = g0 + u * 32 + lane;
             q[u] = make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.0f);
             if (g < total) {
-                e = advance(tab, nent, e, g);
+                e = advance(tab, nk, e, g);
                 const int64_t j = (int64_t)tab.base[e] + g;
                 float sx, sy, sz;
-                stencil_shift(c, e >> c.lg_s3, sx, sy, sz);
+                stencil_shift(c, tab.t[e], sx, sy, sz);
                 q[u].x = fmaf(ldf<FX>(c.x.p[0], c.x.fmt, j), c.x.dec, sx);
                 q[u].y = fmaf(ldf<FX>(c.x.p[1], c.x.fmt, j), c.x.dec, sy);
                 q[u].z = fmaf(ldf<FX>(c.x.p[2], c.x.fmt, j), c.x.dec, sz);
@@ -427,20 +475,17 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
             }
             if (fits) {
                 // rebuild when some lane's h outgrew its list radius (always on pass 0)
+                // (only the lanes whose h outgrew their list rebuild it)
                 if (__any_sync(FULL, ok && hi > h_list)) {
-                    h_list = fminf(hi * (1.0f + kSkin), h_stage);
-                    const float R2l = 4.0f * h_list * h_list;
-                    nlist = 0;
-                    if (ok) {
+                    if (ok && hi > h_list) {
+                        h_list = fminf(hi * (1.0f + kSkin), h_stage);
                         my_tests += (unsigned long long)T;
-                        for (int e = 0; e < T; ++e) {
-                            const float4 q = sj[e];
-                            const float dx = xi - q.x, dy = yi - q.y, dz = zi - q.z;
-                            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                            if (r2 < R2l) {
-                                if (nlist < kLaneCap) lst[nlist * 32 + lane] = (uint16_t)e;
-                                ++nlist;
-                            }
+                        nlist = build_list(sj, T, xi, yi, zi, 4.0f * h_list * h_list, lst, lane);
+                        if (nlist > kLaneCap) {
+                            // too many within the skin: a tighter radius (more
+                            // rebuilds for this lane, but no walk of the whole stage)
+                            h_list = fminf(hi * (1.0f + kSkinTight), h_stage);
+                            nlist = build_list(sj, T, xi, yi, zi, 4.0f * h_list * h_list, lst, lane);
                         }
                     }
                     __syncwarp();
@@ -581,7 +626,7 @@ __device__ int stage_force(const ForceArgs &a, const Tab &tab, int total, const 
 {
     const Common &c = a.c;
     const unsigned lt = (1u << lane) - 1u;
-    const int nent = 27 * c.s3;
+    const int nk = tab.nk;
     int found = 0;
     int ecur = cur.e;
     for (int g0 = cur.g; g0 < total; g0 += 32 * kStageUnroll) {
@@ -596,11 +641,11 @@ __device__ int stage_force(const ForceArgs &a, const Tab &tab, int total, const 
             qa[u] = make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.0f);
             jj[u] = 0;
             if (g < total) {
-                e = advance(tab, nent, e, g);
+                e = advance(tab, nk, e, g);
                 const int64_t j = (int64_t)tab.base[e] + g;
                 jj[u] = j;
                 float sx, sy, sz;
-                stencil_shift(c, e >> c.lg_s3, sx, sy, sz);
+                stencil_shift(c, tab.t[e], sx, sy, sz);
                 qa[u].x = fmaf(ldf<FX>(c.x.p[0], c.x.fmt, j), c.x.dec, sx);
                 qa[u].y = fmaf(ldf<FX>(c.x.p[1], c.x.fmt, j), c.x.dec, sy);
                 qa[u].z = fmaf(ldf<FX>(c.x.p[2], c.x.fmt, j), c.x.dec, sz);
