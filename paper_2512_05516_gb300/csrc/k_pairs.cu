@@ -38,7 +38,12 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kLaneCap = 96;                                 // per-lane pair list entries
-constexpr float kSkin = 0.12f;                               // list / stage radius = 2 h (1 + skin)
+constexpr int kListSlots = kLaneCap + 1;                     // plus one scratch slot per lane
+#ifndef SPH_LIST_SKIN
+#define SPH_LIST_SKIN 0.09f
+#endif
+constexpr float kSkin = SPH_LIST_SKIN;                       // list radius = 2 h (1 + skin)
+constexpr float kStageSkin = 0.12f;                          // stage radius = 2 max h (1 + skin)
 constexpr float kSkinTight = 0.02f;                          // list skin of a lane whose list overflowed
 constexpr int kMaxEnt = 27 * kMaxSub * kMaxSub * kMaxSub;    // stencil sub-cells
 constexpr int kEntPerLane = (kMaxEnt + 31) / 32;
@@ -98,7 +103,7 @@ struct __align__(16) Tab {
 // Each warp's shared-memory region is stage | lists | table; the next warp's
 // float4 stage starts right after, so every part keeps 16-byte multiples.
 static_assert(sizeof(Tab) % 16 == 0, "stencil table size must keep 16-byte alignment");
-static_assert((32 * kLaneCap * sizeof(uint16_t)) % 16 == 0, "list size must keep 16-byte alignment");
+static_assert((32 * kListSlots * sizeof(uint16_t)) % 16 == 0, "list size must keep 16-byte alignment");
 
 __device__ __forceinline__ int pop_item(DevStats *st, int lane)
 {
@@ -250,16 +255,17 @@ __device__ __forceinline__ int advance(const Tab &tab, int nk, int e, int g)
     return e;
 }
 
-// M4 spline w(q) and w'(q), branch-free
+// M4 spline w(q) and w'(q), branch-free, for any q >= 0: with
+// t = max(2 - q, 0) and u = max(1 - q, 0),
+//   w = t^3 / 4 - u^3,   w' = -3 t^2 / 4 + 3 u^2,
+// which is 1 - 3q^2/2 + 3q^3/4 on [0, 1), (2 - q)^3 / 4 on [1, 2) and 0 beyond.
 __device__ __forceinline__ void spline(float q, float &w, float &dw)
 {
-    const float t = 2.0f - q;
-    const float t2 = t * t;
-    const float w_in = fmaf(q * q, fmaf(0.75f, q, -1.5f), 1.0f);
-    const float dw_in = q * fmaf(2.25f, q, -3.0f);
-    const bool inner = q < 1.0f;
-    w = inner ? w_in : 0.25f * t2 * t;
-    dw = inner ? dw_in : -0.75f * t2;
+    const float t = fmaxf(2.0f - q, 0.0f);
+    const float u = fmaxf(1.0f - q, 0.0f);
+    const float t2 = t * t, u2 = u * u;
+    w = fmaf(0.25f * t2, t, -(u2 * u));
+    dw = fmaf(3.0f, u2, -0.75f * t2);
 }
 
 // Kahan compensated accumulation: s - c carries the running sum; c holds the
@@ -288,15 +294,15 @@ __device__ __forceinline__ void dens_pair(DAcc &a, float xi, float yi, float zi,
 {
     const float dx = xi - q.x, dy = yi - q.y, dz = zi - q.z;
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    const bool in = r2 < h2x4;
-    const float r = r2 > 0.0f ? r2 * rsqrtf(r2) : 0.0f;
+    const bool in = r2 < h2x4;                           // the neighbour test (counts)
+    const float r = r2 * rsqrtf(fmaxf(r2, 1.0e-30f));    // 0 for the self pair
     const float qq = r * hinv;
     float w, dw;
-    spline(qq, w, dw);
-    const float mw = in ? q.w * w : 0.0f;
+    spline(qq, w, dw);                                   // w = w' = 0 beyond the support
+    const float mw = q.w * w;
     if (plain) a.s += mw;
     else kahan_add(a.s, a.c, mw);
-    if (deriv) a.d = fmaf(in ? q.w : 0.0f, fmaf(qq, dw, 3.0f * w), a.d);
+    if (deriv) a.d = fmaf(q.w, fmaf(qq, dw, 3.0f * w), a.d);
     a.n += in ? 1 : 0;
 }
 
@@ -317,12 +323,13 @@ __device__ __forceinline__ int build_list(const float4 *sj, int T, float xi, flo
             const float dx = xi - q.x, dy = yi - q.y, dz = zi - q.z;
             r2[u] = e0 + u < T ? fmaf(dx, dx, fmaf(dy, dy, dz * dz)) : R2;
         }
+        // branch-free append: every candidate is written at the next free
+        // slot (slot kLaneCap is scratch once the list is full) and the
+        // count advances only for the kept ones
 #pragma unroll
         for (int u = 0; u < LB; ++u) {
-            if (r2[u] < R2) {
-                if (n < kLaneCap) lst[n * 32 + lane] = (uint16_t)(e0 + u);
-                ++n;
-            }
+            lst[min(n, kLaneCap) * 32 + lane] = (uint16_t)(e0 + u);
+            n += r2[u] < R2 ? 1 : 0;
         }
     }
     return n;
@@ -416,10 +423,10 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
     extern __shared__ __align__(16) unsigned char smem[];
     const Common &c = a.c;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const size_t per_warp = (size_t)c.cap * sizeof(float4) + (size_t)32 * kLaneCap * sizeof(uint16_t) + sizeof(Tab);
+    const size_t per_warp = (size_t)c.cap * sizeof(float4) + (size_t)32 * kListSlots * sizeof(uint16_t) + sizeof(Tab);
     float4 *sj = reinterpret_cast<float4 *>(smem + warp * per_warp);
     uint16_t *lst = reinterpret_cast<uint16_t *>(sj + c.cap);
-    Tab &tab = *reinterpret_cast<Tab *>(lst + 32 * kLaneCap);
+    Tab &tab = *reinterpret_cast<Tab *>(lst + 32 * kListSlots);
 
     unsigned long long my_pairs = 0, my_tests = 0;
     unsigned my_err = 0;
@@ -447,7 +454,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
         const Box box = warp_box(ok, xi, yi, zi);
 
         // stage everything within 2 h_stage of the box, h_stage = max h (1 + skin)
-        float h_stage = fminf(warp_max(ok ? hi : 0.0f) * (1.0f + kSkin), a.h_cap);
+        float h_stage = fminf(warp_max(ok ? hi : 0.0f) * (1.0f + kStageSkin), a.h_cap);
         float R2s = 4.0f * h_stage * h_stage;
         int total = build_stream(c, cell, box, R2s, tab, lane);
         Cursor cur{0, 0};
@@ -465,7 +472,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
             DAcc acc{0.f, 0.f, 0.f, 0};
             if (fits && __any_sync(FULL, ok && hi > h_stage)) {
                 // h outgrew the stage: re-stage with the current h
-                h_stage = fminf(warp_max(ok ? hi : 0.0f) * (1.0f + kSkin), a.h_cap);
+                h_stage = fminf(warp_max(ok ? hi : 0.0f) * (1.0f + kStageSkin), a.h_cap);
                 R2s = 4.0f * h_stage * h_stage;
                 total = build_stream(c, cell, box, R2s, tab, lane);
                 Cursor rc{0, 0};
@@ -493,9 +500,17 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
                 if (ok) {
                     my_tests += (unsigned long long)(nlist <= kLaneCap ? nlist : T);
                     if (nlist <= kLaneCap) {
+                        // the summation mode is fixed per call: one loop body
+                        // each, so that the unrolled iterations overlap
+                        if (a.plain_sum) {
 #pragma unroll 4
-                        for (int e = 0; e < nlist; ++e)
-                            dens_pair(acc, xi, yi, zi, h2x4, hinv, a.plain_sum, deriv, sj[lst[e * 32 + lane]]);
+                            for (int e = 0; e < nlist; ++e)
+                                dens_pair(acc, xi, yi, zi, h2x4, hinv, true, true, sj[lst[e * 32 + lane]]);
+                        } else {
+#pragma unroll 4
+                            for (int e = 0; e < nlist; ++e)
+                                dens_pair(acc, xi, yi, zi, h2x4, hinv, false, true, sj[lst[e * 32 + lane]]);
+                        }
                     } else {
                         // this lane's list overflowed: walk the whole stage
                         for (int e = 0; e < T; ++e) dens_pair(acc, xi, yi, zi, h2x4, hinv, a.plain_sum, deriv, sj[e]);
@@ -702,12 +717,12 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_force(ForceArgs a)
     extern __shared__ __align__(16) unsigned char smem[];
     const Common &c = a.c;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const size_t per_warp = (size_t)c.cap * 3 * sizeof(float4) + (size_t)32 * kLaneCap * sizeof(uint16_t) + sizeof(Tab);
+    const size_t per_warp = (size_t)c.cap * 3 * sizeof(float4) + (size_t)32 * kListSlots * sizeof(uint16_t) + sizeof(Tab);
     float4 *sA = reinterpret_cast<float4 *>(smem + warp * per_warp);         // x, y, z, h
     float4 *sB = sA + c.cap;                                                  // vx, vy, vz, m
     float4 *sC = sB + c.cap;                                                  // P/rho^2, rho, c, slot
     uint16_t *lst = reinterpret_cast<uint16_t *>(sC + c.cap);                 // per-lane pair lists
-    Tab &tab = *reinterpret_cast<Tab *>(lst + 32 * kLaneCap);
+    Tab &tab = *reinterpret_cast<Tab *>(lst + 32 * kListSlots);
     unsigned long long my_pairs = 0, my_tests = 0;
     unsigned my_err = 0;
     const int lo = c.range ? c.range[0] : 0;
@@ -752,6 +767,28 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_force(ForceArgs a)
                 int e = 0;
                 for (;;) {
                     int nl = 0;
+                    if (len <= kLaneCap) {
+                        // the chunk cannot overflow the list: branch-free
+                        // appends in batches (loads first, then the stores)
+                        constexpr int LB = 8;
+                        for (int e0 = 0; e0 < len; e0 += LB) {
+                            bool in[LB];
+#pragma unroll
+                            for (int u = 0; u < LB; ++u) {
+                                const float4 q = sA[min(e0 + u, len - 1)];
+                                const float dx = xi - q.x, dy = yi - q.y, dz = zi - q.z;
+                                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                                const float hs = hi + q.w;
+                                in[u] = e0 + u < len && r2 < hs * hs;
+                            }
+#pragma unroll
+                            for (int u = 0; u < LB; ++u) {
+                                lst[nl * 32 + lane] = (uint16_t)(e0 + u);     // nl <= kLaneCap: slot kLaneCap is scratch
+                                nl += in[u] ? 1 : 0;
+                            }
+                        }
+                        e = len;
+                    }
                     for (; e < len; ++e) {
                         const float4 q = sA[e];
                         const float dx = xi - q.x, dy = yi - q.y, dz = zi - q.z;
@@ -1087,13 +1124,13 @@ struct ForceK {
 size_t density_smem_bytes(int block_threads, int cap)
 {
     return (size_t)(block_threads / 32) *
-           ((size_t)cap * sizeof(float4) + (size_t)32 * kLaneCap * sizeof(uint16_t) + sizeof(Tab));
+           ((size_t)cap * sizeof(float4) + (size_t)32 * kListSlots * sizeof(uint16_t) + sizeof(Tab));
 }
 
 size_t force_smem_bytes(int block_threads, int cap)
 {
     return (size_t)(block_threads / 32) *
-           ((size_t)cap * 3 * sizeof(float4) + (size_t)32 * kLaneCap * sizeof(uint16_t) + sizeof(Tab));
+           ((size_t)cap * 3 * sizeof(float4) + (size_t)32 * kListSlots * sizeof(uint16_t) + sizeof(Tab));
 }
 
 cudaError_t run_density(sph_ctx *c, int newton_steps)
