@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="default launch shapes instead of the autotuner's")
     ap.add_argument("--no-uneven", action="store_true", help="skip the 16.7M-particle clustered batching rows")
     ap.add_argument("--no-vs-plain", action="store_true", help="skip the plain FP32 SoA comparison")
+    ap.add_argument("--no-streaming", action="store_true", help="skip the host-resident AoS comparison")
     ap.add_argument("--profile-case", choices=["pairs", "memory"], default=None,
                     help="run one small fixed workload for an ncu capture and exit")
     return ap.parse_args()
@@ -477,6 +478,50 @@ def run_vs_plain(lattice: int = 124, steps: int = 3):
     return rows
 
 
+def run_streaming(steps: int = 5):
+    """The paper's two GPU variants (Section 6.3) on the Sod set, FP32
+    storage, default launch shapes: in-place (the AoS master in device
+    memory) against streaming (the same records in pinned host memory,
+    which the binning, conversion and kick/drift + write-back kernels read
+    and write over the host link; nothing is staged by copies)."""
+    import torch
+    import paper_2512_05516_gb300 as sph
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    wl = sph_inputs.sod()
+    stream = torch.cuda.Stream(dev)
+    nc = [int(math.floor(b / max(wl.cell_edge, 2 * wl.h_cap))) for b in wl.box]
+    params = sph.make_params(wl.box, gamma=wl.gamma, alpha=wl.alpha_av, beta=wl.beta_av,
+                             eps=wl.eps_av, eta=wl.eta, h_max=wl.h_cap)
+    names = ["bin", "aos_to_soa", "density", "force", "kick_drift_writeback"]
+    rows = {}
+    for where in ("in_place", "streaming"):
+        t = torch.from_numpy(wl.aos.copy())
+        aos = t.to(dev) if where == "in_place" else t.pin_memory()
+        s = sph.Sph(aos, sph.layout_112(), params, int(np.prod(nc)), 0, stream=stream)
+        calls = [lambda: s.bin_cells(wl.cell_edge), lambda: s.aos_to_soa(sph.FIELDS_FORCE),
+                 lambda: s.density(wl.newton_steps), lambda: s.force(),
+                 lambda: s.kick_drift_writeback(wl.dt, wl.dt, sph.FIELDS_OUTPUT)]
+        ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in names]
+              for _ in range(steps)]
+        with torch.cuda.stream(stream):
+            for fn in calls:
+                fn()
+            for k in range(steps):
+                for i, fn in enumerate(calls):
+                    ev[k][i][0].record(stream)
+                    fn()
+                    ev[k][i][1].record(stream)
+            stream.synchronize()
+        ms = {nm: statistics.mean(ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(steps))
+              for i, nm in enumerate(names)}
+        rows[where] = {"ms_per_step": sum(ms.values()), "kernels_ms": ms}
+        s.close()
+        del aos
+    rows["streaming_over_in_place"] = rows["streaming"]["ms_per_step"] / rows["in_place"]["ms_per_step"]
+    rows["workload"] = f"sod_{wl.n}"
+    return rows
+
+
 def run_uneven(n: int = 16_777_216):
     """Uneven occupancy (the clustered Gaussian mixture, one global h, up to
     ~65,000 particles in a cell), BF16 storage of v, m, h, u: one density
@@ -676,6 +721,7 @@ def main():
     long = None if args.no_long_run or world > 1 else run_long_run()
     uneven = None if args.no_uneven or world > 1 else run_uneven()
     vs_plain = None if args.no_vs_plain or world > 1 else run_vs_plain()
+    streaming = None if args.no_streaming or world > 1 else run_streaming()
     out = {
         "metric": METRIC, "value": pairs / total_s, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
@@ -689,6 +735,7 @@ def main():
         "roofline": r["roofline"], "cpu_baseline": cpu, "e2e": r["e2e"],
         "gpu_launches": r["launches"], "clocks": r["clocks"], "kernels": r["kernels"],
         "memory_bound_rows": long, "uneven_batching": uneven, "vs_plain_fp32_soa": vs_plain,
+        "streaming_vs_in_place": streaming,
     }
     print(json.dumps(out))
     if world > 1:

@@ -197,11 +197,18 @@ typedef struct sph_ctx sph_ctx;
 size_t sph_workspace_bytes(const sph_aos_layout *layout, int64_t n, int64_t ncell_max,
                            uint32_t ws_flags);
 
-/* Create a context over n caller-owned AoS records at d_aos (device memory,
- * records in `layout`), using the caller-owned device workspace d_workspace of
+/* Create a context over n caller-owned AoS records at d_aos (records in
+ * `layout`), using the caller-owned device workspace d_workspace of
  * workspace_bytes (at least sph_workspace_bytes(layout, n, ncell_max, ws_flags),
  * 256-byte aligned).  `stream` is a cudaStream_t (NULL: the legacy default
  * stream).  The CUDA device current at this call is used for all later calls.
+ * d_aos is device memory (the paper's in-place variant, Section 6.3) or host
+ * memory the device can address -- pinned with cudaHostAlloc / cudaMallocHost,
+ * whose pointer is a device pointer under unified addressing.  In the second
+ * case the kernels that touch the records (binning, conversion, kick/drift,
+ * write-back) read and write them over the host link while the SoA and the
+ * workspace stay in device memory: the paper's streaming variant without
+ * staging copies.  d_aos must be 16-byte aligned.
  * Errors: SPH_EINVAL (layout, params or pointers), SPH_ENOSPACE (workspace),
  * SPH_ECUDA (device query).  On success *out receives the context. */
 sph_status sph_create(const sph_aos_layout *layout, const sph_params *params, int64_t n,

@@ -227,16 +227,19 @@ def mask(*names) -> int:
 class Sph:
     """A libsph context over a torch-owned AoS on the current CUDA device.
 
-    `aos` is a CUDA tensor holding n records of `layout.record_bytes` bytes
-    (any dtype; e.g. float64 of shape (n, 14) for the 112-byte record).  The
-    workspace is a torch uint8 tensor owned by this object.  All calls run on
-    `stream` (default: torch's current stream)."""
+    `aos` holds n records of `layout.record_bytes` bytes (any dtype; e.g.
+    float64 of shape (n, 14) for the 112-byte record): a CUDA tensor, or a
+    pinned host tensor (`tensor.pin_memory()`), which the kernels then read
+    and write over the host link (the streaming layout; the workspace stays
+    on the current CUDA device).  The workspace is a torch uint8 tensor owned
+    by this object.  All calls run on `stream` (default: torch's current
+    stream)."""
 
     def __init__(self, aos, layout: sph_aos_layout, params: sph_params, ncell_max: int,
                  ws_flags: int = 0, stream=None):
         import torch
-        if not aos.is_cuda:
-            raise ValueError("aos must be a CUDA tensor")
+        if not (aos.is_cuda or aos.is_pinned()):
+            raise ValueError("aos must be a CUDA tensor or a pinned host tensor")
         self.torch = torch
         self.aos = aos
         self.layout = layout
@@ -245,12 +248,13 @@ class Sph:
         if nbytes % layout.record_bytes:
             raise ValueError("AoS size is not a whole number of records")
         self.n = nbytes // layout.record_bytes
-        self.stream = stream if stream is not None else torch.cuda.current_stream(aos.device)
+        dev = aos.device if aos.is_cuda else torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
         self.ws_bytes = sph_workspace_bytes(layout, self.n, ncell_max, ws_flags)
         if self.ws_bytes == 0:
             raise SphError(-1, "sph_workspace_bytes")
-        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=aos.device)
-        with torch.cuda.device(aos.device):
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=dev)
+        with torch.cuda.device(dev):
             st, ctx = sph_create(layout, params, self.n, ncell_max, ws_flags, aos.data_ptr(),
                                  self.ws.data_ptr(), self.ws_bytes, self.stream.cuda_stream)
         _check(st, "sph_create")

@@ -408,8 +408,10 @@ cudaError_t run_binning(sph_ctx *c, int reorder)
             k_gather_records<<<blocks_for(n * 32, 256), 256, 0, s>>>(c->aos, c->aos_tmp, c->perm(), n,
                                                                      c->layout.record_bytes);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            // (cudaMemcpyDefault: the records may live in host memory the
+            // device maps, the streaming layout)
             if ((e = cudaMemcpyAsync(c->aos, c->aos_tmp, (size_t)n * c->layout.record_bytes,
-                                     cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+                                     cudaMemcpyDefault, s)) != cudaSuccess)
                 return e;
             k_iota<<<blocks_for(n, 256), 256, 0, s>>>(c->perm(), n);
             c->launches += 2;   // gather and iota

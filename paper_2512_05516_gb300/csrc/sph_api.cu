@@ -438,7 +438,7 @@ sph_status sph_describe(const sph_ctx *c, sph_desc *out)
 sph_status sph_aos_upload(sph_ctx *c, const void *host, size_t bytes)
 {
     if (!c || !host || bytes > (size_t)c->n * (size_t)c->layout.record_bytes) return SPH_EINVAL;
-    if (cudaMemcpyAsync(c->aos, host, bytes, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+    if (cudaMemcpyAsync(c->aos, host, bytes, cudaMemcpyDefault, c->stream) != cudaSuccess)
         return SPH_ECUDA;
     return SPH_OK;
 }
@@ -446,7 +446,7 @@ sph_status sph_aos_upload(sph_ctx *c, const void *host, size_t bytes)
 sph_status sph_aos_download(sph_ctx *c, void *host, size_t bytes)
 {
     if (!c || !host || bytes > (size_t)c->n * (size_t)c->layout.record_bytes) return SPH_EINVAL;
-    if (cudaMemcpyAsync(host, c->aos, bytes, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+    if (cudaMemcpyAsync(host, c->aos, bytes, cudaMemcpyDefault, c->stream) != cudaSuccess)
         return SPH_ECUDA;
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SPH_ECUDA;
     return SPH_OK;
