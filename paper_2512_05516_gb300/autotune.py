@@ -30,7 +30,7 @@ SPACE = {
     "item_order": (0, 1),
     "block_threads": (32, 64, 128),
     "stage_density": (512, 768, 1024, 1536),
-    "stage_force": (64, 96, 128, 192, 256, 384),
+    "stage_force": (96, 128, 192, 256, 384, 512),
 }
 
 

@@ -87,6 +87,10 @@ struct ForceArgs {
     float *a[3];
     float *dudt;
     int32_t *nngb;
+    // every slot's force inputs decoded to FP32 by the pack pass:
+    const float4 *pA;                // (x, y, z, h), positions cell-relative
+    const float4 *pB;                // (vx, vy, vz, m)
+    const float4 *pC;                // (P / rho^2, rho, c, 0)
 };
 
 // The candidate stream of one warp: the kept (non-empty, within reach)
@@ -579,17 +583,31 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
 // Force
 // ---------------------------------------------------------------------------
 
-// Largest h of every sub-cell: slots are sorted by key, so the lanes of a
-// warp share few keys; each key group reduces in the warp and its leader
+// The force's pack pass: every slot's inputs decoded from their storage
+// formats into three FP32 float4 arrays (so the pair kernel loads a
+// candidate with one 16-byte load per array), and the largest h of every
+// sub-cell for the stencil pruning.  Slots are sorted by key, so the lanes of
+// a warp share few keys; each key group reduces in the warp and its leader
 // does one atomic max (h > 0, so the float order is the unsigned order).
-__global__ void __launch_bounds__(256) k_key_hmax(FieldRef h, const int32_t *slot_key, int64_t n, float h_cap,
-                                                  float *key_hmax)
+__global__ void __launch_bounds__(256) k_force_pack(ForceArgs a, const int32_t *slot_key, float *key_hmax,
+                                                    float4 *pA, float4 *pB, float4 *pC)
 {
+    const Common &c = a.c;
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool ok = k < n;
+    const bool ok = k < c.n;
     const int key = ok ? slot_key[k] : -1;
-    float hv = ok ? ld_val(h.p[0], h.fmt, k) * h.dec : 0.0f;
-    if (ok && !(hv > 0.0f && hv <= 3.0e38f)) hv = h_cap;       // NaN / non-positive: assume h_max
+    float hv = 0.0f;
+    if (ok) {
+        hv = ld_val(c.h.p[0], c.h.fmt, k) * c.h.dec;
+        pA[k] = make_float4(ld_val(c.x.p[0], c.x.fmt, k) * c.x.dec, ld_val(c.x.p[1], c.x.fmt, k) * c.x.dec,
+                            ld_val(c.x.p[2], c.x.fmt, k) * c.x.dec, hv);
+        pB[k] = make_float4(ld_val(a.v.p[0], a.v.fmt, k) * a.v.dec, ld_val(a.v.p[1], a.v.fmt, k) * a.v.dec,
+                            ld_val(a.v.p[2], a.v.fmt, k) * a.v.dec, ld_val(c.m.p[0], c.m.fmt, k) * c.m.dec);
+        const float rho = ld_val(a.rho.p[0], a.rho.fmt, k) * a.rho.dec;
+        const float P = ld_val(a.P.p[0], a.P.fmt, k) * a.P.dec;
+        pC[k] = make_float4(P / (rho * rho), rho, ld_val(a.cs.p[0], a.cs.fmt, k) * a.cs.dec, 0.0f);
+        if (!(hv > 0.0f && hv <= 3.0e38f)) hv = a.h_cap;       // NaN / non-positive: assume h_max
+    }
     const unsigned peers = __match_any_sync(FULL, key);
     const unsigned mx = __reduce_max_sync(peers, __float_as_uint(hv));
     if (ok && (threadIdx.x & 31) == __ffs(peers) - 1)
@@ -629,15 +647,14 @@ __device__ __forceinline__ void force_pair(float &ax, float &ay, float &az, floa
 }
 
 // Stage the force candidates (those within h_max(warp) + h_j of the warp box)
-// from `cur` on, until the stage is full or the stream ends; returns how many
-// were staged and moves `cur` (as stage_density).  The loads a kept
-// candidate needs beyond x and h are issued for all batches in flight before
-// anything is stored.  The 27-cell grid covers pairs up to 2 h_max only; a
+// from `cur` on, until the stage is full or the stream ends: their packed
+// inputs (one 16-byte load per array, issued for every batch in flight before
+// anything is stored), positions shifted into the item's cell frame, and the
+// slot in sC.w.  Returns how many were staged and moves `cur` (as
+// stage_density).  The 27-cell grid covers pairs up to 2 h_max only; a
 // candidate with a larger h sets the h-cap error bit.
-template <int FX, int FV>
-__device__ int stage_force(const ForceArgs &a, const Tab &tab, int total, const Box &box, float hw,
-                           float4 *sA, float4 *sB, float4 *sC, int cap, Cursor &cur, int lane,
-                           unsigned &err)
+__device__ int stage_force(const ForceArgs &a, const Tab &tab, int total, const Box &box, float hw, float4 *sA,
+                           float4 *sB, float4 *sC, int cap, Cursor &cur, int lane, unsigned &err)
 {
     const Common &c = a.c;
     const unsigned lt = (1u << lane) - 1u;
@@ -646,25 +663,24 @@ __device__ int stage_force(const ForceArgs &a, const Tab &tab, int total, const 
     int ecur = cur.e;
     for (int g0 = cur.g; g0 < total; g0 += 32 * kStageUnroll) {
         float4 qa[kStageUnroll], qb[kStageUnroll], qc[kStageUnroll];
-        int64_t jj[kStageUnroll];
         int eu[kStageUnroll];
-        bool keep[kStageUnroll];
         int e = ecur;
 #pragma unroll
         for (int u = 0; u < kStageUnroll; ++u) {
             const int g = g0 + u * 32 + lane;
             qa[u] = make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.0f);
-            jj[u] = 0;
+            qb[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            qc[u] = make_float4(0.f, 1.f, 0.f, 0.f);
             if (g < total) {
                 e = advance(tab, nk, e, g);
-                const int64_t j = (int64_t)tab.base[e] + g;
-                jj[u] = j;
+                const int j = tab.base[e] + g;
                 float sx, sy, sz;
                 stencil_shift(c, tab.t[e], sx, sy, sz);
-                qa[u].x = fmaf(ldf<FX>(c.x.p[0], c.x.fmt, j), c.x.dec, sx);
-                qa[u].y = fmaf(ldf<FX>(c.x.p[1], c.x.fmt, j), c.x.dec, sy);
-                qa[u].z = fmaf(ldf<FX>(c.x.p[2], c.x.fmt, j), c.x.dec, sz);
-                qa[u].w = ldf<FV>(c.h.p[0], c.h.fmt, j) * c.h.dec;
+                const float4 p = __ldg(a.pA + j);
+                qa[u] = make_float4(p.x + sx, p.y + sy, p.z + sz, p.w);
+                qb[u] = __ldg(a.pB + j);
+                qc[u] = __ldg(a.pC + j);
+                qc[u].w = __int_as_float(j);
             }
             eu[u] = e;
         }
@@ -672,21 +688,8 @@ __device__ int stage_force(const ForceArgs &a, const Tab &tab, int total, const 
         for (int u = 0; u < kStageUnroll; ++u) {
             if (qa[u].w > a.h_cap) err |= SPH_ERR_HCAP;
             const float rr = hw + qa[u].w;
-            keep[u] = box_dist2(box, qa[u].x, qa[u].y, qa[u].z) < rr * rr;
-            qb[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-            qc[u] = make_float4(0.f, 1.f, 0.f, 0.f);
-            if (keep[u]) {
-                const int64_t j = jj[u];
-                constexpr int FR = derived_fmt<FX>();
-                qb[u] = make_float4(ldf<FV>(a.v.p[0], a.v.fmt, j) * a.v.dec, ldf<FV>(a.v.p[1], a.v.fmt, j) * a.v.dec,
-                                    ldf<FV>(a.v.p[2], a.v.fmt, j) * a.v.dec, ldf<FV>(c.m.p[0], c.m.fmt, j) * c.m.dec);
-                qc[u] = make_float4(ldf<FR>(a.P.p[0], a.P.fmt, j) * a.P.dec, ldf<FR>(a.rho.p[0], a.rho.fmt, j) * a.rho.dec,
-                                    ldf<FR>(a.cs.p[0], a.cs.fmt, j) * a.cs.dec, __int_as_float((int)j));
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < kStageUnroll; ++u) {
-            const unsigned b = __ballot_sync(FULL, keep[u]);
+            const bool keep = box_dist2(box, qa[u].x, qa[u].y, qa[u].z) < rr * rr;
+            const unsigned b = __ballot_sync(FULL, keep);
             const int nb = __popc(b);
             if (found + nb > cap) {     // stage full: resume at this batch
                 cur.g = g0 + u * 32;
@@ -694,12 +697,11 @@ __device__ int stage_force(const ForceArgs &a, const Tab &tab, int total, const 
                 __syncwarp();
                 return found;
             }
-            if (keep[u]) {
+            if (keep) {
                 const int pos = found + __popc(b & lt);
-                const float rj = qc[u].y;
                 sA[pos] = qa[u];
                 sB[pos] = qb[u];
-                sC[pos] = make_float4(qc[u].x / (rj * rj), rj, qc[u].z, qc[u].w);
+                sC[pos] = qc[u];
             }
             found += nb;
         }
@@ -711,110 +713,99 @@ __device__ int stage_force(const ForceArgs &a, const Tab &tab, int total, const 
     return found;
 }
 
-template <int FX, int FV>
+// shared memory of one force warp: the staged (x, y, z, h), (v, m),
+// (P/rho^2, rho, c, slot), the per-lane pair lists and the stencil table
+__host__ __device__ inline size_t force_warp_bytes(int cap)
+{
+    return (size_t)cap * 3 * sizeof(float4) + (size_t)32 * kListSlots * sizeof(uint16_t) + sizeof(Tab);
+}
+
 __global__ void __launch_bounds__(kMaxBlock, 1) k_force(ForceArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const Common &c = a.c;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const size_t per_warp = (size_t)c.cap * 3 * sizeof(float4) + (size_t)32 * kListSlots * sizeof(uint16_t) + sizeof(Tab);
-    float4 *sA = reinterpret_cast<float4 *>(smem + warp * per_warp);         // x, y, z, h
-    float4 *sB = sA + c.cap;                                                  // vx, vy, vz, m
-    float4 *sC = sB + c.cap;                                                  // P/rho^2, rho, c, slot
-    uint16_t *lst = reinterpret_cast<uint16_t *>(sC + c.cap);                 // per-lane pair lists
+    float4 *sA = reinterpret_cast<float4 *>(smem + warp * force_warp_bytes(c.cap));   // x, y, z, h
+    float4 *sB = sA + c.cap;                                                             // vx, vy, vz, m
+    float4 *sC = sB + c.cap;                                                             // P/rho^2, rho, c, slot
+    uint16_t *lst = reinterpret_cast<uint16_t *>(sC + c.cap);                            // per-lane pair lists
     Tab &tab = *reinterpret_cast<Tab *>(lst + 32 * kListSlots);
     unsigned long long my_pairs = 0, my_tests = 0;
     unsigned my_err = 0;
     const int lo = c.range ? c.range[0] : 0;
-    const int hi = c.range ? c.range[1] : c.st->nitems;
+    const int hi_item = c.range ? c.range[1] : c.st->nitems;
 
-    for (int it = lo + pop_item(c.st, lane); it < hi; it = lo + pop_item(c.st, lane)) {
+    for (int it = lo + pop_item(c.st, lane); it < hi_item; it = lo + pop_item(c.st, lane)) {
         const int cell = c.icell[it];
         const int first = c.ifirst[it];
         const int count = c.icount[it];
         const bool ok = lane < count;
-        const int64_t k = (int64_t)first + lane;
+        const int k = first + lane;
         float xi = 0.f, yi = 0.f, zi = 0.f, hi = 0.f, vxi = 0.f, vyi = 0.f, vzi = 0.f;
         float rhoi = 1.f, Pr2i = 0.f, ci = 0.f;
         if (ok) {
-            xi = ld_val(c.x.p[0], c.x.fmt, k) * c.x.dec;
-            yi = ld_val(c.x.p[1], c.x.fmt, k) * c.x.dec;
-            zi = ld_val(c.x.p[2], c.x.fmt, k) * c.x.dec;
-            hi = ld_val(c.h.p[0], c.h.fmt, k) * c.h.dec;
-            vxi = ld_val(a.v.p[0], a.v.fmt, k) * a.v.dec;
-            vyi = ld_val(a.v.p[1], a.v.fmt, k) * a.v.dec;
-            vzi = ld_val(a.v.p[2], a.v.fmt, k) * a.v.dec;
-            rhoi = ld_val(a.rho.p[0], a.rho.fmt, k) * a.rho.dec;
-            const float Pi = ld_val(a.P.p[0], a.P.fmt, k) * a.P.dec;
-            Pr2i = Pi / (rhoi * rhoi);
-            ci = ld_val(a.cs.p[0], a.cs.fmt, k) * a.cs.dec;
+            const float4 qa = __ldg(a.pA + k), qb = __ldg(a.pB + k), qc = __ldg(a.pC + k);
+            xi = qa.x;
+            yi = qa.y;
+            zi = qa.z;
+            hi = qa.w;
+            vxi = qb.x;
+            vyi = qb.y;
+            vzi = qb.z;
+            Pr2i = qc.x;
+            rhoi = qc.y;
+            ci = qc.z;
         }
         const Box box = warp_box(ok, xi, yi, zi);
         const float hw = warp_max(ok ? hi : 0.0f);
         const int total = build_stream(c, cell, box, 0.0f, tab, lane, a.key_hmax, hw);
-        const int kself = (int)k;
         float ax = 0.f, ay = 0.f, az = 0.f, du = 0.f;
         int cnt = 0;
         if (hi > a.h_cap) my_err |= SPH_ERR_HCAP;
         Cursor cur{0, 0};
         do {
-            const int len = stage_force<FX, FV>(a, tab, total, box, hw, sA, sB, sC, c.cap, cur, lane, my_err);
+            const int len = stage_force(a, tab, total, box, hw, sA, sB, sC, c.cap, cur, lane, my_err);
             if (ok) {
                 my_tests += (unsigned long long)len;
-                // phase 1 collects this lane's pairs into its list, phase 2
-                // evaluates them with every lane busy; a full list is drained
-                // and the scan resumes where it stopped
-                int e = 0;
-                for (;;) {
+                // phase 1 collects this lane's pairs among up to kLaneCap
+                // staged candidates into its list (branch-free appends in
+                // batches: loads first, then the stores; a range of kLaneCap
+                // candidates cannot overflow the list), phase 2 evaluates
+                // them; repeated over the stage
+                for (int s0 = 0; s0 < len; s0 += kLaneCap) {
+                    const int s1 = min(s0 + kLaneCap, len);
                     int nl = 0;
-                    if (len <= kLaneCap) {
-                        // the chunk cannot overflow the list: branch-free
-                        // appends in batches (loads first, then the stores)
-                        constexpr int LB = 8;
-                        for (int e0 = 0; e0 < len; e0 += LB) {
-                            bool in[LB];
+                    constexpr int LB = 8;
+                    for (int e0 = s0; e0 < s1; e0 += LB) {
+                        bool in[LB];
 #pragma unroll
-                            for (int u = 0; u < LB; ++u) {
-                                const float4 q = sA[min(e0 + u, len - 1)];
-                                const float dx = xi - q.x, dy = yi - q.y, dz = zi - q.z;
-                                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                                const float hs = hi + q.w;
-                                in[u] = e0 + u < len && r2 < hs * hs;
-                            }
-#pragma unroll
-                            for (int u = 0; u < LB; ++u) {
-                                lst[nl * 32 + lane] = (uint16_t)(e0 + u);     // nl <= kLaneCap: slot kLaneCap is scratch
-                                nl += in[u] ? 1 : 0;
-                            }
+                        for (int u = 0; u < LB; ++u) {
+                            const float4 q = sA[min(e0 + u, s1 - 1)];
+                            const float dx = xi - q.x, dy = yi - q.y, dz = zi - q.z;
+                            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                            const float hs = hi + q.w;
+                            in[u] = e0 + u < s1 && r2 < hs * hs;
                         }
-                        e = len;
-                    }
-                    for (; e < len; ++e) {
-                        const float4 q = sA[e];
-                        const float dx = xi - q.x, dy = yi - q.y, dz = zi - q.z;
-                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                        const float hs = hi + q.w;
-                        if (r2 < hs * hs) {
-                            if (nl == kLaneCap) break;
-                            lst[nl * 32 + lane] = (uint16_t)e;
-                            ++nl;
+#pragma unroll
+                        for (int u = 0; u < LB; ++u) {
+                            lst[nl * 32 + lane] = (uint16_t)(e0 + u);     // nl <= kLaneCap: slot kLaneCap is scratch
+                            nl += in[u] ? 1 : 0;
                         }
                     }
+#pragma unroll 2
                     for (int l = 0; l < nl; ++l) {
                         const int p = lst[l * 32 + lane];
-                        const float4 q = sA[p];
-                        const float dx = xi - q.x, dy = yi - q.y, dz = zi - q.z;
-                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                        const float hs = hi + q.w;
                         const float4 qc = sC[p];
-                        if (__float_as_int(qc.w) != kself) {
+                        if (__float_as_int(qc.w) != k) {
+                            const float4 q = sA[p];
+                            const float dx = xi - q.x, dy = yi - q.y, dz = zi - q.z;
+                            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                             ++cnt;
                             if (r2 > 0.0f)
-                                force_pair(ax, ay, az, du, vxi, vyi, vzi, rhoi, Pr2i, ci, dx, dy, dz, r2, hs, sB[p],
-                                           qc, a.alpha, a.beta, a.eps);
+                                force_pair(ax, ay, az, du, vxi, vyi, vzi, rhoi, Pr2i, ci, dx, dy, dz, r2,
+                                           hi + q.w, sB[p], qc, a.alpha, a.beta, a.eps);
                         }
                     }
-                    if (e >= len) break;   // every staged candidate scanned
                 }
             }
             __syncwarp();
@@ -1070,7 +1061,6 @@ cudaError_t launch_persistent(sph_ctx *c, K kernel, const A &args, size_t smem, 
 // Which fixed-format instantiation serves positions in fx and fields in fv:
 // 1..10 for (FP32 | FP16) x (FP32 | BF16 | FP16 | FP32-m16 | FP32-m10), 0 for
 // the run-time decoder.
-constexpr int kVariants = 11;
 int fmt_variant(int fx, int fv)
 {
     const int ix = fx == SPH_P_FP32 ? 0 : (fx == SPH_P_FP16 ? 1 : -1);
@@ -1114,10 +1104,6 @@ template <int FX, int FV>
 struct DensityK {
     static constexpr auto fn = k_density<FX, FV>;
 };
-template <int FX, int FV>
-struct ForceK {
-    static constexpr auto fn = k_force<FX, FV>;
-};
 
 }  // namespace
 
@@ -1129,8 +1115,7 @@ size_t density_smem_bytes(int block_threads, int cap)
 
 size_t force_smem_bytes(int block_threads, int cap)
 {
-    return (size_t)(block_threads / 32) *
-           ((size_t)cap * 3 * sizeof(float4) + (size_t)32 * kListSlots * sizeof(uint16_t) + sizeof(Tab));
+    return (size_t)(block_threads / 32) * force_warp_bytes(cap);
 }
 
 cudaError_t run_density(sph_ctx *c, int newton_steps)
@@ -1203,12 +1188,16 @@ cudaError_t run_force(sph_ctx *c)
     for (int k = 0; k < 3; ++k) a.a[k] = (float *)c->soa[SPH_F_A][k];
     a.dudt = (float *)c->soa[SPH_F_DUDT][0];
     a.nngb = c->nngb_force;
-    // the reach of every sub-cell, from the h the force will read
+    // the pack pass: FP32 inputs per slot, and the reach of every sub-cell
+    // from the h the force will read
     cudaError_t e;
     const int64_t nkeys = c->ncell * c->sub * c->sub * c->sub;
     if ((e = cudaMemsetAsync(c->key_hmax, 0, sizeof(float) * nkeys, c->stream)) != cudaSuccess) return e;
-    k_key_hmax<<<(unsigned)((c->n + 255) / 256), 256, 0, c->stream>>>(a.c.h, c->slot_cell(), c->n, a.h_cap,
-                                                                     c->key_hmax);
+    a.pA = c->pack;
+    a.pB = c->pack + c->n;
+    a.pC = c->pack + 2 * c->n;
+    k_force_pack<<<(unsigned)((c->n + 255) / 256), 256, 0, c->stream>>>(a, c->slot_cell(), c->key_hmax, c->pack,
+                                                                       c->pack + c->n, c->pack + 2 * c->n);
     c->launches += 1;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     a.key_hmax = c->key_hmax;
@@ -1217,13 +1206,9 @@ cudaError_t run_force(sph_ctx *c)
         c->launches += 1;
         return cudaGetLastError();
     }
+    // the pair kernel reads only the packed FP32 arrays: one instantiation
     const size_t smem = force_smem_bytes(c->tuning.block_threads, a.c.cap);
-    // fixed-format kernels: v, m, h share one format; rho, P, c are FP32
-    int v = 0;
-    if (a.c.h.fmt == a.c.m.fmt && a.v.fmt == a.c.m.fmt && a.rho.fmt == SPH_P_FP32 &&
-        a.P.fmt == SPH_P_FP32 && a.cs.fmt == SPH_P_FP32)
-        v = fmt_variant(a.c.x.fmt, a.c.m.fmt);
-    return Variants<ForceK>::launch(c, v, a, smem, c->lc_force);
+    return launch_persistent(c, k_force, a, smem, c->lc_force[0]);
 }
 
 }  // namespace sph

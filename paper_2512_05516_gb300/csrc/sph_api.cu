@@ -106,6 +106,7 @@ bool make_plan(const sph_aos_layout &L, int64_t n, int64_t ncell_max, uint32_t w
     p->stage = take(4 * N);
     p->key_hmax = take(4 * (size_t)nkeys);
     p->origin = take(sizeof(double) * 3 * kMaxCellsPerAxis);
+    p->pack = take(3 * 16 * N);
     p->aos_tmp = (ws_flags & SPH_WS_REORDER) ? take((size_t)L.record_bytes * N) : 0;
     p->stats = take(sizeof(DevStats));
     for (int f = 0; f < SPH_NFIELDS; ++f)
@@ -186,6 +187,7 @@ sph_status sph_create(const sph_aos_layout *layout, const sph_params *params, in
     c->stage = (float *)(w + plan.stage);
     c->key_hmax = (float *)(w + plan.key_hmax);
     c->origin = (double *)(w + plan.origin);
+    c->pack = (float4 *)(w + plan.pack);
     c->aos_tmp = (ws_flags & SPH_WS_REORDER) ? w + plan.aos_tmp : nullptr;
     c->dstats = (DevStats *)(w + plan.stats);
     for (int f = 0; f < SPH_NFIELDS; ++f) {

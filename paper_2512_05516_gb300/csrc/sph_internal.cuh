@@ -47,7 +47,7 @@ struct Plan {
     size_t keys[2], vals[2];
     size_t cell_count, cell_start, scan_part, ghist;
     size_t item_cell, item_first, item_count, item_tmp, item_sorted, item_class, class_hist;
-    size_t nngb, nngb_force, stage, aos_tmp, stats, key_hmax, origin;
+    size_t nngb, nngb_force, stage, aos_tmp, stats, key_hmax, origin, pack;
     size_t soa[SPH_NFIELDS][3];
     size_t total;
     int64_t item_max, nblk_radix;
@@ -267,6 +267,7 @@ struct sph_ctx {
     float *stage = nullptr;
     float *key_hmax = nullptr;    // largest h of every sub-cell (force pruning)
     double *origin = nullptr;     // cell origins k * (L_d / nc_d), kMaxCellsPerAxis per axis
+    float4 *pack = nullptr;       // 3 x n: the force's packed FP32 inputs per slot
     uint8_t *aos_tmp = nullptr;
     sph::DevStats *dstats = nullptr;
     void *soa[SPH_NFIELDS][3] = {};
