@@ -76,6 +76,7 @@ struct DensityArgs {
     void *P_out; int P_fmt;
     void *cs_out; int cs_fmt;
     float rho_enc, h_enc, P_enc, cs_enc;   // storage scales of the outputs
+    const float4 *pD;                // every slot's (x, y, z, m) in FP32, from the pack pass
     int32_t *nngb;
 };
 
@@ -344,36 +345,13 @@ struct Cursor {
     int g, e;
 };
 
-// Staging loads.  The pair kernels are compiled for fixed storage formats of
-// the positions (FX) and of the particle fields (FV: v, m, h); those decode
-// with one load each, which keeps the unrolled staging loops small (the
-// kernels are instruction-cache bound otherwise).  kAnyFmt decodes whatever
-// format the field has at run time (mixed or packed formats).
-constexpr int kAnyFmt = -1;
-
-template <int F>
-__device__ __forceinline__ float ldf(const void *p, int fmt, int64_t k)
-{
-    if constexpr (F == SPH_P_FP32) return __ldg((const float *)p + k);
-    else if constexpr (F == SPH_P_FP16) return __half2float(__ushort_as_half(__ldg((const unsigned short *)p + k)));
-    else if constexpr (F == SPH_P_BF16) return dec_bf16(__ldg((const unsigned short *)p + k));
-    else if constexpr (F == SPH_P_FP32_M16) return ld_packed((const uint32_t *)p, k, 25);
-    else if constexpr (F == SPH_P_FP32_M10) return ld_packed((const uint32_t *)p, k, 19);
-    else return ld_val(p, fmt, k);
-}
-
-// derived fields (rho, P, c) are FP32 in the fixed-format kernels
-template <int FX>
-__host__ __device__ constexpr int derived_fmt() { return FX == kAnyFmt ? kAnyFmt : (int)SPH_P_FP32; }
-
 // Stage the stream's candidates within distance sqrt(R2) of the warp box, in
 // stream order, starting at `cur`, until the stage is full or the stream ends.
 // Returns how many were staged (<= cap) and moves `cur` to the first batch
 // not staged (cur.g == total when the stream is exhausted).  A chunk always
 // stages at least one batch, since a batch holds at most 32 <= cap.
-template <int FX, int FV>
-__device__ int stage_density(const Common &c, const Tab &tab, int total, const Box &box, float R2,
-                             float4 *sj, int cap, Cursor &cur, int lane)
+__device__ int stage_density(const Common &c, const float4 *pD, const Tab &tab, int total, const Box &box,
+                             float R2, float4 *sj, int cap, Cursor &cur, int lane)
 {
     const unsigned lt = (1u << lane) - 1u;
     const int nk = tab.nk;
@@ -392,10 +370,8 @@ __device__ int stage_density(const Common &c, const Tab &tab, int total, const B
                 const int64_t j = (int64_t)tab.base[e] + g;
                 float sx, sy, sz;
                 stencil_shift(c, tab.t[e], sx, sy, sz);
-                q[u].x = fmaf(ldf<FX>(c.x.p[0], c.x.fmt, j), c.x.dec, sx);
-                q[u].y = fmaf(ldf<FX>(c.x.p[1], c.x.fmt, j), c.x.dec, sy);
-                q[u].z = fmaf(ldf<FX>(c.x.p[2], c.x.fmt, j), c.x.dec, sz);
-                q[u].w = ldf<FV>(c.m.p[0], c.m.fmt, j) * c.m.dec;
+                const float4 p = __ldg(pD + j);
+                q[u] = make_float4(p.x + sx, p.y + sy, p.z + sz, p.w);
             }
             eu[u] = e;
         }
@@ -421,7 +397,17 @@ __device__ int stage_density(const Common &c, const Tab &tab, int total, const B
     return found;
 }
 
-template <int FX, int FV>
+// The density's pack pass: every slot's (x, y, z, m) decoded from their
+// storage formats into one FP32 float4, so that staging loads a candidate
+// with one 16-byte load.
+__global__ void __launch_bounds__(256) k_density_pack(Common c, float4 *pD)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= c.n) return;
+    pD[k] = make_float4(ld_val(c.x.p[0], c.x.fmt, k) * c.x.dec, ld_val(c.x.p[1], c.x.fmt, k) * c.x.dec,
+                        ld_val(c.x.p[2], c.x.fmt, k) * c.x.dec, ld_val(c.m.p[0], c.m.fmt, k) * c.m.dec);
+}
+
 __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -446,10 +432,11 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
         bool clamped = false;
         float xi = 0.f, yi = 0.f, zi = 0.f, mi = 0.f, hi = 0.f, ui = 0.f;
         if (ok) {
-            xi = ld_val(c.x.p[0], c.x.fmt, k) * c.x.dec;
-            yi = ld_val(c.x.p[1], c.x.fmt, k) * c.x.dec;
-            zi = ld_val(c.x.p[2], c.x.fmt, k) * c.x.dec;
-            mi = ld_val(c.m.p[0], c.m.fmt, k) * c.m.dec;
+            const float4 p = __ldg(a.pD + k);
+            xi = p.x;
+            yi = p.y;
+            zi = p.z;
+            mi = p.w;
             hi = ld_val(c.h.p[0], c.h.fmt, k) * c.h.dec;
             if (a.has_u) ui = ld_val(a.u.p[0], a.u.fmt, k) * a.u.dec;
             if (!(hi > 0.0f) || !isfinite(hi)) { hi = a.h_cap; my_err |= SPH_ERR_NONFINITE; }
@@ -462,7 +449,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
         float R2s = 4.0f * h_stage * h_stage;
         int total = build_stream(c, cell, box, R2s, tab, lane);
         Cursor cur{0, 0};
-        int T = stage_density<FX, FV>(c, tab, total, box, R2s, sj, c.cap, cur, lane);
+        int T = stage_density(c, a.pD, tab, total, box, R2s, sj, c.cap, cur, lane);
         bool fits = cur.g >= total;
         float h_list = 0.0f;       // this lane's list holds every staged candidate within 2 h_list
         int nlist = 0;
@@ -480,7 +467,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
                 R2s = 4.0f * h_stage * h_stage;
                 total = build_stream(c, cell, box, R2s, tab, lane);
                 Cursor rc{0, 0};
-                T = stage_density<FX, FV>(c, tab, total, box, R2s, sj, c.cap, rc, lane);
+                T = stage_density(c, a.pD, tab, total, box, R2s, sj, c.cap, rc, lane);
                 fits = rc.g >= total;
                 h_list = 0.0f;
             }
@@ -527,7 +514,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
                 const int tot = build_stream(c, cell, box, R2, tab, lane);
                 Cursor sc{0, 0};
                 do {
-                    const int len = stage_density<FX, FV>(c, tab, tot, box, R2, sj, c.cap, sc, lane);
+                    const int len = stage_density(c, a.pD, tab, tot, box, R2, sj, c.cap, sc, lane);
                     if (ok) {
                         my_tests += (unsigned long long)len;
                         for (int e = 0; e < len; ++e) dens_pair(acc, xi, yi, zi, h2x4, hinv, a.plain_sum, deriv, sj[e]);
@@ -1058,53 +1045,6 @@ cudaError_t launch_persistent(sph_ctx *c, K kernel, const A &args, size_t smem, 
     return cudaGetLastError();
 }
 
-// Which fixed-format instantiation serves positions in fx and fields in fv:
-// 1..10 for (FP32 | FP16) x (FP32 | BF16 | FP16 | FP32-m16 | FP32-m10), 0 for
-// the run-time decoder.
-int fmt_variant(int fx, int fv)
-{
-    const int ix = fx == SPH_P_FP32 ? 0 : (fx == SPH_P_FP16 ? 1 : -1);
-    int iv = -1;
-    switch (fv) {
-    case SPH_P_FP32: iv = 0; break;
-    case SPH_P_BF16: iv = 1; break;
-    case SPH_P_FP16: iv = 2; break;
-    case SPH_P_FP32_M16: iv = 3; break;
-    case SPH_P_FP32_M10: iv = 4; break;
-    default: break;
-    }
-    if (ix < 0 || iv < 0) return 0;
-    return 1 + 5 * ix + iv;
-}
-
-// One launch table per kernel family, indexed by fmt_variant.
-template <template <int, int> class K>
-struct Variants {
-    template <typename A>
-    static cudaError_t launch(sph_ctx *c, int v, const A &a, size_t smem, LaunchCache *lc)
-    {
-        constexpr int P32 = SPH_P_FP32, P16 = SPH_P_FP16, B16 = SPH_P_BF16, M16 = SPH_P_FP32_M16,
-                      M10 = SPH_P_FP32_M10;
-        switch (v) {
-        case 1: return launch_persistent(c, K<P32, P32>::fn, a, smem, lc[1]);
-        case 2: return launch_persistent(c, K<P32, B16>::fn, a, smem, lc[2]);
-        case 3: return launch_persistent(c, K<P32, P16>::fn, a, smem, lc[3]);
-        case 4: return launch_persistent(c, K<P32, M16>::fn, a, smem, lc[4]);
-        case 5: return launch_persistent(c, K<P32, M10>::fn, a, smem, lc[5]);
-        case 6: return launch_persistent(c, K<P16, P32>::fn, a, smem, lc[6]);
-        case 7: return launch_persistent(c, K<P16, B16>::fn, a, smem, lc[7]);
-        case 8: return launch_persistent(c, K<P16, P16>::fn, a, smem, lc[8]);
-        case 9: return launch_persistent(c, K<P16, M16>::fn, a, smem, lc[9]);
-        case 10: return launch_persistent(c, K<P16, M10>::fn, a, smem, lc[10]);
-        default: return launch_persistent(c, K<kAnyFmt, kAnyFmt>::fn, a, smem, lc[0]);
-        }
-    }
-};
-template <int FX, int FV>
-struct DensityK {
-    static constexpr auto fn = k_density<FX, FV>;
-};
-
 }  // namespace
 
 size_t density_smem_bytes(int block_threads, int cap)
@@ -1157,10 +1097,14 @@ cudaError_t run_density(sph_ctx *c, int newton_steps)
         if (a.write_h && h_packed) return run_pack(c, c->stage, SPH_F_H);
         return cudaSuccess;
     }
-    const size_t smem = density_smem_bytes(c->tuning.block_threads, a.c.cap);
-    // what the staging loads decides the instantiation
-    cudaError_t e = Variants<DensityK>::launch(c, fmt_variant(a.c.x.fmt, a.c.m.fmt), a, smem, c->lc_density);
+    // the pack pass (the force's pack arrays are free until the force runs)
+    a.pD = c->pack;
+    k_density_pack<<<(unsigned)((c->n + 255) / 256), 256, 0, c->stream>>>(a.c, c->pack);
+    c->launches += 1;
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    const size_t smem = density_smem_bytes(c->tuning.block_threads, a.c.cap);
+    if ((e = launch_persistent(c, k_density, a, smem, c->lc_density)) != cudaSuccess) return e;
     if (a.write_h && h_packed) return run_pack(c, c->stage, SPH_F_H);
     return cudaSuccess;
 }
@@ -1208,7 +1152,7 @@ cudaError_t run_force(sph_ctx *c)
     }
     // the pair kernel reads only the packed FP32 arrays: one instantiation
     const size_t smem = force_smem_bytes(c->tuning.block_threads, a.c.cap);
-    return launch_persistent(c, k_force, a, smem, c->lc_force[0]);
+    return launch_persistent(c, k_force, a, smem, c->lc_force);
 }
 
 }  // namespace sph

@@ -250,7 +250,7 @@ struct sph_ctx {
     int64_t ncell = 0;
     int sub = 1;                  // sub-cells per cell edge of the last binning
     bool binned = false;
-    sph::LaunchCache lc_density[12], lc_force[12];   // one per storage-format instantiation
+    sph::LaunchCache lc_density, lc_force;   // launch shapes of the persistent pair kernels
     int sorted_buf = 0;          // which ping-pong buffer holds the sorted keys/values
 
     // workspace arrays
