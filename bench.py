@@ -327,6 +327,9 @@ def run_long_run(steps: int = 3, graph_steps: int = 10):
                              eps=wl.eps_av, eta=wl.eta, h_max=wl.h_cap)
     s = sph.Sph(aos, sph.layout_112(), params, int(np.prod(nc)), sph.WS_REORDER, stream=stream)
     prec = {"x": "fp16", "v": "fp16", "m": "fp16", "h": "fp16", "u": "fp16"}
+    from paper_2512_05516_gb300 import autotune
+    with torch.cuda.stream(stream):
+        tuned = autotune.tune(s, wl.cell_edge, prec, 0)
     names = ["bin", "aos_to_soa", "density", "force", "kick_drift_writeback"]
     calls = [lambda: s.bin_cells(wl.cell_edge), lambda: s.aos_to_soa(sph.FIELDS_FORCE, prec),
              lambda: s.density(0), lambda: s.force(),
@@ -420,6 +423,7 @@ def run_long_run(steps: int = 3, graph_steps: int = 10):
     fp16_step = sum(ms[nm] for nm in names)
     fp32_step = sum(ms32.values())
     return {"workload": "long_run_33554432", "particles": n, "storage": "fp16 (x, v, m, h, u)",
+            "tuning": tuned["tuning"],
             "ms_per_step_graph": graph_ms, "pairs_per_s": pairs / (graph_ms / 1e3),
             "kernels": kern, "hbm_peak_gbs": hbm,
             "vs_fp32_soa": {"fp16_with_conversion_ms": fp16_step,

@@ -250,15 +250,8 @@ __global__ void k_items_fill(const int32_t *cell_start, const int32_t *item_off,
 // optional queue order: work items grouped by cost class, costliest first
 // ---------------------------------------------------------------------------
 
-// class key of every item: the power of two of (its particle count x the
-// particles of the 27 cells around its cell), stored as
-// kItemClasses - 1 - log2 so that ascending keys put the costliest first
-__global__ void k_item_class(const int32_t *cell_start, const int32_t *icell, const int32_t *icount, int3 nc,
-                             int s3, const DevStats *st, int32_t *key, int32_t *hist)
+__device__ __forceinline__ int item_class_key(const int32_t *cell_start, int cell, int count, int3 nc, int s3)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= st->nitems) return;
-    const int cell = icell[i];
     const int kx = cell % nc.x, t = cell / nc.x, ky = t % nc.y, kz = t / nc.y;
     long long occ = 0;
     for (int dz = -1; dz <= 1; ++dz)
@@ -268,10 +261,25 @@ __global__ void k_item_class(const int32_t *cell_start, const int32_t *icell, co
                 const long long cid = x + (long long)nc.x * (y + (long long)nc.y * z);
                 occ += cell_start[(cid + 1) * s3] - cell_start[cid * s3];
             }
-    const long long cost = (long long)icount[i] * occ;
+    const long long cost = (long long)count * occ;
     const int lg = cost > 0 ? min(63 - __clzll(cost), kItemClasses - 1) : 0;
-    key[i] = kItemClasses - 1 - lg;
-    atomicAdd(&hist[key[i]], 1);
+    return kItemClasses - 1 - lg;
+}
+
+// class key of every item: the power of two of (its particle count x the
+// particles of the 27 cells around its cell), stored as
+// kItemClasses - 1 - log2 so that ascending keys put the costliest first
+__global__ void k_item_class(const int32_t *cell_start, const int32_t *icell, const int32_t *icount, int3 nc,
+                             int s3, const DevStats *st, int32_t *key, int32_t *hist)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool ok = i < st->nitems;
+    int kk = -1;
+    if (ok) kk = item_class_key(cell_start, icell[i], icount[i], nc, s3);
+    if (ok) key[i] = kk;
+    // few distinct classes: one atomic per class present in the warp
+    const unsigned peers = __match_any_sync(0xffffffffu, kk);
+    if (ok && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[kk], __popc(peers));
 }
 
 // one warp: class starts (kItemClasses + 1 entries) and scatter cursors
@@ -296,8 +304,18 @@ __global__ void k_item_scatter(const int32_t *icell, const int32_t *ifirst, cons
                                const DevStats *st)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= st->nitems) return;
-    const int pos = atomicAdd(&cursor[key[i]], 1);
+    const int lane = threadIdx.x & 31;
+    const bool ok = i < st->nitems;
+    const int kk = ok ? key[i] : -1;
+    // one atomic per class present in the warp; the lanes of a class take
+    // consecutive positions from it
+    const unsigned peers = __match_any_sync(0xffffffffu, kk);
+    const int leader = __ffs(peers) - 1;
+    int base = 0;
+    if (ok && lane == leader) base = atomicAdd(&cursor[kk], __popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (!ok) return;
+    const int pos = base + __popc(peers & ((1u << lane) - 1u));
     sorted[pos] = icell[i];
     sorted[item_max + pos] = ifirst[i];
     sorted[2 * item_max + pos] = icount[i];
