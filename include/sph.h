@@ -90,6 +90,15 @@ typedef enum {
     SPH_P_FP32_M16 = 3,  /* 25-bit code */
     SPH_P_FP32_M10 = 4   /* 19-bit code */
 } sph_prec;
+/* The truncated family at any width (Table 2's rows from 31 down to 10 total
+ * bits): FP32 with the top n mantissa bits kept by truncation, n in [1, 22],
+ * stored as a packed stream of (9 + n)-bit codes.  SPH_P_FP32_TRUNC(16) and
+ * SPH_P_FP32_TRUNC(10) are SPH_P_FP32_M16 and SPH_P_FP32_M10 under other
+ * codes.  Wider formats (FP64-based, 33..63 bits) would decode to values that
+ * the FP32 arithmetic rounds to FP32 anyway, so FP32 storage covers them. */
+#define SPH_P_FP32_TRUNC(n) (100 + (n))
+#define SPH_P_FP32_TRUNC_MIN 1
+#define SPH_P_FP32_TRUNC_MAX 22
 
 /* element type of a field inside the caller's AoS record */
 enum { SPH_AOS_F64 = 0, SPH_AOS_F32 = 1 };

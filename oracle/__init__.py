@@ -28,6 +28,10 @@ _LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
 
 FMT = {"fp32": 0, "bf16": 1, "fp16": 2, "m16": 3, "m10": 4}
 FMT_BITS = {"fp32": 32, "bf16": 16, "fp16": 16, "m16": 25, "m10": 19}
+# the truncated family at every width: "m<n>" keeps n mantissa bits, n in 1..22
+for _n in range(1, 23):
+    FMT.setdefault(f"m{_n}", 100 + _n)
+    FMT_BITS.setdefault(f"m{_n}", 9 + _n)
 FLAG_HCAP, FLAG_NEWTON, FLAG_NONFINITE = 1, 2, 4
 
 _lock = threading.Lock()

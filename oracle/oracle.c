@@ -571,6 +571,7 @@ uint32_t orc_f32_from_trunc(uint32_t code, int mant_bits)
 
 int orc_fmt_bits(int fmt)
 {
+    if (fmt > 100 && fmt <= 122) return 9 + (fmt - 100);
     switch (fmt) {
     case ORC_FMT_FP32: return 32;
     case ORC_FMT_BF16: return 16;
@@ -591,7 +592,15 @@ void orc_quantize(int64_t n, const double *in, int fmt, double *value, uint32_t 
         case ORC_FMT_FP16: cd = orc_f16_from_f32(fb); back = orc_f32_from_f16((uint16_t)cd); break;
         case ORC_FMT_M16:  cd = orc_trunc_code(fb, 16); back = orc_f32_from_trunc(cd, 16); break;
         case ORC_FMT_M10:  cd = orc_trunc_code(fb, 10); back = orc_f32_from_trunc(cd, 10); break;
-        default:           cd = fb; back = fb; break;
+        default:
+            if (fmt > 100 && fmt <= 122) {        /* ORC_FMT_TRUNC(n) */
+                cd = orc_trunc_code(fb, fmt - 100);
+                back = orc_f32_from_trunc(cd, fmt - 100);
+            } else {
+                cd = fb;
+                back = fb;
+            }
+            break;
         }
         if (value) value[i] = orc_f32_value(back);
         if (code) code[i] = cd;

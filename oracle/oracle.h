@@ -32,6 +32,7 @@ extern "C" {
 #define ORC_FMT_FP16   2
 #define ORC_FMT_M16    3   /* single with 16 mantissa bits: 25-bit code */
 #define ORC_FMT_M10    4   /* single with 10 mantissa bits: 19-bit code */
+#define ORC_FMT_TRUNC(n) (100 + (n))   /* single with n mantissa bits (1..22): (9+n)-bit code */
 
 /* ---- smoothing kernel: M4 cubic spline, support 2h, sigma = 1/pi (3D) ---- */
 double orc_w(double q);

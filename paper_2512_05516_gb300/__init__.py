@@ -370,7 +370,7 @@ class Sph:
             return self._ws_view(off, self.n, torch.float32)
         if fmt in (P_BF16, P_FP16):
             return self._ws_view(off, self.n, torch.int16)
-        bits = 25 if fmt == P_FP32_M16 else 19
+        bits = 25 if fmt == P_FP32_M16 else (19 if fmt == P_FP32_M10 else 9 + (fmt - 100))
         return self._ws_view(off, (self.n * bits + 31) // 32, torch.int32)
 
     def close(self):

@@ -27,6 +27,9 @@ FIELDS_OUTPUT = BIT(F_V) | BIT(F_A) | BIT(F_H) | BIT(F_RHO) | BIT(F_U) | BIT(F_P
 
 P_FP32, P_BF16, P_FP16, P_FP32_M16, P_FP32_M10 = range(5)
 PREC = {"fp32": P_FP32, "bf16": P_BF16, "fp16": P_FP16, "m16": P_FP32_M16, "m10": P_FP32_M10}
+# the truncated family at every width: "m<n>" keeps n mantissa bits (n in 1..22)
+for _n in range(1, 23):
+    PREC.setdefault(f"m{_n}", 100 + _n)
 AOS_F64, AOS_F32 = 0, 1
 FLAG_PLAIN_SUM = 1
 WS_REORDER = 1

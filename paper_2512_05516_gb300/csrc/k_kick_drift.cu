@@ -64,7 +64,12 @@ __device__ __forceinline__ float quantize_fmt(float x, int fmt)
     case SPH_P_FP16: return __half2float(__float2half_rn(x));
     case SPH_P_FP32_M16: return __uint_as_float(enc_trunc(x, 25) << 7);
     case SPH_P_FP32_M10: return __uint_as_float(enc_trunc(x, 19) << 13);
-    default: return x;
+    default:
+        if (fmt_trunc_any(fmt)) {
+            const int B = fmt_bits(fmt);
+            return __uint_as_float(enc_trunc(x, B) << (32 - B));
+        }
+        return x;
     }
 }
 

@@ -41,7 +41,7 @@ bool params_ok(const sph_params *p)
 // which storage formats each SoA field accepts
 bool fmt_allowed(int f, int fmt)
 {
-    if (fmt < SPH_P_FP32 || fmt > SPH_P_FP32_M10) return false;
+    if ((fmt < SPH_P_FP32 || fmt > SPH_P_FP32_M10) && !fmt_trunc_any(fmt)) return false;
     switch (f) {
     case SPH_F_X: return fmt == SPH_P_FP32 || fmt == SPH_P_FP16;
     case SPH_F_V: case SPH_F_M: case SPH_F_H: case SPH_F_U: return true;

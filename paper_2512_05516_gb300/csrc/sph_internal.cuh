@@ -75,8 +75,14 @@ struct FieldRef {
 // ---------------------------------------------------------------------------
 // storage-format codecs (Table 2 and bfloat16).  All formats decode to FP32.
 // ---------------------------------------------------------------------------
+// truncated FP32 with n mantissa bits at any width (SPH_P_FP32_TRUNC(n))
+__host__ __device__ inline bool fmt_trunc_any(int fmt)
+{
+    return fmt >= SPH_P_FP32_TRUNC(SPH_P_FP32_TRUNC_MIN) && fmt <= SPH_P_FP32_TRUNC(SPH_P_FP32_TRUNC_MAX);
+}
 __host__ __device__ inline int fmt_bits(int fmt)
 {
+    if (fmt_trunc_any(fmt)) return 9 + (fmt - 100);
     switch (fmt) {
     case SPH_P_BF16: case SPH_P_FP16: return 16;
     case SPH_P_FP32_M16: return 25;
@@ -86,7 +92,7 @@ __host__ __device__ inline int fmt_bits(int fmt)
 }
 __host__ __device__ inline bool fmt_packed(int fmt)
 {
-    return fmt == SPH_P_FP32_M16 || fmt == SPH_P_FP32_M10;
+    return fmt == SPH_P_FP32_M16 || fmt == SPH_P_FP32_M10 || fmt_trunc_any(fmt);
 }
 
 __device__ __forceinline__ float dec_bf16(uint16_t b) { return __uint_as_float((uint32_t)b << 16); }
@@ -126,7 +132,9 @@ __device__ __forceinline__ float ld_val(const void *p, int fmt, int64_t k)
     case SPH_P_FP16: return __half2float(__ushort_as_half(__ldg((const unsigned short *)p + k)));
     case SPH_P_FP32_M16: return ld_packed((const uint32_t *)p, k, 25);
     case SPH_P_FP32_M10: return ld_packed((const uint32_t *)p, k, 19);
-    default: return __ldg((const float *)p + k);
+    default:
+        if (fmt_trunc_any(fmt)) return ld_packed((const uint32_t *)p, k, fmt_bits(fmt));
+        return __ldg((const float *)p + k);
     }
 }
 
@@ -155,8 +163,12 @@ __device__ __forceinline__ void st_packed_warp(uint32_t *w, int64_t k, float v, 
     const int v0 = (32 * j) / B;
     const int v1 = (32 * j + 31) / B;
     uint32_t word = 0u;
+    // a word holds parts of at most floor(31 / B) + 2 values (5 at B = 10);
+    // the bound is warp-uniform, so every lane runs the same shuffles
+    const int nt = 31 / B + 2;
 #pragma unroll
-    for (int t = 0; t < 3; ++t) {
+    for (int t = 0; t < 5; ++t) {
+        if (t >= nt) break;
         int src = v0 + t;
         uint32_t cv = __shfl_sync(0xffffffffu, code, src < 32 ? src : 31);
         if (j < B && src <= v1 && src < 32) {

@@ -17,7 +17,10 @@ the first step the trajectories diverge chaotically: those errors are
 reported, not gated.  Step times are CUDA-event means over 10 steps without
 L2 flushing (indicative; bench.py times the benchmark).
 
-Usage (GPU):  python tests/precision_report.py [--json out.json] [--quick]
+With --sweep: the truncated family at every width instead, v, m, h, u stored
+with 23 down to 1 mantissa bits (32 down to 10 total bits), one Sod step.
+
+Usage (GPU):  python tests/precision_report.py [--json out.json] [--quick | --sweep]
 """
 import argparse
 import json
@@ -120,6 +123,27 @@ def one_step_report(wl, torch, sph, time_it):
     return rows, t_orc
 
 
+def sweep_report(wl, torch, sph):
+    """The truncated family at every width (the paper's error-against-bits
+    study, Section 7 and Table 2): v, m, h, u stored as FP32 with n mantissa
+    bits, n = 23 (FP32 itself) down to 1, i.e. 32 down to 10 total bits;
+    positions FP32; one step against FP64 on sampled targets."""
+    rng = np.random.default_rng(11)
+    tgt = np.sort(rng.choice(wl.n, N_TARGETS, replace=False))
+    o = oracle.step(wl, targets=tgt)
+    rows = []
+    for n in range(23, 0, -1):
+        fmt = "fp32" if n == 23 else f"m{n}"
+        out, st, _, _ = run_steps(wl, fmt, "fp32", 1, torch, sph)
+        r = {"workload": wl.name, "n": wl.n, "steps": 1, "storage": fmt, "total_bits": 9 + n,
+             "positions": "fp32", "error_bits": st["error_bits"],
+             "rho": errors(out[tgt, 11], o["rho"]), "h": errors(out[tgt, 10], o["h"]),
+             "P": errors(out[tgt, 13], o["P"]), "a": errors(out[tgt, 6:9], o["a"], True)}
+        rows.append(r)
+        print(json.dumps(r), flush=True)
+    return rows
+
+
 def hundred_step_report(name, wl, torch, sph):
     path = os.path.join(ROOT, "tests", "golden", f"trajectory_{name}.npz")
     if not os.path.exists(path):
@@ -167,11 +191,25 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--json", default=None)
     ap.add_argument("--quick", action="store_true", help="1-step rows only")
+    ap.add_argument("--sweep", action="store_true",
+                    help="only the truncated-mantissa sweep (32 down to 10 total bits) on the Sod set")
     args = ap.parse_args()
     import torch
     import paper_2512_05516_gb300 as sph
     if not torch.cuda.is_available():
         raise SystemExit("the precision report runs the CUDA path: no GPU here")
+    if args.sweep:
+        rows = sweep_report(sph_inputs.sod(), torch, sph)
+        print()
+        print("| total bits | storage | rho | h | P | a |")
+        print("|---|---|---|---|---|---|")
+        for r in rows:
+            print(f"| {r['total_bits']} | {r['storage']} | " +
+                  " | ".join(f"{r[f]['rel_rmse']:.2e} / {r[f]['max_rel']:.1e}" for f in ("rho", "h", "P", "a")) + " |")
+        if args.json:
+            with open(args.json, "w") as f:
+                json.dump(rows, f, indent=1)
+        return
     rows = []
     sod = sph_inputs.sod()
     r1, _ = one_step_report(sod, torch, sph, time_it=True)

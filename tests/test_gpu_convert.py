@@ -10,7 +10,7 @@ from gpu_util import make_sph
 
 pytestmark = pytest.mark.gpu
 
-FMTS = ["fp32", "bf16", "fp16", "m16", "m10"]
+FMTS = ["fp32", "bf16", "fp16", "m16", "m10", "m1", "m5", "m22"]      # m1, m5, m22: 10, 14 and 31-bit codes
 
 
 def _codes(orc, vals, fmt):

@@ -47,7 +47,7 @@ def _records(wl, dudt, layout_name):
 
 
 @pytest.mark.parametrize("layout_name", ["112", "136", "96"])
-@pytest.mark.parametrize("fmt", ["fp32", "bf16", "fp16s", "m16", "m10"])
+@pytest.mark.parametrize("fmt", ["fp32", "bf16", "fp16s", "m16", "m10", "m3"])
 def test_fused_equals_separate(fmt, layout_name):
     wl, dudt = _workload()
     base = "fp16" if fmt == "fp16s" else fmt

@@ -64,7 +64,8 @@ def test_fp32_is_ieee_rounding(orc):
     assert np.array_equal(v, d.astype(np.float32).astype(np.float64))
 
 
-@pytest.mark.parametrize("fmt,mant", [("m16", 16), ("m10", 10)])
+@pytest.mark.parametrize("fmt,mant", [("m16", 16), ("m10", 10), ("m1", 1), ("m7", 7), ("m13", 13),
+                                      ("m22", 22)])
 def test_truncated_formats(orc, fmt, mant):
     rng = np.random.default_rng(3)
     d = rng.standard_normal(100_000) * 10.0 ** rng.uniform(-10, 10, 100_000)
@@ -127,3 +128,16 @@ def test_scaled_half_keeps_eleven_bits_of_a_subnormal_mass(orc):
     q, _ = orc.quantize([262144.0, 1e-6], "fp16", exp2=-7)
     assert q[0] == 262144.0
     assert q[1] == 0.0                                    # 1e-6 * 2^-7 underflows
+
+
+def test_truncated_family_matches_the_named_widths(orc):
+    # "m16"/"m10" and the generic codes of the same width are one format
+    rng = np.random.default_rng(4)
+    d = rng.standard_normal(10_000) * 10.0 ** rng.uniform(-5, 5, 10_000)
+    for n in (16, 10):
+        v0, c0 = orc.quantize(d, f"m{n}")
+        L = orc.lib()
+        out = np.zeros_like(d)
+        code = np.zeros(d.shape, np.uint32)
+        L.orc_quantize(d.shape[0], orc._ptr(d), 100 + n, orc._ptr(out), orc._ptr(code))
+        assert np.array_equal(code, c0) and np.array_equal(out, v0)
