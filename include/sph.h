@@ -217,7 +217,8 @@ size_t sph_workspace_bytes(const sph_aos_layout *layout, int64_t n, int64_t ncel
  * case the kernels that touch the records (binning, conversion, kick/drift,
  * write-back) read and write them over the host link while the SoA and the
  * workspace stay in device memory: the paper's streaming variant without
- * staging copies.  d_aos must be 16-byte aligned.
+ * staging copies.  d_aos must be 16-byte aligned (it may be NULL when n = 0:
+ * every call is then a no-op).
  * Errors: SPH_EINVAL (layout, params or pointers), SPH_ENOSPACE (workspace),
  * SPH_ECUDA (device query).  On success *out receives the context. */
 sph_status sph_create(const sph_aos_layout *layout, const sph_params *params, int64_t n,

@@ -137,7 +137,7 @@ sph_status sph_create(const sph_aos_layout *layout, const sph_params *params, in
 {
     if (!out) return SPH_EINVAL;
     *out = nullptr;
-    if (!layout_ok(layout) || !params_ok(params) || !d_aos || !d_workspace) return SPH_EINVAL;
+    if (!layout_ok(layout) || !params_ok(params) || (!d_aos && n > 0) || !d_workspace) return SPH_EINVAL;
     if (((uintptr_t)d_aos & 15) != 0 || ((uintptr_t)d_workspace & 255) != 0) return SPH_EINVAL;
     Plan plan;
     if (!make_plan(*layout, n, ncell_max, ws_flags, &plan)) return SPH_EINVAL;
