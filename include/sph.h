@@ -157,6 +157,8 @@ typedef struct {
 #define SPH_ERR_OUTSIDE   2      /* a position lay outside [0, box) at binning */
 #define SPH_ERR_HCAP      4      /* some h was clamped at h_max */
 #define SPH_ERR_NEWTON    8      /* a Newton step met a non-positive derivative */
+#define SPH_ERR_TIMEOUT   16     /* an asynchronous record copy did not complete within its bounded
+                                    wait; the records of that warp were skipped */
 
 /* Launch shapes of the pair kernels (an autotuner sets them; the defaults
  * after sph_create are block_threads 32, ctas_per_sm 0, stage_density 1024,
@@ -217,8 +219,11 @@ size_t sph_workspace_bytes(const sph_aos_layout *layout, int64_t n, int64_t ncel
  * case the kernels that touch the records (binning, conversion, kick/drift,
  * write-back) read and write them over the host link while the SoA and the
  * workspace stay in device memory: the paper's streaming variant without
- * staging copies.  d_aos must be 16-byte aligned (it may be NULL when n = 0:
- * every call is then a no-op).
+ * staging copies.  Device-resident records whose size is a multiple of 16
+ * bytes (and an odd number of 16-byte chunks) move by bulk asynchronous
+ * copies where a warp's 32 records are consecutive; host-mapped records
+ * always take per-lane loads.  d_aos must be 16-byte aligned (it may be NULL
+ * when n = 0: every call is then a no-op).
  * Errors: SPH_EINVAL (layout, params or pointers), SPH_ENOSPACE (workspace),
  * SPH_ECUDA (device query).  On success *out receives the context. */
 sph_status sph_create(const sph_aos_layout *layout, const sph_params *params, int64_t n,
@@ -320,8 +325,8 @@ sph_status sph_soa_to_aos(sph_ctx *ctx, uint32_t fields);
 sph_status sph_kick_drift_writeback(sph_ctx *ctx, double dt_kick, double dt_drift, uint32_t fields);
 
 /* Copy the device counters to *out.  Synchronises the context's stream.
- * Returns SPH_ENUMERIC when error_bits has SPH_ERR_NONFINITE or
- * SPH_ERR_OUTSIDE set (the counters are still filled in), else SPH_OK. */
+ * Returns SPH_ENUMERIC when error_bits has SPH_ERR_NONFINITE, SPH_ERR_OUTSIDE
+ * or SPH_ERR_TIMEOUT set (the counters are still filled in), else SPH_OK. */
 sph_status sph_get_stats(sph_ctx *ctx, sph_stats *out);
 
 /* Zero the device counters and the sticky error word (asynchronous). */

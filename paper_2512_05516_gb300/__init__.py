@@ -13,7 +13,7 @@ from __future__ import annotations
 import ctypes as C
 
 from . import _capi
-from ._capi import (AOS_F32, AOS_F64, BIT, ERR_HCAP, ERR_NEWTON, ERR_NONFINITE, ERR_OUTSIDE,
+from ._capi import (AOS_F32, AOS_F64, BIT, ERR_HCAP, ERR_NEWTON, ERR_NONFINITE, ERR_OUTSIDE, ERR_TIMEOUT,
                     F_A, F_CS, F_DUDT, F_H, F_M, F_P, F_RHO, F_U, F_V, F_X, FIELD_NAMES,
                     FIELDS_DENSITY, FIELDS_FORCE, FIELDS_KICK, FIELDS_OUTPUT, FLAG_PLAIN_SUM,
                     NCOMP, P_BF16, P_FP16, P_FP32, P_FP32_M10, P_FP32_M16, PREC, SPH_NFIELDS,

@@ -33,7 +33,7 @@ for _n in range(1, 23):
 AOS_F64, AOS_F32 = 0, 1
 FLAG_PLAIN_SUM = 1
 WS_REORDER = 1
-ERR_NONFINITE, ERR_OUTSIDE, ERR_HCAP, ERR_NEWTON = 1, 2, 4, 8
+ERR_NONFINITE, ERR_OUTSIDE, ERR_HCAP, ERR_NEWTON, ERR_TIMEOUT = 1, 2, 4, 8, 16
 
 OK, EINVAL, ENOSPACE, ECUDA, ESTATE, ECAPACITY, ETIMEOUT, ENUMERIC = 0, -1, -2, -3, -4, -5, -6, -7
 

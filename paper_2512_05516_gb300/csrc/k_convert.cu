@@ -4,14 +4,17 @@
 //   C^T N^T U^T    decode SoA values, widen to the AoS element type, scatter
 //                  to the particle's record
 // One thread per sorted slot.  A warp moves the records of its 32 slots
-// through shared memory in 16-byte chunks (8-byte ones when the record size
-// is not a multiple of 16), lane-contiguous, so each load or store
+// through shared memory: with bulk copies (TMA) when the 32 records are
+// consecutive in memory, else in 16-byte chunks (8-byte ones when the record
+// size is not a multiple of 16), lane-contiguous, so each load or store
 // instruction covers whole records; each lane then reads (or writes) its own
-// record's fields there.  The fields a call moves are unrolled on the host
-// into a table of scalar components.  All 32 lanes stay alive so that packed
-// formats can be written warp-cooperatively.  No FP64 arithmetic: widening
-// and narrowing work on the bit patterns, and the cell-relative offsets of
-// the positions are formed exactly in integer arithmetic.
+// record's fields there.  The bulk write-back loads the whole block, places
+// the fields in it and stores it whole, so every DRAM sector is written
+// whole.  The fields a call moves are unrolled on the host into a table of
+// scalar components.  All 32 lanes stay alive so that packed formats can be
+// written warp-cooperatively.  Widening and narrowing work on the bit
+// patterns (integer pipes); the cell-relative offsets of the positions take
+// one FP64 subtraction per component, exact, before that rounding.
 #include <cstring>
 
 #include "k_records.cuh"
@@ -44,6 +47,9 @@ struct ConvArgs {
     int32_t nc0, nc1;
     const double *origin[3];     // cell origin k * (L / nc) per axis
     bool has_x;
+    BulkPlan bulk;               // bulk copies of consecutive record blocks
+    int32_t rb;                  // record bytes
+    unsigned int *err;           // sticky error bits
     int ncomp;
     Comp comp[kMaxComp];
 };
@@ -70,7 +76,15 @@ __global__ void __launch_bounds__(kConvThreads, 12) k_aos_to_soa(ConvArgs a)
         org1 = __ldg(a.origin[1] + ky);
         org2 = __ldg(a.origin[2] + kz);
     }
-    load_chunks<T>(reinterpret_cast<const T *>(a.aos), rec, o, a.g, a.run, lane);
+    const WarpRuns w = warp_runs(o, ok, lane);
+    if (sizeof(T) == 16 && a.bulk.load) {
+        uint64_t *bar = reinterpret_cast<uint64_t *>(smem + (size_t)(blockDim.x >> 5) * 32 * a.g.Up) + warp;
+        if (!bulk_load_runs(a.aos, o, w, a.rb, reinterpret_cast<uint4 *>(smem + (size_t)warp * 32 * a.g.Up), a.g.U,
+                            bar, a.err, lane))
+            return;
+    } else {
+        load_chunks<T>(reinterpret_cast<const T *>(a.aos), rec, o, a.g, a.run, lane);
+    }
     const unsigned char *mine = reinterpret_cast<const unsigned char *>(rec + lane * a.g.Up);
     for (int i = 0; i < a.ncomp; ++i) {
         const Comp cp = a.comp[i];
@@ -103,6 +117,14 @@ __global__ void __launch_bounds__(kConvThreads, 12) k_soa_to_aos(ConvArgs a)
     const bool ok = k < a.n;
     const int64_t o = ok ? a.perm[k] : -1;
     unsigned char *mine = reinterpret_cast<unsigned char *>(rec + lane * a.g.Up);
+    const WarpRuns w = warp_runs(o, ok, lane);
+    const bool bulk = sizeof(T) == 16 && a.bulk.store;
+    uint4 *img = reinterpret_cast<uint4 *>(smem + (size_t)warp * 32 * a.g.Up);
+    if (bulk) {
+        // whole records, so that the image holds every byte it stores
+        uint64_t *bar = reinterpret_cast<uint64_t *>(smem + (size_t)(blockDim.x >> 5) * 32 * a.g.Up) + warp;
+        if (!bulk_load_runs(a.aos, o, w, a.rb, img, a.g.U, bar, a.err, lane)) return;
+    }
     if (ok) {
         for (int i = 0; i < a.ncomp; ++i) {
             const Comp cp = a.comp[i];
@@ -111,7 +133,8 @@ __global__ void __launch_bounds__(kConvThreads, 12) k_soa_to_aos(ConvArgs a)
             else *reinterpret_cast<double *>(mine + cp.off) = f2d_bits(v);
         }
     }
-    store_chunks<T>(reinterpret_cast<T *>(a.aos), rec, o, a.g, a.run, a.umask, lane);
+    if (bulk) bulk_store_runs(a.aos, o, w, a.rb, img, a.g.U, lane);
+    else store_chunks<T>(reinterpret_cast<T *>(a.aos), rec, o, a.g, a.run, a.umask, lane);
 }
 
 __global__ void __launch_bounds__(256) k_pack(const float *src, void *dst, int fmt, int64_t n)
@@ -158,6 +181,10 @@ ConvArgs make_args(sph_ctx *c, uint32_t fields, bool to_soa)
         for (int u = b0 / 4; u <= (b1 - 1) / 4; ++u) a.umask[u >> 6] |= 1ull << (u & 63);
     }
     a.run = chunk_run(to_soa ? cmask : chunks_of_units(a.umask, cb));
+    a.rb = c->layout.record_bytes;
+    a.err = &c->dstats->error_bits;
+    const bool can = cb == 16 && a.g.Up == a.g.U && c->aos_device;
+    a.bulk = to_soa ? bulk_plan(can, a.g.U, cmask, nullptr) : bulk_plan(can, a.g.U, 0, a.umask);
     return a;
 }
 
@@ -166,7 +193,7 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 template <typename T>
 cudaError_t launch_conv(sph_ctx *c, const ConvArgs &a, bool to_soa)
 {
-    const size_t smem = (size_t)(kConvThreads / 32) * 32 * a.g.Up * sizeof(T);
+    const size_t smem = (size_t)(kConvThreads / 32) * 32 * a.g.Up * sizeof(T) + (kConvThreads / 32) * sizeof(uint64_t);
     cudaError_t e;
     auto kern = to_soa ? k_aos_to_soa<T> : k_soa_to_aos<T>;
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)

@@ -7,6 +7,9 @@
 // memory in 16-byte chunks (k_records.cuh): the chunks holding x are loaded,
 // the new x (and, with a write-back, every written field) is placed in the
 // record image, and the written 4-byte units go back lane-contiguously.
+// When the write-back covers most of the record and the warp's records are
+// consecutive in memory, the whole block moves by bulk copies instead: one
+// load, the new values placed in the image, one store.
 // With the write-back, x and the fields share one pass over the records, so
 // the sectors they cover are written whole instead of being merged twice.
 #include <algorithm>
@@ -51,6 +54,8 @@ struct KDArgs {
     float udec, uenc;
     const float *dudt;
     bool write_soa;              // store the kicked v, u in the SoA
+    BulkPlan bulk;               // bulk copies of consecutive record blocks
+    int32_t rb;                  // record bytes
     int nwb;
     WbComp wb[kMaxWb];
     DevStats *st;
@@ -97,7 +102,15 @@ __global__ void __launch_bounds__(kKDThreads, 10) k_kick_drift(KDArgs a)
 #pragma unroll
     for (int i = 0; i < W; ++i)
         if (ok && i < a.nwb && a.wb[i].src == 0) pre[i] = ld_val(a.wb[i].soa, a.wb[i].fmt, k);
-    load_chunks<T>(reinterpret_cast<const T *>(a.aos), rec, o, a.g, a.xrun, lane);
+    const WarpRuns w = warp_runs(o, ok, lane);
+    const bool bulk = sizeof(T) == 16 && a.bulk.store;
+    uint4 *img = reinterpret_cast<uint4 *>(smem + (size_t)warp * 32 * a.g.Up);
+    if (bulk) {
+        uint64_t *bar = reinterpret_cast<uint64_t *>(smem + (size_t)(blockDim.x >> 5) * 32 * a.g.Up) + warp;
+        if (!bulk_load_runs(a.aos, o, w, a.rb, img, a.g.U, bar, &a.st->error_bits, lane)) return;
+    } else {
+        load_chunks<T>(reinterpret_cast<const T *>(a.aos), rec, o, a.g, a.xrun, lane);
+    }
     unsigned char *mine = reinterpret_cast<unsigned char *>(rec + lane * a.g.Up);
     if (ok) {
         double *xs = reinterpret_cast<double *>(mine + a.xoff);
@@ -144,7 +157,8 @@ __global__ void __launch_bounds__(kKDThreads, 10) k_kick_drift(KDArgs a)
             else *reinterpret_cast<float *>(mine + w.off) = val;
         }
     }
-    store_chunks<T>(reinterpret_cast<T *>(a.aos), rec, o, a.g, a.wrun, a.umask, lane);
+    if (bulk) bulk_store_runs(a.aos, o, w, a.rb, img, a.g.U, lane);
+    else store_chunks<T>(reinterpret_cast<T *>(a.aos), rec, o, a.g, a.wrun, a.umask, lane);
     if (a.write_soa) {
         for (int c = 0; c < 3; ++c) st_any(a.v[c], a.vfmt, k, vn[c] * a.venc, ok, a.n);
         st_any(a.u, a.ufmt, k, un * a.uenc, ok, a.n);
@@ -159,7 +173,7 @@ inline void add_units(uint64_t umask[2], int b0, int b1)
 template <typename T>
 cudaError_t launch_kd(sph_ctx *c, const KDArgs &a)
 {
-    const size_t smem = (size_t)(kKDThreads / 32) * 32 * a.g.Up * sizeof(T);
+    const size_t smem = (size_t)(kKDThreads / 32) * 32 * a.g.Up * sizeof(T) + (kKDThreads / 32) * sizeof(uint64_t);
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_kick_drift<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
         cudaSuccess)
@@ -224,6 +238,8 @@ cudaError_t run_kick_drift(sph_ctx *c, double dt_kick, double dt_drift, uint32_t
     // SoA-sourced components first: the kernel preloads the first ones
     std::stable_partition(a.wb, a.wb + a.nwb, [](const WbComp &w) { return w.src == 0; });
     a.wrun = chunk_run(chunks_of_units(a.umask, cb));
+    a.rb = c->layout.record_bytes;
+    a.bulk = bulk_plan(cb == 16 && a.g.Up == a.g.U && c->aos_device, a.g.U, xm, a.umask);
     a.st = c->dstats;
     return cb == 16 ? launch_kd<uint4>(c, a) : launch_kd<uint2>(c, a);
 }

@@ -12,6 +12,8 @@
 // rec[r * Up + q] (Up >= U, odd where that helps the bank layout).
 #pragma once
 
+#include <cstring>
+
 #include "sph_internal.cuh"
 
 namespace sph {
@@ -52,6 +54,19 @@ inline uint64_t chunks_of_units(const uint64_t umask[2], int chunk)
     uint64_t m = 0;
     for (int u = 0; u < 128; ++u)
         if ((umask[u >> 6] >> (u & 63)) & 1ull) m |= 1ull << (u / K);
+    return m;
+}
+
+// the chunks (of `chunk` bytes) all of whose units are in a unit mask
+inline uint64_t full_chunks_of_units(const uint64_t umask[2], int chunk)
+{
+    const int K = chunk / 4;
+    uint64_t m = 0;
+    for (int q = 0; q < 128 / K && q < 64; ++q) {
+        bool all = true;
+        for (int u = q * K; u < (q + 1) * K; ++u) all = all && ((umask[u >> 6] >> (u & 63)) & 1ull);
+        if (all) m |= 1ull << q;
+    }
     return m;
 }
 
@@ -152,50 +167,154 @@ __device__ __forceinline__ void store_chunks(T *__restrict__ aos, const T *rec, 
 // x - o rounded once to FP32 (nearest, ties to even), for the cell-relative
 // position offsets.  The origin o is 0 or, for cells k >= 1, satisfies
 // o/2 <= x <= 2o, so the FP64 difference is exact (Sterbenz) and the only
-// rounding is the final one; the integer form below subtracts the aligned
-// significands exactly and rounds that to 24 bits, keeping the work off the
-// FP64 pipe.  Anything outside that frame (signs, subnormals, exponents more
-// than one apart, results outside the normal FP32 range) takes the hardware
-// FP64 subtraction and conversion.
-__device__ __forceinline__ float cell_offset_f32(double x, double o)
+// rounding is the final one.  One FP64 subtraction per component; the
+// rounding to FP32 runs on the integer pipes (d2f_bits_rn).  Outside that
+// frame the result is the FP64 difference rounded to FP32.
+__device__ __forceinline__ float cell_offset_f32(double x, double o) { return d2f_bits_rn(__dsub_rn(x, o)); }
+
+// ---------------------------------------------------------------------------
+// Bulk asynchronous copies (the non-tensor form of TMA) of record runs.
+// In cell-ordered records (the usual case once they have been reordered) a
+// warp's 32 records form one run of consecutive records, or a few runs where
+// particles changed cells since the reorder (a few more per warp every step
+// in a flow).  The warp moves its records with one cp.async.bulk per run,
+// completion counted in bytes on a per-warp mbarrier, and stores them back
+// the same way.  Fully scattered records (one run per lane) move as fast
+// this way as by per-lane chunk loads, and their write-back faster.  Every
+// wait is bounded: a copy that has not landed after kBulkPolls polls sets
+// SPH_ERR_TIMEOUT, and the warp waits once more (bounded) for it and skips
+// its records.
+constexpr uint32_t kBulkPolls = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
 {
-    const uint64_t bx = (uint64_t)__double_as_longlong(x);
-    const uint64_t bo = (uint64_t)__double_as_longlong(o);
-    if (bo == 0u) return d2f_bits_rn(x);
-    const int ex = (int)(bx >> 52), eo = (int)(bo >> 52);      // sign bit included: negative -> > 0x7FF
-    const bool plain = ex >= 1 && ex <= 0x7FE && eo >= 1 && eo <= 0x7FE && ex - eo <= 1 && eo - ex <= 1;
-    if (plain) {
-        const int e = min(ex, eo);
-        const uint64_t hid = 1ull << 52, frac = hid - 1u;
-        const int64_t mx = (int64_t)(((bx & frac) | hid) << (ex - e));
-        const int64_t mo = (int64_t)(((bo & frac) | hid) << (eo - e));
-        const int64_t D = mx - mo;                               // x - o = D * 2^(e - 1075), exactly
-        if (D == 0) return 0.0f;
-        const uint32_t s = D < 0 ? 0x80000000u : 0u;
-        const uint64_t A = D < 0 ? (uint64_t)(-D) : (uint64_t)D;
-        const int msb = 63 - __clzll((long long)A);
-        int E = msb + e - 1075 + 127;                            // biased FP32 exponent
-        if (A < (1ull << 53) && E >= 1 && E <= 253) {
-            uint32_t m;
-            if (msb > 23) {
-                const int sh = msb - 23;
-                m = (uint32_t)(A >> sh);
-                const uint64_t rem = A & ((1ull << sh) - 1u);
-                const uint64_t half = 1ull << (sh - 1);
-                if (rem > half || (rem == half && (m & 1u))) {
-                    ++m;
-                    if (m == (1u << 24)) {
-                        m >>= 1;
-                        ++E;
-                    }
-                }
-            } else {
-                m = (uint32_t)(A << (23 - msb));
-            }
-            return __uint_as_float(s | ((uint32_t)E << 23) | (m & 0x7FFFFFu));
-        }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// arrive on `bar` and add `bytes` to the transaction count its phase waits for
+__device__ __forceinline__ void mbar_arrive_expect(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// global -> shared, `bytes` (a multiple of 16, both addresses 16-byte aligned)
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t polls)
+{
+    for (uint32_t i = 0; i < polls; ++i) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done)
+                     : "r"(smem_addr(bar)), "r"(parity)
+                     : "memory");
+        if (done) return true;
     }
-    return __double2float_rn(__dsub_rn(x, o));
+    return false;
+}
+
+// shared -> global from one lane, returning once the shared source has been
+// read (the global writes complete asynchronously, before the kernel ends)
+__device__ __forceinline__ void bulk_s2g_wait(void *dst, const void *src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(src)),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
+// What a kernel moves by bulk copies.
+struct BulkPlan {
+    int32_t load;                // load whole records, one copy per run
+    int32_t store;               // store whole records, one copy per run (after a whole-record load)
+};
+
+// The warp's records as runs of consecutive records.  Lane l starts a run
+// when it holds a record and lane l-1 holds none or not record o_l - 1; a run
+// ends at the next start or the next lane without a record.  Warp-uniform
+// fields; `len` (lanes in the run) is meaningful in start lanes only.
+struct WarpRuns {
+    int nvalid;                  // lanes holding a record
+    bool start;
+    int len;
+};
+
+__device__ __forceinline__ WarpRuns warp_runs(int64_t o, bool ok, int lane)
+{
+    WarpRuns w;
+    const int64_t prev = __shfl_up_sync(0xffffffffu, o, 1);
+    const unsigned valid = __ballot_sync(0xffffffffu, ok);
+    w.start = ok && (lane == 0 || !((valid >> (lane - 1)) & 1u) || prev + 1 != o);
+    const unsigned starts = __ballot_sync(0xffffffffu, w.start);
+    const unsigned after = ~((2u << lane) - 1u);                // lanes above this one (none for lane 31)
+    const unsigned stop = (starts | ~valid) & after;
+    w.len = (stop ? __ffs((int)stop) - 1 : 32) - lane;
+    w.nvalid = __popc(valid);
+    return w;
+}
+
+// Bulk-load the warp's record runs (rb bytes per record) into its image rec
+// (lane l's record at chunk l * U).  Every lane calls it; false after a
+// timeout (error bit set).
+__device__ __forceinline__ bool bulk_load_runs(const uint8_t *aos, int64_t o, const WarpRuns &w, int rb,
+                                               uint4 *rec, int U, uint64_t *bar, unsigned int *err, int lane)
+{
+    if (lane == 0) {
+        mbar_init(bar, 1);
+        mbar_arrive_expect(bar, (uint32_t)w.nvalid * (uint32_t)rb);
+    }
+    __syncwarp();
+    if (w.start) bulk_g2s(rec + lane * U, aos + o * rb, (uint32_t)w.len * (uint32_t)rb, bar);
+    if (__all_sync(0xffffffffu, mbar_wait(bar, 0, kBulkPolls))) return true;
+    if (lane == 0) {
+        atomicOr(err, (unsigned)SPH_ERR_TIMEOUT);
+        mbar_wait(bar, 0, kBulkPolls);
+    }
+    return false;
+}
+
+// Store the warp's record runs back from its image with one bulk copy per
+// run.  The image must hold every byte of those records.  Every lane calls it.
+__device__ __forceinline__ void bulk_store_runs(uint8_t *aos, int64_t o, const WarpRuns &w, int rb,
+                                                const uint4 *rec, int U, int lane)
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes -> async proxy
+    __syncwarp();
+    if (w.start) bulk_s2g_wait(aos + o * rb, rec + lane * U, (uint32_t)w.len * (uint32_t)rb);
+    __syncwarp();
+}
+
+// Host: the bulk plan of a kernel.  `can`: 16-byte chunks, records packed in
+// shared memory as in global memory (Up == U), device-resident records.
+// need: chunks a gather reads; written: 4-byte units a write-back writes
+// (null for a gather).  A gather loads whole records when it reads at least
+// 3/4 of each.  A write-back loads and stores whole records when its written
+// chunks make up at least 3/4 of the record: the sectors it leaves partly
+// written would be read from DRAM anyway, and below that share whole-record
+// stores move more bytes than partial stores.
+inline BulkPlan bulk_plan(bool can, int U, uint64_t need, const uint64_t *written)
+{
+    BulkPlan p;
+    std::memset(&p, 0, sizeof(p));
+    if (!can) return p;
+    const uint64_t all = U >= 64 ? ~0ull : (1ull << U) - 1ull;
+    const uint64_t mask = written ? chunks_of_units(written, 16) & all : need & all;
+    if (__builtin_popcountll(mask) * 4 < U * 3) return p;
+    p.load = 1;
+    p.store = written ? 1 : 0;
+    return p;
 }
 
 // Chunk size of a record layout: 16 bytes when the record size allows it.

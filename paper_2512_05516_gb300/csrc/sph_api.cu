@@ -158,6 +158,15 @@ sph_status sph_create(const sph_aos_layout *layout, const sph_params *params, in
     c->ncell_max = ncell_max;
     c->ws_flags = ws_flags;
     c->aos = (uint8_t *)d_aos;
+    if (d_aos) {
+        cudaPointerAttributes pa;
+        if (cudaPointerGetAttributes(&pa, d_aos) != cudaSuccess) {
+            cudaGetLastError();
+            delete c;
+            return SPH_EINVAL;
+        }
+        c->aos_device = pa.type == cudaMemoryTypeDevice;
+    }
     c->ws = (uint8_t *)d_workspace;
     c->ws_bytes = workspace_bytes;
     c->stream = (cudaStream_t)stream;
@@ -357,7 +366,7 @@ sph_status sph_get_stats(sph_ctx *c, sph_stats *out)
     out->nitems = d.nitems;
     out->max_occupancy = d.max_occ;
     out->launches = c->launches;
-    if (d.error_bits & (SPH_ERR_NONFINITE | SPH_ERR_OUTSIDE)) return SPH_ENUMERIC;
+    if (d.error_bits & (SPH_ERR_NONFINITE | SPH_ERR_OUTSIDE | SPH_ERR_TIMEOUT)) return SPH_ENUMERIC;
     return SPH_OK;
 }
 

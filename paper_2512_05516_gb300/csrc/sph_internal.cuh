@@ -247,6 +247,7 @@ struct sph_ctx {
     int64_t n = 0, ncell_max = 0;
     uint32_t ws_flags = 0;
     uint8_t *aos = nullptr;
+    bool aos_device = false;      // the records are in device memory (not host-mapped)
     uint8_t *ws = nullptr;
     size_t ws_bytes = 0;
     cudaStream_t stream = nullptr;
