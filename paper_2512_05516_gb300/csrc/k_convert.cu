@@ -116,6 +116,13 @@ __global__ void __launch_bounds__(kConvThreads, 12) k_soa_to_aos(ConvArgs a)
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool ok = k < a.n;
     const int64_t o = ok ? a.perm[k] : -1;
+    // the first SoA values are loaded before anything waits: they depend on
+    // neither the permutation nor the records
+    constexpr int W = 8;
+    float pre[W];
+#pragma unroll
+    for (int i = 0; i < W; ++i)
+        if (ok && i < a.ncomp) pre[i] = ld_val(a.comp[i].soa, a.comp[i].fmt, k);
     unsigned char *mine = reinterpret_cast<unsigned char *>(rec + lane * a.g.Up);
     const WarpRuns w = warp_runs(o, ok, lane);
     const bool bulk = sizeof(T) == 16 && a.bulk.store;
@@ -128,7 +135,12 @@ __global__ void __launch_bounds__(kConvThreads, 12) k_soa_to_aos(ConvArgs a)
     if (ok) {
         for (int i = 0; i < a.ncomp; ++i) {
             const Comp cp = a.comp[i];
-            const float v = ld_val(cp.soa, cp.fmt, k) * cp.scl;
+            float v = 0.0f;
+#pragma unroll
+            for (int j = 0; j < W; ++j)
+                if (j == i) v = pre[j];
+            if (i >= W) v = ld_val(cp.soa, cp.fmt, k);
+            v *= cp.scl;
             if (cp.kind == 1) *reinterpret_cast<float *>(mine + cp.off) = v;
             else *reinterpret_cast<double *>(mine + cp.off) = f2d_bits(v);
         }

@@ -265,11 +265,10 @@ __device__ __forceinline__ WarpRuns warp_runs(int64_t o, bool ok, int lane)
     return w;
 }
 
-// Bulk-load the warp's record runs (rb bytes per record) into its image rec
-// (lane l's record at chunk l * U).  Every lane calls it; false after a
-// timeout (error bit set).
-__device__ __forceinline__ bool bulk_load_runs(const uint8_t *aos, int64_t o, const WarpRuns &w, int rb,
-                                               uint4 *rec, int U, uint64_t *bar, unsigned int *err, int lane)
+// Start bulk loads of the warp's record runs (rb bytes per record) into its
+// image rec (lane l's record at chunk l * U).  Every lane calls it.
+__device__ __forceinline__ void bulk_issue_runs(const uint8_t *aos, int64_t o, const WarpRuns &w, int rb,
+                                                uint4 *rec, int U, uint64_t *bar, int lane)
 {
     if (lane == 0) {
         mbar_init(bar, 1);
@@ -277,12 +276,24 @@ __device__ __forceinline__ bool bulk_load_runs(const uint8_t *aos, int64_t o, co
     }
     __syncwarp();
     if (w.start) bulk_g2s(rec + lane * U, aos + o * rb, (uint32_t)w.len * (uint32_t)rb, bar);
+}
+
+// Wait for them; false after a timeout (error bit set).  Every lane calls it.
+__device__ __forceinline__ bool bulk_wait(uint64_t *bar, unsigned int *err, int lane)
+{
     if (__all_sync(0xffffffffu, mbar_wait(bar, 0, kBulkPolls))) return true;
     if (lane == 0) {
         atomicOr(err, (unsigned)SPH_ERR_TIMEOUT);
         mbar_wait(bar, 0, kBulkPolls);
     }
     return false;
+}
+
+__device__ __forceinline__ bool bulk_load_runs(const uint8_t *aos, int64_t o, const WarpRuns &w, int rb,
+                                               uint4 *rec, int U, uint64_t *bar, unsigned int *err, int lane)
+{
+    bulk_issue_runs(aos, o, w, rb, rec, U, bar, lane);
+    return bulk_wait(bar, err, lane);
 }
 
 // Store the warp's record runs back from its image with one bulk copy per
