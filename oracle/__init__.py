@@ -86,6 +86,11 @@ def _declare(L):
     L.orc_force.restype = None
     L.orc_force.argtypes = [_i64, _p, _p, _p, _p, _p, _p, _p, _p, _d, _d, _d, C.c_int,
                             _i64, _p, _p, _p, _p]
+    L.orc_buffer_density.restype = None
+    L.orc_buffer_density.argtypes = [_i64, _i32, _p, _p, _p, _p, _p, _d, _p, _p, _p, _p]
+    L.orc_buffer_force.restype = None
+    L.orc_buffer_force.argtypes = [_i64, _i32, _p, _p, _p, _p, _p, _p, _p, _p, _d, _d, _d,
+                                   _p, _p, _p]
     L.orc_kick_drift.restype = None
     L.orc_kick_drift.argtypes = [_i64, _p, _p, _p, _p, _p, _d, _d, _p]
     L.orc_ball_mark.restype = _i64
@@ -218,6 +223,47 @@ def kick_drift(x, v, a, u, dudt, dt_kick, dt_drift, box):
     lib().orc_kick_drift(x.shape[0], _ptr(x), _ptr(v), _ptr(_f64(a, (-1, 3))), _ptr(u),
                          _ptr(_f64(dudt)), float(dt_kick), float(dt_drift), _ptr(_f64(box)))
     return x, v, u
+
+
+# ---------------------------------------------------------------- buffers
+def buffer_density(x, m, h, u, box, gamma, B):
+    """Density over each particle's buffer of B consecutive particles (Section 6
+    benchmark grouping; Eq. 6, h fixed, self included) and the EOS."""
+    x = _f64(x, (-1, 3))
+    n = x.shape[0]
+    rho, P, c = np.zeros(n), np.zeros(n), np.zeros(n)
+    nngb = np.zeros(n, np.int32)
+    lib().orc_buffer_density(n, int(B), _ptr(x), _ptr(_f64(m)), _ptr(_f64(h)), _ptr(_f64(u)),
+                             _ptr(_f64(box)), float(gamma), _ptr(rho), _ptr(P), _ptr(c), _ptr(nngb))
+    return {"rho": rho, "P": P, "c": c, "nngb": nngb}
+
+
+def buffer_force(x, v, m, h, rho, P, c, box, alpha, beta, eps, B):
+    """Force over each particle's buffer of B consecutive particles (Eq. 7, Eq. 5)."""
+    x = _f64(x, (-1, 3))
+    n = x.shape[0]
+    a = np.zeros((n, 3))
+    dudt = np.zeros(n)
+    nngb = np.zeros(n, np.int32)
+    lib().orc_buffer_force(n, int(B), _ptr(x), _ptr(_f64(v, (-1, 3))), _ptr(_f64(m)), _ptr(_f64(h)),
+                           _ptr(_f64(rho)), _ptr(_f64(P)), _ptr(_f64(c)), _ptr(_f64(box)),
+                           float(alpha), float(beta), float(eps), _ptr(a), _ptr(dudt), _ptr(nngb))
+    return {"a": a, "dudt": dudt, "nngb": nngb}
+
+
+def buffer_relative(x, box, B, fmt="fp32", exp2=0):
+    """Positions as the library stores them in buffer mode: the offset from the
+    buffer's first particle, moved to the nearest periodic image (FP64: one
+    subtraction, then -L when >= L/2 or +L when < -L/2), rounded to `fmt`.
+    Returns (origins per particle, offsets as stored)."""
+    x = _f64(x, (-1, 3))
+    box = _f64(box)
+    n = x.shape[0]
+    origin = x[(np.arange(n) // B) * B]
+    d = x - origin
+    d = np.where(d >= 0.5 * box, d - box, np.where(d < -0.5 * box, d + box, d))
+    q, _ = quantize(d.ravel(), fmt, exp2)
+    return origin, q.reshape(d.shape)
 
 
 def ball_mark(x, box, radius, targets):

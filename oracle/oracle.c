@@ -362,6 +362,37 @@ void orc_eos(int64_t n, const double *rho, const double *u, double gamma,
 /* Symmetric hydro force with artificial viscosity (Eq. 7, Eq. 5; R7-R9)      */
 /* ------------------------------------------------------------------------- */
 
+/* one interacting pair (r2 > 0) of the force sums: adds particle j's terms to
+ * the acceleration acc[0..2] and du/dt of particle i; d = x_i - x_j */
+static void force_pair(int64_t i, int64_t j, const double *d, double r2, const double *v,
+                       const double *m, const double *h, const double *rho, const double *P,
+                       const double *c, double alpha, double beta, double eps, double *acc,
+                       double *du)
+{
+    const double Pi_rho2 = P[i] / (rho[i] * rho[i]);
+    double r = sqrt(r2);
+    double hb = 0.5 * (h[i] + h[j]);
+    double gw = orc_dWdr(r, hb) / r;  /* grad_i W = d * gw */
+    double vij[3] = { v[3 * i] - v[3 * j], v[3 * i + 1] - v[3 * j + 1],
+                      v[3 * i + 2] - v[3 * j + 2] };
+    double vdotr = vij[0] * d[0] + vij[1] * d[1] + vij[2] * d[2];
+    /* R8: Monaghan viscosity, only for approaching pairs */
+    double visc = 0.0;
+    if (vdotr < 0.0) {
+        double mu = hb * vdotr / (r2 + eps * hb * hb);
+        double cbar = 0.5 * (c[i] + c[j]);
+        double rhobar = 0.5 * (rho[i] + rho[j]);
+        visc = (-alpha * cbar * mu + beta * mu * mu) / rhobar;
+    }
+    double Pj_rho2 = P[j] / (rho[j] * rho[j]);
+    double fac = m[j] * (Pi_rho2 + Pj_rho2 + visc) * gw;
+    acc[0] -= fac * d[0];
+    acc[1] -= fac * d[1];
+    acc[2] -= fac * d[2];
+    /* Eq. 5: du/dt = (P_i/rho_i^2) sum_j m_j v_ij . grad W + 1/2 sum_j m_j Pi_ij v_ij . grad W */
+    *du += m[j] * (Pi_rho2 + 0.5 * visc) * (vdotr * gw);
+}
+
 void orc_force(int64_t n, const double *x, const double *v, const double *m,
                const double *h, const double *rho, const double *P, const double *c,
                const double *box, double alpha, double beta, double eps,
@@ -389,42 +420,83 @@ void orc_force(int64_t n, const double *x, const double *v, const double *m,
                 if (j != i && all.c[s].r2 < hs * hs) cbuf_push(&nb, j, all.c[s].d, all.c[s].r2);
             }
             qsort(nb.c, (size_t)nb.n, sizeof(cand_t), cmp_cand);
-            const double Pi_rho2 = P[i] / (rho[i] * rho[i]);
-            double ax = 0.0, ay = 0.0, az = 0.0, du = 0.0;
+            double acc[3] = {0.0, 0.0, 0.0}, du = 0.0;
             for (int64_t s = 0; s < nb.n; ++s) {
-                int64_t j = nb.c[s].j;
                 double r2 = nb.c[s].r2;
                 if (r2 == 0.0) continue;        /* coincident pair: grad W = 0 */
-                const double *d = nb.c[s].d;    /* x_i - x_j */
-                double r = sqrt(r2);
-                double hb = 0.5 * (h[i] + h[j]);
-                double gw = orc_dWdr(r, hb) / r;  /* grad_i W = d * gw */
-                double vij[3] = { v[3 * i] - v[3 * j], v[3 * i + 1] - v[3 * j + 1],
-                                  v[3 * i + 2] - v[3 * j + 2] };
-                double vdotr = vij[0] * d[0] + vij[1] * d[1] + vij[2] * d[2];
-                /* R8: Monaghan viscosity, only for approaching pairs */
-                double visc = 0.0;
-                if (vdotr < 0.0) {
-                    double mu = hb * vdotr / (r2 + eps * hb * hb);
-                    double cbar = 0.5 * (c[i] + c[j]);
-                    double rhobar = 0.5 * (rho[i] + rho[j]);
-                    visc = (-alpha * cbar * mu + beta * mu * mu) / rhobar;
-                }
-                double Pj_rho2 = P[j] / (rho[j] * rho[j]);
-                double fac = m[j] * (Pi_rho2 + Pj_rho2 + visc) * gw;
-                ax -= fac * d[0];
-                ay -= fac * d[1];
-                az -= fac * d[2];
-                /* Eq. 5: du/dt = (P_i/rho_i^2) sum_j m_j v_ij . grad W + 1/2 sum_j m_j Pi_ij v_ij . grad W */
-                du += m[j] * (Pi_rho2 + 0.5 * visc) * (vdotr * gw);
+                force_pair(i, nb.c[s].j, nb.c[s].d, r2, v, m, h, rho, P, c, alpha, beta, eps, acc, &du);
             }
-            a[3 * t + 0] = ax; a[3 * t + 1] = ay; a[3 * t + 2] = az;
+            a[3 * t + 0] = acc[0]; a[3 * t + 1] = acc[1]; a[3 * t + 2] = acc[2];
             dudt[t] = du;
             if (nngb) nngb[t] = (int32_t)nb.n;
         }
         free(all.c); free(nb.c);
     }
     if (use_grid) grid_free(&g);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Buffers of co-located particles (Section 6, the benchmark's grouping)      */
+/* ------------------------------------------------------------------------- */
+/* The paper's benchmark keeps particles in contiguous buffers of B spatially
+ * co-located particles and evaluates the quadratic kernels over every pair of
+ * a buffer (64 x 64 for B = 64).  Buffer b holds particles [bB, min((b+1)B, n));
+ * separations are minimum images; partners in ascending j.
+ * Density: Eq. 6 restricted to the buffer, self included, h fixed, then the
+ * EOS (R6).  Force: Eq. 7 and Eq. 5 restricted to the buffer, pairs
+ * r < h_i + h_j (R7-R9).  nngb counts partners j != i within the support. */
+
+void orc_buffer_density(int64_t n, int32_t B, const double *x, const double *m,
+                        const double *h, const double *u, const double *box, double gamma,
+                        double *rho, double *P, double *c, int32_t *nngb)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t j0 = (i / B) * B;
+        const int64_t j1 = j0 + B < n ? j0 + B : n;
+        double sr = 0.0;
+        int32_t k = 0;
+        for (int64_t j = j0; j < j1; ++j) {
+            double d[3];
+            min_image(x + 3 * i, x + 3 * j, box, d);
+            double r2 = norm2(d);
+            if (!(r2 < 4.0 * h[i] * h[i])) continue;
+            sr += m[j] * orc_W(sqrt(r2), h[i]);
+            if (j != i) ++k;
+        }
+        rho[i] = sr;
+        P[i] = (gamma - 1.0) * sr * u[i];
+        c[i] = sqrt(gamma * P[i] / sr);
+        if (nngb) nngb[i] = k;
+    }
+}
+
+void orc_buffer_force(int64_t n, int32_t B, const double *x, const double *v, const double *m,
+                      const double *h, const double *rho, const double *P, const double *c,
+                      const double *box, double alpha, double beta, double eps,
+                      double *a, double *dudt, int32_t *nngb)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t j0 = (i / B) * B;
+        const int64_t j1 = j0 + B < n ? j0 + B : n;
+        double acc[3] = {0.0, 0.0, 0.0}, du = 0.0;
+        int32_t k = 0;
+        for (int64_t j = j0; j < j1; ++j) {
+            if (j == i) continue;
+            double d[3];
+            min_image(x + 3 * i, x + 3 * j, box, d);
+            double r2 = norm2(d);
+            double hs = h[i] + h[j];
+            if (!(r2 < hs * hs)) continue;
+            ++k;
+            if (r2 == 0.0) continue;            /* coincident pair: grad W = 0 */
+            force_pair(i, j, d, r2, v, m, h, rho, P, c, alpha, beta, eps, acc, &du);
+        }
+        a[3 * i + 0] = acc[0]; a[3 * i + 1] = acc[1]; a[3 * i + 2] = acc[2];
+        dudt[i] = du;
+        if (nngb) nngb[i] = k;
+    }
 }
 
 /* ------------------------------------------------------------------------- */

@@ -65,6 +65,16 @@ void orc_force(int64_t n, const double *x, const double *v, const double *m,
                int brute, int64_t ntarget, const int64_t *targets,
                double *a, double *dudt, int32_t *nngb);
 
+/* ---- buffers of B co-located particles (Section 6 benchmark): every pair of
+ *      a buffer; density (h fixed, self included) + EOS, and force ---- */
+void orc_buffer_density(int64_t n, int32_t B, const double *x, const double *m,
+                        const double *h, const double *u, const double *box, double gamma,
+                        double *rho, double *P, double *c, int32_t *nngb);
+void orc_buffer_force(int64_t n, int32_t B, const double *x, const double *v, const double *m,
+                      const double *h, const double *rho, const double *P, const double *c,
+                      const double *box, double alpha, double beta, double eps,
+                      double *a, double *dudt, int32_t *nngb);
+
 /* ---- kick/drift (symplectic Euler, periodic wrap) ---- */
 void orc_kick_drift(int64_t n, double *x, double *v, const double *a, double *u,
                     const double *dudt, double dt_kick, double dt_drift,

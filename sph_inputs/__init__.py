@@ -19,6 +19,8 @@ follows one workload description:
 * ``gaussian_mixture`` 8 isotropic Gaussians plus a 20% uniform background,
   one global h with 48 neighbours on average.
 * ``long_run``         large jittered lattice with random velocities.
+* ``buffer_blocks``    the paper's benchmark grouping: blocks of 4x4x4 (B = 64)
+  jittered lattice particles, each block a contiguous buffer of records.
 
 Record layout (the default 112-byte FP64 record): x[3]@0, v[3]@24, a[3]@48,
 m@72, h@80, rho@88, u@96, P@104.  The number of neighbours 48 enters only
@@ -263,6 +265,46 @@ def long_run(nx: int = 512, ny: int = 256, nz: int = 256, seed: int = SEED_BASE 
     cell = 1.0 / ncell
     return Workload("long_run", aos, box, h_cap=0.5 * cell, cell_edge=cell,
                     newton_steps=0, meta={"m": m, "h0": h0})
+
+
+def buffer_blocks(nb=(16, 16, 16), block=(4, 4, 4), seed: int = SEED_BASE + 7,
+                  jitter: float = 0.3) -> Workload:
+    """Particles in contiguous buffers of B = bx*by*bz spatially co-located
+    particles, the grouping of the paper's benchmark (Section 6; B = 64 for
+    4x4x4 blocks).  A jittered cubic lattice of spacing s = 1/(nb_x bx) fills
+    the box (1, nb_y by s, nb_z bz s); it is cut into blocks of bx x by x bz
+    sites, and the records run block after block (x-fastest block order), a
+    block's sites consecutive (x fastest).  Density 1 (m = s^3), h = eta s
+    (48 neighbours in the full lattice) times a uniform factor in [0.9, 1.1],
+    velocities uniform in [-1, 1]^3, u uniform in [0.5, 2], rho = 1 and P the
+    ideal-gas pressure at rho = 1, so the force can run without a density
+    pass.  meta["B"] is the buffer size."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    nbx, nby, nbz = (int(v) for v in nb)
+    bx, by, bz = (int(v) for v in block)
+    B = bx * by * bz
+    s = 1.0 / (nbx * bx)
+    box = (nbx * bx * s, nby * by * s, nbz * bz * s)
+    site = _lattice(bx, by, bz, s, (0.0, 0.0, 0.0), rng, 0.0)           # one block, x fastest
+    corner = _lattice(nbx, nby, nbz, 1.0, (0.0, 0.0, 0.0), rng, 0.0) - 0.5   # block indices
+    corner *= np.array([bx * s, by * s, bz * s])
+    pos = (corner[:, None, :] + site[None, :, :]).reshape(-1, 3)
+    pos += rng.uniform(-jitter * s, jitter * s, size=pos.shape)
+    pos = _wrap(pos, box)
+    n = pos.shape[0]
+    aos = _empty(n)
+    _set(aos, "x", pos)
+    _set(aos, "v", rng.uniform(-1.0, 1.0, size=(n, 3)))
+    _set(aos, "m", s ** 3)
+    h0 = ETA * s
+    _set(aos, "h", h0 * rng.uniform(0.9, 1.1, size=n))
+    _set(aos, "rho", 1.0)
+    u = rng.uniform(0.5, 2.0, size=n)
+    _set(aos, "u", u)
+    gamma = 5.0 / 3.0
+    _set(aos, "P", (gamma - 1.0) * u)
+    return Workload("buffer_blocks", aos, box, gamma=gamma, h_cap=1.25 * h0, newton_steps=0,
+                    meta={"B": B, "spacing": s, "h0": h0})
 
 
 def random_cloud(n: int, seed: int, box=(1.0, 1.0, 1.0), h: float | None = None,
