@@ -9,7 +9,9 @@
  *   C   AoS -> SoA layout change                    -> sph_aos_to_soa
  *   U   unpack reduced precision / U^T pack         -> per-field `prec`
  *   f   the compute kernel                          -> sph_density, sph_force,
- *                                                      sph_kick_drift
+ *                                                      sph_kick_drift (cell
+ *                                                      lists) or sph_buffer_*
+ *                                                      (the paper's buffers)
  *   C^T N^T U^T  widen and scatter back to the AoS  -> sph_soa_to_aos (or fused
  *                                                      with the kick/drift:
  *                                                      sph_kick_drift_writeback)
@@ -307,10 +309,69 @@ sph_status sph_kick_drift(sph_ctx *ctx, double dt_kick, double dt_drift);
 
 /* S7, C^T o N^T o U^T (Section 4, the write-back epilogue): widen the SoA
  * fields in `fields` to the AoS element type and scatter them to their
- * records.  Positions are not written (the AoS keeps them in FP64; drift
- * updates them in place).  Errors: SPH_EINVAL (X requested or field absent
- * from the layout), SPH_ESTATE (field not current), SPH_ECUDA. */
+ * records.  Positions are not written after sph_bin_cells (the AoS keeps
+ * them in FP64; drift updates them in place).  After sph_bin_buffers they
+ * may be: x = buffer origin + offset in FP64, wrapped into [0, box).
+ * Errors: SPH_EINVAL (X requested after sph_bin_cells, or field absent from
+ * the layout), SPH_ESTATE (field not current), SPH_ECUDA. */
 sph_status sph_soa_to_aos(sph_ctx *ctx, uint32_t fields);
+
+/* ---- Buffer kernels: the paper's benchmark grouping (Section 6) ----------
+ * The paper keeps particles in contiguous buffers of 64 spatially co-located
+ * particles; its quadratic kernels Density and Force evaluate every pair of
+ * a buffer (64 x 64), its linear kernels Kick and Drift every particle once,
+ * and it times them reading the AoS directly against reading the converted
+ * SoA (Fig. 2).  These calls run the four kernels on such buffers, reading
+ * either layout:
+ *   source = SPH_SRC_AOS: the records directly (strided; positions made
+ *            relative to the buffer origin inside the kernel); outputs go to
+ *            the records, and their SoA copies become stale;
+ *   source = SPH_SRC_SOA: the SoA arrays sph_aos_to_soa wrote (inputs must
+ *            be current); outputs go to the SoA arrays in their storage
+ *            formats, and the records keep their old values until
+ *            sph_soa_to_aos.
+ * Arithmetic is FP32 in both (the AoS drift is FP64). */
+#define SPH_SRC_AOS 0
+#define SPH_SRC_SOA 1
+#define SPH_BUFFER_MIN 32
+#define SPH_BUFFER_MAX 256
+
+/* Switch the context to buffers: buffer b holds records
+ * [b buffer_size, min((b+1) buffer_size, n)); buffer_size is a power of two
+ * in [SPH_BUFFER_MIN, SPH_BUFFER_MAX] (the paper uses 64).  The caller groups
+ * co-located particles into consecutive records; nothing is sorted (slot k is
+ * record k).  Each buffer's origin is the position of its first record; SoA
+ * positions (sph_aos_to_soa of X) are then offsets from it, moved to the
+ * nearest periodic image (FP64 difference, -box when >= box/2, +box when
+ * < -box/2), rounded to the storage format.  Invalidates every SoA field;
+ * sph_density and sph_force need sph_bin_cells again (SPH_ESTATE before).
+ * Errors: SPH_EINVAL (buffer_size), SPH_ECUDA. */
+sph_status sph_bin_buffers(sph_ctx *ctx, int32_t buffer_size);
+
+/* Density over the buffer, h fixed: rho_i = sum_j m_j W(r_ij, h_i) over the
+ * particles j of i's buffer, self included (Eq. 6 restricted to the buffer),
+ * then P = (gamma - 1) rho u and c = sqrt(gamma P / rho).  Reads X, M, H, U;
+ * writes RHO, P and CS (CS in the records only when the layout has it).
+ * pairs_density counts the pairs j != i with r < 2 h_i.  Errors: SPH_EINVAL
+ * (source, or with SPH_SRC_AOS a field absent from the layout), SPH_ESTATE
+ * (not in buffer mode, or SoA inputs not current), SPH_ECUDA. */
+sph_status sph_buffer_density(sph_ctx *ctx, int32_t source);
+
+/* Force over the buffer: the symmetric pair force with Monaghan viscosity
+ * (Eq. 7, Eq. 5) over the pairs j != i of i's buffer with r < h_i + h_j,
+ * c = sqrt(gamma P / rho).  Reads X, V, M, H, RHO, P; writes A and DUDT
+ * (FP32 in the SoA).  pairs_force counts the pairs.  Errors as
+ * sph_buffer_density. */
+sph_status sph_buffer_force(sph_ctx *ctx, int32_t source);
+
+/* Kick: v += a dt, u += du/dt dt (FP32).  Reads V, A, U, DUDT; writes V, U.
+ * Errors as sph_buffer_density, and SPH_EINVAL for a non-finite dt. */
+sph_status sph_buffer_kick(sph_ctx *ctx, int32_t source, double dt);
+
+/* Drift: x += v dt.  SPH_SRC_AOS: FP64 in the records, wrapped into
+ * [0, box).  SPH_SRC_SOA: the FP32 offsets from the buffer origin (wrapped
+ * when written back).  Reads X, V; writes X.  Errors as sph_buffer_kick. */
+sph_status sph_buffer_drift(sph_ctx *ctx, int32_t source, double dt);
 
 /* S6 + S7 in one pass over the records: the same results in the AoS as
  * sph_kick_drift(dt_kick, dt_drift) followed by sph_soa_to_aos(fields) --

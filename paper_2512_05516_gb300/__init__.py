@@ -17,7 +17,8 @@ from ._capi import (AOS_F32, AOS_F64, BIT, ERR_HCAP, ERR_NEWTON, ERR_NONFINITE, 
                     F_A, F_CS, F_DUDT, F_H, F_M, F_P, F_RHO, F_U, F_V, F_X, FIELD_NAMES,
                     FIELDS_DENSITY, FIELDS_FORCE, FIELDS_KICK, FIELDS_OUTPUT, FLAG_PLAIN_SUM,
                     NCOMP, P_BF16, P_FP16, P_FP32, P_FP32_M10, P_FP32_M16, PREC, SPH_NFIELDS,
-                    WS_REORDER, sph_aos_layout, sph_desc, sph_params, sph_stats, sph_tuning)
+                    BUFFER_MAX, BUFFER_MIN, SRC_AOS, SRC_SOA, WS_REORDER, sph_aos_layout, sph_desc,
+                    sph_params, sph_stats, sph_tuning)
 
 _lib = _capi.load()
 
@@ -80,6 +81,26 @@ def sph_soa_to_aos(ctx, fields: int) -> int:
 
 def sph_kick_drift_writeback(ctx, dt_kick: float, dt_drift: float, fields: int) -> int:
     return _lib.sph_kick_drift_writeback(ctx, float(dt_kick), float(dt_drift), fields)
+
+
+def sph_bin_buffers(ctx, buffer_size: int) -> int:
+    return _lib.sph_bin_buffers(ctx, int(buffer_size))
+
+
+def sph_buffer_density(ctx, source: int) -> int:
+    return _lib.sph_buffer_density(ctx, int(source))
+
+
+def sph_buffer_force(ctx, source: int) -> int:
+    return _lib.sph_buffer_force(ctx, int(source))
+
+
+def sph_buffer_kick(ctx, source: int, dt: float) -> int:
+    return _lib.sph_buffer_kick(ctx, int(source), float(dt))
+
+
+def sph_buffer_drift(ctx, source: int, dt: float) -> int:
+    return _lib.sph_buffer_drift(ctx, int(source), float(dt))
 
 
 def sph_set_field_scale(ctx, exp2) -> int:
@@ -171,6 +192,19 @@ def make_layout(offsets: dict, record_bytes: int, f32_fields=()) -> sph_aos_layo
 def layout_112() -> sph_aos_layout:
     """The 112-byte FP64 record {x[3], v[3], a[3], m, h, rho, u, P}."""
     return make_layout(RECORD_112, 112)
+
+
+#: the paper's single-precision benchmark record (Section 6): a 64-bit ID and
+#: FP64 positions, every other field FP32, 144 bytes in all (bytes 84..143
+#: stand for the record's further fields, which no kernel here touches)
+RECORD_144 = {"x": 8, "v": 32, "a": 44, "m": 56, "h": 60, "rho": 64, "u": 68, "P": 72, "cs": 76,
+              "dudt": 80}
+F32_144 = ("v", "a", "m", "h", "rho", "u", "P", "cs", "dudt")
+
+
+def layout_144() -> sph_aos_layout:
+    """The 144-byte record of the paper's benchmark: ID, FP64 x, FP32 fields."""
+    return make_layout(RECORD_144, 144, F32_144)
 
 
 def make_params(box, gamma=5.0 / 3.0, alpha=1.0, beta=2.0, eps=0.01, eta=1.1272516517868265,
@@ -292,6 +326,28 @@ class Sph:
 
     def kick_drift_writeback(self, dt_kick: float, dt_drift: float, fields: int = FIELDS_OUTPUT):
         _check(sph_kick_drift_writeback(self.ctx, dt_kick, dt_drift, fields), "sph_kick_drift_writeback")
+
+    # ---- buffer kernels (the paper's 64-particle buffers, Section 6)
+    @staticmethod
+    def _source(source) -> int:
+        if isinstance(source, str):
+            return {"aos": SRC_AOS, "soa": SRC_SOA}[source]
+        return int(source)
+
+    def bin_buffers(self, buffer_size: int = 64):
+        _check(sph_bin_buffers(self.ctx, buffer_size), "sph_bin_buffers")
+
+    def buffer_density(self, source="soa"):
+        _check(sph_buffer_density(self.ctx, self._source(source)), "sph_buffer_density")
+
+    def buffer_force(self, source="soa"):
+        _check(sph_buffer_force(self.ctx, self._source(source)), "sph_buffer_force")
+
+    def buffer_kick(self, dt: float, source="soa"):
+        _check(sph_buffer_kick(self.ctx, self._source(source), dt), "sph_buffer_kick")
+
+    def buffer_drift(self, dt: float, source="soa"):
+        _check(sph_buffer_drift(self.ctx, self._source(source), dt), "sph_buffer_drift")
 
     def step(self, dt: float, newton_steps: int = 5, prec=None, cell_edge: float = 0.0,
              reorder: bool = False, out_fields: int = FIELDS_OUTPUT):

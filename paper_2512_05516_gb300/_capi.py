@@ -34,6 +34,8 @@ AOS_F64, AOS_F32 = 0, 1
 FLAG_PLAIN_SUM = 1
 WS_REORDER = 1
 ERR_NONFINITE, ERR_OUTSIDE, ERR_HCAP, ERR_NEWTON, ERR_TIMEOUT = 1, 2, 4, 8, 16
+SRC_AOS, SRC_SOA = 0, 1
+BUFFER_MIN, BUFFER_MAX = 32, 256
 
 OK, EINVAL, ENOSPACE, ECUDA, ESTATE, ECAPACITY, ETIMEOUT, ENUMERIC = 0, -1, -2, -3, -4, -5, -6, -7
 
@@ -95,6 +97,11 @@ PROTOTYPES = {
     "sph_aos_download": (C.c_int, [_P, _P, C.c_size_t]),
     "sph_bin_cells_noalloc": (C.c_int, [_P, C.POINTER(sph_aos_layout), C.c_int64, C.POINTER(C.c_double),
                                         C.POINTER(C.c_int32), _P, _P, _P, _P]),
+    "sph_bin_buffers": (C.c_int, [_P, C.c_int32]),
+    "sph_buffer_density": (C.c_int, [_P, C.c_int32]),
+    "sph_buffer_force": (C.c_int, [_P, C.c_int32]),
+    "sph_buffer_kick": (C.c_int, [_P, C.c_int32, C.c_double]),
+    "sph_buffer_drift": (C.c_int, [_P, C.c_int32, C.c_double]),
     "sph_destroy": (None, [_P]),
     "sph_status_str": (C.c_char_p, [C.c_int]),
 }

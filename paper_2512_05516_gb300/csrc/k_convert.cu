@@ -46,6 +46,10 @@ struct ConvArgs {
     uint64_t m_nc0, m_nc1;       // magic divisors for nc_x, nc_y
     int32_t nc0, nc1;
     const double *origin[3];     // cell origin k * (L / nc) per axis
+    const double *bufo;          // buffer mode: buffer origins, 3 x nbuf, axis-major (else null)
+    int64_t nbuf;
+    int32_t lgB;                 // buffer size 2^lgB
+    double box[3];
     bool has_x;
     BulkPlan bulk;               // bulk copies of consecutive record blocks
     int32_t rb;                  // record bytes
@@ -65,7 +69,13 @@ __global__ void __launch_bounds__(kConvThreads, 12) k_aos_to_soa(ConvArgs a)
     const bool ok = k < a.n;
     const int64_t o = ok ? a.perm[k] : -1;
     double org0 = 0.0, org1 = 0.0, org2 = 0.0;
-    if (a.has_x && ok) {
+    if (a.has_x && ok && a.bufo) {
+        // buffer mode: slot k is record k, in buffer k / B
+        const int64_t b = k >> a.lgB;
+        org0 = __ldg(a.bufo + b);
+        org1 = __ldg(a.bufo + a.nbuf + b);
+        org2 = __ldg(a.bufo + 2 * a.nbuf + b);
+    } else if (a.has_x && ok) {
         // the cell's coordinates from its key, then its origin (tables)
         const uint32_t cell = (uint32_t)a.slot_cell[k] >> a.lg_s3;
         const uint32_t t = div_magic(cell, a.m_nc0);
@@ -96,7 +106,7 @@ __global__ void __launch_bounds__(kConvThreads, 12) k_aos_to_soa(ConvArgs a)
                 const double d = *reinterpret_cast<const double *>(mine + cp.off);
                 if (cp.kind >= 2) {
                     const double og = cp.kind == 2 ? org0 : (cp.kind == 3 ? org1 : org2);
-                    v = cell_offset_f32(d, og);
+                    v = a.bufo ? buffer_offset_f32(d, og, a.box[cp.kind - 2]) : cell_offset_f32(d, og);
                 } else {
                     v = d2f_bits_rn(d);
                 }
@@ -106,7 +116,8 @@ __global__ void __launch_bounds__(kConvThreads, 12) k_aos_to_soa(ConvArgs a)
     }
 }
 
-template <typename T>
+// kPos: positions are among the fields (buffer mode only)
+template <typename T, bool kPos>
 __global__ void __launch_bounds__(kConvThreads, 12) k_soa_to_aos(ConvArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -141,8 +152,21 @@ __global__ void __launch_bounds__(kConvThreads, 12) k_soa_to_aos(ConvArgs a)
                 if (j == i) v = pre[j];
             if (i >= W) v = ld_val(cp.soa, cp.fmt, k);
             v *= cp.scl;
-            if (cp.kind == 1) *reinterpret_cast<float *>(mine + cp.off) = v;
-            else *reinterpret_cast<double *>(mine + cp.off) = f2d_bits(v);
+            if (cp.kind == 1) {
+                *reinterpret_cast<float *>(mine + cp.off) = v;
+            } else if (kPos && cp.kind >= 2) {
+                // buffer mode: position = buffer origin + offset, wrapped into [0, L)
+                const int ax = cp.kind - 2;
+                const double L = a.box[ax];
+                double y = __dadd_rn(__ldg(a.bufo + ax * a.nbuf + (k >> a.lgB)), f2d_bits(v));
+                if (y < 0.0 || y >= L) {
+                    y = __dsub_rn(y, __dmul_rn(L, floor(y / L)));
+                    if (y >= L) y = 0.0;                         // rounding onto L
+                }
+                *reinterpret_cast<double *>(mine + cp.off) = y;
+            } else {
+                *reinterpret_cast<double *>(mine + cp.off) = f2d_bits(v);
+            }
         }
     }
     if (bulk) bulk_store_runs(a.aos, o, w, a.rb, img, a.g.U, lane);
@@ -172,6 +196,12 @@ ConvArgs make_args(sph_ctx *c, uint32_t fields, bool to_soa)
     a.m_nc0 = magic64((uint32_t)c->nc[0]);
     a.m_nc1 = magic64((uint32_t)c->nc[1]);
     for (int d = 0; d < 3; ++d) a.origin[d] = c->origin + d * kMaxCellsPerAxis;
+    for (int d = 0; d < 3; ++d) a.box[d] = c->params.box[d];
+    if (c->buffer) {
+        a.bufo = c->buf_origin;
+        a.lgB = 31 - __builtin_clz((unsigned)c->buffer);
+        a.nbuf = (c->n + c->buffer - 1) / c->buffer;
+    }
     a.has_x = false;
     a.ncomp = 0;
     uint64_t cmask = 0;
@@ -207,7 +237,7 @@ cudaError_t launch_conv(sph_ctx *c, const ConvArgs &a, bool to_soa)
 {
     const size_t smem = (size_t)(kConvThreads / 32) * 32 * a.g.Up * sizeof(T) + (kConvThreads / 32) * sizeof(uint64_t);
     cudaError_t e;
-    auto kern = to_soa ? k_aos_to_soa<T> : k_soa_to_aos<T>;
+    auto kern = to_soa ? k_aos_to_soa<T> : (a.has_x ? k_soa_to_aos<T, true> : k_soa_to_aos<T, false>);
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return e;
     kern<<<blocks_for(c->n, kConvThreads), kConvThreads, smem, c->stream>>>(a);

@@ -1,0 +1,66 @@
+// Per-pair arithmetic of the SPH kernels, in FP32: the M4 spline (support
+// 2h, sigma = 1/pi in 3D), compensated accumulation and one symmetric force
+// pair with Monaghan viscosity (Eq. 7, Eq. 5).  Shared by the cell-list pair
+// kernels (k_pairs.cu) and the buffer kernels (k_buffers.cu).
+#pragma once
+
+#include "sph_internal.cuh"
+
+namespace sph {
+
+// M4 spline w(q) and w'(q), branch-free, for any q >= 0: with
+// t = max(2 - q, 0) and u = max(1 - q, 0),
+//   w = t^3 / 4 - u^3,   w' = -3 t^2 / 4 + 3 u^2,
+// which is 1 - 3q^2/2 + 3q^3/4 on [0, 1), (2 - q)^3 / 4 on [1, 2) and 0 beyond.
+__device__ __forceinline__ void spline(float q, float &w, float &dw)
+{
+    const float t = fmaxf(2.0f - q, 0.0f);
+    const float u = fmaxf(1.0f - q, 0.0f);
+    const float t2 = t * t, u2 = u * u;
+    w = fmaf(0.25f * t2, t, -(u2 * u));
+    dw = fmaf(3.0f, u2, -0.75f * t2);
+}
+
+// Kahan compensated accumulation: s - c carries the running sum; c holds the
+// low-order part lost by the last addition (the terms are non-negative)
+__device__ __forceinline__ void kahan_add(float &s, float &c, float x)
+{
+    const float y = __fsub_rn(x, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+}
+
+// One interacting force pair (r2 > 0, j != i): separation d = x_i - x_j,
+// hs = h_i + h_j, qb = (v_j, m_j), qc = (P_j / rho_j^2, rho_j, c_j, -).
+__device__ __forceinline__ void force_pair(float &ax, float &ay, float &az, float &du, float vxi, float vyi,
+                                           float vzi, float rhoi, float Pr2i, float ci, float dx, float dy,
+                                           float dz, float r2, float hs, const float4 qb, const float4 qc,
+                                           float alpha, float beta, float eps)
+{
+    const float rinv = rsqrtf(r2);
+    const float r = r2 * rinv;
+    const float hb = 0.5f * hs;
+    const float hbinv = 2.0f / hs;
+    const float qq = r * hbinv;
+    float w, dw;
+    spline(qq, w, dw);
+    const float hb2 = hbinv * hbinv;
+    const float gw = kSigma * hb2 * hb2 * dw * rinv;   // grad_i W = d * gw
+    const float vx = vxi - qb.x, vy = vyi - qb.y, vz = vzi - qb.z;
+    const float vdotr = fmaf(vx, dx, fmaf(vy, dy, vz * dz));
+    float visc = 0.0f;
+    if (vdotr < 0.0f) {
+        const float mu = hb * vdotr / fmaf(eps * hb, hb, r2);
+        const float cbar = 0.5f * (ci + qc.z);
+        const float rbar = 0.5f * (rhoi + qc.y);
+        visc = fmaf(-alpha * cbar, mu, beta * mu * mu) / rbar;
+    }
+    const float fac = qb.w * (Pr2i + qc.x + visc) * gw;
+    ax = fmaf(-fac, dx, ax);
+    ay = fmaf(-fac, dy, ay);
+    az = fmaf(-fac, dz, az);
+    du = fmaf(qb.w * fmaf(0.5f, visc, Pr2i), vdotr * gw, du);
+}
+
+}  // namespace sph

@@ -29,7 +29,7 @@
 // Summation order: every lane accumulates its pairs in staged order
 // (stencil cell, sub-cell, slot), whatever the chunking, list or launch
 // shape, so results do not depend on the tuning.
-#include "sph_internal.cuh"
+#include "k_pair_math.cuh"
 
 namespace sph {
 cudaError_t run_pack(sph_ctx *c, const float *src, int f);
@@ -258,29 +258,6 @@ __device__ __forceinline__ int advance(const Tab &tab, int nk, int e, int g)
 {
     while (e < nk - 1 && tab.incl[e] <= g) ++e;
     return e;
-}
-
-// M4 spline w(q) and w'(q), branch-free, for any q >= 0: with
-// t = max(2 - q, 0) and u = max(1 - q, 0),
-//   w = t^3 / 4 - u^3,   w' = -3 t^2 / 4 + 3 u^2,
-// which is 1 - 3q^2/2 + 3q^3/4 on [0, 1), (2 - q)^3 / 4 on [1, 2) and 0 beyond.
-__device__ __forceinline__ void spline(float q, float &w, float &dw)
-{
-    const float t = fmaxf(2.0f - q, 0.0f);
-    const float u = fmaxf(1.0f - q, 0.0f);
-    const float t2 = t * t, u2 = u * u;
-    w = fmaf(0.25f * t2, t, -(u2 * u));
-    dw = fmaf(3.0f, u2, -0.75f * t2);
-}
-
-// Kahan compensated accumulation: s - c carries the running sum; c holds the
-// low-order part lost by the last addition (the terms are non-negative)
-__device__ __forceinline__ void kahan_add(float &s, float &c, float x)
-{
-    const float y = __fsub_rn(x, c);
-    const float t = __fadd_rn(s, y);
-    c = __fsub_rn(__fsub_rn(t, s), y);
-    s = t;
 }
 
 // ---------------------------------------------------------------------------
@@ -599,38 +576,6 @@ __global__ void __launch_bounds__(256) k_force_pack(ForceArgs a, const int32_t *
     const unsigned mx = __reduce_max_sync(peers, __float_as_uint(hv));
     if (ok && (threadIdx.x & 31) == __ffs(peers) - 1)
         atomicMax(reinterpret_cast<unsigned *>(key_hmax) + key, mx);
-}
-
-// One interacting force pair (r2 > 0, j != i): separation d = x_i - x_j,
-// hs = h_i + h_j, qb = (v_j, m_j), qc = (P_j / rho_j^2, rho_j, c_j, -).
-__device__ __forceinline__ void force_pair(float &ax, float &ay, float &az, float &du, float vxi, float vyi,
-                                           float vzi, float rhoi, float Pr2i, float ci, float dx, float dy,
-                                           float dz, float r2, float hs, const float4 qb, const float4 qc,
-                                           float alpha, float beta, float eps)
-{
-    const float rinv = rsqrtf(r2);
-    const float r = r2 * rinv;
-    const float hb = 0.5f * hs;
-    const float hbinv = 2.0f / hs;
-    const float qq = r * hbinv;
-    float w, dw;
-    spline(qq, w, dw);
-    const float hb2 = hbinv * hbinv;
-    const float gw = kSigma * hb2 * hb2 * dw * rinv;   // grad_i W = d * gw
-    const float vx = vxi - qb.x, vy = vyi - qb.y, vz = vzi - qb.z;
-    const float vdotr = fmaf(vx, dx, fmaf(vy, dy, vz * dz));
-    float visc = 0.0f;
-    if (vdotr < 0.0f) {
-        const float mu = hb * vdotr / fmaf(eps * hb, hb, r2);
-        const float cbar = 0.5f * (ci + qc.z);
-        const float rbar = 0.5f * (rhoi + qc.y);
-        visc = fmaf(-alpha * cbar, mu, beta * mu * mu) / rbar;
-    }
-    const float fac = qb.w * (Pr2i + qc.x + visc) * gw;
-    ax = fmaf(-fac, dx, ax);
-    ay = fmaf(-fac, dy, ay);
-    az = fmaf(-fac, dz, az);
-    du = fmaf(qb.w * fmaf(0.5f, visc, Pr2i), vdotr * gw, du);
 }
 
 // Stage the force candidates (those within h_max(warp) + h_j of the warp box)

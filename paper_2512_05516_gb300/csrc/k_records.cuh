@@ -172,6 +172,17 @@ __device__ __forceinline__ void store_chunks(T *__restrict__ aos, const T *rec, 
 // frame the result is the FP64 difference rounded to FP32.
 __device__ __forceinline__ float cell_offset_f32(double x, double o) { return d2f_bits_rn(__dsub_rn(x, o)); }
 
+// x - o moved to the nearest periodic image, rounded once to FP32: positions
+// relative to a buffer's first particle.  FP64: the difference, then - L when
+// it is >= L/2 or + L when it is < -L/2.
+__device__ __forceinline__ float buffer_offset_f32(double x, double o, double L)
+{
+    double d = __dsub_rn(x, o);
+    if (d >= 0.5 * L) d = __dsub_rn(d, L);
+    else if (d < -0.5 * L) d = __dadd_rn(d, L);
+    return d2f_bits_rn(d);
+}
+
 // ---------------------------------------------------------------------------
 // Bulk asynchronous copies (the non-tensor form of TMA) of record runs.
 // In cell-ordered records (the usual case once they have been reordered) a

@@ -107,6 +107,7 @@ bool make_plan(const sph_aos_layout &L, int64_t n, int64_t ncell_max, uint32_t w
     p->key_hmax = take(4 * (size_t)nkeys);
     p->origin = take(sizeof(double) * 3 * kMaxCellsPerAxis);
     p->pack = take(3 * 16 * N);
+    p->buf_origin = take(sizeof(double) * 3 * (N / 32 + 1));    // buffers of >= 32 records
     p->aos_tmp = (ws_flags & SPH_WS_REORDER) ? take((size_t)L.record_bytes * N) : 0;
     p->stats = take(sizeof(DevStats));
     for (int f = 0; f < SPH_NFIELDS; ++f)
@@ -197,6 +198,7 @@ sph_status sph_create(const sph_aos_layout *layout, const sph_params *params, in
     c->key_hmax = (float *)(w + plan.key_hmax);
     c->origin = (double *)(w + plan.origin);
     c->pack = (float4 *)(w + plan.pack);
+    c->buf_origin = (double *)(w + plan.buf_origin);
     c->aos_tmp = (ws_flags & SPH_WS_REORDER) ? w + plan.aos_tmp : nullptr;
     c->dstats = (DevStats *)(w + plan.stats);
     for (int f = 0; f < SPH_NFIELDS; ++f) {
@@ -236,6 +238,7 @@ sph_status sph_bin_cells(sph_ctx *c, double cell_edge, int32_t reorder_aos)
     c->sub = c->tuning.subcells;
     c->valid = 0;
     c->binned = false;
+    c->buffer = 0;
     if (run_binning(c, reorder_aos ? 1 : 0) != cudaSuccess) return SPH_ECUDA;
     if (run_items(c) != cudaSuccess) return SPH_ECUDA;
     c->binned = true;
@@ -284,7 +287,7 @@ sph_status sph_get_field_scale(const sph_ctx *c, int32_t *exp2_out)
 sph_status sph_density(sph_ctx *c, int32_t newton_steps)
 {
     if (!c || newton_steps < 0 || newton_steps > 32) return SPH_EINVAL;
-    if (!c->binned) return SPH_ESTATE;
+    if (!c->binned || c->buffer) return SPH_ESTATE;
     const uint32_t need = SPH_BIT(SPH_F_X) | SPH_BIT(SPH_F_M) | SPH_BIT(SPH_F_H);
     if ((c->valid & need) != need) return SPH_ESTATE;
     // outputs keep their current format; packed outputs are not supported for
@@ -298,7 +301,7 @@ sph_status sph_density(sph_ctx *c, int32_t newton_steps)
 sph_status sph_force(sph_ctx *c)
 {
     if (!c) return SPH_EINVAL;
-    if (!c->binned) return SPH_ESTATE;
+    if (!c->binned || c->buffer) return SPH_ESTATE;
     const uint32_t need = SPH_BIT(SPH_F_X) | SPH_BIT(SPH_F_V) | SPH_BIT(SPH_F_M) |
                           SPH_BIT(SPH_F_H) | SPH_BIT(SPH_F_RHO) | SPH_BIT(SPH_F_P) |
                           SPH_BIT(SPH_F_CS);
@@ -339,12 +342,106 @@ sph_status sph_kick_drift_writeback(sph_ctx *c, double dt_kick, double dt_drift,
 sph_status sph_soa_to_aos(sph_ctx *c, uint32_t fields)
 {
     if (!c) return SPH_EINVAL;
-    if (fields == 0 || (fields >> SPH_NFIELDS) != 0 || (fields & SPH_BIT(SPH_F_X))) return SPH_EINVAL;
+    if (fields == 0 || (fields >> SPH_NFIELDS) != 0) return SPH_EINVAL;
+    if ((fields & SPH_BIT(SPH_F_X)) && !c->buffer) return SPH_EINVAL;   // positions: buffer mode only
     for (int f = 0; f < SPH_NFIELDS; ++f)
         if ((fields & SPH_BIT(f)) && c->layout.offset[f] < 0) return SPH_EINVAL;
     if (!c->binned) return SPH_ESTATE;
     if ((c->valid & fields) != fields) return SPH_ESTATE;
     if (run_soa_to_aos(c, fields) != cudaSuccess) return SPH_ECUDA;
+    return SPH_OK;
+}
+
+sph_status sph_bin_buffers(sph_ctx *c, int32_t buffer_size)
+{
+    if (!c) return SPH_EINVAL;
+    if (buffer_size < SPH_BUFFER_MIN || buffer_size > SPH_BUFFER_MAX || (buffer_size & (buffer_size - 1)))
+        return SPH_EINVAL;
+    c->valid = 0;
+    c->binned = false;
+    c->buffer = buffer_size;
+    if (run_bin_buffers(c) != cudaSuccess) return SPH_ECUDA;
+    c->binned = true;
+    return SPH_OK;
+}
+
+namespace {
+
+// a buffer call's checks: the source, the mode, and its inputs (in the
+// layout for SPH_SRC_AOS, where its outputs must exist too; current in the
+// SoA for SPH_SRC_SOA)
+sph_status buffer_call_ok(const sph_ctx *c, int32_t source, uint32_t in, uint32_t out)
+{
+    if (source != SPH_SRC_AOS && source != SPH_SRC_SOA) return SPH_EINVAL;
+    if (source == SPH_SRC_AOS) {
+        for (int f = 0; f < SPH_NFIELDS; ++f)
+            if (((in | out) & SPH_BIT(f)) && c->layout.offset[f] < 0) return SPH_EINVAL;
+    }
+    if (!c->binned || !c->buffer) return SPH_ESTATE;
+    if (source == SPH_SRC_SOA && (c->valid & in) != in) return SPH_ESTATE;
+    return SPH_OK;
+}
+
+// after a buffer call: SoA outputs are current; AoS outputs leave their SoA
+// copies stale
+void buffer_call_done(sph_ctx *c, int32_t source, uint32_t out)
+{
+    if (source == SPH_SRC_SOA) c->valid |= out;
+    else c->valid &= ~out;
+}
+
+}  // namespace
+
+sph_status sph_buffer_density(sph_ctx *c, int32_t source)
+{
+    if (!c) return SPH_EINVAL;
+    const uint32_t in = SPH_BIT(SPH_F_X) | SPH_BIT(SPH_F_M) | SPH_BIT(SPH_F_H) | SPH_BIT(SPH_F_U);
+    const uint32_t out = SPH_BIT(SPH_F_RHO) | SPH_BIT(SPH_F_P);
+    const sph_status st = buffer_call_ok(c, source, in, out);
+    if (st != SPH_OK) return st;
+    if (run_buffer_density(c, source) != cudaSuccess) return SPH_ECUDA;
+    buffer_call_done(c, source, out | SPH_BIT(SPH_F_CS));
+    return SPH_OK;
+}
+
+sph_status sph_buffer_force(sph_ctx *c, int32_t source)
+{
+    if (!c) return SPH_EINVAL;
+    const uint32_t in = SPH_BIT(SPH_F_X) | SPH_BIT(SPH_F_V) | SPH_BIT(SPH_F_M) | SPH_BIT(SPH_F_H) |
+                        SPH_BIT(SPH_F_RHO) | SPH_BIT(SPH_F_P);
+    const uint32_t out = SPH_BIT(SPH_F_A) | SPH_BIT(SPH_F_DUDT);
+    const sph_status st = buffer_call_ok(c, source, in, out);
+    if (st != SPH_OK) return st;
+    if (source == SPH_SRC_SOA) {
+        c->prec[SPH_F_A] = SPH_P_FP32;
+        c->prec[SPH_F_DUDT] = SPH_P_FP32;
+    }
+    if (run_buffer_force(c, source) != cudaSuccess) return SPH_ECUDA;
+    buffer_call_done(c, source, out);
+    return SPH_OK;
+}
+
+sph_status sph_buffer_kick(sph_ctx *c, int32_t source, double dt)
+{
+    if (!c || !std::isfinite(dt)) return SPH_EINVAL;
+    const uint32_t in = SPH_BIT(SPH_F_V) | SPH_BIT(SPH_F_A) | SPH_BIT(SPH_F_U) | SPH_BIT(SPH_F_DUDT);
+    const uint32_t out = SPH_BIT(SPH_F_V) | SPH_BIT(SPH_F_U);
+    const sph_status st = buffer_call_ok(c, source, in, out);
+    if (st != SPH_OK) return st;
+    if (run_buffer_kick(c, source, dt) != cudaSuccess) return SPH_ECUDA;
+    buffer_call_done(c, source, out);
+    return SPH_OK;
+}
+
+sph_status sph_buffer_drift(sph_ctx *c, int32_t source, double dt)
+{
+    if (!c || !std::isfinite(dt)) return SPH_EINVAL;
+    const uint32_t in = SPH_BIT(SPH_F_X) | SPH_BIT(SPH_F_V);
+    const uint32_t out = SPH_BIT(SPH_F_X);
+    const sph_status st = buffer_call_ok(c, source, in, out);
+    if (st != SPH_OK) return st;
+    if (run_buffer_drift(c, source, dt) != cudaSuccess) return SPH_ECUDA;
+    buffer_call_done(c, source, out);
     return SPH_OK;
 }
 

@@ -47,7 +47,7 @@ struct Plan {
     size_t keys[2], vals[2];
     size_t cell_count, cell_start, scan_part, ghist;
     size_t item_cell, item_first, item_count, item_tmp, item_sorted, item_class, class_hist;
-    size_t nngb, nngb_force, stage, aos_tmp, stats, key_hmax, origin, pack;
+    size_t nngb, nngb_force, stage, aos_tmp, stats, key_hmax, origin, pack, buf_origin;
     size_t soa[SPH_NFIELDS][3];
     size_t total;
     int64_t item_max, nblk_radix;
@@ -263,6 +263,7 @@ struct sph_ctx {
     int64_t ncell = 0;
     int sub = 1;                  // sub-cells per cell edge of the last binning
     bool binned = false;
+    int32_t buffer = 0;           // buffer mode: records taken in buffers of this size (0: cell lists)
     sph::LaunchCache lc_density, lc_force;   // launch shapes of the persistent pair kernels
     int sorted_buf = 0;          // which ping-pong buffer holds the sorted keys/values
 
@@ -280,6 +281,7 @@ struct sph_ctx {
     float *stage = nullptr;
     float *key_hmax = nullptr;    // largest h of every sub-cell (force pruning)
     double *origin = nullptr;     // cell origins k * (L_d / nc_d), kMaxCellsPerAxis per axis
+    double *buf_origin = nullptr; // buffer mode: first position of every buffer, 3 x nbuf, axis-major
     float4 *pack = nullptr;       // 3 x n: the force's packed FP32 inputs per slot
     uint8_t *aos_tmp = nullptr;
     sph::DevStats *dstats = nullptr;
@@ -304,6 +306,12 @@ cudaError_t run_soa_to_aos(sph_ctx *c, uint32_t fields);
 cudaError_t run_density(sph_ctx *c, int newton_steps);
 cudaError_t run_force(sph_ctx *c);
 cudaError_t run_kick_drift(sph_ctx *c, double dt_kick, double dt_drift, uint32_t wb_fields);
+// buffer mode (k_buffers.cu)
+cudaError_t run_bin_buffers(sph_ctx *c);
+cudaError_t run_buffer_density(sph_ctx *c, int source);
+cudaError_t run_buffer_force(sph_ctx *c, int source);
+cudaError_t run_buffer_kick(sph_ctx *c, int source, double dt);
+cudaError_t run_buffer_drift(sph_ctx *c, int source, double dt);
 cudaError_t scan_exclusive(const int32_t *in, int32_t *out, int64_t len, int32_t *part,
                            cudaStream_t s, uint64_t *launches);
 int max_dynamic_smem(const sph_ctx *c);
