@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-uneven", action="store_true", help="skip the 16.7M-particle clustered batching rows")
     ap.add_argument("--no-vs-plain", action="store_true", help="skip the plain FP32 SoA comparison")
     ap.add_argument("--no-streaming", action="store_true", help="skip the host-resident AoS comparison")
+    ap.add_argument("--no-buffers", action="store_true", help="skip the 64-particle-buffer AoS/SoA comparison")
     ap.add_argument("--profile-case", choices=["pairs", "memory"], default=None,
                     help="run one small fixed workload for an ncu capture and exit")
     return ap.parse_args()
@@ -526,6 +527,103 @@ def run_streaming(steps: int = 5):
     return rows
 
 
+def _records_144(wl, seed: int = 9):
+    """The paper's 144-byte benchmark record (ID, FP64 x, FP32 fields) for a
+    workload, with random accelerations and du/dt for the kick."""
+    import paper_2512_05516_gb300 as sph
+    offs = {k: v for k, v in sph.RECORD_144.items() if k not in ("cs", "dudt")}
+    raw = sph_inputs.pack_records(wl, offs, 144, f32_fields=sph.F32_144)
+    raw[:, 0:8] = np.arange(wl.n, dtype=np.int64).view(np.uint8).reshape(-1, 8)
+    raw[:, 76:80] = 0
+    rng = np.random.Generator(np.random.PCG64(seed))
+    raw[:, 44:56] = rng.uniform(-1, 1, (wl.n, 3)).astype(np.float32).view(np.uint8).reshape(-1, 12)
+    raw[:, 80:84] = rng.uniform(-1, 1, wl.n).astype(np.float32).view(np.uint8).reshape(-1, 4)
+    return raw
+
+
+def run_buffers(nb=(64, 64, 32), reps: int = 5):
+    """The paper's benchmark shape (Section 6, Fig. 2): 4x4x4 lattice blocks,
+    each a contiguous buffer of 64 records in the paper's 144-byte record;
+    density and force over every pair of a buffer, kick and drift per
+    particle.  Each kernel reads the records directly (AoS) or the converted
+    SoA (FP32, and 16-bit: v, m, h, u in FP16 under power-of-two scales,
+    positions FP32 offsets); the pair kernels in two forms, partners staged
+    in shared memory (the default) and read from global memory (the
+    structure of the paper's kernels).  CUDA-event mean over `reps` calls
+    after one warm-up, inputs larger than L2.  Also the conversion and
+    write-back that the SoA variants need around the kernels, for a whole
+    step."""
+    import torch
+    import paper_2512_05516_gb300 as sph
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    wl = sph_inputs.buffer_blocks(nb=nb)
+    B = wl.meta["B"]
+    raw = _records_144(wl)
+    stream = torch.cuda.Stream(dev)
+    nc = [int(math.floor(b / (2 * wl.h_cap))) for b in wl.box]
+    params = sph.make_params(wl.box, gamma=wl.gamma, alpha=wl.alpha_av, beta=wl.beta_av,
+                             eps=wl.eps_av, eta=wl.eta, h_max=wl.h_cap)
+    aos = torch.from_numpy(raw.reshape(-1)).to(dev)
+    del raw
+    s = sph.Sph(aos, sph.layout_144(), params, max(int(np.prod(nc)), 27), 0, stream=stream)
+    s.bin_buffers(B)
+    col = lambda name: wl.col(name)
+    scale16 = {k: sph.suggest_scale(float(np.abs(col(k)).max()), "fp16") for k in ("v", "m", "h", "u")}
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fn()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    kernels = ["density", "force", "kick", "drift"]
+    calls = {"density": lambda src: s.buffer_density(src), "force": lambda src: s.buffer_force(src),
+             "kick": lambda src: s.buffer_kick(1e-6, src), "drift": lambda src: s.buffer_drift(1e-6, src)}
+    inputs = sph.mask("x", "v", "a", "m", "h", "u", "dudt")
+    outputs = sph.mask("x", "v", "a", "rho", "P", "cs", "u", "dudt")
+    rows = {}
+    with torch.cuda.stream(stream):
+        s.reset_stats()
+        s.buffer_density("aos")
+        s.buffer_force("aos")
+        st = s.stats()
+        rows["aos"] = {k: timed(lambda k=k: calls[k]("aos")) for k in kernels}
+        s.set_tuning(pair_kernel=1)
+        rows["aos"].update({k + "_plain": timed(lambda k=k: calls[k]("aos")) for k in ("density", "force")})
+        s.set_tuning(pair_kernel=0)
+        for name, prec, scale in (("soa_fp32", None, {}),
+                                  ("soa_16bit", {"v": "fp16", "m": "fp16", "h": "fp16", "u": "fp16"}, scale16)):
+            s.set_scale(scale)
+            conv = timed(lambda: s.aos_to_soa(inputs, prec))
+            r = {k: timed(lambda k=k: calls[k]("soa")) for k in kernels}
+            s.set_tuning(pair_kernel=1)
+            r.update({k + "_plain": timed(lambda k=k: calls[k]("soa")) for k in ("density", "force")})
+            s.set_tuning(pair_kernel=0)
+            r["aos_to_soa"] = conv
+            r["soa_to_aos"] = timed(lambda: s.soa_to_aos(outputs))
+            rows[name] = r
+        s.set_scale({})
+    out = {"workload": f"buffer_blocks_{wl.n}", "buffer": B, "record_bytes": 144, "n": wl.n,
+           "pairs_per_step": {"density": st["pairs_density"], "force": st["pairs_force"]},
+           "ms": rows, "soa_16bit_scales": scale16}
+    speed = {}
+    for name in ("soa_fp32", "soa_16bit"):
+        speed[name] = {k: rows["aos"][k] / rows[name][k] for k in kernels + ["density_plain", "force_plain"]}
+        step_aos = sum(rows["aos"][k] for k in kernels)
+        step_soa = sum(rows[name][k] for k in kernels) + rows[name]["aos_to_soa"] + rows[name]["soa_to_aos"]
+        speed[name]["step_with_conversions"] = step_aos / step_soa
+    out["soa_speedup_over_aos"] = speed
+    out["pairs_per_s"] = {src: {"density": st["pairs_density"] / (rows[src]["density"] * 1e-3),
+                                "force": st["pairs_force"] / (rows[src]["force"] * 1e-3)}
+                          for src in ("aos", "soa_fp32", "soa_16bit")}
+    s.close()
+    return out
+
+
 def run_uneven(n: int = 16_777_216):
     """Uneven occupancy (the clustered Gaussian mixture, one global h, up to
     ~65,000 particles in a cell), BF16 storage of v, m, h, u: one density
@@ -726,6 +824,7 @@ def main():
     uneven = None if args.no_uneven or world > 1 else run_uneven()
     vs_plain = None if args.no_vs_plain or world > 1 else run_vs_plain()
     streaming = None if args.no_streaming or world > 1 else run_streaming()
+    buffers = None if args.no_buffers or world > 1 else run_buffers()
     out = {
         "metric": METRIC, "value": pairs / total_s, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
@@ -740,6 +839,7 @@ def main():
         "gpu_launches": r["launches"], "clocks": r["clocks"], "kernels": r["kernels"],
         "memory_bound_rows": long, "uneven_batching": uneven, "vs_plain_fp32_soa": vs_plain,
         "streaming_vs_in_place": streaming,
+        "buffers_aos_vs_soa": buffers,
     }
     print(json.dumps(out))
     if world > 1:

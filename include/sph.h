@@ -182,7 +182,10 @@ typedef struct {
     int32_t pair_kernel;         /* 0: the batched kernels (warp work items, staged and
                                     pruned neighbourhoods); 1: the plain form, one thread
                                     per particle looping over the 27 neighbour cells
-                                    straight from the SoA (a baseline); -1 keeps the current */
+                                    straight from the SoA (a baseline).  For the buffer
+                                    kernels, 0 stages each buffer in shared memory and
+                                    1 reads every partner from global memory (the
+                                    paper's kernel structure); -1 keeps the current */
 } sph_tuning;
 
 /* Where the library's arrays live inside the workspace (byte offsets from the

@@ -11,8 +11,13 @@
 // Each thread loads its own particle -- from the records with the record
 // stride, its position made relative to the buffer's first particle there
 // (one FP64 subtraction per component); from the SoA coalesced, the relative
-// position already stored -- into shared memory, and the pair loop reads its
-// partners there.  Arithmetic is FP32 (the cell-list kernels' per-pair code,
+// position already stored.  Staged form (the default): each thread puts its
+// particle in shared memory and the pair loop reads its partners there.
+// Plain form (tuning pair_kernel = 1, the structure of the paper's kernels):
+// the pair loop reads every partner through the accessor from global memory
+// (the L1 cache serves the repeats), so that the record layout acts on every
+// pair.  Both forms do the same arithmetic in the same order and give
+// identical bits.  Arithmetic is FP32 (the cell-list kernels' per-pair code,
 // k_pair_math.cuh); the drift of AoS positions is FP64.
 #include <cstring>
 
@@ -103,9 +108,16 @@ __device__ __forceinline__ void count_pairs(unsigned long long *ctr, int k)
 // ---- Density: rho_i = sum over the buffer of m_j W(r_ij, h_i), self included;
 //      then P = (gamma - 1) rho u and c = sqrt(gamma P / rho) ----------------
 template <bool kAos>
+__device__ __forceinline__ float4 partner_xm(const BufArgs &a, int64_t j)
+{
+    const float3 x = pos_rel<kAos>(a, j);
+    return make_float4(x.x, x.y, x.z, get<kAos>(a, j, SPH_F_M));
+}
+
+template <bool kAos, bool kStaged>
 __global__ void __launch_bounds__(kBufThreads) k_buf_density(BufArgs a)
 {
-    __shared__ float4 sj[kBufThreads];              // (x, y, z, m), buffer-relative
+    __shared__ float4 sj[kStaged ? kBufThreads : 1];   // (x, y, z, m), buffer-relative
     const int t = threadIdx.x;
     const int64_t i = (int64_t)blockIdx.x * kBufThreads + t;
     const bool ok = i < a.n;
@@ -117,18 +129,21 @@ __global__ void __launch_bounds__(kBufThreads) k_buf_density(BufArgs a)
         h = get<kAos>(a, i, SPH_F_H);
         u = get<kAos>(a, i, SPH_F_U);
     }
-    sj[t] = make_float4(xi.x, xi.y, xi.z, m);
-    __syncthreads();
+    if (kStaged) {
+        sj[t] = make_float4(xi.x, xi.y, xi.z, m);
+        __syncthreads();
+    }
     const int B = 1 << a.lgB;
     const int me = t & (B - 1);
     const int t0 = t - me;
-    const int64_t cnt64 = a.n - (i - me);                // particles from the buffer's first on
+    const int64_t first = i - me;                        // the buffer's first record
+    const int64_t cnt64 = a.n - first;
     const int cnt = ok ? (int)(cnt64 < B ? cnt64 : B) : 0;
     const float hinv = 1.0f / h, h2x4 = 4.0f * h * h;
     float s = 0.f, cs = 0.f;
     int k = 0;
     for (int j = 0; j < cnt; ++j) {
-        const float4 q = sj[t0 + j];
+        const float4 q = kStaged ? sj[t0 + j] : partner_xm<kAos>(a, first + j);
         const float dx = xi.x - q.x, dy = xi.y - q.y, dz = xi.z - q.z;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         const float r = r2 * rsqrtf(fmaxf(r2, 1.0e-30f));     // 0 for the self pair
@@ -158,10 +173,23 @@ __global__ void __launch_bounds__(kBufThreads) k_buf_density(BufArgs a)
 
 // ---- Force: the symmetric pair force with Monaghan viscosity over the
 //      buffer's pairs r < h_i + h_j (Eq. 7, Eq. 5); c from the EOS --------------
+// a partner's force inputs: (x, y, z, h), (v, m), (P / rho^2, rho, c, -)
 template <bool kAos>
+__device__ __forceinline__ void partner_force(const BufArgs &a, int64_t j, float4 &qa, float4 &qb, float4 &qc)
+{
+    const float3 x = pos_rel<kAos>(a, j);
+    qa = make_float4(x.x, x.y, x.z, get<kAos>(a, j, SPH_F_H));
+    qb = make_float4(get<kAos>(a, j, SPH_F_V, 0), get<kAos>(a, j, SPH_F_V, 1), get<kAos>(a, j, SPH_F_V, 2),
+                     get<kAos>(a, j, SPH_F_M));
+    const float rho = get<kAos>(a, j, SPH_F_RHO), P = get<kAos>(a, j, SPH_F_P);
+    qc = make_float4(P / (rho * rho), rho, sqrtf(a.gamma * P / rho), 0.f);
+}
+
+template <bool kAos, bool kStaged>
 __global__ void __launch_bounds__(kBufThreads) k_buf_force(BufArgs a)
 {
-    __shared__ float4 sA[kBufThreads], sB[kBufThreads], sC[kBufThreads];
+    constexpr int S = kStaged ? kBufThreads : 1;
+    __shared__ float4 sA[S], sB[S], sC[S];
     const int t = threadIdx.x;
     const int64_t i = (int64_t)blockIdx.x * kBufThreads + t;
     const bool ok = i < a.n;
@@ -177,28 +205,38 @@ __global__ void __launch_bounds__(kBufThreads) k_buf_force(BufArgs a)
     }
     const float Pr2 = P / (rho * rho);
     const float c = sqrtf(a.gamma * P / rho);
-    sA[t] = make_float4(xi.x, xi.y, xi.z, h);
-    sB[t] = make_float4(vi.x, vi.y, vi.z, m);
-    sC[t] = make_float4(Pr2, rho, c, 0.f);
-    __syncthreads();
+    if (kStaged) {
+        sA[t] = make_float4(xi.x, xi.y, xi.z, h);
+        sB[t] = make_float4(vi.x, vi.y, vi.z, m);
+        sC[t] = make_float4(Pr2, rho, c, 0.f);
+        __syncthreads();
+    }
     const int B = 1 << a.lgB;
     const int me = t & (B - 1);
     const int t0 = t - me;
-    const int64_t cnt64 = a.n - (i - me);
+    const int64_t first = i - me;
+    const int64_t cnt64 = a.n - first;
     const int cnt = ok ? (int)(cnt64 < B ? cnt64 : B) : 0;
     float ax = 0.f, ay = 0.f, az = 0.f, du = 0.f;
     int k = 0;
     for (int j = 0; j < cnt; ++j) {
         if (j == me) continue;
-        const float4 qa = sA[t0 + j];
+        float4 qa, qb, qc;
+        if (kStaged) {
+            qa = sA[t0 + j];
+            qb = sB[t0 + j];
+            qc = sC[t0 + j];
+        } else {
+            partner_force<kAos>(a, first + j, qa, qb, qc);
+        }
         const float dx = xi.x - qa.x, dy = xi.y - qa.y, dz = xi.z - qa.z;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         const float hs = h + qa.w;
         if (!(r2 < hs * hs)) continue;
         ++k;
         if (r2 == 0.0f) continue;                             // coincident pair: grad W = 0
-        force_pair(ax, ay, az, du, vi.x, vi.y, vi.z, rho, Pr2, c, dx, dy, dz, r2, hs, sB[t0 + j], sC[t0 + j],
-                   a.alpha, a.beta, a.eps);
+        force_pair(ax, ay, az, du, vi.x, vi.y, vi.z, rho, Pr2, c, dx, dy, dz, r2, hs, qb, qc, a.alpha, a.beta,
+                   a.eps);
     }
     if (ok && !(isfinite(ax) && isfinite(ay) && isfinite(az) && isfinite(du))) set_error(a.st, SPH_ERR_NONFINITE);
     if (kAos) {
@@ -339,13 +377,19 @@ cudaError_t run_bin_buffers(sph_ctx *c)
 cudaError_t run_buffer_density(sph_ctx *c, int source)
 {
     const BufArgs a = make_buf_args(c);
-    return source == SPH_SRC_AOS ? launch_buf(c, k_buf_density<true>, a) : launch_buf(c, k_buf_density<false>, a);
+    const bool staged = c->tuning.pair_kernel != 1;
+    if (source == SPH_SRC_AOS)
+        return staged ? launch_buf(c, k_buf_density<true, true>, a) : launch_buf(c, k_buf_density<true, false>, a);
+    return staged ? launch_buf(c, k_buf_density<false, true>, a) : launch_buf(c, k_buf_density<false, false>, a);
 }
 
 cudaError_t run_buffer_force(sph_ctx *c, int source)
 {
     const BufArgs a = make_buf_args(c);
-    return source == SPH_SRC_AOS ? launch_buf(c, k_buf_force<true>, a) : launch_buf(c, k_buf_force<false>, a);
+    const bool staged = c->tuning.pair_kernel != 1;
+    if (source == SPH_SRC_AOS)
+        return staged ? launch_buf(c, k_buf_force<true, true>, a) : launch_buf(c, k_buf_force<true, false>, a);
+    return staged ? launch_buf(c, k_buf_force<false, true>, a) : launch_buf(c, k_buf_force<false, false>, a);
 }
 
 cudaError_t run_buffer_kick(sph_ctx *c, int source, double dt)

@@ -219,6 +219,28 @@ def test_aos_and_soa_sources_agree_bitwise():
     assert np.array_equal(outs[0], outs[1])
 
 
+@pytest.mark.parametrize("source", ["aos", "soa"])
+def test_plain_form_equals_staged(source):
+    # reading every partner from global memory (tuning pair_kernel = 1) does
+    # the same arithmetic in the same order as the shared-memory stage
+    B = 64
+    wl, raw, n = _setup(B, seed=28)
+    outs = []
+    for plain in (0, 1):
+        s = _ctx(wl, raw, B)
+        s.set_tuning(pair_kernel=plain)
+        if source == "soa":
+            s.aos_to_soa(sph_mod.mask("x", "v", "m", "h", "u"))
+        s.buffer_density(source)
+        s.buffer_force(source)
+        if source == "soa":
+            s.soa_to_aos(sph_mod.mask("rho", "P", "cs", "a", "dudt"))
+        outs.append((_out(s, raw.shape), s.stats()["pairs_density"], s.stats()["pairs_force"]))
+        s.close()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert outs[0][1:] == outs[1][1:]
+
+
 @pytest.mark.parametrize("fmt", ["bf16", "fp16", "m10"])
 def test_buffer_kernels_reduced_storage(orc, fmt):
     # v, m, h, u stored in a reduced format: the oracle is fed the same
