@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--no-vs-plain", action="store_true", help="skip the plain FP32 SoA comparison")
     ap.add_argument("--no-streaming", action="store_true", help="skip the host-resident AoS comparison")
     ap.add_argument("--no-buffers", action="store_true", help="skip the 64-particle-buffer AoS/SoA comparison")
-    ap.add_argument("--profile-case", choices=["pairs", "memory"], default=None,
+    ap.add_argument("--profile-case", choices=["pairs", "memory", "buffers"], default=None,
                     help="run one small fixed workload for an ncu capture and exit")
     return ap.parse_args()
 
@@ -125,9 +125,18 @@ def prec_of(args):
     return {"v": args.prec, "m": args.prec, "h": args.prec, "u": args.prec}
 
 
-def traffic_from_profile(kernel_src: str, kernel: str):
+def kernel_sources_sha256(paths) -> str:
+    """SHA-256 over the concatenated bytes of a kernel's source files."""
+    h = hashlib.sha256()
+    for p in paths:
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def traffic_from_profile(kernel_srcs, kernel: str):
     """DRAM bytes per launch of a pair kernel from the committed ncu summary,
-    if it was taken on the current kernel source (else None)."""
+    if it was taken on the current kernel sources (else None)."""
     path = os.path.join(ROOT, "profiles", "k_pairs_sod1m.md")
     if not os.path.exists(path):
         return None
@@ -136,8 +145,7 @@ def traffic_from_profile(kernel_src: str, kernel: str):
     m_tr = re.search(re.escape(kernel) + r"\.dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
     if not m_src or not m_tr:
         return None
-    sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
-    return float(m_tr.group(1)) if sha == m_src.group(1) else None
+    return float(m_tr.group(1)) if kernel_sources_sha256(kernel_srcs) == m_src.group(1) else None
 
 
 def fp32_peak_tflops(sm_count: int, mhz: float) -> float:
@@ -256,7 +264,7 @@ def run_ours(args, rank, world):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = fp32_peak_tflops(sms, clk.get("sm_max_mhz") or 2070.0)
     achieved = flops / t_dom / 1e12
-    kernel_src = os.path.join(ROOT, "paper_2512_05516_gb300", "csrc", "k_pairs.cu")
+    kernel_src = [os.path.join(ROOT, "paper_2512_05516_gb300", "csrc", f) for f in ("k_pairs.cu", "k_pair_math.cuh")]
     roofline = {"bound": "alu", "kernel": f"k_{dominant}", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic_from_profile(kernel_src, f"k_{dominant}"),
@@ -726,6 +734,38 @@ def combine_ranks(total_s: float, pairs: float, e2e_value: float, device: str):
     return float(t[0].item()), float(p[0].item()), float(p[1].item())
 
 
+def profile_buffers():
+    """'buffers': 4x4x4 lattice blocks, 2,097,152 particles in 144-byte
+    records (302 MB > L2), buffers of 64: density and force from the records
+    and from FP32 SoA, staged and plain, then kick and drift from the SoA and
+    from the records."""
+    import torch
+    import paper_2512_05516_gb300 as sph
+    wl = sph_inputs.buffer_blocks(nb=(32, 32, 32))
+    raw = _records_144(wl)
+    nc = [int(math.floor(b / (2 * wl.h_cap))) for b in wl.box]
+    params = sph.make_params(wl.box, gamma=wl.gamma, alpha=wl.alpha_av, beta=wl.beta_av,
+                             eps=wl.eps_av, eta=wl.eta, h_max=wl.h_cap)
+    aos = torch.from_numpy(raw.reshape(-1)).cuda()
+    s = sph.Sph(aos, sph.layout_144(), params, max(int(np.prod(nc)), 27), 0)
+    s.bin_buffers(wl.meta["B"])
+    s.aos_to_soa(sph.mask("x", "v", "a", "m", "h", "u", "dudt"))
+    for plain in (0, 1):
+        s.set_tuning(pair_kernel=plain)
+        for src in ("aos", "soa"):
+            s.buffer_density(src)
+            s.buffer_force(src)
+    for src in ("soa", "aos"):              # an AoS call leaves the SoA copies of its outputs stale
+        s.buffer_kick(1e-6, src)
+        s.buffer_drift(1e-6, src)
+    torch.cuda.synchronize()
+    st = s.stats()
+    print(json.dumps({"profile_case": "buffers", "n": wl.n, "error_bits": st["error_bits"],
+                      "pairs_density": st["pairs_density"], "pairs_force": st["pairs_force"]}))
+    if st["error_bits"] & (sph.ERR_NONFINITE | sph.ERR_OUTSIDE):
+        raise SystemExit(1)
+
+
 def profile_case(which: str):
     """Small fixed workloads for ncu captures (profiles/ summaries name the
     command).  'pairs': the 1,072,476-particle Sod step twice (the second is
@@ -735,6 +775,9 @@ def profile_case(which: str):
     write-back, step 2 with the fused call."""
     import torch
     import paper_2512_05516_gb300 as sph
+    if which == "buffers":
+        profile_buffers()
+        return
     if which == "pairs":
         wl = sph_inputs.sod()
         prec, ws, steps = None, 0, 2
