@@ -297,3 +297,66 @@ def test_buffer_mode_state_rules():
     with pytest.raises(sph_mod.SphError):
         s.buffer_force("aos")                    # cell mode again
     s.close()
+
+
+def test_buffer_step_graph_replay_equals_eager():
+    # a whole buffer step (conversion, the four kernels, write-back) captured
+    # in a CUDA graph and replayed gives the eager run's records exactly
+    B = 64
+    wl, raw, n = _setup(B, seed=29)
+    fields_in = sph_mod.mask("x", "v", "a", "m", "h", "u", "dudt")
+    fields_out = sph_mod.mask("x", "v", "a", "rho", "P", "cs", "u", "dudt")
+    prec = {"v": "fp16", "m": "bf16", "h": "m10", "u": "fp16"}
+
+    def run(graph):
+        st = torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            s = make_sph(wl, aos=torch.from_numpy(raw.reshape(-1).copy()).cuda(), layout=sph_mod.layout_144())
+            s.set_scale({"m": sph_mod.suggest_scale(float(col(raw, "m").max()), "bf16")})
+            s.bin_buffers(B)
+
+            def step():
+                s.aos_to_soa(fields_in, prec)
+                s.buffer_density("soa")
+                s.buffer_force("soa")
+                s.buffer_kick(DT, "soa")
+                s.buffer_drift(DT, "soa")
+                s.soa_to_aos(fields_out)
+
+            step()
+            if graph:
+                st.synchronize()
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=st):
+                    step()
+                g.replay()
+                g.replay()
+            else:
+                step()
+                step()
+        st.synchronize()
+        out = s.aos.cpu().numpy().view(np.uint8).reshape(raw.shape).copy()
+        assert s.stats()["error_bits"] == 0
+        s.close()
+        return out
+
+    assert np.array_equal(run(False), run(True))
+
+
+def test_host_resident_records_equal_device_records():
+    # records in pinned host memory, read by the AoS-source kernels over the
+    # host link, give the device-resident run's bytes
+    B = 64
+    wl, raw, n = _setup(B, seed=30)
+    outs = []
+    for host in (False, True):
+        t = torch.from_numpy(raw.reshape(-1).copy())
+        s = make_sph(wl, aos=t.pin_memory() if host else t.cuda(), layout=sph_mod.layout_144())
+        s.bin_buffers(B)
+        s.buffer_density("aos")
+        s.buffer_force("aos")
+        s.buffer_kick(DT, "aos")
+        s.buffer_drift(DT, "aos")
+        outs.append(_out(s, raw.shape))
+        s.close()
+    assert np.array_equal(outs[0], outs[1])
