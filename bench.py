@@ -318,11 +318,11 @@ def algorithmic_bytes(prec_bytes: float, pos_bytes: float):
     return {"aos_to_soa": conv, "kick_drift": kick, "soa_to_aos": back, "kick_drift_writeback": fused}
 
 
-def run_long_run(steps: int = 3, graph_steps: int = 10):
+def run_long_run(steps: int = 3, graph_steps: int = 100):
     """Memory-bound rows on the 33,554,432-particle long-run lattice (box
     2x1x1, FP64 AoS master, FP16 storage of x, v, m, h, u): per-call CUDA-event
     times of the conversion, kick/drift and write-back kernels against the
-    HBM peak, and whole steps replayed from a CUDA graph."""
+    HBM peak, and 100 whole steps captured in one CUDA graph and replayed."""
     import torch
     import paper_2512_05516_gb300 as sph
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
@@ -359,6 +359,21 @@ def run_long_run(steps: int = 3, graph_steps: int = 10):
         stream.synchronize()
         ms = {nm: statistics.mean(ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(steps))
               for i, nm in enumerate(names)}
+        # S6 and S7 as separate calls (kick/drift alone, then the write-back),
+        # timed at the same distance from the reorder as the rows above
+        sep = ["kick_drift", "soa_to_aos"]
+        ev_sep = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in sep]
+                  for _ in range(steps)]
+        for k in range(steps):
+            for fn in calls[:4]:
+                fn()
+            for i, fn in enumerate([lambda: s.kick_drift(wl.dt, wl.dt), lambda: s.soa_to_aos(sph.FIELDS_OUTPUT)]):
+                ev_sep[k][i][0].record(stream)
+                fn()
+                ev_sep[k][i][1].record(stream)
+        stream.synchronize()
+        for i, nm in enumerate(sep):
+            ms[nm] = statistics.mean(ev_sep[k][i][0].elapsed_time(ev_sep[k][i][1]) for k in range(steps))
         # whole steps as one CUDA graph
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=stream):
@@ -376,21 +391,6 @@ def run_long_run(steps: int = 3, graph_steps: int = 10):
     if st["error_bits"] & (sph.ERR_NONFINITE | sph.ERR_OUTSIDE):
         raise RuntimeError(f"long run: device error bits {st['error_bits']}")
     pairs = (st["pairs_density"] + st["pairs_force"]) / graph_steps
-    # S6 and S7 as separate calls (kick/drift alone, then the write-back)
-    sep = ["kick_drift", "soa_to_aos"]
-    ev_sep = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in sep]
-              for _ in range(steps)]
-    with torch.cuda.stream(stream):
-        for k in range(steps):
-            for fn in calls[:4]:
-                fn()
-            for i, fn in enumerate([lambda: s.kick_drift(wl.dt, wl.dt), lambda: s.soa_to_aos(sph.FIELDS_OUTPUT)]):
-                ev_sep[k][i][0].record(stream)
-                fn()
-                ev_sep[k][i][1].record(stream)
-        stream.synchronize()
-    for i, nm in enumerate(sep):
-        ms[nm] = statistics.mean(ev_sep[k][i][0].elapsed_time(ev_sep[k][i][1]) for k in range(steps))
     # the comparison: an FP32 SoA kept across steps needs no conversion or
     # write-back; its step is binning + density + force + kick/drift on FP32
     # storage (timed per call; the FP32 conversion that refreshes the SoA
@@ -433,7 +433,7 @@ def run_long_run(steps: int = 3, graph_steps: int = 10):
     fp32_step = sum(ms32.values())
     return {"workload": "long_run_33554432", "particles": n, "storage": "fp16 (x, v, m, h, u)",
             "tuning": tuned["tuning"],
-            "ms_per_step_graph": graph_ms, "pairs_per_s": pairs / (graph_ms / 1e3),
+            "ms_per_step_graph": graph_ms, "graph_steps": graph_steps, "pairs_per_s": pairs / (graph_ms / 1e3),
             "kernels": kern, "hbm_peak_gbs": hbm,
             "vs_fp32_soa": {"fp16_with_conversion_ms": fp16_step,
                             "fp32_soa_no_conversion_ms": fp32_step,
