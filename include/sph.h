@@ -6,7 +6,8 @@
  *
  * The paper's operator algebra (Section 4) maps onto the calls below:
  *   N   narrowing to the fields a kernel reads     -> `fields` masks
- *   C   AoS -> SoA layout change                    -> sph_aos_to_soa
+ *   C   AoS -> SoA layout change                    -> sph_aos_to_soa (on the GPU) or
+ *                                                      sph_aos_to_soa_host (on the CPU)
  *   U   unpack reduced precision / U^T pack         -> per-field `prec`
  *   f   the compute kernel                          -> sph_density, sph_force,
  *                                                      sph_kick_drift (cell
@@ -318,6 +319,34 @@ sph_status sph_kick_drift(sph_ctx *ctx, double dt_kick, double dt_drift);
  * Errors: SPH_EINVAL (X requested after sph_bin_cells, or field absent from
  * the layout), SPH_ESTATE (field not current), SPH_ECUDA. */
 sph_status sph_soa_to_aos(sph_ctx *ctx, uint32_t fields);
+
+/* ---- The conversion on the host: the paper's CPU placement --------------
+ * Section 6.3 (Eq. 13-14) converts on the CPU and then moves the narrowed,
+ * reduced-precision SoA to the device, or moves the AoS first and converts
+ * on the GPU.  sph_aos_to_soa is the GPU placement; these two calls are the
+ * CPU one, over records in host memory (any host memory; the staging buffer
+ * should be pinned for the copies to run at full speed).  They produce the
+ * same codes and record bytes as their device counterparts.  Both read the
+ * permutation (and what positions need) from the device and synchronise the
+ * context's stream first, convert with `nthreads` host threads (<= 0: one
+ * per hardware thread), and move the data with one copy per SoA array.
+ * host_stage is a caller-owned host buffer of at least
+ * sph_host_stage_bytes(ctx) bytes; after sph_aos_to_soa_host returns, the
+ * copies out of it may still be in flight on the stream, so it must not be
+ * rewritten before the stream has passed them. */
+size_t sph_host_stage_bytes(const sph_ctx *ctx);
+
+/* As sph_aos_to_soa (same fields, formats, scales, slot order and position
+ * offsets), reading the records at host_aos (n records in the context's
+ * layout).  Errors: SPH_EINVAL (pointers, fields, formats), SPH_ENOSPACE
+ * (stage too small), SPH_ESTATE (not binned), SPH_ECUDA. */
+sph_status sph_aos_to_soa_host(sph_ctx *ctx, const void *host_aos, uint32_t fields, const int32_t *prec,
+                               void *host_stage, size_t stage_bytes, int32_t nthreads);
+
+/* As sph_soa_to_aos, writing the records at host_aos.  Returns once the
+ * records are written.  Errors as sph_soa_to_aos, and SPH_ENOSPACE. */
+sph_status sph_soa_to_aos_host(sph_ctx *ctx, void *host_aos, uint32_t fields, void *host_stage,
+                               size_t stage_bytes, int32_t nthreads);
 
 /* ---- Buffer kernels: the paper's benchmark grouping (Section 6) ----------
  * The paper keeps particles in contiguous buffers of 64 spatially co-located

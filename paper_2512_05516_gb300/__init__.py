@@ -63,6 +63,25 @@ def sph_aos_to_soa(ctx, fields: int, prec) -> int:
     return _lib.sph_aos_to_soa(ctx, fields, arr)
 
 
+def sph_host_stage_bytes(ctx) -> int:
+    return int(_lib.sph_host_stage_bytes(ctx))
+
+
+def sph_aos_to_soa_host(ctx, host_aos: int, fields: int, prec, host_stage: int, stage_bytes: int,
+                        nthreads: int = 0) -> int:
+    arr = None
+    if prec is not None:
+        arr = (C.c_int32 * SPH_NFIELDS)(*prec)
+    return _lib.sph_aos_to_soa_host(ctx, C.c_void_p(host_aos), fields, arr, C.c_void_p(host_stage),
+                                    int(stage_bytes), int(nthreads))
+
+
+def sph_soa_to_aos_host(ctx, host_aos: int, fields: int, host_stage: int, stage_bytes: int,
+                        nthreads: int = 0) -> int:
+    return _lib.sph_soa_to_aos_host(ctx, C.c_void_p(host_aos), fields, C.c_void_p(host_stage),
+                                    int(stage_bytes), int(nthreads))
+
+
 def sph_density(ctx, newton_steps: int) -> int:
     return _lib.sph_density(ctx, int(newton_steps))
 
@@ -326,6 +345,28 @@ class Sph:
 
     def kick_drift_writeback(self, dt_kick: float, dt_drift: float, fields: int = FIELDS_OUTPUT):
         _check(sph_kick_drift_writeback(self.ctx, dt_kick, dt_drift, fields), "sph_kick_drift_writeback")
+
+    # ---- the conversion on the host (the paper's CPU placement)
+    def host_stage(self):
+        """A pinned host staging buffer sized for the host-side conversion
+        (allocated once per context)."""
+        if getattr(self, "_stage", None) is None:
+            nbytes = sph_host_stage_bytes(self.ctx)
+            self._stage = self.torch.empty(max(nbytes, 1), dtype=self.torch.uint8).pin_memory()
+        return self._stage
+
+    def aos_to_soa_host(self, host_aos, fields: int, prec=None, nthreads: int = 0):
+        """sph_aos_to_soa on the host: `host_aos` is a host tensor of records."""
+        arr = prec if isinstance(prec, list) else (prec_array(prec) if prec is not None else None)
+        st = self.host_stage()
+        _check(sph_aos_to_soa_host(self.ctx, host_aos.data_ptr(), fields, arr, st.data_ptr(), st.numel(),
+                                   nthreads), "sph_aos_to_soa_host")
+
+    def soa_to_aos_host(self, host_aos, fields: int, nthreads: int = 0):
+        """sph_soa_to_aos on the host, into the host tensor of records `host_aos`."""
+        st = self.host_stage()
+        _check(sph_soa_to_aos_host(self.ctx, host_aos.data_ptr(), fields, st.data_ptr(), st.numel(), nthreads),
+               "sph_soa_to_aos_host")
 
     # ---- buffer kernels (the paper's 64-particle buffers, Section 6)
     @staticmethod

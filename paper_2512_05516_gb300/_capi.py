@@ -97,6 +97,9 @@ PROTOTYPES = {
     "sph_aos_download": (C.c_int, [_P, _P, C.c_size_t]),
     "sph_bin_cells_noalloc": (C.c_int, [_P, C.POINTER(sph_aos_layout), C.c_int64, C.POINTER(C.c_double),
                                         C.POINTER(C.c_int32), _P, _P, _P, _P]),
+    "sph_host_stage_bytes": (C.c_size_t, [_P]),
+    "sph_aos_to_soa_host": (C.c_int, [_P, _P, C.c_uint32, C.POINTER(C.c_int32), _P, C.c_size_t, C.c_int32]),
+    "sph_soa_to_aos_host": (C.c_int, [_P, _P, C.c_uint32, _P, C.c_size_t, C.c_int32]),
     "sph_bin_buffers": (C.c_int, [_P, C.c_int32]),
     "sph_buffer_density": (C.c_int, [_P, C.c_int32]),
     "sph_buffer_force": (C.c_int, [_P, C.c_int32]),

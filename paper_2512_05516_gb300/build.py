@@ -19,8 +19,10 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB_NAME = "libsph.so"
 LIB_PATH = os.path.join(OUT_DIR, LIB_NAME)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# host code: no FMA contraction, so that the host-side conversion rounds
+# exactly as written (and as the device kernels do)
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
-              "-I", INCLUDE, "-I", CSRC]
+              "-Xcompiler", "-ffp-contract=off", "-I", INCLUDE, "-I", CSRC]
 
 
 def nvcc() -> str:

@@ -1,0 +1,292 @@
+// The conversion operators on the host: the paper's CPU placement (Section
+// 6.3, Eq. 13-14: U o N o C on the host, then M moves the SoA to the device;
+// the write-back moves the SoA back and scatters it there).  The device
+// kernels (k_convert.cu) are the GPU placement; both produce the same codes.
+//
+// Host threads split the sorted slots into ranges of whole 32-slot blocks,
+// so that every packed word belongs to one thread.  Each thread reads its
+// slots' records in permutation order, rounds each component the way the
+// device does (IEEE round-to-nearest-even FP64 -> FP32 by the C++ cast, then
+// the shared encoders of sph_internal.cuh) and writes the SoA image in a
+// caller-provided staging buffer; the image then moves with one copy per
+// component array.  The permutation (and the cell keys or buffer origins
+// the positions need) come from the device first.
+#include <algorithm>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+#include "sph_internal.cuh"
+
+namespace sph {
+namespace {
+
+struct StageLayout {
+    size_t perm, keys, origin, soa[SPH_NFIELDS][3], total;
+};
+
+// perm (4 B per slot), cell keys (4 B per slot), buffer origins (3 doubles
+// per 32 slots), then every SoA array at its device size
+StageLayout stage_layout(const sph_ctx *c)
+{
+    StageLayout s;
+    std::memset(&s, 0, sizeof(s));
+    const size_t n = (size_t)c->n;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += (bytes + 255) & ~(size_t)255;
+        return o;
+    };
+    s.perm = take(4 * n);
+    s.keys = take(4 * n);
+    s.origin = take(sizeof(double) * 3 * (n / 32 + 1));
+    for (int f = 0; f < SPH_NFIELDS; ++f)
+        for (int k = 0; k < ncomp(f); ++k) s.soa[f][k] = take(4 * n + 64);
+    s.total = off;
+    return s;
+}
+
+// bytes of one SoA component array in format fmt
+size_t soa_bytes(int64_t n, int fmt)
+{
+    if (fmt_packed(fmt)) return (size_t)((n * fmt_bits(fmt) + 31) / 32) * 4;
+    return (size_t)n * (fmt == SPH_P_BF16 || fmt == SPH_P_FP16 ? 2 : 4);
+}
+
+float decode(const void *p, int fmt, int64_t k)
+{
+    switch (fmt) {
+    case SPH_P_BF16: return dec_bf16(static_cast<const uint16_t *>(p)[k]);
+    case SPH_P_FP16: return __half2float(static_cast<const __half *>(p)[k]);
+    case SPH_P_FP32: return static_cast<const float *>(p)[k];
+    default: {
+        const int B = fmt_bits(fmt);
+        const uint32_t *w = static_cast<const uint32_t *>(p);
+        const int64_t bit = k * (int64_t)B;
+        const int64_t wi = bit >> 5;
+        const int sh = (int)(bit & 31);
+        uint64_t two = w[wi];
+        if (sh + B > 32) two |= (uint64_t)w[wi + 1] << 32;
+        const uint32_t code = (uint32_t)(two >> sh) & ((1u << B) - 1u);
+        return f32_from_bits(code << (32 - B));
+    }
+    }
+}
+
+// one component of every slot in [k0, k1) (k0 a multiple of 32): values from
+// `value(k)`, already scaled, encoded into the array at p
+template <typename F>
+void encode_range(void *p, int fmt, int64_t k0, int64_t k1, F value)
+{
+    if (!fmt_packed(fmt)) {
+        for (int64_t k = k0; k < k1; ++k) {
+            const float v = value(k);
+            switch (fmt) {
+            case SPH_P_BF16: static_cast<uint16_t *>(p)[k] = enc_bf16(v); break;
+            case SPH_P_FP16: static_cast<__half *>(p)[k] = __float2half_rn(v); break;
+            default: static_cast<float *>(p)[k] = v; break;
+            }
+        }
+        return;
+    }
+    // packed: value k at bits [kB, (k+1)B); 32 values fill B whole words
+    const int B = fmt_bits(fmt);
+    uint32_t *w = static_cast<uint32_t *>(p);
+    for (int64_t b0 = k0; b0 < k1; b0 += 32) {
+        uint32_t words[32] = {};
+        for (int j = 0; j < 32; ++j) {
+            const int64_t k = b0 + j;
+            const uint32_t code = k < k1 ? enc_trunc(value(k), B) : 0u;
+            const int bit = j * B;
+            words[bit >> 5] |= code << (bit & 31);
+            if ((bit & 31) + B > 32) words[(bit >> 5) + 1] |= code >> (32 - (bit & 31));
+        }
+        const int64_t wbase = (b0 / 32) * B;
+        const int64_t nw = ((k1 - b0 >= 32) ? B : ((k1 - b0) * B + 31) / 32);
+        for (int64_t i = 0; i < nw; ++i) w[wbase + i] = words[i];
+    }
+}
+
+template <typename F>
+void parallel_blocks(int64_t n, int nthreads, F body)
+{
+    const int64_t nblk = (n + 31) / 32;
+    const int T = (int)std::max<int64_t>(1, std::min<int64_t>(nthreads, nblk));
+    if (T == 1) {
+        body((int64_t)0, n);
+        return;
+    }
+    std::vector<std::thread> pool;
+    pool.reserve((size_t)T);
+    for (int t = 0; t < T; ++t) {
+        const int64_t k0 = std::min(n, (nblk * t / T) * 32);
+        const int64_t k1 = std::min(n, (nblk * (t + 1) / T) * 32);
+        pool.emplace_back([=] { body(k0, k1); });
+    }
+    for (auto &th : pool) th.join();
+}
+
+int default_threads(int32_t nthreads)
+{
+    if (nthreads > 0) return nthreads;
+    const unsigned hw = std::thread::hardware_concurrency();
+    return hw ? (int)hw : 1;
+}
+
+double rec_value(const uint8_t *rec, const sph_aos_layout &L, int f, int comp)
+{
+    const uint8_t *p = rec + L.offset[f];
+    if (L.type[f] == SPH_AOS_F64) {
+        double d;
+        std::memcpy(&d, p + 8 * comp, 8);
+        return d;
+    }
+    float x;
+    std::memcpy(&x, p + 4 * comp, 4);
+    return (double)x;
+}
+
+}  // namespace
+
+size_t host_stage_bytes(const sph_ctx *c) { return stage_layout(c).total; }
+
+cudaError_t run_aos_to_soa_host(sph_ctx *c, const uint8_t *host_aos, uint32_t fields, uint8_t *stage,
+                                int32_t nthreads)
+{
+    if (c->n == 0) return cudaSuccess;
+    const StageLayout S = stage_layout(c);
+    const int64_t n = c->n;
+    const bool want_x = (fields & SPH_BIT(SPH_F_X)) != 0;
+    cudaError_t e;
+    // the slot order (and what the position offsets need) from the device
+    if ((e = cudaMemcpyAsync(stage + S.perm, c->perm(), 4 * (size_t)n, cudaMemcpyDeviceToHost, c->stream)) !=
+        cudaSuccess)
+        return e;
+    const int64_t nbuf = c->buffer ? (n + c->buffer - 1) / c->buffer : 0;
+    if (want_x && c->buffer) {
+        if ((e = cudaMemcpyAsync(stage + S.origin, c->buf_origin, sizeof(double) * 3 * (size_t)nbuf,
+                                 cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
+            return e;
+    } else if (want_x) {
+        if ((e = cudaMemcpyAsync(stage + S.keys, c->slot_cell(), 4 * (size_t)n, cudaMemcpyDeviceToHost, c->stream)) !=
+            cudaSuccess)
+            return e;
+    }
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return e;
+    const int32_t *perm = reinterpret_cast<const int32_t *>(stage + S.perm);
+    const int32_t *keys = reinterpret_cast<const int32_t *>(stage + S.keys);
+    const double *bufo = reinterpret_cast<const double *>(stage + S.origin);
+    const sph_aos_layout L = c->layout;
+    const int64_t rb = L.record_bytes;
+    const int lgB = c->buffer ? 31 - __builtin_clz((unsigned)c->buffer) : 0;
+    const int s3 = c->sub * c->sub * c->sub;
+    double edge[3];
+    for (int d = 0; d < 3; ++d) edge[d] = c->edge[d];
+    const int nc0 = c->nc[0], nc1 = c->nc[1];
+    const double box[3] = {c->params.box[0], c->params.box[1], c->params.box[2]};
+
+    parallel_blocks(n, default_threads(nthreads), [&](int64_t k0, int64_t k1) {
+        for (int f = 0; f < SPH_NFIELDS; ++f) {
+            if (!(fields & SPH_BIT(f))) continue;
+            const int fmt = c->prec[f];
+            const float enc = c->enc(f);
+            for (int comp = 0; comp < ncomp(f); ++comp) {
+                void *dst = stage + S.soa[f][comp];
+                encode_range(dst, fmt, k0, k1, [&](int64_t k) {
+                    const uint8_t *rec = host_aos + (int64_t)perm[k] * rb;
+                    const double x = rec_value(rec, L, f, comp);
+                    float v;
+                    if (f != SPH_F_X) {
+                        v = (float)x;                                  // round to nearest, ties to even
+                    } else if (c->buffer) {
+                        const double o = bufo[comp * nbuf + (k >> lgB)];
+                        const double Lb = box[comp];
+                        double d = x - o;
+                        if (d >= 0.5 * Lb) d = d - Lb;
+                        else if (d < -0.5 * Lb) d = d + Lb;
+                        v = (float)d;
+                    } else {
+                        // the cell's coordinate on this axis from its key, origin k * edge
+                        const int cell = keys[k] / s3;
+                        const int kc = comp == 0 ? cell % nc0 : (comp == 1 ? (cell / nc0) % nc1 : cell / (nc0 * nc1));
+                        const double o = (double)kc * edge[comp];
+                        v = (float)(x - o);
+                    }
+                    return v * enc;
+                });
+            }
+        }
+    });
+    // move the SoA image: one copy per component array
+    for (int f = 0; f < SPH_NFIELDS; ++f) {
+        if (!(fields & SPH_BIT(f))) continue;
+        for (int comp = 0; comp < ncomp(f); ++comp)
+            if ((e = cudaMemcpyAsync(c->soa[f][comp], stage + S.soa[f][comp], soa_bytes(n, c->prec[f]),
+                                     cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
+                return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t run_soa_to_aos_host(sph_ctx *c, uint8_t *host_aos, uint32_t fields, uint8_t *stage, int32_t nthreads)
+{
+    if (c->n == 0) return cudaSuccess;
+    const StageLayout S = stage_layout(c);
+    const int64_t n = c->n;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(stage + S.perm, c->perm(), 4 * (size_t)n, cudaMemcpyDeviceToHost, c->stream)) !=
+        cudaSuccess)
+        return e;
+    const int64_t nbuf = c->buffer ? (n + c->buffer - 1) / c->buffer : 0;
+    if ((fields & SPH_BIT(SPH_F_X)) &&
+        (e = cudaMemcpyAsync(stage + S.origin, c->buf_origin, sizeof(double) * 3 * (size_t)nbuf,
+                             cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
+        return e;
+    for (int f = 0; f < SPH_NFIELDS; ++f) {
+        if (!(fields & SPH_BIT(f))) continue;
+        for (int comp = 0; comp < ncomp(f); ++comp)
+            if ((e = cudaMemcpyAsync(stage + S.soa[f][comp], c->soa[f][comp], soa_bytes(n, c->prec[f]),
+                                     cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
+                return e;
+    }
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return e;
+    const int32_t *perm = reinterpret_cast<const int32_t *>(stage + S.perm);
+    const double *bufo = reinterpret_cast<const double *>(stage + S.origin);
+    const sph_aos_layout L = c->layout;
+    const int64_t rb = L.record_bytes;
+    const int lgB = c->buffer ? 31 - __builtin_clz((unsigned)c->buffer) : 0;
+    const double box[3] = {c->params.box[0], c->params.box[1], c->params.box[2]};
+
+    parallel_blocks(n, default_threads(nthreads), [&](int64_t k0, int64_t k1) {
+        for (int64_t k = k0; k < k1; ++k) {
+            uint8_t *rec = host_aos + (int64_t)perm[k] * rb;
+            for (int f = 0; f < SPH_NFIELDS; ++f) {
+                if (!(fields & SPH_BIT(f))) continue;
+                const float dec = c->dec(f);
+                for (int comp = 0; comp < ncomp(f); ++comp) {
+                    const float v = decode(stage + S.soa[f][comp], c->prec[f], k) * dec;
+                    uint8_t *p = rec + L.offset[f];
+                    if (L.type[f] != SPH_AOS_F64) {
+                        std::memcpy(p + 4 * comp, &v, 4);
+                    } else if (f == SPH_F_X) {
+                        // buffer mode: origin + offset, wrapped into [0, L)
+                        const double Lb = box[comp];
+                        double y = bufo[comp * nbuf + (k >> lgB)] + (double)v;
+                        if (y < 0.0 || y >= Lb) {
+                            y = y - Lb * std::floor(y / Lb);
+                            if (y >= Lb) y = 0.0;
+                        }
+                        std::memcpy(p + 8 * comp, &y, 8);
+                    } else {
+                        const double d = (double)v;                  // exact widening
+                        std::memcpy(p + 8 * comp, &d, 8);
+                    }
+                }
+            }
+        }
+    });
+    return cudaSuccess;
+}
+
+}  // namespace sph

@@ -277,6 +277,44 @@ sph_status sph_set_field_scale(sph_ctx *c, const int32_t *exp2)
     return SPH_OK;
 }
 
+size_t sph_host_stage_bytes(const sph_ctx *c) { return c ? host_stage_bytes(c) : 0; }
+
+sph_status sph_aos_to_soa_host(sph_ctx *c, const void *host_aos, uint32_t fields, const int32_t *prec,
+                               void *host_stage, size_t stage_bytes, int32_t nthreads)
+{
+    if (!c || (!host_aos && c->n > 0) || (!host_stage && c->n > 0)) return SPH_EINVAL;
+    if (fields == 0 || (fields >> SPH_NFIELDS) != 0) return SPH_EINVAL;
+    for (int f = 0; f < SPH_NFIELDS; ++f) {
+        if (!(fields & SPH_BIT(f))) continue;
+        if (c->layout.offset[f] < 0) return SPH_EINVAL;
+        if (!fmt_allowed(f, prec ? prec[f] : SPH_P_FP32)) return SPH_EINVAL;
+    }
+    if (stage_bytes < host_stage_bytes(c)) return SPH_ENOSPACE;
+    if (!c->binned) return SPH_ESTATE;
+    for (int f = 0; f < SPH_NFIELDS; ++f)
+        if (fields & SPH_BIT(f)) c->prec[f] = prec ? prec[f] : SPH_P_FP32;
+    if (run_aos_to_soa_host(c, (const uint8_t *)host_aos, fields, (uint8_t *)host_stage, nthreads) != cudaSuccess)
+        return SPH_ECUDA;
+    c->valid |= fields;
+    return SPH_OK;
+}
+
+sph_status sph_soa_to_aos_host(sph_ctx *c, void *host_aos, uint32_t fields, void *host_stage, size_t stage_bytes,
+                               int32_t nthreads)
+{
+    if (!c || (!host_aos && c->n > 0) || (!host_stage && c->n > 0)) return SPH_EINVAL;
+    if (fields == 0 || (fields >> SPH_NFIELDS) != 0) return SPH_EINVAL;
+    if ((fields & SPH_BIT(SPH_F_X)) && !c->buffer) return SPH_EINVAL;
+    for (int f = 0; f < SPH_NFIELDS; ++f)
+        if ((fields & SPH_BIT(f)) && c->layout.offset[f] < 0) return SPH_EINVAL;
+    if (stage_bytes < host_stage_bytes(c)) return SPH_ENOSPACE;
+    if (!c->binned) return SPH_ESTATE;
+    if ((c->valid & fields) != fields) return SPH_ESTATE;
+    if (run_soa_to_aos_host(c, (uint8_t *)host_aos, fields, (uint8_t *)host_stage, nthreads) != cudaSuccess)
+        return SPH_ECUDA;
+    return SPH_OK;
+}
+
 sph_status sph_get_field_scale(const sph_ctx *c, int32_t *exp2_out)
 {
     if (!c || !exp2_out) return SPH_EINVAL;

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstddef>
 #include <cstdint>
+#include <cstring>
 
 #include "sph.h"
 
@@ -95,21 +96,43 @@ __host__ __device__ inline bool fmt_packed(int fmt)
     return fmt == SPH_P_FP32_M16 || fmt == SPH_P_FP32_M10 || fmt_trunc_any(fmt);
 }
 
-__device__ __forceinline__ float dec_bf16(uint16_t b) { return __uint_as_float((uint32_t)b << 16); }
+// bit casts usable on both sides (the host-side conversion shares the encoders)
+__host__ __device__ __forceinline__ uint32_t f32_bits(float f)
+{
+#ifdef __CUDA_ARCH__
+    return __float_as_uint(f);
+#else
+    uint32_t u;
+    std::memcpy(&u, &f, sizeof(u));
+    return u;
+#endif
+}
+__host__ __device__ __forceinline__ float f32_from_bits(uint32_t u)
+{
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(u);
+#else
+    float f;
+    std::memcpy(&f, &u, sizeof(f));
+    return f;
+#endif
+}
+
+__host__ __device__ __forceinline__ float dec_bf16(uint16_t b) { return f32_from_bits((uint32_t)b << 16); }
 
 // round to nearest, ties to even, on the upper 16 bits; NaN stays a quiet NaN
-__device__ __forceinline__ uint16_t enc_bf16(float f)
+__host__ __device__ __forceinline__ uint16_t enc_bf16(float f)
 {
-    uint32_t u = __float_as_uint(f);
+    uint32_t u = f32_bits(f);
     if ((u & 0x7F800000u) == 0x7F800000u && (u & 0x7FFFFFu)) return (uint16_t)((u >> 16) | 0x40u);
     u += 0x7FFFu + ((u >> 16) & 1u);
     return (uint16_t)(u >> 16);
 }
 
 // truncated single: keep the top B bits (sign, exponent, B-9 mantissa bits)
-__device__ __forceinline__ uint32_t enc_trunc(float f, int B)
+__host__ __device__ __forceinline__ uint32_t enc_trunc(float f, int B)
 {
-    uint32_t u = __float_as_uint(f);
+    uint32_t u = f32_bits(f);
     if ((u & 0x7F800000u) == 0x7F800000u && (u & 0x7FFFFFu)) u |= 0x400000u;
     return u >> (32 - B);
 }
@@ -306,6 +329,11 @@ cudaError_t run_soa_to_aos(sph_ctx *c, uint32_t fields);
 cudaError_t run_density(sph_ctx *c, int newton_steps);
 cudaError_t run_force(sph_ctx *c);
 cudaError_t run_kick_drift(sph_ctx *c, double dt_kick, double dt_drift, uint32_t wb_fields);
+// host-side conversion (host_convert.cu)
+size_t host_stage_bytes(const sph_ctx *c);
+cudaError_t run_aos_to_soa_host(sph_ctx *c, const uint8_t *host_aos, uint32_t fields, uint8_t *stage,
+                                int32_t nthreads);
+cudaError_t run_soa_to_aos_host(sph_ctx *c, uint8_t *host_aos, uint32_t fields, uint8_t *stage, int32_t nthreads);
 // buffer mode (k_buffers.cu)
 cudaError_t run_bin_buffers(sph_ctx *c);
 cudaError_t run_buffer_density(sph_ctx *c, int source);
