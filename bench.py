@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-vs-plain", action="store_true", help="skip the plain FP32 SoA comparison")
     ap.add_argument("--no-streaming", action="store_true", help="skip the host-resident AoS comparison")
     ap.add_argument("--no-buffers", action="store_true", help="skip the 64-particle-buffer AoS/SoA comparison")
+    ap.add_argument("--no-placement", action="store_true", help="skip the host-vs-GPU conversion placement rows")
     ap.add_argument("--profile-case", choices=["pairs", "memory", "buffers"], default=None,
                     help="run one small fixed workload for an ncu capture and exit")
     return ap.parse_args()
@@ -632,6 +633,80 @@ def run_buffers(nb=(64, 64, 32), reps: int = 5):
     return out
 
 
+def run_placement(reps: int = 5):
+    """Where the conversion runs (Section 6.3, Fig. 1): the Sod records in
+    pinned host memory end up as SoA in device memory either by moving the
+    AoS and converting on the GPU (one upload, then sph_aos_to_soa), or by
+    converting on the host cores and moving the narrowed SoA
+    (sph_aos_to_soa_host: the permutation comes down, the SoA goes up), or by
+    GPU kernels reading the host records in place (no copy).  Per kernel's
+    field set (density, force, kick, drift, full record) in 32-bit storage
+    and in 16-bit storage (FP16 under power-of-two scales; a stays FP32).
+    Times: CUDA events for the GPU placements, the host clock around the
+    synchronised host call for the CPU one; mean over `reps` after a
+    warm-up."""
+    import torch
+    import paper_2512_05516_gb300 as sph
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    wl = sph_inputs.sod()
+    n = wl.n
+    stream = torch.cuda.Stream(dev)
+    nc = [int(math.floor(b / max(wl.cell_edge, 2 * wl.h_cap))) for b in wl.box]
+    params = sph.make_params(wl.box, gamma=wl.gamma, alpha=wl.alpha_av, beta=wl.beta_av,
+                             eps=wl.eps_av, eta=wl.eta, h_max=wl.h_cap)
+    host = torch.from_numpy(np.ascontiguousarray(wl.aos)).pin_memory()
+    s = sph.Sph(host.to(dev), sph.layout_112(), params, int(np.prod(nc)), 0, stream=stream)
+    sh = sph.Sph(host, sph.layout_112(), params, int(np.prod(nc)), 0, stream=stream)   # kernels on host records
+    sets = {"density": sph.FIELDS_DENSITY, "force": sph.FIELDS_FORCE, "kick": sph.mask("v", "a", "u"),
+            "drift": sph.mask("x", "v"), "full": sph.mask("x", "v", "a", "m", "h", "rho", "u", "P")}
+    half = {"x": "fp16", "v": "fp16", "m": "fp16", "h": "fp16", "u": "fp16", "rho": "fp16", "P": "fp16"}
+    scale16 = {k: sph.suggest_scale(float(np.abs(wl.col(k)).max()), "fp16") for k in ("v", "m", "h", "u", "rho", "P")}
+    cores = os.cpu_count() or 1
+
+    def ev_time(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fn()
+        stream.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def wall_time(fn):
+        fn()
+        stream.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+            stream.synchronize()
+        return (time.perf_counter() - t0) / reps * 1e3
+
+    rows = {}
+    with torch.cuda.stream(stream):
+        for ctx in (s, sh):
+            ctx.bin_cells(wl.cell_edge)
+        for bits, prec, scale in (("32", None, {}), ("16", half, scale16)):
+            for ctx in (s, sh):
+                ctx.set_scale(scale)
+            for name, fields in sets.items():
+                pr = None if prec is None else {k: v for k, v in prec.items() if fields & sph.mask(k)}
+                gpu = ev_time(lambda: (sph._check(sph.sph_aos_upload(s.ctx, host.data_ptr(), n * 112), "upload"),
+                                       s.aos_to_soa(fields, pr)))
+                in_place = ev_time(lambda: sh.aos_to_soa(fields, pr))
+                cpu = wall_time(lambda: s.aos_to_soa_host(host, fields, pr))
+                rows[f"{name}_{bits}bit"] = {"gpu_move_then_convert_ms": gpu, "gpu_kernels_on_host_records_ms": in_place,
+                                            "cpu_convert_then_move_ms": cpu, "gpu_speedup_over_cpu": cpu / gpu}
+        for ctx in (s, sh):
+            ctx.set_scale({})
+    s.close()
+    sh.close()
+    return {"workload": f"sod_{n}", "host_threads": cores, "rows": rows,
+            "note": "paper, Fig. 1 (other hardware, context): GPU conversion up to 35x faster than the CPU's "
+                    "in 32-bit and up to 500x in 16-bit on GH200 and MI300A"}
+
+
 def run_uneven(n: int = 16_777_216):
     """Uneven occupancy (the clustered Gaussian mixture, one global h, up to
     ~65,000 particles in a cell), BF16 storage of v, m, h, u: one density
@@ -868,6 +943,7 @@ def main():
     vs_plain = None if args.no_vs_plain or world > 1 else run_vs_plain()
     streaming = None if args.no_streaming or world > 1 else run_streaming()
     buffers = None if args.no_buffers or world > 1 else run_buffers()
+    placement = None if args.no_placement or world > 1 else run_placement()
     out = {
         "metric": METRIC, "value": pairs / total_s, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
@@ -883,6 +959,7 @@ def main():
         "memory_bound_rows": long, "uneven_batching": uneven, "vs_plain_fp32_soa": vs_plain,
         "streaming_vs_in_place": streaming,
         "buffers_aos_vs_soa": buffers,
+        "conversion_placement": placement,
     }
     print(json.dumps(out))
     if world > 1:
