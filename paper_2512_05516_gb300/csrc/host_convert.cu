@@ -4,10 +4,12 @@
 // kernels (k_convert.cu) are the GPU placement; both produce the same codes.
 //
 // Host threads split the sorted slots into ranges of whole 32-slot blocks,
-// so that every packed word belongs to one thread.  Each thread reads its
-// slots' records in permutation order, rounds each component the way the
-// device does (IEEE round-to-nearest-even FP64 -> FP32 by the C++ cast, then
-// the shared encoders of sph_internal.cuh) and writes the SoA image in a
+// so that every packed word belongs to one thread.  Each thread walks its
+// blocks: it reads every record of a block once, in permutation order (the
+// records of a block several blocks ahead are prefetched, since the gather
+// is the cost), rounds each component the way the device does (IEEE
+// round-to-nearest-even FP64 -> FP32 by the C++ cast, then the shared
+// encoders of sph_internal.cuh) and writes the block into the SoA image in a
 // caller-provided staging buffer; the image then moves with one copy per
 // component array.  The permutation (and the cell keys or buffer origins
 // the positions need) come from the device first.
@@ -74,38 +76,34 @@ float decode(const void *p, int fmt, int64_t k)
     }
 }
 
-// one component of every slot in [k0, k1) (k0 a multiple of 32): values from
-// `value(k)`, already scaled, encoded into the array at p
-template <typename F>
-void encode_range(void *p, int fmt, int64_t k0, int64_t k1, F value)
+// the 32-slot block starting at b0 (a multiple of 32; slots >= n get code 0)
+// of one component, values vals[0..31] already scaled, into the array at p
+void encode_block(void *p, int fmt, int64_t b0, int64_t n, const float *vals)
 {
+    const int cnt = (int)std::min<int64_t>(32, n - b0);
     if (!fmt_packed(fmt)) {
-        for (int64_t k = k0; k < k1; ++k) {
-            const float v = value(k);
+        for (int j = 0; j < cnt; ++j) {
+            const int64_t k = b0 + j;
             switch (fmt) {
-            case SPH_P_BF16: static_cast<uint16_t *>(p)[k] = enc_bf16(v); break;
-            case SPH_P_FP16: static_cast<__half *>(p)[k] = __float2half_rn(v); break;
-            default: static_cast<float *>(p)[k] = v; break;
+            case SPH_P_BF16: static_cast<uint16_t *>(p)[k] = enc_bf16(vals[j]); break;
+            case SPH_P_FP16: static_cast<__half *>(p)[k] = __float2half_rn(vals[j]); break;
+            default: static_cast<float *>(p)[k] = vals[j]; break;
             }
         }
         return;
     }
     // packed: value k at bits [kB, (k+1)B); 32 values fill B whole words
     const int B = fmt_bits(fmt);
-    uint32_t *w = static_cast<uint32_t *>(p);
-    for (int64_t b0 = k0; b0 < k1; b0 += 32) {
-        uint32_t words[32] = {};
-        for (int j = 0; j < 32; ++j) {
-            const int64_t k = b0 + j;
-            const uint32_t code = k < k1 ? enc_trunc(value(k), B) : 0u;
-            const int bit = j * B;
-            words[bit >> 5] |= code << (bit & 31);
-            if ((bit & 31) + B > 32) words[(bit >> 5) + 1] |= code >> (32 - (bit & 31));
-        }
-        const int64_t wbase = (b0 / 32) * B;
-        const int64_t nw = ((k1 - b0 >= 32) ? B : ((k1 - b0) * B + 31) / 32);
-        for (int64_t i = 0; i < nw; ++i) w[wbase + i] = words[i];
+    uint32_t words[32] = {};
+    for (int j = 0; j < 32; ++j) {
+        const uint32_t code = j < cnt ? enc_trunc(vals[j], B) : 0u;
+        const int bit = j * B;
+        words[bit >> 5] |= code << (bit & 31);
+        if ((bit & 31) + B > 32) words[(bit >> 5) + 1] |= code >> (32 - (bit & 31));
     }
+    uint32_t *w = static_cast<uint32_t *>(p) + (b0 / 32) * B;
+    const int nw = cnt == 32 ? B : (cnt * B + 31) / 32;
+    for (int i = 0; i < nw; ++i) w[i] = words[i];
 }
 
 template <typename F>
@@ -186,15 +184,33 @@ cudaError_t run_aos_to_soa_host(sph_ctx *c, const uint8_t *host_aos, uint32_t fi
     const int nc0 = c->nc[0], nc1 = c->nc[1];
     const double box[3] = {c->params.box[0], c->params.box[1], c->params.box[2]};
 
-    parallel_blocks(n, default_threads(nthreads), [&](int64_t k0, int64_t k1) {
-        for (int f = 0; f < SPH_NFIELDS; ++f) {
-            if (!(fields & SPH_BIT(f))) continue;
-            const int fmt = c->prec[f];
-            const float enc = c->enc(f);
+    // the components to convert: field, component
+    int cf[3 * SPH_NFIELDS], cc[3 * SPH_NFIELDS], nc_tot = 0;
+    float cenc[3 * SPH_NFIELDS];
+    for (int f = 0; f < SPH_NFIELDS; ++f)
+        if (fields & SPH_BIT(f))
             for (int comp = 0; comp < ncomp(f); ++comp) {
-                void *dst = stage + S.soa[f][comp];
-                encode_range(dst, fmt, k0, k1, [&](int64_t k) {
-                    const uint8_t *rec = host_aos + (int64_t)perm[k] * rb;
+                cf[nc_tot] = f;
+                cenc[nc_tot] = c->enc(f);
+                cc[nc_tot++] = comp;
+            }
+    constexpr int kAhead = 4;      // blocks prefetched ahead of the one converted
+
+    parallel_blocks(n, default_threads(nthreads), [&](int64_t k0, int64_t k1) {
+        float vals[3 * SPH_NFIELDS][32];
+        for (int64_t b0 = k0; b0 < k1; b0 += 32) {
+            const int64_t pf0 = b0 + 32 * kAhead, pf1 = std::min(k1, pf0 + 32);
+            for (int64_t k = pf0; k < pf1; ++k) {
+                const uint8_t *r = host_aos + (int64_t)perm[k] * rb;
+                __builtin_prefetch(r);
+                __builtin_prefetch(r + rb - 1);
+            }
+            const int cnt = (int)std::min<int64_t>(32, k1 - b0);
+            for (int j = 0; j < cnt; ++j) {
+                const int64_t k = b0 + j;
+                const uint8_t *rec = host_aos + (int64_t)perm[k] * rb;
+                for (int i = 0; i < nc_tot; ++i) {
+                    const int f = cf[i], comp = cc[i];
                     const double x = rec_value(rec, L, f, comp);
                     float v;
                     if (f != SPH_F_X) {
@@ -213,9 +229,11 @@ cudaError_t run_aos_to_soa_host(sph_ctx *c, const uint8_t *host_aos, uint32_t fi
                         const double o = (double)kc * edge[comp];
                         v = (float)(x - o);
                     }
-                    return v * enc;
-                });
+                    vals[i][j] = v * cenc[i];
+                }
             }
+            for (int i = 0; i < nc_tot; ++i)
+                encode_block(stage + S.soa[cf[i]][cc[i]], c->prec[cf[i]], b0, k1, vals[i]);
         }
     });
     // move the SoA image: one copy per component array
@@ -260,6 +278,11 @@ cudaError_t run_soa_to_aos_host(sph_ctx *c, uint8_t *host_aos, uint32_t fields, 
 
     parallel_blocks(n, default_threads(nthreads), [&](int64_t k0, int64_t k1) {
         for (int64_t k = k0; k < k1; ++k) {
+            if (k + 128 < k1) {
+                uint8_t *r = host_aos + (int64_t)perm[k + 128] * rb;
+                __builtin_prefetch(r, 1);
+                __builtin_prefetch(r + rb - 1, 1);
+            }
             uint8_t *rec = host_aos + (int64_t)perm[k] * rb;
             for (int f = 0; f < SPH_NFIELDS; ++f) {
                 if (!(fields & SPH_BIT(f))) continue;
