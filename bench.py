@@ -698,6 +698,16 @@ def run_placement(reps: int = 5):
                 cpu = wall_time(lambda: s.aos_to_soa_host(host, fields, pr))
                 rows[f"{name}_{bits}bit"] = {"gpu_move_then_convert_ms": gpu, "gpu_kernels_on_host_records_ms": in_place,
                                             "cpu_convert_then_move_ms": cpu, "gpu_speedup_over_cpu": cpu / gpu}
+            # the way back (C^T N^T U^T): the step's outputs to the host records
+            out = sph.FIELDS_OUTPUT
+            pr = None if prec is None else {k: v for k, v in prec.items() if out & sph.mask(k)}
+            s.aos_to_soa(out, pr)
+            back = host.clone().pin_memory()
+            gpu = ev_time(lambda: (s.soa_to_aos(out),
+                                   sph._check(sph.sph_aos_download(s.ctx, back.data_ptr(), n * 112), "download")))
+            cpu = wall_time(lambda: s.soa_to_aos_host(back, out))
+            rows[f"write_back_{bits}bit"] = {"gpu_convert_then_move_ms": gpu, "cpu_move_then_convert_ms": cpu,
+                                             "gpu_speedup_over_cpu": cpu / gpu}
         for ctx in (s, sh):
             ctx.set_scale({})
     s.close()
