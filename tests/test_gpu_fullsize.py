@@ -114,3 +114,38 @@ def test_gaussian_mixture_uneven_cells(orc):
     cnt = np.empty(wl.n, np.int32)
     cnt[s.perm().cpu().numpy()] = s.nngb().cpu().numpy()
     assert np.abs(cnt[targets] - o["nngb"]).max() <= 2
+
+
+def test_gaussian_mixture_16777216_bf16_sampled(orc):
+    # the uneven-occupancy workload at full size, BF16 storage of v, m, h, u
+    # as bench.py runs it: densest cell ~65,000 particles, core particles with
+    # ~10^5 neighbours; the oracle evaluates sampled targets (core ones
+    # included) on the same BF16-rounded m and h (mode Q)
+    import paper_2512_05516_gb300 as sph
+    wl = sph_inputs.gaussian_mixture(n=16_777_216)
+    assert wl.n == 16_777_216
+    prec = {"v": "bf16", "m": "bf16", "h": "bf16", "u": "bf16"}
+    s = make_sph(wl)
+    s.bin_cells(wl.cell_edge)
+    st = s.stats()
+    assert st["max_occupancy"] > 60000
+    s.aos_to_soa(sph.FIELDS_DENSITY, prec)
+    s.density(0)
+    s.soa_to_aos(sph.mask("rho"))
+    rho = s.aos.cpu().numpy()[:, 11]
+    assert s.stats()["error_bits"] == 0
+    x = wl.col("x")
+    centre = wl.meta["centres"][0]                 # the sigma = 0.01 Gaussian
+    d = x - centre
+    d -= np.round(d)
+    core = np.argsort(np.sum(d * d, axis=1))[:40]
+    targets = _sample(wl, 160, core, seed=4)
+    mq = orc.quantize(wl.col("m"), "bf16")[0]
+    hq = orc.quantize(wl.col("h"), "bf16")[0]
+    o = orc.density(x, mq, hq, wl.box, wl.eta, wl.h_cap, 0, targets=targets)
+    assert (np.abs(rho[targets] - o["rho"]) / o["rho"]).max() <= 1e-5
+    assert o["nngb"].max() > 50000                  # some targets sit in the dense core
+    cnt = np.empty(wl.n, np.int32)
+    cnt[s.perm().cpu().numpy()] = s.nngb().cpu().numpy()
+    assert np.abs(cnt[targets] - o["nngb"]).max() <= 2
+    s.close()
