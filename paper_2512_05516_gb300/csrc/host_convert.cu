@@ -115,12 +115,23 @@ void parallel_blocks(int64_t n, int nthreads, F body)
         body((int64_t)0, n);
         return;
     }
+    // no exception may cross the C ABI: a thread that cannot be started
+    // leaves its range to the calling thread
     std::vector<std::thread> pool;
-    pool.reserve((size_t)T);
+    try {
+        pool.reserve((size_t)T);
+    } catch (...) {
+    }
     for (int t = 0; t < T; ++t) {
         const int64_t k0 = std::min(n, (nblk * t / T) * 32);
         const int64_t k1 = std::min(n, (nblk * (t + 1) / T) * 32);
-        pool.emplace_back([=] { body(k0, k1); });
+        bool started = false;
+        try {
+            pool.emplace_back([=] { body(k0, k1); });
+            started = true;
+        } catch (...) {
+        }
+        if (!started) body(k0, k1);
     }
     for (auto &th : pool) th.join();
 }
