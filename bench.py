@@ -36,7 +36,11 @@ import sph_inputs  # noqa: E402
 
 METRIC = "SPH pair-interactions/s (density+force)"
 UNIT = "pairs/s"
-FLOPS_PER_PAIR = {"density": 29, "force": 50}   # counting convention, see the design doc
+# flops per interacting pair (FMA 2; add, mul, compare, rsqrt 1): density 29 =
+# distance 8 + r and q 3 + spline and derivative 11 + compensated sum 4 + dh
+# sum 3; force 50 = distance 8 + r, mean h and q 6 + spline derivative 3 +
+# gradient 4 + v.r 8 + viscosity 13 + accumulation 8
+FLOPS_PER_PAIR = {"density": 29, "force": 50}
 L2_FLUSH_BYTES = 512 << 20
 
 
