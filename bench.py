@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--lattice", type=int, default=124, help="Sod lattice (124 -> 1,072,476 particles)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="time eager steps instead of graph replays")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--prec", default="fp32", help="SoA storage of v, m, h, u (fp32|bf16|fp16|m16|m10)")
     ap.add_argument("--no-long-run", action="store_true", help="skip the 33.5M-particle memory-bound rows")
@@ -223,11 +224,37 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize(dev)
         if world > 1:
             dist.barrier()
-        clk = clocks.stop()
         st = s.stats()
         launches = st["launches"] - launches0
         step_ms = [a.elapsed_time(b) for a, b in ev_step]
+        step_ms_eager = step_ms
         kern_ms = {nm: [ev_k[k][i][0].elapsed_time(ev_k[k][i][1]) for k in range(K)] for i, nm in enumerate(names)}
+        if not args.no_graph:
+            # the same step captured once as a CUDA graph and replayed K times
+            # (L2 flushed between replays): the timed steps of the result
+            l0 = s.stats()["launches"]
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                step()
+            per_step = s.stats()["launches"] - l0
+            s.reset_stats()
+            ev_g = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+            if world > 1:
+                dist.barrier()
+            torch.cuda.synchronize(dev)
+            for k in range(K):
+                flush.fill_(k & 0xFF)
+                ev_g[k][0].record(stream)
+                g.replay()
+                ev_g[k][1].record(stream)
+            torch.cuda.synchronize(dev)
+            if world > 1:
+                dist.barrier()
+            st = s.stats()
+            launches = per_step * K
+            step_ms = [a.elapsed_time(b) for a, b in ev_g]
+            del g
+        clk = clocks.stop()
 
     total_s = sum(step_ms) / 1e3
     pairs = st["pairs_density"] + st["pairs_force"]
@@ -296,7 +323,8 @@ def run_ours(args, rank, world):
     kernels["density"]["tests"] = st["tests_density"] / K
     kernels["force"]["tests"] = st["tests_force"] / K
     s.close()
-    return {"total_s": total_s, "pairs": pairs, "step_ms": step_ms, "clocks": clk, "e2e": e2e,
+    return {"total_s": total_s, "pairs": pairs, "step_ms": step_ms, "step_ms_eager": step_ms_eager,
+            "clocks": clk, "e2e": e2e,
             "roofline": roofline, "kernels": kernels, "launches": launches, "n": n,
             "tuning": tuned["tuning"], "tuning_source": ("default" if tuned["cached"] is None else
                                                          "autotuner cache" if tuned["cached"] else "autotuner search")}
@@ -968,6 +996,8 @@ def main():
                    "particles_per_gpu": r["n"], "newton_steps": 5, "storage": args.prec,
                    "aos_record_bytes": 112, "parallelism": f"replicas{world}",
                    "l2": "flushed between steps (512 MiB write)",
+                   "timed": "one captured CUDA graph of the step, replayed" if not args.no_graph else "eager calls",
+                   "ms_per_step_eager": statistics.mean(r["step_ms_eager"]),
                    "tuning": r["tuning"], "tuning_source": r["tuning_source"]},
         "roofline": r["roofline"], "cpu_baseline": cpu, "e2e": r["e2e"],
         "gpu_launches": r["launches"], "clocks": r["clocks"], "kernels": r["kernels"],
