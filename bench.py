@@ -671,6 +671,13 @@ def run_buffers(nb=(64, 64, 32), reps: int = 5):
         step_aos = sum(rows["aos"][k] for k in kernels)
         step_soa = sum(rows[name][k] for k in kernels) + rows[name]["aos_to_soa"] + rows[name]["soa_to_aos"]
         speed[name]["step_with_conversions"] = step_aos / step_soa
+        # the paper's kernel structure (partners read from global memory): its
+        # end-to-end in-place comparison (conversions included) against the
+        # AoS baseline
+        plain_aos = rows["aos"]["density_plain"] + rows["aos"]["force_plain"] + rows["aos"]["kick"] + rows["aos"]["drift"]
+        plain_soa = (rows[name]["density_plain"] + rows[name]["force_plain"] + rows[name]["kick"] + rows[name]["drift"]
+                     + rows[name]["aos_to_soa"] + rows[name]["soa_to_aos"])
+        speed[name]["plain_step_with_conversions"] = plain_aos / plain_soa
     out["soa_speedup_over_aos"] = speed
     out["pairs_per_s"] = {src: {"density": st["pairs_density"] / (rows[src]["density"] * 1e-3),
                                 "force": st["pairs_force"] / (rows[src]["force"] * 1e-3)}
