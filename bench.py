@@ -62,7 +62,9 @@ def parse():
     ap.add_argument("--no-streaming", action="store_true", help="skip the host-resident AoS comparison")
     ap.add_argument("--no-buffers", action="store_true", help="skip the 64-particle-buffer AoS/SoA comparison")
     ap.add_argument("--no-placement", action="store_true", help="skip the host-vs-GPU conversion placement rows")
-    ap.add_argument("--profile-case", choices=["pairs", "memory", "buffers"], default=None,
+    ap.add_argument("--no-levels", action="store_true", help="skip the per-particle-h level hierarchy rows")
+    ap.add_argument("--levels-only", action="store_true", help="print only the level hierarchy rows")
+    ap.add_argument("--profile-case", choices=["pairs", "memory", "buffers", "levels"], default=None,
                     help="run one small fixed workload for an ncu capture and exit")
     return ap.parse_args()
 
@@ -818,6 +820,89 @@ def run_uneven(n: int = 16_777_216):
             "cells_per_axis": nc[0], "variants": rows}
 
 
+def _levels_density(sph, wl, dev, stream, margin, reps):
+    """Bin for the hierarchy, convert, and time the density with 5 Newton
+    steps over it (reps timed runs after one warm-up; counters of the last)."""
+    import torch
+    lo, hi = wl.meta["levels"]
+    aos = torch.from_numpy(wl.aos).to(dev)
+    params = sph.make_params(wl.box, eta=wl.eta, h_max=wl.h_cap)
+    s = sph.Sph(aos, sph.layout_112(), params, 27, sph.WS_LEVELS, stream=stream)
+    ms_bin, ms_den = [], []
+    with torch.cuda.stream(stream):
+        for r in range(reps + 1):
+            s.reset_stats()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record(stream)
+            s.bin_levels(lo, hi, margin)
+            s.aos_to_soa(sph.FIELDS_DENSITY)
+            ev[1].record(stream)
+            s.density_levels(5)
+            ev[2].record(stream)
+            ev[2].synchronize()
+            if r:
+                ms_bin.append(ev[0].elapsed_time(ev[1]))
+                ms_den.append(ev[1].elapsed_time(ev[2]))
+        st = s.stats()
+        done, prom = s.level_counts()
+    s.close()
+    del aos
+    torch.cuda.empty_cache()
+    td = statistics.median(ms_den)
+    return {"margin": margin, "bin_and_convert_ms": statistics.median(ms_bin), "density_ms": td,
+            "density_pairs_per_s": st["pairs_density"] / (ms_den[-1] / 1e3),
+            "tests_per_pair": st["tests_density"] / max(st["pairs_density"], 1),
+            "particles_per_level": {str(l): done[l] for l in range(lo, hi + 1)},
+            "promoted_per_level": {str(l): prom[l] for l in range(lo, hi + 1)},
+            "error_bits": st["error_bits"]}
+
+
+def run_levels(n: int = 16_777_216, n_compare=(262_144, 1_048_576), reps: int = 3):
+    """Per-particle h on the clustered set (h from the mixture's local number
+    density, 48 neighbours; 5 Newton steps): the density over the level
+    hierarchy at full size for three level margins, and at smaller sizes the
+    same density next to one grid sized for the largest h (the only grid the
+    single-level path can use: its cells hold the whole support of the
+    background particles, so the dense cores share a handful of cells)."""
+    import torch
+    import paper_2512_05516_gb300 as sph
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.Stream(dev)
+    wl = sph_inputs.gaussian_mixture_adaptive(n)
+    rows = [_levels_density(sph, wl, dev, stream, m, reps) for m in (0.0, 0.1, 0.25)]
+    out = {"workload": f"gaussian_mixture_adaptive_{n}", "storage": "fp32", "newton_steps": 5,
+           "levels": list(wl.meta["levels"]), "h_range": [wl.meta["h_min"], wl.meta["h_max"]],
+           "hierarchy": rows, "vs_single_grid": []}
+    del wl
+    for nc_ in n_compare:
+        w = sph_inputs.gaussian_mixture_adaptive(nc_)
+        lv = _levels_density(sph, w, dev, stream, 0.1, 1)
+        aos = torch.from_numpy(w.aos).to(dev)
+        nc = int(math.floor(1.0 / (2.0 * w.h_cap)))
+        params = sph.make_params(w.box, eta=w.eta, h_max=w.h_cap)
+        s = sph.Sph(aos, sph.layout_112(), params, nc ** 3, 0, stream=stream)
+        with torch.cuda.stream(stream):
+            s.bin_cells(2.0 * w.h_cap)
+            s.aos_to_soa(sph.FIELDS_DENSITY)
+            s.reset_stats()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record(stream)
+            s.density(5)
+            ev[1].record(stream)
+            ev[1].synchronize()
+            st = s.stats()
+        s.close()
+        del aos
+        torch.cuda.empty_cache()
+        t1 = ev[0].elapsed_time(ev[1])
+        out["vs_single_grid"].append({
+            "n": nc_, "levels": list(w.meta["levels"]), "single_grid_cells_per_axis": nc,
+            "single_grid_max_occupancy": st["max_occupancy"], "single_grid_density_ms": t1,
+            "single_grid_tests_per_pair": st["tests_density"] / max(st["pairs_density"], 1),
+            "hierarchy_density_ms": lv["density_ms"], "speedup": t1 / lv["density_ms"]})
+    return out
+
+
 # ----------------------------------------------------------------- oracle
 def run_oracle_sample(n_targets: int, seed: int = 1):
     """The FP64 oracle (as it stands) on a sample of the same workload: the
@@ -904,6 +989,31 @@ def profile_buffers():
         raise SystemExit(1)
 
 
+def profile_levels():
+    """'levels': the adaptive-h clustered set at 2,097,152 particles (AoS
+    235 MB > L2), levels from the set, margin 0.1: bin, convert, and the
+    density with 5 Newton steps over the hierarchy, twice."""
+    import torch
+    import paper_2512_05516_gb300 as sph
+    wl = sph_inputs.gaussian_mixture_adaptive(2_097_152)
+    lo, hi = wl.meta["levels"]
+    params = sph.make_params(wl.box, eta=wl.eta, h_max=wl.h_cap)
+    aos = torch.from_numpy(wl.aos).cuda()
+    s = sph.Sph(aos, sph.layout_112(), params, 27, sph.WS_LEVELS)
+    for _ in range(2):
+        s.bin_levels(lo, hi, 0.1)
+        s.aos_to_soa(sph.FIELDS_DENSITY)
+        s.density_levels(5)
+    torch.cuda.synchronize()
+    st = s.stats()
+    done, prom = s.level_counts()
+    print(json.dumps({"profile_case": "levels", "n": wl.n, "levels": [lo, hi], "error_bits": st["error_bits"],
+                      "pairs_density": st["pairs_density"], "done": done[lo:hi + 1],
+                      "promoted": prom[lo:hi + 1]}))
+    if st["error_bits"] & (sph.ERR_NONFINITE | sph.ERR_OUTSIDE):
+        raise SystemExit(1)
+
+
 def profile_case(which: str):
     """Small fixed workloads for ncu captures (profiles/ summaries name the
     command).  'pairs': the 1,072,476-particle Sod step twice (the second is
@@ -915,6 +1025,9 @@ def profile_case(which: str):
     import paper_2512_05516_gb300 as sph
     if which == "buffers":
         profile_buffers()
+        return
+    if which == "levels":
+        profile_levels()
         return
     if which == "pairs":
         wl = sph_inputs.sod()
@@ -950,6 +1063,9 @@ def main():
     args = parse()
     if args.profile_case:
         profile_case(args.profile_case)
+        return
+    if args.levels_only:
+        print(json.dumps({"adaptive_h_levels": run_levels()}))
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -1007,6 +1123,7 @@ def main():
     streaming = None if args.no_streaming or world > 1 else run_streaming()
     buffers = None if args.no_buffers or world > 1 else run_buffers()
     placement = None if args.no_placement or world > 1 else run_placement()
+    levels = None if args.no_levels or world > 1 else run_levels()
     out = {
         "metric": METRIC, "value": pairs / total_s, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
@@ -1025,6 +1142,7 @@ def main():
         "streaming_vs_in_place": streaming,
         "buffers_aos_vs_soa": buffers,
         "conversion_placement": placement,
+        "adaptive_h_levels": levels,
     }
     print(json.dumps(out))
     if world > 1:

@@ -141,6 +141,7 @@ typedef struct {
 
 /* workspace options */
 #define SPH_WS_REORDER 1       /* reserve room for sph_bin_cells(reorder_aos = 1) */
+#define SPH_WS_LEVELS 2        /* reserve room for the level hierarchy (sph_bin_levels) */
 
 /* Counters accumulated on the device since creation or sph_reset_stats. */
 typedef struct {
@@ -196,7 +197,8 @@ typedef struct {
     int32_t ncell[3];
     double cell_edge[3];
     int64_t off_perm;            /* int32[n]: sorted slot -> original particle index */
-    int64_t off_cell_of_slot;    /* int32[n]: sorted slot -> key = cell * s^3 + sub-cell */
+    int64_t off_cell_of_slot;    /* int32[n]: sorted slot -> key = cell * s^3 + sub-cell
+                                    (after sph_bin_levels: the finest cell's Morton key) */
     int64_t off_cell_start;      /* int32[ncell s^3 + 1]: first slot of each key */
     int64_t off_nngb;            /* int32[n], neighbour counts of the last density call */
     int64_t off_nngb_force;      /* int32[n], neighbour counts of the last force call */
@@ -204,6 +206,9 @@ typedef struct {
     int32_t prec[SPH_NFIELDS];   /* current storage format of each SoA field */
     uint32_t valid;              /* fields whose SoA copy is current */
     int32_t subcells;            /* s: sub-cells per cell edge of the last binning */
+    int64_t off_level;           /* int8[n]: level of every slot (sph_bin_levels; -1 without
+                                    SPH_WS_LEVELS); after sph_density_levels, the level each
+                                    particle's density was computed at */
 } sph_desc;
 
 typedef struct sph_ctx sph_ctx;
@@ -404,6 +409,64 @@ sph_status sph_buffer_kick(sph_ctx *ctx, int32_t source, double dt);
  * [0, box).  SPH_SRC_SOA: the FP32 offsets from the buffer origin (wrapped
  * when written back).  Reads X, V; writes X.  Errors as sph_buffer_kick. */
 sph_status sph_buffer_drift(sph_ctx *ctx, int32_t source, double dt);
+
+/* ---- Adaptive smoothing lengths: a hierarchy of cell levels --------------
+ * The density's Newton iteration (Eq. 6 with f(h) = rho(h) - m (eta/h)^3)
+ * gives every particle its own h, and in a clustered set those differ by a
+ * factor of 30 or more between the dense cores and the background.  One grid
+ * whose cells hold the largest 2h then puts hundreds of thousands of
+ * particles into a core cell, and every core particle tests all of them.
+ * These calls keep one grid per level l = level_min..level_max with 2^l
+ * cells per axis (edge e_l,d = box_d / 2^l), nested like an octree, and
+ * compute each particle's density on the finest level whose cells hold its
+ * support.
+ *
+ * Cell of a particle at level_max: f_d = clamp(floor(x_d * (2^level_max /
+ * box_d)), 0, 2^level_max - 1) in FP64; its key is the Morton code of
+ * (f_x, f_y, f_z) (bit b of f_x, f_y, f_z at bits 3b, 3b+1, 3b+2).  Slots are
+ * ordered by key, ascending original index among equal keys, so the cell of
+ * every level is one run of consecutive slots (its key prefix).  Positions
+ * in the SoA (sph_aos_to_soa) are offsets from the level_max cell origin
+ * f_d * box_d / 2^level_max.
+ *
+ * Level of a particle: the largest l in [level_min, level_max] with
+ * h_i (1 + h_margin) <= h_l = min_d e_l,d / 2, evaluated in FP64 on the
+ * record's h; level_min when there is none or h_i is not finite and
+ * positive.  The margin leaves room for h to grow during the Newton steps. */
+#define SPH_LEVEL_MIN 2
+#define SPH_LEVEL_MAX 10
+
+/* Bin for the hierarchy: keys, the stable sort, and every particle's level.
+ * Needs a context created with SPH_WS_LEVELS; requires
+ * SPH_LEVEL_MIN <= level_min <= level_max <= SPH_LEVEL_MAX, h_margin >= 0
+ * and h_max <= h_level_min (the coarsest cells hold the largest support).
+ * Invalidates every SoA field; leaves cell and buffer mode (sph_density,
+ * sph_force and the buffer calls return SPH_ESTATE until sph_bin_cells or
+ * sph_bin_buffers).  Errors: SPH_EINVAL (levels,
+ * margin), SPH_ENOSPACE (workspace without SPH_WS_LEVELS), SPH_ECAPACITY
+ * (h_max > h_level_min), SPH_ECUDA. */
+sph_status sph_bin_levels(sph_ctx *ctx, int32_t level_min, int32_t level_max, double h_margin);
+
+/* S3+S4 over the hierarchy: the density of sph_density (same Newton steps,
+ * sums, EOS and outputs) with each particle's neighbours gathered from the
+ * 27 cells of its level around its own cell (periodic).  Levels run from
+ * level_max to level_min.  At level l the Newton steps clamp h at
+ * min(h_max, h_l); a particle whose h met that clamp while l > level_min
+ * moves to level l - 1 and is computed again there from its original h, so
+ * that every particle's result is the one a single grid of cells >= 2 h_max
+ * gives (up to the order of the sums).  hcap_clamps counts the particles
+ * clamped at level_min.  Reads X, M, H (and U); writes RHO, H (newton_steps
+ * > 0), P and CS (U current) and the neighbour counts.  Requires
+ * sph_bin_levels and sph_aos_to_soa of X, M, H.  Errors: SPH_EINVAL
+ * (newton_steps < 0 or > 32), SPH_ESTATE, SPH_ECUDA. */
+sph_status sph_density_levels(sph_ctx *ctx, int32_t newton_steps);
+
+/* Per level l (index l of both arrays, SPH_LEVEL_MAX + 1 entries each):
+ * done[l] the particles whose density was computed at level l, promoted[l]
+ * those moved from level l to l - 1, summed since creation or
+ * sph_reset_stats.  Synchronises the context's stream.  Errors: SPH_EINVAL,
+ * SPH_ECUDA. */
+sph_status sph_level_counts(sph_ctx *ctx, int64_t *done, int64_t *promoted);
 
 /* S6 + S7 in one pass over the records: the same results in the AoS as
  * sph_kick_drift(dt_kick, dt_drift) followed by sph_soa_to_aos(fields) --

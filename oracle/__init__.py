@@ -78,6 +78,8 @@ def _declare(L):
     L.orc_bin.argtypes = [_i64, _p, _p, _p, _p, _p, _p]
     L.orc_bin_sub.restype = C.c_int
     L.orc_bin_sub.argtypes = [_i64, _p, _p, _p, C.c_int32, _p, _p, _p]
+    L.orc_levels.restype = C.c_int
+    L.orc_levels.argtypes = [_i64, _p, _p, _p, C.c_int32, C.c_int32, _d, _p, _p, _p]
     L.orc_density.restype = None
     L.orc_density.argtypes = [_i64, _p, _p, _p, _p, _d, _d, C.c_int, C.c_int, _i64, _p,
                               _p, _p, _p, _p, _p, _p]
@@ -163,6 +165,22 @@ def bin_cells(x, box, nc, sub=1):
     if rc != 0:
         raise ValueError("orc_bin failed")
     return cell_of, perm, start
+
+
+def levels(x, h, box, level_min, level_max, margin=0.0):
+    """The level hierarchy's binning: Morton key of every particle's finest
+    cell (2^level_max per axis), its level from h, and the stable order by
+    key.  Returns (key[n] int32, level[n] int8, perm[n] int64)."""
+    x = _f64(x, (-1, 3))
+    n = x.shape[0]
+    key = np.zeros(n, np.int32)
+    lev = np.zeros(n, np.int8)
+    perm = np.zeros(n, np.int64)
+    rc = lib().orc_levels(n, _ptr(x), _ptr(_f64(h)), _ptr(_f64(box)), int(level_min), int(level_max),
+                          float(margin), _ptr(key), _ptr(lev), _ptr(perm))
+    if rc != 0:
+        raise ValueError("orc_levels: bad levels")
+    return key, lev, perm
 
 
 def grid_dims(box, cell_edge):

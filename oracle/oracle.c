@@ -167,6 +167,77 @@ int orc_bin_sub(int64_t n, const double *x, const double *box, const int32_t *nc
     return 0;
 }
 
+/* ------------------------------------------------------------------------- */
+/* Level hierarchy for per-particle h: Morton keys of the finest cells        */
+/* ------------------------------------------------------------------------- */
+
+/* Morton (Z-order) code, written bit by bit: bit b of fx, fy, fz goes to bit
+ * 3b, 3b + 1, 3b + 2 of the key */
+static int64_t morton3(int32_t fx, int32_t fy, int32_t fz, int bits)
+{
+    int64_t k = 0;
+    for (int b = 0; b < bits; ++b) {
+        k |= (int64_t)((fx >> b) & 1) << (3 * b);
+        k |= (int64_t)((fy >> b) & 1) << (3 * b + 1);
+        k |= (int64_t)((fz >> b) & 1) << (3 * b + 2);
+    }
+    return k;
+}
+
+typedef struct { int64_t key, idx; } keyidx_t;
+
+static int cmp_keyidx(const void *pa, const void *pb)
+{
+    const keyidx_t *a = (const keyidx_t *)pa, *b = (const keyidx_t *)pb;
+    if (a->key != b->key) return a->key < b->key ? -1 : 1;
+    return a->idx < b->idx ? -1 : (a->idx > b->idx ? 1 : 0);
+}
+
+/*
+ * Levels l = level_min..level_max: 2^l cells per axis, edge L_d / 2^l.  The
+ * key of a particle is the Morton code of its finest cell, f_d =
+ * clamp(floor(x_d * (2^level_max / L_d)), 0, 2^level_max - 1).  Its level is
+ * the largest l with h (1 + margin) <= h_l = min_d (L_d / 2^l) / 2, or
+ * level_min when no level qualifies or h is not finite and positive.  perm
+ * lists the particles by key, ascending index among equal keys.  Returns 0,
+ * or -1 on bad levels.
+ */
+int orc_levels(int64_t n, const double *x, const double *h, const double *box, int32_t level_min,
+               int32_t level_max, double margin, int32_t *key, int8_t *level, int64_t *perm)
+{
+    if (level_min < 0 || level_max > 20 || level_min > level_max) return -1;
+    const int32_t F = (int32_t)1 << level_max;
+    const double grow = 1.0 + margin;
+    keyidx_t *ki = (keyidx_t *)malloc(sizeof(keyidx_t) * (size_t)(n > 0 ? n : 1));
+    if (!ki) return -1;
+    for (int64_t i = 0; i < n; ++i) {
+        int32_t f[3];
+        for (int a = 0; a < 3; ++a) f[a] = cell_coord(x[3 * i + a], (double)F / box[a], F);
+        const int64_t k = morton3(f[0], f[1], f[2], level_max);
+        key[i] = (int32_t)k;
+        ki[i].key = k;
+        ki[i].idx = i;
+        int lv = level_min;
+        if (isfinite(h[i]) && h[i] > 0.0) {
+            const double t = h[i] * grow;
+            for (int l = level_max; l > level_min; --l) {
+                double e = ldexp(box[0], -l);
+                for (int a = 1; a < 3; ++a)
+                    if (ldexp(box[a], -l) < e) e = ldexp(box[a], -l);
+                if (t <= 0.5 * e) {
+                    lv = l;
+                    break;
+                }
+            }
+        }
+        level[i] = (int8_t)lv;
+    }
+    qsort(ki, (size_t)n, sizeof(keyidx_t), cmp_keyidx);
+    for (int64_t s = 0; s < n; ++s) perm[s] = ki[s].idx;
+    free(ki);
+    return 0;
+}
+
 /* plain cell list: one sub-cell per cell */
 int orc_bin(int64_t n, const double *x, const double *box, const int32_t *nc,
             int32_t *cell_of, int64_t *perm, int64_t *cell_start)

@@ -47,6 +47,11 @@ int orc_bin_sub(int64_t n, const double *x, const double *box, const int32_t *nc
 int orc_bin(int64_t n, const double *x, const double *box, const int32_t *nc,
             int32_t *cell_of, int64_t *perm, int64_t *cell_start);
 
+/* ---- level hierarchy for per-particle h: Morton keys of the finest cells,
+ *      levels from h, stable order by key ---- */
+int orc_levels(int64_t n, const double *x, const double *h, const double *box, int32_t level_min,
+               int32_t level_max, double margin, int32_t *key, int8_t *level, int64_t *perm);
+
 /* ---- density with Newton smoothing-length iteration (Eq. 6) ---- */
 void orc_density(int64_t n, const double *x, const double *m, const double *h_in,
                  const double *box, double eta, double h_cap, int newton_steps,

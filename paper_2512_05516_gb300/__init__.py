@@ -17,7 +17,8 @@ from ._capi import (AOS_F32, AOS_F64, BIT, ERR_HCAP, ERR_NEWTON, ERR_NONFINITE, 
                     F_A, F_CS, F_DUDT, F_H, F_M, F_P, F_RHO, F_U, F_V, F_X, FIELD_NAMES,
                     FIELDS_DENSITY, FIELDS_FORCE, FIELDS_KICK, FIELDS_OUTPUT, FLAG_PLAIN_SUM,
                     NCOMP, P_BF16, P_FP16, P_FP32, P_FP32_M10, P_FP32_M16, PREC, SPH_NFIELDS,
-                    BUFFER_MAX, BUFFER_MIN, SRC_AOS, SRC_SOA, WS_REORDER, sph_aos_layout, sph_desc,
+                    BUFFER_MAX, BUFFER_MIN, LEVEL_MAX, LEVEL_MIN, SRC_AOS, SRC_SOA, WS_LEVELS, WS_REORDER,
+                    sph_aos_layout, sph_desc,
                     sph_params, sph_stats, sph_tuning)
 
 _lib = _capi.load()
@@ -120,6 +121,21 @@ def sph_buffer_kick(ctx, source: int, dt: float) -> int:
 
 def sph_buffer_drift(ctx, source: int, dt: float) -> int:
     return _lib.sph_buffer_drift(ctx, int(source), float(dt))
+
+
+def sph_bin_levels(ctx, level_min: int, level_max: int, h_margin: float) -> int:
+    return _lib.sph_bin_levels(ctx, int(level_min), int(level_max), float(h_margin))
+
+
+def sph_density_levels(ctx, newton_steps: int) -> int:
+    return _lib.sph_density_levels(ctx, int(newton_steps))
+
+
+def sph_level_counts(ctx):
+    done = (C.c_int64 * (LEVEL_MAX + 1))()
+    prom = (C.c_int64 * (LEVEL_MAX + 1))()
+    st = _lib.sph_level_counts(ctx, done, prom)
+    return st, list(done), list(prom)
 
 
 def sph_set_field_scale(ctx, exp2) -> int:
@@ -390,6 +406,20 @@ class Sph:
     def buffer_drift(self, dt: float, source="soa"):
         _check(sph_buffer_drift(self.ctx, self._source(source), dt), "sph_buffer_drift")
 
+    # ---- the level hierarchy (adaptive h; needs ws_flags=WS_LEVELS)
+    def bin_levels(self, level_min: int, level_max: int, h_margin: float = 0.1):
+        _check(sph_bin_levels(self.ctx, level_min, level_max, h_margin), "sph_bin_levels")
+
+    def density_levels(self, newton_steps: int = 0):
+        _check(sph_density_levels(self.ctx, newton_steps), "sph_density_levels")
+
+    def level_counts(self):
+        """(done, promoted): per level l (index l), the particles computed
+        there and those moved from it to level l - 1."""
+        st, done, prom = sph_level_counts(self.ctx)
+        _check(st, "sph_level_counts")
+        return done, prom
+
     def step(self, dt: float, newton_steps: int = 5, prec=None, cell_edge: float = 0.0,
              reorder: bool = False, out_fields: int = FIELDS_OUTPUT):
         """One SPH time step: bin, convert, density (+h), force, kick/drift
@@ -445,6 +475,13 @@ class Sph:
     def slot_cell(self):
         d = self.describe()
         return self._ws_view(d.off_cell_of_slot, self.n, self.torch.int32)
+
+    def levels(self):
+        """Level of every slot (int8; level mode)."""
+        d = self.describe()
+        if d.off_level < 0:
+            raise SphError(-2, "levels: workspace created without WS_LEVELS")
+        return self._ws_view(d.off_level, self.n, self.torch.int8)
 
     def cell_start(self):
         d = self.describe()

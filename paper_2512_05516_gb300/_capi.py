@@ -33,6 +33,8 @@ for _n in range(1, 23):
 AOS_F64, AOS_F32 = 0, 1
 FLAG_PLAIN_SUM = 1
 WS_REORDER = 1
+WS_LEVELS = 2
+LEVEL_MIN, LEVEL_MAX = 2, 10
 ERR_NONFINITE, ERR_OUTSIDE, ERR_HCAP, ERR_NEWTON, ERR_TIMEOUT = 1, 2, 4, 8, 16
 SRC_AOS, SRC_SOA = 0, 1
 BUFFER_MIN, BUFFER_MAX = 32, 256
@@ -70,7 +72,8 @@ class sph_desc(C.Structure):
                 ("off_perm", C.c_int64), ("off_cell_of_slot", C.c_int64),
                 ("off_cell_start", C.c_int64), ("off_nngb", C.c_int64),
                 ("off_nngb_force", C.c_int64), ("off_soa", (C.c_int64 * 3) * SPH_NFIELDS),
-                ("prec", C.c_int32 * SPH_NFIELDS), ("valid", C.c_uint32), ("subcells", C.c_int32)]
+                ("prec", C.c_int32 * SPH_NFIELDS), ("valid", C.c_uint32), ("subcells", C.c_int32),
+                ("off_level", C.c_int64)]
 
 
 # every symbol the header declares, with its prototype
@@ -105,6 +108,9 @@ PROTOTYPES = {
     "sph_buffer_force": (C.c_int, [_P, C.c_int32]),
     "sph_buffer_kick": (C.c_int, [_P, C.c_int32, C.c_double]),
     "sph_buffer_drift": (C.c_int, [_P, C.c_int32, C.c_double]),
+    "sph_bin_levels": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_double]),
+    "sph_density_levels": (C.c_int, [_P, C.c_int32]),
+    "sph_level_counts": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "sph_destroy": (None, [_P]),
     "sph_status_str": (C.c_char_p, [C.c_int]),
 }

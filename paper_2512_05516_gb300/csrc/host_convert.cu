@@ -236,7 +236,9 @@ cudaError_t run_aos_to_soa_host(sph_ctx *c, const uint8_t *host_aos, uint32_t fi
                     } else {
                         // the cell's coordinate on this axis from its key, origin k * edge
                         const int cell = keys[k] / s3;
-                        const int kc = comp == 0 ? cell % nc0 : (comp == 1 ? (cell / nc0) % nc1 : cell / (nc0 * nc1));
+                        const int kc = c->levels ? (int)morton_compact((uint32_t)keys[k] >> comp)
+                                       : comp == 0 ? cell % nc0
+                                       : (comp == 1 ? (cell / nc0) % nc1 : cell / (nc0 * nc1));
                         const double o = (double)kc * edge[comp];
                         v = (float)(x - o);
                     }

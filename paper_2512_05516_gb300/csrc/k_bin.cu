@@ -352,6 +352,124 @@ __global__ void k_iota(int32_t *p, int64_t n)
     if (i < n) p[i] = (int32_t)i;
 }
 
+// ---------------------------------------------------------------------------
+// level hierarchy: Morton key of the finest cell and the level of every
+// particle
+// ---------------------------------------------------------------------------
+struct LevelArgs {
+    const uint8_t *aos;
+    int64_t n;
+    int32_t stride, xoff, hoff;
+    bool h64;                    // h stored as FP64 in the record (else FP32)
+    double inv[3], box[3];       // inv = 2^lmax / L per axis
+    int32_t F;                   // 2^lmax cells per axis
+    int32_t lmin, lmax;
+    double grow;                 // 1 + margin
+    double cap[kLevelMax + 1];   // h_l = min_d (L_d / 2^l) / 2
+    int32_t *keys, *vals;
+    int8_t *lvl;
+    DevStats *st;
+};
+
+__global__ void k_level_keys(LevelArgs a)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const uint8_t *rec = a.aos + i * a.stride;
+    const double *x = (const double *)(rec + a.xoff);
+    const double x0 = x[0], x1 = x[1], x2 = x[2];
+    const bool outside = !(in_box(x0, a.box[0]) && in_box(x1, a.box[1]) && in_box(x2, a.box[2]));
+    if (outside) set_error(a.st, SPH_ERR_OUTSIDE | ((isfinite(x0) && isfinite(x1) && isfinite(x2)) ? 0u : SPH_ERR_NONFINITE));
+    const uint32_t fx = (uint32_t)cell_coord(x0, a.inv[0], a.F);
+    const uint32_t fy = (uint32_t)cell_coord(x1, a.inv[1], a.F);
+    const uint32_t fz = (uint32_t)cell_coord(x2, a.inv[2], a.F);
+    a.keys[i] = (int32_t)morton_key(fx, fy, fz);
+    a.vals[i] = (int32_t)i;
+    const double h = a.h64 ? *(const double *)(rec + a.hoff) : (double)*(const float *)(rec + a.hoff);
+    int lv = a.lmin;
+    if (h > 0.0 && isfinite(h)) {
+        // the finest level whose cap holds h (1 + margin); caps shrink with l
+        const double t = __dmul_rn(h, a.grow);
+        for (int l = a.lmax; l > a.lmin; --l)
+            if (t <= a.cap[l]) {
+                lv = l;
+                break;
+            }
+    }
+    a.lvl[i] = (int8_t)lv;
+}
+
+__global__ void k_level_permute(const int8_t *lvl_in, const int32_t *perm, int64_t n, int8_t *lvl_out)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) lvl_out[k] = lvl_in[perm[k]];
+}
+
+// ---------------------------------------------------------------------------
+// work items of one level: the level's particles in slot order, split into
+// tiles of <= 32 that share a cell of the level
+// ---------------------------------------------------------------------------
+__global__ void k_lvl_flags(const int8_t *level, int64_t n, int l, int32_t *flag)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) flag[k] = level[k] == l ? 1 : 0;
+}
+
+// pos: exclusive scan of the flags; the level's slots and their cell codes
+// at the level (key >> sh) in slot order
+__global__ void k_lvl_compact(const int8_t *level, const int32_t *pos, const int32_t *key, int64_t n, int l, int sh,
+                              int32_t *tlist, int32_t *tcode)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n || level[k] != l) return;
+    const int32_t j = pos[k];
+    tlist[j] = (int32_t)k;
+    tcode[j] = key[k] >> sh;
+}
+
+// first index in [lo, hi) whose code is >= v (codes ascend)
+__device__ __forceinline__ int32_t code_lower_bound(const int32_t *code, int32_t lo, int32_t hi, int32_t v)
+{
+    while (lo < hi) {
+        const int32_t mid = lo + ((hi - lo) >> 1);
+        if (code[mid] < v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// entry j opens a work item when its rank inside its cell's run is a
+// multiple of 32; *M (the scan total) is the level's particle count
+__global__ void k_lvl_starts(const int32_t *tcode, const int32_t *M, int64_t n, int32_t *start)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    if (j >= *M) {
+        start[j] = 0;
+        return;
+    }
+    const int32_t head = code_lower_bound(tcode, 0, (int32_t)j, tcode[j]);
+    start[j] = (((int32_t)j - head) & (kItemTile - 1)) == 0 ? 1 : 0;
+}
+
+// iscan: exclusive scan of the start flags (iscan[n] = items)
+__global__ void k_lvl_items(const int32_t *tcode, const int32_t *M, const int32_t *iscan, int64_t n, int64_t item_max,
+                            int32_t *icell, int32_t *ifirst, int32_t *icount, DevStats *st)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j == 0) st->nitems = (int)min((int64_t)iscan[n], item_max);
+    if (j >= n) return;
+    const int32_t m = *M;
+    if (j >= m || iscan[j + 1] == iscan[j]) return;
+    const int32_t o = iscan[j];
+    if (o >= item_max) return;     // cannot happen: item_max >= n/32 + n + 1
+    const int32_t code = tcode[j];
+    const int32_t end = code_lower_bound(tcode, (int32_t)j, m, code + 1);
+    icell[o] = code;
+    ifirst[o] = (int32_t)j;
+    icount[o] = min(kItemTile, end - (int32_t)j);
+}
+
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
@@ -369,6 +487,35 @@ cudaError_t scan_exclusive(const int32_t *in, int32_t *out, int64_t len, int32_t
     k_scan_down<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, len, part);
     return cudaGetLastError();
 }
+
+namespace {
+
+// stable LSD radix sort of the (keys[0], vals[0]) pairs on their low `bits`
+// bits, 8 per pass; sorted_buf names the buffer that holds the result
+cudaError_t radix_sort(sph_ctx *c, int bits)
+{
+    cudaStream_t s = c->stream;
+    cudaError_t e;
+    const int64_t n = c->n;
+    const int64_t nblk = c->plan.nblk_radix;
+    int cur = 0;
+    for (int shift = 0; shift < bits; shift += 8) {
+        k_radix_hist<<<(unsigned)nblk, kRadixThreads, 0, s>>>(c->keys[cur], n, shift, c->ghist, nblk);
+        c->launches += 2;   // histogram and scatter
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = scan_exclusive((const int32_t *)c->ghist, (int32_t *)c->ghist, 256 * nblk, c->scan_part, s,
+                                &c->launches)) != cudaSuccess)
+            return e;
+        k_radix_scatter<<<(unsigned)nblk, kRadixThreads, 0, s>>>(c->keys[cur], c->vals[cur], c->keys[cur ^ 1],
+                                                                 c->vals[cur ^ 1], n, shift, c->ghist, nblk);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        cur ^= 1;
+    }
+    c->sorted_buf = cur;
+    return cudaSuccess;
+}
+
+}  // namespace
 
 cudaError_t run_binning(sph_ctx *c, int reorder)
 {
@@ -408,20 +555,7 @@ cudaError_t run_binning(sph_ctx *c, int reorder)
     if (n > 0) {
         int bits = 0;
         while (bits < 31 && ((int64_t)1 << bits) < nkeys) ++bits;
-        const int64_t nblk = c->plan.nblk_radix;
-        int cur = 0;
-        for (int shift = 0; shift < bits; shift += 8) {
-            k_radix_hist<<<(unsigned)nblk, kRadixThreads, 0, s>>>(c->keys[cur], n, shift, c->ghist, nblk);
-            c->launches += 2;   // histogram and scatter
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
-            if ((e = scan_exclusive((const int32_t *)c->ghist, (int32_t *)c->ghist, 256 * nblk, c->scan_part, s, &c->launches)) != cudaSuccess)
-                return e;
-            k_radix_scatter<<<(unsigned)nblk, kRadixThreads, 0, s>>>(c->keys[cur], c->vals[cur], c->keys[cur ^ 1],
-                                                                     c->vals[cur ^ 1], n, shift, c->ghist, nblk);
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
-            cur ^= 1;
-        }
-        c->sorted_buf = cur;
+        if ((e = radix_sort(c, bits)) != cudaSuccess) return e;
         if (reorder) {
             k_gather_records<<<blocks_for(n * 32, 256), 256, 0, s>>>(c->aos, c->aos_tmp, c->perm(), n,
                                                                      c->layout.record_bytes);
@@ -487,6 +621,75 @@ cudaError_t bin_raw(const BinRaw &b, cudaStream_t s)
     const size_t bytes = sizeof(int32_t) * (size_t)b.n;
     if ((e = cudaMemcpyAsync(b.out_perm, b.vals[cur], bytes, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
     return cudaMemcpyAsync(b.out_cell, b.keys[cur], bytes, cudaMemcpyDeviceToDevice, s);
+}
+
+cudaError_t run_bin_levels(sph_ctx *c, double grow)
+{
+    cudaStream_t s = c->stream;
+    cudaError_t e;
+    const int64_t n = c->n;
+    if ((e = cudaMemsetAsync(&c->dstats->max_occ, 0, sizeof(int), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(&c->dstats->nitems, 0, sizeof(int), s)) != cudaSuccess) return e;
+    c->sorted_buf = 0;
+    // origins of the finest cells, for the conversion's offsets
+    k_origins<<<kMaxCellsPerAxis / 256, 256, 0, s>>>(c->origin, make_int3(c->nc[0], c->nc[1], c->nc[2]),
+                                                     make_double3(c->edge[0], c->edge[1], c->edge[2]));
+    c->launches += 1;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (n == 0) return cudaSuccess;
+    LevelArgs a;
+    a.aos = c->aos;
+    a.n = n;
+    a.stride = c->layout.record_bytes;
+    a.xoff = c->layout.offset[SPH_F_X];
+    a.hoff = c->layout.offset[SPH_F_H];
+    a.h64 = c->layout.type[SPH_F_H] == SPH_AOS_F64;
+    a.F = c->nc[0];
+    for (int k = 0; k < 3; ++k) {
+        a.inv[k] = c->inv[k];
+        a.box[k] = c->params.box[k];
+    }
+    a.lmin = c->lvl_min;
+    a.lmax = c->lvl_max;
+    a.grow = grow;
+    for (int l = 0; l <= kLevelMax; ++l) {
+        double e_l = std::ldexp(c->params.box[0], -l);
+        for (int k = 1; k < 3; ++k) e_l = std::fmin(e_l, std::ldexp(c->params.box[k], -l));
+        a.cap[l] = 0.5 * e_l;
+    }
+    a.keys = c->keys[0];
+    a.vals = c->vals[0];
+    a.lvl = c->level_tmp;
+    a.st = c->dstats;
+    k_level_keys<<<blocks_for(n, 256), 256, 0, s>>>(a);
+    c->launches += 1;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = radix_sort(c, 3 * c->lvl_max)) != cudaSuccess) return e;
+    k_level_permute<<<blocks_for(n, 256), 256, 0, s>>>(c->level_tmp, c->perm(), n, c->level);
+    c->launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t run_level_items(sph_ctx *c, int l)
+{
+    cudaStream_t s = c->stream;
+    cudaError_t e;
+    const int64_t n = c->n;
+    const unsigned g = blocks_for(n, 256);
+    k_lvl_flags<<<g, 256, 0, s>>>(c->level, n, l, c->tscan);
+    c->launches += 1;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = scan_exclusive(c->tscan, c->tscan, n, c->scan_part, s, &c->launches)) != cudaSuccess) return e;
+    k_lvl_compact<<<g, 256, 0, s>>>(c->level, c->tscan, c->slot_cell(), n, l, 3 * (c->lvl_max - l), c->tlist,
+                                    c->tcode);
+    k_lvl_starts<<<g, 256, 0, s>>>(c->tcode, c->tscan + n, n, c->iscan);
+    c->launches += 2;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = scan_exclusive(c->iscan, c->iscan, n, c->scan_part, s, &c->launches)) != cudaSuccess) return e;
+    k_lvl_items<<<g, 256, 0, s>>>(c->tcode, c->tscan + n, c->iscan, n, c->plan.item_max, c->item_cell,
+                                  c->item_first, c->item_count, c->dstats);
+    c->launches += 1;
+    return cudaGetLastError();
 }
 
 cudaError_t run_items(sph_ctx *c)

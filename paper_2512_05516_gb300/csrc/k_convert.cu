@@ -43,6 +43,7 @@ struct ConvArgs {
     const int32_t *perm;
     const int32_t *slot_cell;    // key = cell * s^3 + sub-cell
     int32_t lg_s3;
+    bool morton;                 // level mode: the key is the Morton code of the finest cell
     uint64_t m_nc0, m_nc1;       // magic divisors for nc_x, nc_y
     int32_t nc0, nc1;
     const double *origin[3];     // cell origin k * (L / nc) per axis
@@ -75,6 +76,11 @@ __global__ void __launch_bounds__(kConvThreads, 12) k_aos_to_soa(ConvArgs a)
         org0 = __ldg(a.bufo + b);
         org1 = __ldg(a.bufo + a.nbuf + b);
         org2 = __ldg(a.bufo + 2 * a.nbuf + b);
+    } else if (a.has_x && ok && a.morton) {
+        const uint32_t key = (uint32_t)a.slot_cell[k];
+        org0 = __ldg(a.origin[0] + morton_compact(key));
+        org1 = __ldg(a.origin[1] + morton_compact(key >> 1));
+        org2 = __ldg(a.origin[2] + morton_compact(key >> 2));
     } else if (a.has_x && ok) {
         // the cell's coordinates from its key, then its origin (tables)
         const uint32_t cell = (uint32_t)a.slot_cell[k] >> a.lg_s3;
@@ -191,6 +197,7 @@ ConvArgs make_args(sph_ctx *c, uint32_t fields, bool to_soa)
     a.perm = c->perm();
     a.slot_cell = c->slot_cell();
     a.lg_s3 = c->sub == 2 ? 3 : 0;
+    a.morton = c->levels;
     a.nc0 = c->nc[0];
     a.nc1 = c->nc[1];
     a.m_nc0 = magic64((uint32_t)c->nc[0]);

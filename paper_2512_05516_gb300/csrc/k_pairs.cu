@@ -61,6 +61,15 @@ struct Common {
     DevStats *st;
     FieldRef x, m, h;
     int cap;                         // staged candidates per warp
+    // level hierarchy: cells of one level, particles in Morton order of
+    // their finest cell, positions offsets from that cell's origin
+    const int32_t *tslot;            // item entry -> slot (null: entry = slot)
+    const int32_t *mkey;             // finest-cell Morton key of every slot (null: dense cells)
+    int lvl_dn;                      // levels from this one to the finest
+    int lvl_n;                       // cells per axis at this level
+    int fine_n;                      // cells per axis at the finest level
+    float fine_edge[3];
+    int32_t *defer;                  // slots of the targets gathered one by one (k_density_one)
 };
 
 struct DensityArgs {
@@ -78,6 +87,10 @@ struct DensityArgs {
     float rho_enc, h_enc, P_enc, cs_enc;   // storage scales of the outputs
     const float4 *pD;                // every slot's (x, y, z, m) in FP32, from the pack pass
     int32_t *nngb;
+    // level hierarchy: this level, and whether a clamped particle moves up
+    int8_t *level;
+    int lvl;
+    bool promote;
 };
 
 struct ForceArgs {
@@ -109,12 +122,21 @@ struct __align__(16) Tab {
 // float4 stage starts right after, so every part keeps 16-byte multiples.
 static_assert(sizeof(Tab) % 16 == 0, "stencil table size must keep 16-byte alignment");
 static_assert((32 * kListSlots * sizeof(uint16_t)) % 16 == 0, "list size must keep 16-byte alignment");
+// the level kernel adds the 27 x 9 run boundaries of its item's stencil
+constexpr size_t kBndBytes = (27 * 9 * sizeof(int) + 15) / 16 * 16;
 
 __device__ __forceinline__ int pop_item(DevStats *st, int lane)
 {
     int it = 0;
     if (lane == 0) it = (int)atomicAdd(&st->queue, 1u);
     return __shfl_sync(FULL, it, 0);
+}
+
+__device__ __forceinline__ unsigned pop_deferred(DevStats *st, int lane)
+{
+    unsigned j = 0;
+    if (lane == 0) j = atomicAdd(&st->defer_q, 1u);
+    return __shfl_sync(FULL, j, 0);
 }
 
 __device__ __forceinline__ float warp_max(float v)
@@ -261,6 +283,149 @@ __device__ __forceinline__ int advance(const Tab &tab, int nk, int e, int g)
 }
 
 // ---------------------------------------------------------------------------
+// Level hierarchy: a candidate's position in the item cell's frame, and the
+// candidate stream of the 27 cells of the item's level
+// ---------------------------------------------------------------------------
+
+// Slot position p (offset from its finest cell, FP32) moved into the frame
+// whose origin is the finest cell `org`: + (periodic cell difference) x
+// finest edge, one rounding per axis.  Every stencil particle lies within
+// [-2^dn, 2^(dn+1)) finest cells of the origin (level >= 2), inside the
+// wrap window [-F/2, F/2).
+__device__ __forceinline__ float4 lvl_frame(const Common &c, uint32_t key, int3 org, float4 p)
+{
+    const int hf = c.fine_n >> 1, m = c.fine_n - 1;
+    const int dx = (((int)morton_compact(key) - org.x + hf) & m) - hf;
+    const int dy = (((int)morton_compact(key >> 1) - org.y + hf) & m) - hf;
+    const int dz = (((int)morton_compact(key >> 2) - org.z + hf) & m) - hf;
+    return make_float4(__fmaf_rn((float)dx, c.fine_edge[0], p.x), __fmaf_rn((float)dy, c.fine_edge[1], p.y),
+                       __fmaf_rn((float)dz, c.fine_edge[2], p.z), p.w);
+}
+
+// first slot in [lo, hi) whose key is >= v (keys ascend)
+__device__ __forceinline__ int key_lower_bound(const int32_t *key, int lo, int hi, int32_t v)
+{
+    while (lo < hi) {
+        const int mid = lo + ((hi - lo) >> 1);
+        if (__ldg(key + mid) < v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Slot runs of the 27 cells of the item's level around `cell` (its Morton
+// code at that level), periodic, and of their 8 children at the next level:
+// a cell of level l is the run of keys with its code as prefix, found by
+// binary search; its children are sub-runs found inside it.  Lane t < 27
+// writes the 9 boundaries of stencil cell t to bnd[9t .. 9t+8] (children
+// 0..7 span [bnd[9t+q], bnd[9t+q+1])).  At the finest level there are no
+// children: child 0 is the whole cell and 1..7 are empty.  Computed once
+// per work item; the candidate tables below only prune them.
+__device__ void lvl_bounds(const Common &c, int cell, int *bnd, int lane)
+{
+    if (lane < 27) {
+        const int da[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
+        const uint32_t m = (uint32_t)c.lvl_n - 1u, cc = (uint32_t)cell;
+        const uint32_t nx = (morton_compact(cc) + (uint32_t)da[0]) & m;
+        const uint32_t ny = (morton_compact(cc >> 1) + (uint32_t)da[1]) & m;
+        const uint32_t nz = (morton_compact(cc >> 2) + (uint32_t)da[2]) & m;
+        const int sh = 3 * c.lvl_dn;
+        const int32_t code = (int32_t)morton_key(nx, ny, nz);
+        const int s0 = key_lower_bound(c.mkey, 0, (int)c.n, code << sh);
+        const int e0 = key_lower_bound(c.mkey, s0, (int)c.n, (code + 1) << sh);
+        int *b = bnd + 9 * lane;
+        b[0] = s0;
+        b[8] = e0;
+        int lo = s0;
+#pragma unroll
+        for (int q = 1; q < 8; ++q) {
+            if (c.lvl_dn > 0 && lo < e0) lo = key_lower_bound(c.mkey, lo, e0, ((code << 3) + q) << (sh - 3));
+            else lo = c.lvl_dn > 0 ? lo : e0;
+            b[q] = lo;
+        }
+    }
+    __syncwarp();
+}
+
+// As build_stream, from the runs of lvl_bounds: the children (or, at the
+// finest level, the cells) whose box comes within reach sqrt(R2) of `box`,
+// compacted in (stencil cell, child) order.  Returns the candidate count.
+__device__ int lvl_table(const Common &c, const int *bnd, const Box &box, float R2, Tab &tab, int lane)
+{
+    int cnt[8], st[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        cnt[q] = 0;
+        st[q] = 0;
+    }
+    if (lane < 27) {
+        const int da[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
+        const bool kids = c.lvl_dn > 0;
+        float lo[3];
+        float d2 = 0.0f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float margin = c.edge[a] * (1.0f / 512.0f);
+            lo[a] = (float)da[a] * c.edge[a] - margin;
+            const float g = fmaxf(0.0f, fmaxf(lo[a] - box.hi[a], box.lo[a] - (lo[a] + c.edge[a] + 2.0f * margin)));
+            d2 = fmaf(g, g, d2);
+        }
+        if (d2 < R2) {
+            const int *b = bnd + 9 * lane;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int s0 = b[q], e0 = b[q + 1];
+                if (e0 <= s0) continue;
+                float g2 = 0.0f;
+                if (kids) {
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        const float half = 0.5f * c.edge[a], margin = c.edge[a] * (1.0f / 512.0f);
+                        const float l0 = lo[a] + (float)((q >> a) & 1) * half;
+                        const float g = fmaxf(0.0f, fmaxf(l0 - box.hi[a], box.lo[a] - (l0 + half + 2.0f * margin)));
+                        g2 = fmaf(g, g, g2);
+                    }
+                }
+                if (g2 < R2) {
+                    cnt[q] = e0 - s0;
+                    st[q] = s0;
+                }
+            }
+        }
+    }
+    int local = 0, kept = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        local += cnt[q];
+        kept += cnt[q] > 0 ? 1 : 0;
+    }
+    int inc = local, kinc = kept;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(FULL, inc, o);
+        const int w = __shfl_up_sync(FULL, kinc, o);
+        if (lane >= o) {
+            inc += v;
+            kinc += w;
+        }
+    }
+    int run = inc - local, pos = kinc - kept;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        if (cnt[q] > 0) {
+            run += cnt[q];
+            tab.incl[pos] = run;
+            tab.base[pos] = st[q] - (run - cnt[q]);
+            tab.t[pos] = (uint8_t)lane;
+            ++pos;
+        }
+    }
+    if (lane == 31) tab.nk = kinc;
+    __syncwarp();
+    return __shfl_sync(FULL, inc, 31);
+}
+
+// ---------------------------------------------------------------------------
 // Density
 // ---------------------------------------------------------------------------
 
@@ -327,8 +492,9 @@ struct Cursor {
 // Returns how many were staged (<= cap) and moves `cur` to the first batch
 // not staged (cur.g == total when the stream is exhausted).  A chunk always
 // stages at least one batch, since a batch holds at most 32 <= cap.
+template <bool kLvl>
 __device__ int stage_density(const Common &c, const float4 *pD, const Tab &tab, int total, const Box &box,
-                             float R2, float4 *sj, int cap, Cursor &cur, int lane)
+                             float R2, float4 *sj, int cap, Cursor &cur, int lane, int3 org)
 {
     const unsigned lt = (1u << lane) - 1u;
     const int nk = tab.nk;
@@ -345,10 +511,14 @@ __device__ int stage_density(const Common &c, const float4 *pD, const Tab &tab, 
             if (g < total) {
                 e = advance(tab, nk, e, g);
                 const int64_t j = (int64_t)tab.base[e] + g;
-                float sx, sy, sz;
-                stencil_shift(c, tab.t[e], sx, sy, sz);
                 const float4 p = __ldg(pD + j);
-                q[u] = make_float4(p.x + sx, p.y + sy, p.z + sz, p.w);
+                if (kLvl) {
+                    q[u] = lvl_frame(c, (uint32_t)__ldg(c.mkey + j), org, p);
+                } else {
+                    float sx, sy, sz;
+                    stencil_shift(c, tab.t[e], sx, sy, sz);
+                    q[u] = make_float4(p.x + sx, p.y + sy, p.z + sz, p.w);
+                }
             }
             eu[u] = e;
         }
@@ -385,17 +555,20 @@ __global__ void __launch_bounds__(256) k_density_pack(Common c, float4 *pD)
                         ld_val(c.x.p[2], c.x.fmt, k) * c.x.dec, ld_val(c.m.p[0], c.m.fmt, k) * c.m.dec);
 }
 
+template <bool kLvl>
 __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const Common &c = a.c;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const size_t per_warp = (size_t)c.cap * sizeof(float4) + (size_t)32 * kListSlots * sizeof(uint16_t) + sizeof(Tab);
+    const size_t per_warp = (size_t)c.cap * sizeof(float4) + (size_t)32 * kListSlots * sizeof(uint16_t) + sizeof(Tab) +
+                            (kLvl ? kBndBytes : 0);
     float4 *sj = reinterpret_cast<float4 *>(smem + warp * per_warp);
     uint16_t *lst = reinterpret_cast<uint16_t *>(sj + c.cap);
     Tab &tab = *reinterpret_cast<Tab *>(lst + 32 * kListSlots);
+    int *bnd = reinterpret_cast<int *>(&tab + 1);          // level kernel: the item's stencil runs
 
-    unsigned long long my_pairs = 0, my_tests = 0;
+    unsigned long long my_pairs = 0, my_tests = 0, my_done = 0, my_prom = 0;
     unsigned my_err = 0;
     const int lo = c.range ? c.range[0] : 0;
     const int hi = c.range ? c.range[1] : c.st->nitems;
@@ -405,11 +578,20 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
         const int first = c.ifirst[it];
         const int count = c.icount[it];
         const bool ok = lane < count;
-        const int64_t k = (int64_t)first + lane;
+        int64_t k = (int64_t)first + lane;
+        int3 org = make_int3(0, 0, 0);       // level mode: the item cell's origin in finest cells
+        if (kLvl) {
+            k = ok ? (int64_t)__ldg(c.tslot + first + lane) : 0;
+            const uint32_t cc = (uint32_t)cell;
+            org = make_int3((int)(morton_compact(cc) << c.lvl_dn), (int)(morton_compact(cc >> 1) << c.lvl_dn),
+                            (int)(morton_compact(cc >> 2) << c.lvl_dn));
+            lvl_bounds(c, cell, bnd, lane);
+        }
         bool clamped = false;
         float xi = 0.f, yi = 0.f, zi = 0.f, mi = 0.f, hi = 0.f, ui = 0.f;
         if (ok) {
-            const float4 p = __ldg(a.pD + k);
+            float4 p = __ldg(a.pD + k);
+            if (kLvl) p = lvl_frame(c, (uint32_t)__ldg(c.mkey + k), org, p);
             xi = p.x;
             yi = p.y;
             zi = p.z;
@@ -424,15 +606,18 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
         // stage everything within 2 h_stage of the box, h_stage = max h (1 + skin)
         float h_stage = fminf(warp_max(ok ? hi : 0.0f) * (1.0f + kStageSkin), a.h_cap);
         float R2s = 4.0f * h_stage * h_stage;
-        int total = build_stream(c, cell, box, R2s, tab, lane);
+        int total = kLvl ? lvl_table(c, bnd, box, R2s, tab, lane) : build_stream(c, cell, box, R2s, tab, lane);
         Cursor cur{0, 0};
-        int T = stage_density(c, a.pD, tab, total, box, R2s, sj, c.cap, cur, lane);
+        int T = stage_density<kLvl>(c, a.pD, tab, total, box, R2s, sj, c.cap, cur, lane, org);
         bool fits = cur.g >= total;
         float h_list = 0.0f;       // this lane's list holds every staged candidate within 2 h_list
         int nlist = 0;
 
         float rho = 0.f, drdh = 0.f;
         int cnt = 0;
+        unsigned long long lane_pairs = 0;
+        bool per_target = kLvl && !fits;
+        if (!per_target)
         for (int pass = 0; pass < a.npass; ++pass) {
             const float h2x4 = 4.0f * hi * hi;
             const float hinv = 1.0f / hi;
@@ -442,11 +627,17 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
                 // h outgrew the stage: re-stage with the current h
                 h_stage = fminf(warp_max(ok ? hi : 0.0f) * (1.0f + kStageSkin), a.h_cap);
                 R2s = 4.0f * h_stage * h_stage;
-                total = build_stream(c, cell, box, R2s, tab, lane);
+                total = kLvl ? lvl_table(c, bnd, box, R2s, tab, lane) : build_stream(c, cell, box, R2s, tab, lane);
                 Cursor rc{0, 0};
-                T = stage_density(c, a.pD, tab, total, box, R2s, sj, c.cap, rc, lane);
+                T = stage_density<kLvl>(c, a.pD, tab, total, box, R2s, sj, c.cap, rc, lane, org);
                 fits = rc.g >= total;
                 h_list = 0.0f;
+                if (kLvl && !fits) {
+                    // the grown neighbourhood no longer fits: the level
+                    // kernel starts the item over, target by target
+                    per_target = true;
+                    break;
+                }
             }
             if (fits) {
                 // rebuild when some lane's h outgrew its list radius (always on pass 0)
@@ -488,10 +679,10 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
                 // the neighbourhood does not fit: stream it through the stage
                 const float hw = warp_max(ok ? hi : 0.0f);
                 const float R2 = 4.0f * hw * hw;
-                const int tot = build_stream(c, cell, box, R2, tab, lane);
+                const int tot = kLvl ? lvl_table(c, bnd, box, R2, tab, lane) : build_stream(c, cell, box, R2, tab, lane);
                 Cursor sc{0, 0};
                 do {
-                    const int len = stage_density(c, a.pD, tab, tot, box, R2, sj, c.cap, sc, lane);
+                    const int len = stage_density<kLvl>(c, a.pD, tab, tot, box, R2, sj, c.cap, sc, lane, org);
                     if (ok) {
                         my_tests += (unsigned long long)len;
                         for (int e = 0; e < len; ++e) dens_pair(acc, xi, yi, zi, h2x4, hinv, a.plain_sum, deriv, sj[e]);
@@ -504,7 +695,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
                 rho = kSigma * h3inv * (acc.s - acc.c);
                 drdh = -kSigma * h3inv * hinv * acc.d;
                 cnt = acc.n - 1;           // the self term is in rho, not in the count
-                my_pairs += (unsigned long long)cnt;
+                lane_pairs += (unsigned long long)cnt;
                 if (pass + 1 < a.npass) {
                     // Newton step on f(h) = rho(h) - m (eta/h)^3
                     const float f = rho - mi * a.eta3 * h3inv;
@@ -517,8 +708,30 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
                     hi = hn;
                 }
             }
+                }
+        if (kLvl && per_target) {
+            // The item's box gathers (or, as h grows, comes to gather) more
+            // than the stage holds: coarse-level targets spread over their
+            // cell next to a dense cluster, or started from an h far too large
+            // for what surrounds them.  Its targets go to the per-target list
+            // and are gathered one by one, each by a whole warp, in the
+            // launch that follows (k_density_one); nothing is written here.
+            const unsigned bal = __ballot_sync(FULL, ok);
+            unsigned base = 0;
+            if (lane == 0) base = atomicAdd(&c.st->defer_n, (unsigned)__popc(bal));
+            base = __shfl_sync(FULL, base, 0);
+            if (ok) c.defer[base + __popc(bal & ((1u << lane) - 1u))] = (int32_t)k;
+            continue;
         }
-        if (ok) {
+
+        if (kLvl && ok && clamped && a.promote) {
+            // h met this level's cap: the particle moves one level up and is
+            // computed again there from its original h (nothing written)
+            a.level[k] = (int8_t)(a.lvl - 1);
+            ++my_prom;
+        } else if (ok) {
+            my_pairs += lane_pairs;
+            if (kLvl) ++my_done;
             if (!isfinite(rho)) my_err |= SPH_ERR_NONFINITE;
             st_val(a.rho_out, a.rho_fmt, k, rho * a.rho_enc);
             if (a.write_h) st_val(a.h_out, a.h_fmt, k, hi * a.h_enc);
@@ -536,9 +749,150 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
     }
     my_pairs = warp_sum_u64(my_pairs);
     my_tests = warp_sum_u64(my_tests);
+    if (kLvl) {
+        my_done = warp_sum_u64(my_done);
+        my_prom = warp_sum_u64(my_prom);
+    }
     if (lane == 0) {
         if (my_pairs) atomicAdd(&c.st->pairs_density, my_pairs);
         if (my_tests) atomicAdd(&c.st->tests_density, my_tests);
+        if (kLvl && my_done) atomicAdd(&c.st->lvl_done[a.lvl], my_done);
+        if (kLvl && my_prom) atomicAdd(&c.st->lvl_promoted[a.lvl], my_prom);
+    }
+    if (my_err) set_error(c.st, my_err);
+}
+
+// The level kernel's per-target pass: every target of the per-target list
+// (k_density deferred it) is gathered by one whole warp.  Its stream is pruned
+// to its own reach with the children of the stencil cells; the lanes take its
+// candidates in turn and the partial sums meet in a butterfly, so every lane
+// holds the same bits and runs the same Newton steps.  Persistent warps pop
+// targets from the list; the outputs, promotion and counters follow
+// k_density's epilogue.
+__global__ void __launch_bounds__(kMaxBlock, 1) k_density_one(DensityArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Common &c = a.c;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const size_t per_warp = (size_t)c.cap * sizeof(float4) + (size_t)32 * kListSlots * sizeof(uint16_t) + sizeof(Tab) +
+                            kBndBytes;
+    float4 *sj = reinterpret_cast<float4 *>(smem + warp * per_warp);
+    uint16_t *lst = reinterpret_cast<uint16_t *>(sj + c.cap);
+    Tab &tab = *reinterpret_cast<Tab *>(lst + 32 * kListSlots);
+    int *bnd = reinterpret_cast<int *>(&tab + 1);
+    unsigned long long my_pairs = 0, my_tests = 0, my_done = 0, my_prom = 0;
+    unsigned my_err = 0;
+    const unsigned nd = c.st->defer_n;
+    for (unsigned j = pop_deferred(c.st, lane); j < nd; j = pop_deferred(c.st, lane)) {
+        const int64_t k = c.defer[j];
+        const uint32_t key = (uint32_t)__ldg(c.mkey + k);
+        const int cell = (int)(key >> (3 * c.lvl_dn));
+        const int3 org = make_int3((int)(morton_compact((uint32_t)cell) << c.lvl_dn),
+                                   (int)(morton_compact((uint32_t)cell >> 1) << c.lvl_dn),
+                                   (int)(morton_compact((uint32_t)cell >> 2) << c.lvl_dn));
+        lvl_bounds(c, cell, bnd, lane);
+        const float4 p = lvl_frame(c, key, org, __ldg(a.pD + k));
+        const float xt = p.x, yt = p.y, zt = p.z, mt = p.w;
+        float ht = ld_val(c.h.p[0], c.h.fmt, k) * c.h.dec;
+        bool clamped = false;
+        if (!(ht > 0.0f) || !isfinite(ht)) {
+            ht = a.h_cap;
+            if (lane == 0) my_err |= SPH_ERR_NONFINITE;
+        }
+        if (ht > a.h_cap) {
+            ht = a.h_cap;
+            clamped = true;
+        }
+        const Box pb{{xt, yt, zt}, {xt, yt, zt}};
+        float hs = 0.0f, rt = 0.0f, dt = 0.0f;
+        int Tt = 0, nt = 0;
+        bool fit_t = false;
+        unsigned long long pt = 0;
+        for (int pass = 0; pass < a.npass; ++pass) {
+            if (pass == 0 || (fit_t && ht > hs)) {
+                hs = fminf(ht * (1.0f + kStageSkin), a.h_cap);
+                const float R2p = 4.0f * hs * hs;
+                const int tot = lvl_table(c, bnd, pb, R2p, tab, lane);
+                Cursor pc{0, 0};
+                Tt = stage_density<true>(c, a.pD, tab, tot, pb, R2p, sj, c.cap, pc, lane, org);
+                fit_t = pc.g >= tot;
+            }
+            const float h2x4 = 4.0f * ht * ht;
+            const float hinv = 1.0f / ht;
+            const bool deriv = pass + 1 < a.npass;
+            DAcc acc{0.f, 0.f, 0.f, 0};
+            if (fit_t) {
+                for (int e = lane; e < Tt; e += 32) dens_pair(acc, xt, yt, zt, h2x4, hinv, a.plain_sum, deriv, sj[e]);
+                my_tests += (unsigned long long)max(0, (Tt - lane + 31) >> 5);
+            } else {
+                // more than the stage within the target's own reach: stream it
+                const int tot = lvl_table(c, bnd, pb, h2x4, tab, lane);
+                Cursor sc{0, 0};
+                do {
+                    const int len = stage_density<true>(c, a.pD, tab, tot, pb, h2x4, sj, c.cap, sc, lane, org);
+                    for (int e = lane; e < len; e += 32)
+                        dens_pair(acc, xt, yt, zt, h2x4, hinv, a.plain_sum, deriv, sj[e]);
+                    my_tests += (unsigned long long)max(0, (len - lane + 31) >> 5);
+                    __syncwarp();
+                } while (sc.g < tot);
+            }
+            float sum = acc.s - acc.c, dsum = acc.d;
+            int nn = acc.n;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                sum += __shfl_xor_sync(FULL, sum, o);
+                dsum += __shfl_xor_sync(FULL, dsum, o);
+                nn += __shfl_xor_sync(FULL, nn, o);
+            }
+            const float h3inv = hinv * hinv * hinv;
+            rt = kSigma * h3inv * sum;
+            dt = -kSigma * h3inv * hinv * dsum;
+            nt = nn - 1;
+            pt += (unsigned long long)nt;
+            if (pass + 1 < a.npass) {
+                // Newton step on f(h) = rho(h) - m (eta/h)^3, as in k_density
+                const float f = rt - mt * a.eta3 * h3inv;
+                const float fp = dt + 3.0f * mt * a.eta3 * h3inv * hinv;
+                float hn = ht;
+                if (fp > 0.0f && isfinite(f) && isfinite(fp)) hn = ht - f / fp;
+                else if (lane == 0) my_err |= SPH_ERR_NEWTON;
+                hn = fminf(fmaxf(hn, 0.5f * ht), 2.0f * ht);
+                if (hn > a.h_cap) {
+                    hn = a.h_cap;
+                    clamped = true;
+                }
+                ht = hn;
+            }
+        }
+        if (lane != 0) continue;
+        if (clamped && a.promote) {
+            a.level[k] = (int8_t)(a.lvl - 1);
+            ++my_prom;
+            continue;
+        }
+        my_pairs += pt;
+        ++my_done;
+        if (!isfinite(rt)) my_err |= SPH_ERR_NONFINITE;
+        st_val(a.rho_out, a.rho_fmt, k, rt * a.rho_enc);
+        if (a.write_h) st_val(a.h_out, a.h_fmt, k, ht * a.h_enc);
+        a.nngb[k] = nt;
+        if (a.has_u) {
+            const float ui = ld_val(a.u.p[0], a.u.fmt, k) * a.u.dec;
+            const float P = a.gm1 * rt * ui;
+            st_val(a.P_out, a.P_fmt, k, P * a.P_enc);
+            st_val(a.cs_out, a.cs_fmt, k, __fsqrt_rn(a.gamma * P / rt) * a.cs_enc);
+        }
+        if (clamped) {
+            atomicAdd(&c.st->hcap_clamps, 1ull);
+            my_err |= SPH_ERR_HCAP;
+        }
+    }
+    my_tests = warp_sum_u64(my_tests);
+    if (lane == 0) {
+        if (my_pairs) atomicAdd(&c.st->pairs_density, my_pairs);
+        if (my_tests) atomicAdd(&c.st->tests_density, my_tests);
+        if (my_done) atomicAdd(&c.st->lvl_done[a.lvl], my_done);
+        if (my_prom) atomicAdd(&c.st->lvl_promoted[a.lvl], my_prom);
     }
     if (my_err) set_error(c.st, my_err);
 }
@@ -937,6 +1291,13 @@ Common make_common(sph_ctx *c, int cap)
     m.ifirst = c->item_first;
     m.icount = c->item_count;
     m.range = nullptr;
+    m.tslot = nullptr;
+    m.mkey = nullptr;
+    m.lvl_dn = 0;
+    m.lvl_n = 0;
+    m.fine_n = 0;
+    for (int k = 0; k < 3; ++k) m.fine_edge[k] = 0.0f;
+    m.defer = nullptr;
     m.st = c->dstats;
     auto ref = [&](int f) {
         FieldRef r;
@@ -992,10 +1353,10 @@ cudaError_t launch_persistent(sph_ctx *c, K kernel, const A &args, size_t smem, 
 
 }  // namespace
 
-size_t density_smem_bytes(int block_threads, int cap)
+size_t density_smem_bytes(int block_threads, int cap, bool levels)
 {
-    return (size_t)(block_threads / 32) *
-           ((size_t)cap * sizeof(float4) + (size_t)32 * kListSlots * sizeof(uint16_t) + sizeof(Tab));
+    return (size_t)(block_threads / 32) * ((size_t)cap * sizeof(float4) + (size_t)32 * kListSlots * sizeof(uint16_t) +
+                                           sizeof(Tab) + (levels ? kBndBytes : 0));
 }
 
 size_t force_smem_bytes(int block_threads, int cap)
@@ -1003,9 +1364,10 @@ size_t force_smem_bytes(int block_threads, int cap)
     return (size_t)(block_threads / 32) * force_warp_bytes(cap);
 }
 
-cudaError_t run_density(sph_ctx *c, int newton_steps)
+namespace {
+
+DensityArgs density_args(sph_ctx *c, int newton_steps)
 {
-    if (c->n == 0) return cudaSuccess;
     DensityArgs a;
     a.c = make_common(c, c->tuning.stage_density);
     a.has_u = (c->valid & SPH_BIT(SPH_F_U)) != 0;
@@ -1034,6 +1396,20 @@ cudaError_t run_density(sph_ctx *c, int newton_steps)
     a.P_enc = c->enc(SPH_F_P);
     a.cs_enc = c->enc(SPH_F_CS);
     a.nngb = c->nngb;
+    a.level = nullptr;
+    a.lvl = 0;
+    a.promote = false;
+    a.pD = c->pack;
+    return a;
+}
+
+}  // namespace
+
+cudaError_t run_density(sph_ctx *c, int newton_steps)
+{
+    if (c->n == 0) return cudaSuccess;
+    DensityArgs a = density_args(c, newton_steps);
+    const bool h_packed = fmt_packed(c->prec[SPH_F_H]);
     if (c->tuning.pair_kernel == 1) {
         k_density_plain<<<(unsigned)((c->n + 127) / 128), 128, 0, c->stream>>>(a, c->slot_cell());
         c->launches += 1;
@@ -1043,13 +1419,54 @@ cudaError_t run_density(sph_ctx *c, int newton_steps)
         return cudaSuccess;
     }
     // the pack pass (the force's pack arrays are free until the force runs)
-    a.pD = c->pack;
     k_density_pack<<<(unsigned)((c->n + 255) / 256), 256, 0, c->stream>>>(a.c, c->pack);
     c->launches += 1;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t smem = density_smem_bytes(c->tuning.block_threads, a.c.cap);
-    if ((e = launch_persistent(c, k_density, a, smem, c->lc_density)) != cudaSuccess) return e;
+    if ((e = launch_persistent(c, k_density<false>, a, smem, c->lc_density)) != cudaSuccess) return e;
+    if (a.write_h && h_packed) return run_pack(c, c->stage, SPH_F_H);
+    return cudaSuccess;
+}
+
+// The density over the level hierarchy: one pack pass (offsets from the
+// finest cells), then the levels from the finest to the coarsest, each with
+// its own work items and h cap; particles promoted at a level are in the
+// next level's items.
+cudaError_t run_density_levels(sph_ctx *c, int newton_steps)
+{
+    if (c->n == 0) return cudaSuccess;
+    DensityArgs a = density_args(c, newton_steps);
+    const bool h_packed = fmt_packed(c->prec[SPH_F_H]);
+    a.c.mkey = c->slot_cell();
+    a.c.tslot = c->tlist;
+    a.c.fine_n = 1 << c->lvl_max;
+    for (int k = 0; k < 3; ++k) a.c.fine_edge[k] = (float)c->edge[k];
+    a.level = c->level;
+    a.c.defer = c->tcode;     // free while the level's kernels run (its items are built)
+    k_density_pack<<<(unsigned)((c->n + 255) / 256), 256, 0, c->stream>>>(a.c, c->pack);
+    c->launches += 1;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t smem = density_smem_bytes(c->tuning.block_threads, a.c.cap, true);
+    for (int l = c->lvl_max; l >= c->lvl_min; --l) {
+        if ((e = run_level_items(c, l)) != cudaSuccess) return e;
+        double cap = std::ldexp(c->params.box[0], -l);
+        for (int k = 0; k < 3; ++k) {
+            const double e_l = std::ldexp(c->params.box[k], -l);
+            a.c.edge[k] = (float)e_l;
+            cap = std::fmin(cap, e_l);
+        }
+        cap = std::fmin(0.5 * cap, c->params.h_max);
+        a.c.lvl_dn = c->lvl_max - l;
+        a.c.lvl_n = 1 << l;
+        a.h_cap = (float)cap;
+        a.lvl = l;
+        a.promote = l > c->lvl_min;
+        if ((e = cudaMemsetAsync(&c->dstats->defer_n, 0, 2 * sizeof(unsigned), c->stream)) != cudaSuccess) return e;
+        if ((e = launch_persistent(c, k_density<true>, a, smem, c->lc_density_lv)) != cudaSuccess) return e;
+        if ((e = launch_persistent(c, k_density_one, a, smem, c->lc_density_one)) != cudaSuccess) return e;
+    }
     if (a.write_h && h_packed) return run_pack(c, c->stage, SPH_F_H);
     return cudaSuccess;
 }

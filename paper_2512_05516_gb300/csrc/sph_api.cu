@@ -92,8 +92,12 @@ bool make_plan(const sph_aos_layout &L, int64_t n, int64_t ncell_max, uint32_t w
     p->ghist = take(4 * (256 * (size_t)p->nblk_radix + 1));  // +1: the scan writes its total
     int64_t scan_len = 256 * p->nblk_radix;
     if (nkeys + 1 > scan_len) scan_len = nkeys + 1;
+    if ((ws_flags & SPH_WS_LEVELS) && n + 1 > scan_len) scan_len = n + 1;   // per-slot scans of a level
     p->scan_part = take(4 * ((size_t)(scan_len + kScanTile - 1) / kScanTile + 2));
-    p->item_max = n / 32 + (n < ncell_max ? n : ncell_max) + 1;
+    // items of one binning: n/32 full tiles plus one partial tile per cell;
+    // a level of the hierarchy may have a partial tile per particle
+    const bool lv = (ws_flags & SPH_WS_LEVELS) != 0;
+    p->item_max = n / 32 + (lv ? n : (n < ncell_max ? n : ncell_max)) + 1;
     p->item_cell = take(4 * (size_t)p->item_max);
     p->item_first = take(4 * (size_t)p->item_max);
     p->item_count = take(4 * (size_t)p->item_max);
@@ -109,6 +113,14 @@ bool make_plan(const sph_aos_layout &L, int64_t n, int64_t ncell_max, uint32_t w
     p->pack = take(3 * 16 * N);
     p->buf_origin = take(sizeof(double) * 3 * (N / 32 + 1));    // buffers of >= 32 records
     p->aos_tmp = (ws_flags & SPH_WS_REORDER) ? take((size_t)L.record_bytes * N) : 0;
+    if (lv) {
+        p->level = take(N);
+        p->level_tmp = take(N);
+        p->tlist = take(4 * N);
+        p->tcode = take(4 * N);
+        p->tscan = take(4 * (N + 1));
+        p->iscan = take(4 * (N + 1));
+    }
     p->stats = take(sizeof(DevStats));
     for (int f = 0; f < SPH_NFIELDS; ++f)
         for (int c = 0; c < 3; ++c)
@@ -200,6 +212,14 @@ sph_status sph_create(const sph_aos_layout *layout, const sph_params *params, in
     c->pack = (float4 *)(w + plan.pack);
     c->buf_origin = (double *)(w + plan.buf_origin);
     c->aos_tmp = (ws_flags & SPH_WS_REORDER) ? w + plan.aos_tmp : nullptr;
+    if (ws_flags & SPH_WS_LEVELS) {
+        c->level = (int8_t *)(w + plan.level);
+        c->level_tmp = (int8_t *)(w + plan.level_tmp);
+        c->tlist = (int32_t *)(w + plan.tlist);
+        c->tcode = (int32_t *)(w + plan.tcode);
+        c->tscan = (int32_t *)(w + plan.tscan);
+        c->iscan = (int32_t *)(w + plan.iscan);
+    }
     c->dstats = (DevStats *)(w + plan.stats);
     for (int f = 0; f < SPH_NFIELDS; ++f) {
         c->prec[f] = SPH_P_FP32;
@@ -239,6 +259,7 @@ sph_status sph_bin_cells(sph_ctx *c, double cell_edge, int32_t reorder_aos)
     c->valid = 0;
     c->binned = false;
     c->buffer = 0;
+    c->levels = false;
     if (run_binning(c, reorder_aos ? 1 : 0) != cudaSuccess) return SPH_ECUDA;
     if (run_items(c) != cudaSuccess) return SPH_ECUDA;
     c->binned = true;
@@ -325,7 +346,7 @@ sph_status sph_get_field_scale(const sph_ctx *c, int32_t *exp2_out)
 sph_status sph_density(sph_ctx *c, int32_t newton_steps)
 {
     if (!c || newton_steps < 0 || newton_steps > 32) return SPH_EINVAL;
-    if (!c->binned || c->buffer) return SPH_ESTATE;
+    if (!c->binned || c->buffer || c->levels) return SPH_ESTATE;
     const uint32_t need = SPH_BIT(SPH_F_X) | SPH_BIT(SPH_F_M) | SPH_BIT(SPH_F_H);
     if ((c->valid & need) != need) return SPH_ESTATE;
     // outputs keep their current format; packed outputs are not supported for
@@ -339,7 +360,7 @@ sph_status sph_density(sph_ctx *c, int32_t newton_steps)
 sph_status sph_force(sph_ctx *c)
 {
     if (!c) return SPH_EINVAL;
-    if (!c->binned || c->buffer) return SPH_ESTATE;
+    if (!c->binned || c->buffer || c->levels) return SPH_ESTATE;
     const uint32_t need = SPH_BIT(SPH_F_X) | SPH_BIT(SPH_F_V) | SPH_BIT(SPH_F_M) |
                           SPH_BIT(SPH_F_H) | SPH_BIT(SPH_F_RHO) | SPH_BIT(SPH_F_P) |
                           SPH_BIT(SPH_F_CS);
@@ -398,8 +419,76 @@ sph_status sph_bin_buffers(sph_ctx *c, int32_t buffer_size)
     c->valid = 0;
     c->binned = false;
     c->buffer = buffer_size;
+    c->levels = false;
     if (run_bin_buffers(c) != cudaSuccess) return SPH_ECUDA;
     c->binned = true;
+    return SPH_OK;
+}
+
+namespace {
+
+// h_l = min_d (box_d / 2^l) / 2: the largest h whose support fits a level-l
+// cell (exact in FP64: a power-of-two scaling)
+double level_cap(const sph_ctx *c, int l)
+{
+    double e = std::ldexp(c->params.box[0], -l);
+    for (int k = 1; k < 3; ++k) e = std::fmin(e, std::ldexp(c->params.box[k], -l));
+    return 0.5 * e;
+}
+
+}  // namespace
+
+sph_status sph_bin_levels(sph_ctx *c, int32_t level_min, int32_t level_max, double h_margin)
+{
+    if (!c) return SPH_EINVAL;
+    if (level_min < SPH_LEVEL_MIN || level_max > SPH_LEVEL_MAX || level_min > level_max) return SPH_EINVAL;
+    if (!std::isfinite(h_margin) || !(h_margin >= 0.0)) return SPH_EINVAL;
+    if (c->layout.offset[SPH_F_H] < 0) return SPH_EINVAL;
+    if (!(c->ws_flags & SPH_WS_LEVELS)) return SPH_ENOSPACE;
+    if (c->params.h_max > level_cap(c, level_min)) return SPH_ECAPACITY;
+    const int32_t F = 1 << level_max;
+    for (int k = 0; k < 3; ++k) {
+        c->nc[k] = F;
+        c->inv[k] = (double)F / c->params.box[k];
+        c->edge[k] = c->params.box[k] / (double)F;
+    }
+    c->ncell = (int64_t)F * F * F;
+    c->sub = 1;
+    c->valid = 0;
+    c->binned = false;
+    c->buffer = 0;
+    c->levels = true;
+    c->lvl_min = level_min;
+    c->lvl_max = level_max;
+    c->items_by_class = false;
+    if (run_bin_levels(c, 1.0 + h_margin) != cudaSuccess) return SPH_ECUDA;
+    c->binned = true;
+    return SPH_OK;
+}
+
+sph_status sph_density_levels(sph_ctx *c, int32_t newton_steps)
+{
+    if (!c || newton_steps < 0 || newton_steps > 32) return SPH_EINVAL;
+    if (!c->binned || !c->levels) return SPH_ESTATE;
+    const uint32_t need = SPH_BIT(SPH_F_X) | SPH_BIT(SPH_F_M) | SPH_BIT(SPH_F_H);
+    if ((c->valid & need) != need) return SPH_ESTATE;
+    if (run_density_levels(c, newton_steps) != cudaSuccess) return SPH_ECUDA;
+    c->valid |= SPH_BIT(SPH_F_RHO) | SPH_BIT(SPH_F_H);
+    if (c->valid & SPH_BIT(SPH_F_U)) c->valid |= SPH_BIT(SPH_F_P) | SPH_BIT(SPH_F_CS);
+    return SPH_OK;
+}
+
+sph_status sph_level_counts(sph_ctx *c, int64_t *done, int64_t *promoted)
+{
+    if (!c || !done || !promoted) return SPH_EINVAL;
+    DevStats d;
+    if (cudaMemcpyAsync(&d, c->dstats, sizeof(d), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+        return SPH_ECUDA;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SPH_ECUDA;
+    for (int l = 0; l <= SPH_LEVEL_MAX; ++l) {
+        done[l] = (int64_t)d.lvl_done[l];
+        promoted[l] = (int64_t)d.lvl_promoted[l];
+    }
     return SPH_OK;
 }
 
@@ -511,6 +600,10 @@ sph_status sph_reset_stats(sph_ctx *c)
     // keep nitems / max_occ (they describe the current binning)
     if (cudaMemsetAsync(c->dstats, 0, offsetof(DevStats, queue), c->stream) != cudaSuccess)
         return SPH_ECUDA;
+    const size_t lv = offsetof(DevStats, lvl_done);
+    if (cudaMemsetAsync(reinterpret_cast<uint8_t *>(c->dstats) + lv, 0, sizeof(DevStats) - lv, c->stream) !=
+        cudaSuccess)
+        return SPH_ECUDA;
     return SPH_OK;
 }
 
@@ -544,7 +637,8 @@ sph_status sph_set_tuning(sph_ctx *c, const sph_tuning *t)
     }
     if (n.stage_density < 32 || n.stage_force < 32) return SPH_EINVAL;
     if (n.stage_density > 65535 || n.stage_force > 65535) return SPH_EINVAL;
-    if (density_smem_bytes(n.block_threads, n.stage_density) > c->smem_optin) return SPH_EINVAL;
+    if (density_smem_bytes(n.block_threads, n.stage_density, (c->ws_flags & SPH_WS_LEVELS) != 0) > c->smem_optin)
+        return SPH_EINVAL;
     if (force_smem_bytes(n.block_threads, n.stage_force) > c->smem_optin) return SPH_EINVAL;
     c->tuning = n;
     return SPH_OK;
@@ -578,6 +672,7 @@ sph_status sph_describe(const sph_ctx *c, sph_desc *out)
     }
     out->valid = c->valid;
     out->subcells = c->sub;
+    out->off_level = rel(c->level);
     return SPH_OK;
 }
 

@@ -26,6 +26,34 @@ constexpr int kMaxBlock = 256;
 constexpr int kItemClasses = 32;                           // power-of-two cost classes of work items
 constexpr int kMaxCellsPerAxis = 4096;                     // the binning caps n_c per axis here
 constexpr float kSigma = 0.318309886183790671538f;        // 1/pi, 3D M4 normalisation
+constexpr int kLevelMin = SPH_LEVEL_MIN;                   // coarsest level allowed (4 cells per axis)
+constexpr int kLevelMax = SPH_LEVEL_MAX;                   // finest level: 3 x 10 key bits
+
+// Morton (Z-order) keys of 10-bit cell coordinates: bit b of x, y, z goes to
+// bit 3b, 3b + 1, 3b + 2.  Spreading by shifted masks (each step doubles the
+// gap between the bit groups) is the usual bit-interleave construction.
+__host__ __device__ __forceinline__ uint32_t morton_spread(uint32_t v)
+{
+    v &= 0x3FFu;
+    v = (v | (v << 16)) & 0x030000FFu;
+    v = (v | (v << 8)) & 0x0300F00Fu;
+    v = (v | (v << 4)) & 0x030C30C3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+__host__ __device__ __forceinline__ uint32_t morton_compact(uint32_t v)
+{
+    v &= 0x09249249u;
+    v = (v | (v >> 2)) & 0x030C30C3u;
+    v = (v | (v >> 4)) & 0x0300F00Fu;
+    v = (v | (v >> 8)) & 0x030000FFu;
+    v = (v | (v >> 16)) & 0x3FFu;
+    return v;
+}
+__host__ __device__ __forceinline__ uint32_t morton_key(uint32_t x, uint32_t y, uint32_t z)
+{
+    return morton_spread(x) | (morton_spread(y) << 1) | (morton_spread(z) << 2);
+}
 
 inline int ncomp(int f) { return (f == SPH_F_X || f == SPH_F_V || f == SPH_F_A) ? 3 : 1; }
 
@@ -40,7 +68,13 @@ struct DevStats {
     unsigned int queue;          // persistent work-queue head (zeroed before each launch)
     int nitems;                  // pair-kernel work items of the current binning
     int max_occ;                 // particles in the fullest cell
-    int pad[6];
+    unsigned int defer_n;        // level hierarchy: targets gathered one by one, and their queue head
+    unsigned int defer_q;
+    int pad[4];
+    // level hierarchy: per level, the particles computed there (final) and
+    // those moved from it to the next coarser level
+    unsigned long long lvl_done[kLevelMax + 1];
+    unsigned long long lvl_promoted[kLevelMax + 1];
 };
 
 // Byte offsets of every workspace array.
@@ -49,6 +83,7 @@ struct Plan {
     size_t cell_count, cell_start, scan_part, ghist;
     size_t item_cell, item_first, item_count, item_tmp, item_sorted, item_class, class_hist;
     size_t nngb, nngb_force, stage, aos_tmp, stats, key_hmax, origin, pack, buf_origin;
+    size_t level, level_tmp, tlist, tcode, tscan, iscan;   // level hierarchy (SPH_WS_LEVELS)
     size_t soa[SPH_NFIELDS][3];
     size_t total;
     int64_t item_max, nblk_radix;
@@ -287,7 +322,10 @@ struct sph_ctx {
     int sub = 1;                  // sub-cells per cell edge of the last binning
     bool binned = false;
     int32_t buffer = 0;           // buffer mode: records taken in buffers of this size (0: cell lists)
+    bool levels = false;          // level mode: Morton order over a hierarchy of grids
+    int32_t lvl_min = 0, lvl_max = 0;
     sph::LaunchCache lc_density, lc_force;   // launch shapes of the persistent pair kernels
+    sph::LaunchCache lc_density_lv, lc_density_one;   // ... and of the density over the level hierarchy
     int sorted_buf = 0;          // which ping-pong buffer holds the sorted keys/values
 
     // workspace arrays
@@ -307,6 +345,10 @@ struct sph_ctx {
     double *buf_origin = nullptr; // buffer mode: first position of every buffer, 3 x nbuf, axis-major
     float4 *pack = nullptr;       // 3 x n: the force's packed FP32 inputs per slot
     uint8_t *aos_tmp = nullptr;
+    // level hierarchy: level of every slot, of every particle before the
+    // sort, and one level's target slots, their cell codes and two scans
+    int8_t *level = nullptr, *level_tmp = nullptr;
+    int32_t *tlist = nullptr, *tcode = nullptr, *tscan = nullptr, *iscan = nullptr;
     sph::DevStats *dstats = nullptr;
     void *soa[SPH_NFIELDS][3] = {};
     int prec[SPH_NFIELDS] = {};
@@ -329,6 +371,10 @@ cudaError_t run_soa_to_aos(sph_ctx *c, uint32_t fields);
 cudaError_t run_density(sph_ctx *c, int newton_steps);
 cudaError_t run_force(sph_ctx *c);
 cudaError_t run_kick_drift(sph_ctx *c, double dt_kick, double dt_drift, uint32_t wb_fields);
+// level hierarchy (k_bin.cu, k_pairs.cu)
+cudaError_t run_bin_levels(sph_ctx *c, double grow);
+cudaError_t run_level_items(sph_ctx *c, int level);
+cudaError_t run_density_levels(sph_ctx *c, int newton_steps);
 // host-side conversion (host_convert.cu)
 size_t host_stage_bytes(const sph_ctx *c);
 cudaError_t run_aos_to_soa_host(sph_ctx *c, const uint8_t *host_aos, uint32_t fields, uint8_t *stage,
@@ -358,6 +404,6 @@ struct BinRaw {
     int32_t *out_perm, *out_cell, *out_start;
 };
 cudaError_t bin_raw(const BinRaw &b, cudaStream_t s);
-size_t density_smem_bytes(int block_threads, int stage_cap);
+size_t density_smem_bytes(int block_threads, int stage_cap, bool levels = false);
 size_t force_smem_bytes(int block_threads, int stage_cap);
 }  // namespace sph

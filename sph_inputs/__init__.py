@@ -18,6 +18,8 @@ follows one workload description:
   particles.
 * ``gaussian_mixture`` 8 isotropic Gaussians plus a 20% uniform background,
   one global h with 48 neighbours on average.
+* ``gaussian_mixture_adaptive`` the same positions, h per particle from the
+  mixture's number density (48 neighbours locally).
 * ``long_run``         large jittered lattice with random velocities.
 * ``buffer_blocks``    the paper's benchmark grouping: blocks of 4x4x4 (B = 64)
   jittered lattice particles, each block a contiguous buffer of records.
@@ -241,6 +243,45 @@ def gaussian_mixture(n: int = 16_777_216, seed: int = SEED_BASE + 4, n_blob: int
     return Workload("gaussian_mixture", aos, (1.0, 1.0, 1.0), h_cap=h,
                     cell_edge=1.0 / ncell, newton_steps=0,
                     meta={"h": h, "sigma": sig, "centres": centres})
+
+
+def gaussian_mixture_adaptive(n: int = 16_777_216, seed: int = SEED_BASE + 4, n_blob: int = 8,
+                              background: float = 0.2) -> Workload:
+    """The clustered set of ``gaussian_mixture`` (the same positions for the
+    same seed) with one smoothing length per particle, from the number density
+    of the distribution the positions are drawn from,
+        nd(x) = n_bg + sum_k N_k (2 pi sigma_k^2)^(-3/2) exp(-|x - c_k|^2 / (2 sigma_k^2))
+    (nearest periodic image of each centre), through (4 pi / 3) (2h)^3 nd = 48,
+    the neighbour number of the global-h sets; the density's Newton steps refine
+    it.  At N = 2^24, h runs from ~2.4e-4 in the densest core to ~7.5e-3 in the
+    background.  The level range of a cell hierarchy (2^l cells per axis, h
+    cap 2^-l / 2) follows from it: level_max is the finest level whose cap holds
+    the smallest h (at most 10), level_min the finest whose cap holds twice the
+    largest h (at least 2), and h_cap is level_min's cap."""
+    wl = gaussian_mixture(n, seed, n_blob, background)
+    pos = wl.col("x")
+    sig, centres = wl.meta["sigma"], wl.meta["centres"]
+    n_bg = int(round(background * n))
+    per = (n - n_bg) // n_blob
+    counts = [per] * n_blob
+    counts[-1] += (n - n_bg) - per * n_blob
+    nd = np.full(n, float(n_bg))
+    step = 1 << 20
+    for k in range(n_blob):
+        norm = counts[k] * (2.0 * math.pi * sig[k] ** 2) ** -1.5
+        for a in range(0, n, step):
+            d = pos[a:a + step] - centres[k]
+            d -= np.round(d)
+            nd[a:a + step] += norm * np.exp(-np.einsum("ij,ij->i", d, d) / (2.0 * sig[k] ** 2))
+    h = 0.5 * (3.0 * N_NGB / (4.0 * math.pi * nd)) ** (1.0 / 3.0)
+    _set(wl.aos, "h", h)
+    lvl_max = int(min(10, math.floor(math.log2(1.0 / (2.0 * h.min())))))
+    lvl_min = int(max(2, min(lvl_max, math.floor(math.log2(1.0 / (4.0 * h.max()))))))
+    h_cap = 0.5 * 2.0 ** -lvl_min
+    meta = dict(wl.meta)
+    meta.update({"levels": (lvl_min, lvl_max), "h_min": float(h.min()), "h_max": float(h.max())})
+    return Workload("gaussian_mixture_adaptive", wl.aos, (1.0, 1.0, 1.0), h_cap=h_cap,
+                    cell_edge=2.0 * h_cap, newton_steps=5, meta=meta)
 
 
 def long_run(nx: int = 512, ny: int = 256, nz: int = 256, seed: int = SEED_BASE + 5,

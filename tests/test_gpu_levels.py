@@ -1,0 +1,189 @@
+"""The density over the level hierarchy (per-particle h on the clustered set).
+
+* Binning: the finest cells' Morton keys, the levels and the slot order are
+  bit-exact with the oracle's (integer work).
+* Density with Newton steps: rho, h and P match the FP64 oracle -- one
+  global h cap, brute-force neighbours -- within 1e-5 relative on sampled
+  particles of every level, the promoted ones (h outgrew their level) among
+  them; the level counters account for every particle.
+* One level: the hierarchy reproduces the single-grid density of the same
+  cells bit for bit (same candidates in the same order, same frames).
+"""
+import numpy as np
+import pytest
+
+import sph_inputs
+from gpu_util import make_sph
+
+pytestmark = pytest.mark.gpu
+
+import paper_2512_05516_gb300 as sph_mod  # noqa: E402
+
+
+def _wl(n, seed=sph_inputs.SEED_BASE + 4):
+    return sph_inputs.gaussian_mixture_adaptive(n, seed=seed)
+
+
+@pytest.mark.parametrize("n,margin", [(50_003, 0.0), (65_536, 0.1)])
+def test_level_binning_is_bit_exact(orc, n, margin):
+    wl = _wl(n)
+    lo, hi = wl.meta["levels"]
+    s = make_sph(wl, ws_flags=sph_mod.WS_LEVELS)
+    s.bin_levels(lo, hi, margin)
+    key, lev, perm = orc.levels(wl.col("x"), wl.col("h"), wl.box, lo, hi, margin)
+    assert np.array_equal(s.perm().cpu().numpy(), perm)
+    assert np.array_equal(s.slot_cell().cpu().numpy(), key[perm])
+    assert np.array_equal(s.levels().cpu().numpy(), lev[perm])
+    s.close()
+
+
+def _run_levels(wl, newton, margin, prec=None):
+    lo, hi = wl.meta["levels"]
+    s = make_sph(wl, ws_flags=sph_mod.WS_LEVELS)
+    s.bin_levels(lo, hi, margin)
+    lev0 = s.levels().cpu().numpy().copy()
+    s.aos_to_soa(sph_mod.FIELDS_DENSITY, prec)
+    s.density_levels(newton)
+    s.soa_to_aos(sph_mod.mask("rho", "h", "P"))
+    perm = s.perm().cpu().numpy()
+    out = s.aos.cpu().numpy()
+    lev = np.empty(wl.n, np.int8)
+    lev[perm] = s.levels().cpu().numpy()
+    first = np.empty(wl.n, np.int8)
+    first[perm] = lev0
+    res = {"rho": out[:, 11].copy(), "h": out[:, 10].copy(), "P": out[:, 13].copy(),
+           "level": lev, "level0": first, "counts": s.level_counts(), "stats": s.stats()}
+    s.close()
+    return res
+
+
+def _targets(g, n, rng, k_random=300, k_level=25, k_promoted=150):
+    t = [rng.choice(n, k_random, replace=False)]
+    for l in np.unique(g["level"]):
+        idx = np.flatnonzero(g["level"] == l)
+        t.append(rng.choice(idx, min(k_level, idx.size), replace=False))
+    prom = np.flatnonzero(g["level"] < g["level0"])
+    if prom.size:
+        t.append(rng.choice(prom, min(k_promoted, prom.size), replace=False))
+    return np.unique(np.concatenate(t))
+
+
+@pytest.mark.parametrize("margin", [0.0, 0.1])
+def test_level_density_matches_oracle(orc, margin):
+    wl = _wl(262_144 - 77)
+    lo, hi = wl.meta["levels"]
+    g = _run_levels(wl, 5, margin)
+    done, prom = g["counts"]
+    # every particle was computed once, at the level it ended on
+    assert sum(done) == wl.n
+    assert np.array_equal(np.bincount(g["level"], minlength=sph_mod.LEVEL_MAX + 1), done)
+    assert np.all(g["level"] <= g["level0"]) and g["level"].min() >= lo
+    assert sum(prom) == int((g["level0"] - g["level"]).sum())
+    if margin == 0.0:
+        assert sum(prom) > 100          # the margin-free start exercises the promotion
+    assert g["stats"]["error_bits"] & (sph_mod.ERR_NONFINITE | sph_mod.ERR_OUTSIDE) == 0
+    rng = np.random.default_rng(5)
+    t = _targets(g, wl.n, rng)
+    o = orc.density(wl.col("x"), wl.col("m"), wl.col("h"), wl.box, wl.eta, wl.h_cap, 5, brute=True,
+                    targets=t)
+    assert (np.abs(g["h"][t] - o["h"]) / o["h"]).max() <= 1e-5
+    assert (np.abs(g["rho"][t] - o["rho"]) / o["rho"]).max() <= 1e-5
+    P, _ = orc.eos(o["rho"], wl.col("u")[t], wl.gamma)
+    assert (np.abs(g["P"][t] - P) / P).max() <= 1e-5
+    # each particle's final h fits the cells of the level it was computed at
+    cap = 0.5 * 2.0 ** -g["level"].astype(np.float64)
+    assert np.all(g["h"] <= cap * (1 + 1e-6))
+
+
+def test_level_density_reduced_storage(orc):
+    # m and h stored in BF16: the oracle takes the same rounded inputs
+    wl = _wl(131_072 + 13)
+    lo, hi = wl.meta["levels"]
+    s = make_sph(wl, ws_flags=sph_mod.WS_LEVELS)
+    s.bin_levels(lo, hi, 0.05)
+    s.aos_to_soa(sph_mod.FIELDS_DENSITY, {"m": "bf16", "h": "bf16"})
+    s.density_levels(3)
+    s.soa_to_aos(sph_mod.mask("rho", "h"))
+    out = s.aos.cpu().numpy()
+    s.close()
+    m_q = orc.quantize(wl.col("m"), "bf16")[0]
+    h_q = orc.quantize(wl.col("h"), "bf16")[0]
+    t = np.random.default_rng(6).choice(wl.n, 400, replace=False)
+    o = orc.density(wl.col("x"), m_q, h_q, wl.box, wl.eta, wl.h_cap, 3, brute=True, targets=t)
+    assert (np.abs(out[t, 11] - o["rho"]) / o["rho"]).max() <= 1e-5
+    # h is written back through BF16: within one BF16 step of the oracle's
+    h_o = orc.quantize(o["h"], "bf16")[0]
+    assert (np.abs(out[t, 10] - h_o) / h_o).max() <= 2.0 ** -7
+
+
+def test_one_level_equals_the_single_grid():
+    # levels l..l over 2^l cells per axis and sph_density over the same
+    # cells (one sub-cell): identical candidates, order and frames.  The
+    # stage holds every item's neighbourhood, so both kernels take their list
+    # path (a level item that does not fit is gathered target by target, a
+    # cell item is streamed: the same pairs, summed in another order).
+    wl = sph_inputs.uniform_density(131_072, seed=sph_inputs.SEED_BASE + 21)
+    h = float(wl.col("h").max())
+    l = int(np.floor(np.log2(1.0 / (4.0 * h))))
+    wl.h_cap = 0.5 * 2.0 ** -l
+    wl.cell_edge = 2.0 ** -l
+    a = make_sph(wl, ws_flags=sph_mod.WS_LEVELS)
+    a.set_tuning(subcells=1, item_order=0, stage_density=4096)
+    a.bin_levels(l, l, 0.0)
+    a.aos_to_soa(sph_mod.FIELDS_DENSITY)
+    a.density_levels(4)
+    a.soa_to_aos(sph_mod.mask("rho", "h", "P"))
+    b = make_sph(wl)
+    b.set_tuning(subcells=1, item_order=0, stage_density=4096)
+    b.bin_cells(wl.cell_edge)
+    assert b.stats()["ncell"] == (2 ** l,) * 3
+    b.aos_to_soa(sph_mod.FIELDS_DENSITY)
+    b.density(4)
+    b.soa_to_aos(sph_mod.mask("rho", "h", "P"))
+    ra, rb = a.aos.cpu().numpy(), b.aos.cpu().numpy()
+    for col in (10, 11, 13):
+        assert np.array_equal(ra[:, col], rb[:, col]), col
+    pa = np.empty(wl.n, np.int32)
+    pa[a.perm().cpu().numpy()] = a.nngb().cpu().numpy()
+    pb = np.empty(wl.n, np.int32)
+    pb[b.perm().cpu().numpy()] = b.nngb().cpu().numpy()
+    assert np.array_equal(pa, pb)
+    assert a.stats()["pairs_density"] == b.stats()["pairs_density"]
+    a.close()
+    b.close()
+
+
+def test_level_calls_check_their_arguments_and_order():
+    wl = _wl(20_000)
+    lo, hi = wl.meta["levels"]
+    s = make_sph(wl)                                    # no level workspace
+    with pytest.raises(sph_mod.SphError) as e:
+        s.bin_levels(lo, hi)
+    assert e.value.status == sph_mod._capi.ENOSPACE
+    s.close()
+    s = make_sph(wl, ws_flags=sph_mod.WS_LEVELS)
+    with pytest.raises(sph_mod.SphError) as e:         # not binned for levels
+        s.density_levels(0)
+    assert e.value.status == sph_mod._capi.ESTATE
+    for a, b, m in ((1, hi, 0.0), (lo, 11, 0.0), (hi, lo, 0.0), (lo, hi, -0.1), (lo, hi, float("nan"))):
+        with pytest.raises(sph_mod.SphError) as e:
+            s.bin_levels(a, b, m)
+        assert e.value.status == sph_mod._capi.EINVAL, (a, b, m)
+    with pytest.raises(sph_mod.SphError) as e:         # h_max above the coarsest cap
+        s.bin_levels(lo + 1, hi, 0.0)
+    assert e.value.status == sph_mod._capi.ECAPACITY
+    s.bin_levels(lo, hi, 0.0)
+    s.aos_to_soa(sph_mod.FIELDS_FORCE)
+    for call in (lambda: s.density(0), s.force):       # single-grid kernels refuse level mode
+        with pytest.raises(sph_mod.SphError) as e:
+            call()
+        assert e.value.status == sph_mod._capi.ESTATE
+    with pytest.raises(sph_mod.SphError):              # positions are not written back
+        s.soa_to_aos(sph_mod.mask("x"))
+    s.density_levels(2)
+    # back to cells: the single-grid density runs again
+    s.bin_cells(wl.cell_edge)
+    s.aos_to_soa(sph_mod.FIELDS_DENSITY)
+    s.density(0)
+    assert s.stats()["error_bits"] & (sph_mod.ERR_NONFINITE | sph_mod.ERR_OUTSIDE) == 0
+    s.close()

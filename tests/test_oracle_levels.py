@@ -1,0 +1,83 @@
+"""Pins of the oracle's level-hierarchy binning (per-particle h): Morton keys
+against hand-derived codes and their inverse, the nesting of the levels
+(a level-l cell is a key prefix), the level rule at its boundaries, and the
+stable order by key."""
+import math
+
+import numpy as np
+import pytest
+
+
+def _centre(f, F):
+    return (np.asarray(f, dtype=np.float64) + 0.5) / F
+
+
+def test_morton_keys_of_hand_derived_cells(orc):
+    F = 16
+    cells = [(1, 0, 0), (0, 1, 0), (0, 0, 1), (2, 0, 0), (5, 3, 6), (15, 15, 15), (0, 0, 0)]
+    # (5, 3, 6) = (101, 011, 110): bit 0 -> 0b011, bit 1 -> 0b110, bit 2 -> 0b101
+    want = [1, 2, 4, 8, 3 + (6 << 3) + (5 << 6), 4095, 0]
+    x = _centre(cells, F)
+    key, lev, perm = orc.levels(x, np.full(len(cells), 1e-4), (1.0, 1.0, 1.0), 2, 4)
+    assert key.tolist() == want
+
+
+def _decode(key, bits):
+    f = np.zeros((key.shape[0], 3), np.int64)
+    k = key.astype(np.int64)
+    for b in range(bits):
+        for a in range(3):
+            f[:, a] |= ((k >> (3 * b + a)) & 1) << b
+    return f
+
+
+def test_keys_invert_to_the_finest_cell_and_nest(orc):
+    rng = np.random.default_rng(3)
+    box = (1.0, 0.5, 2.0)
+    x = rng.uniform(0.0, 1.0, (5000, 3)) * np.asarray(box)
+    lmax = 9
+    key, _, _ = orc.levels(x, np.full(5000, 1e-6), box, 2, lmax)
+    F = 2 ** lmax
+    # the inverse map gives floor(x F / L) on every axis
+    assert np.array_equal(_decode(key, lmax), np.floor(x * (F / np.asarray(box))).astype(np.int64))
+    # level l's cell is the key prefix: the keys of a hierarchy ending at l
+    for l in (2, 5, 8):
+        kl, _, _ = orc.levels(x, np.full(5000, 1e-6), box, 2, l)
+        assert np.array_equal(key >> (3 * (lmax - l)), kl)
+
+
+def test_level_rule_at_its_boundaries(orc):
+    box = (1.0, 1.0, 0.5)                # caps follow the shortest edge
+    lo, hi = 3, 7
+    cap = {l: 0.5 * min(b / 2 ** l for b in box) for l in range(lo, hi + 1)}
+    margin = 0.25
+    h = [cap[5] / (1 + margin),                           # exactly at level 5's cap
+         math.nextafter(cap[5] / (1 + margin), 1.0),      # just above it -> level 4
+         cap[hi] / 4,                                     # small -> the finest level
+         cap[lo] * 10,                                    # larger than every cap -> level_min
+         float("nan"), float("inf"), 0.0, -1e-3]          # not finite and positive -> level_min
+    want = [5, 4, hi, lo, lo, lo, lo, lo]
+    # the exact-boundary case must hold in the product h (1 + margin)
+    assert h[0] * (1 + margin) <= cap[5]
+    assert h[1] * (1 + margin) > cap[5]
+    x = np.full((len(h), 3), 0.1)
+    _, lev, _ = orc.levels(x, np.asarray(h), box, lo, hi, margin)
+    assert lev.tolist() == want
+
+
+def test_order_is_stable_by_key(orc):
+    rng = np.random.default_rng(4)
+    x = rng.uniform(0.0, 1.0, (20000, 3))
+    x[::7] = x[3]                        # many equal keys
+    key, _, perm = orc.levels(x, np.full(20000, 1e-3), (1.0, 1.0, 1.0), 2, 6)
+    assert np.array_equal(perm, np.argsort(key, kind="stable"))
+    k = key[perm]
+    assert np.all(np.diff(k) >= 0)
+    same = np.flatnonzero(np.diff(k) == 0)
+    assert np.all(perm[same + 1] > perm[same])
+
+
+def test_bad_levels_are_refused(orc):
+    x = np.zeros((1, 3))
+    with pytest.raises(ValueError):
+        orc.levels(x, np.ones(1), (1, 1, 1), 5, 4)
