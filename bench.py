@@ -820,48 +820,58 @@ def run_uneven(n: int = 16_777_216):
             "cells_per_axis": nc[0], "variants": rows}
 
 
-def _levels_density(sph, wl, dev, stream, margin, reps):
+def _levels_density(sph, wl, dev, stream, margin, reps, force=True):
     """Bin for the hierarchy, convert, and time the density with 5 Newton
-    steps over it (reps timed runs after one warm-up; counters of the last)."""
+    steps and the force over it (reps timed runs after one warm-up; counters
+    of the last)."""
     import torch
     lo, hi = wl.meta["levels"]
     aos = torch.from_numpy(wl.aos).to(dev)
     params = sph.make_params(wl.box, eta=wl.eta, h_max=wl.h_cap)
     s = sph.Sph(aos, sph.layout_112(), params, 27, sph.WS_LEVELS, stream=stream)
-    ms_bin, ms_den = [], []
+    ms_bin, ms_den, ms_frc = [], [], []
     with torch.cuda.stream(stream):
         for r in range(reps + 1):
             s.reset_stats()
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
             ev[0].record(stream)
             s.bin_levels(lo, hi, margin)
-            s.aos_to_soa(sph.FIELDS_DENSITY)
+            s.aos_to_soa(sph.FIELDS_FORCE)
             ev[1].record(stream)
             s.density_levels(5)
             ev[2].record(stream)
-            ev[2].synchronize()
+            if force:
+                s.force_levels()
+            ev[3].record(stream)
+            ev[3].synchronize()
             if r:
                 ms_bin.append(ev[0].elapsed_time(ev[1]))
                 ms_den.append(ev[1].elapsed_time(ev[2]))
+                ms_frc.append(ev[2].elapsed_time(ev[3]))
         st = s.stats()
         done, prom = s.level_counts()
     s.close()
     del aos
     torch.cuda.empty_cache()
     td = statistics.median(ms_den)
-    return {"margin": margin, "bin_and_convert_ms": statistics.median(ms_bin), "density_ms": td,
+    out = {"margin": margin, "bin_and_convert_ms": statistics.median(ms_bin), "density_ms": td,
             "density_pairs_per_s": st["pairs_density"] / (ms_den[-1] / 1e3),
             "tests_per_pair": st["tests_density"] / max(st["pairs_density"], 1),
             "particles_per_level": {str(l): done[l] for l in range(lo, hi + 1)},
             "promoted_per_level": {str(l): prom[l] for l in range(lo, hi + 1)},
             "error_bits": st["error_bits"]}
+    if force:
+        out.update({"force_ms": statistics.median(ms_frc),
+                    "force_pairs_per_s": st["pairs_force"] / (ms_frc[-1] / 1e3),
+                    "force_tests_per_pair": st["tests_force"] / max(st["pairs_force"], 1)})
+    return out
 
 
 def run_levels(n: int = 16_777_216, n_compare=(262_144, 1_048_576), reps: int = 3):
     """Per-particle h on the clustered set (h from the mixture's local number
-    density, 48 neighbours; 5 Newton steps): the density over the level
-    hierarchy at full size for three level margins, and at smaller sizes the
-    same density next to one grid sized for the largest h (the only grid the
+    density, 48 neighbours; 5 Newton steps): the density and the force over
+    the level hierarchy at full size for three level margins, and at smaller
+    sizes the density next to one grid sized for the largest h (the only grid the
     single-level path can use: its cells hold the whole support of the
     background particles, so the dense cores share a handful of cells)."""
     import torch
@@ -876,7 +886,7 @@ def run_levels(n: int = 16_777_216, n_compare=(262_144, 1_048_576), reps: int = 
     del wl
     for nc_ in n_compare:
         w = sph_inputs.gaussian_mixture_adaptive(nc_)
-        lv = _levels_density(sph, w, dev, stream, 0.1, 1)
+        lv = _levels_density(sph, w, dev, stream, 0.1, 1, force=False)
         aos = torch.from_numpy(w.aos).to(dev)
         nc = int(math.floor(1.0 / (2.0 * w.h_cap)))
         params = sph.make_params(w.box, eta=w.eta, h_max=w.h_cap)

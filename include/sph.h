@@ -435,10 +435,12 @@ sph_status sph_buffer_drift(sph_ctx *ctx, int32_t source, double dt);
  * positive.  The margin leaves room for h to grow during the Newton steps. */
 #define SPH_LEVEL_MIN 2
 #define SPH_LEVEL_MAX 10
+#define SPH_LEVELS_MAX 8       /* levels in one hierarchy, at most */
 
 /* Bin for the hierarchy: keys, the stable sort, and every particle's level.
  * Needs a context created with SPH_WS_LEVELS; requires
- * SPH_LEVEL_MIN <= level_min <= level_max <= SPH_LEVEL_MAX, h_margin >= 0
+ * SPH_LEVEL_MIN <= level_min <= level_max <= SPH_LEVEL_MAX,
+ * level_max - level_min < SPH_LEVELS_MAX, h_margin >= 0
  * and h_max <= h_level_min (the coarsest cells hold the largest support).
  * Invalidates every SoA field; leaves cell and buffer mode (sph_density,
  * sph_force and the buffer calls return SPH_ESTATE until sph_bin_cells or
@@ -460,6 +462,17 @@ sph_status sph_bin_levels(sph_ctx *ctx, int32_t level_min, int32_t level_max, do
  * sph_bin_levels and sph_aos_to_soa of X, M, H.  Errors: SPH_EINVAL
  * (newton_steps < 0 or > 32), SPH_ESTATE, SPH_ECUDA. */
 sph_status sph_density_levels(sph_ctx *ctx, int32_t newton_steps);
+
+/* S5 over the hierarchy: the force of sph_force (Eq. 7 with Monaghan
+ * viscosity, Eq. 5; pairs r < h_i + h_j) with every particle's own h, after
+ * sph_density_levels has fixed the levels.  A level-l particle's h is at
+ * most h_l, so a partner of a finer or equal level lies in the 27 cells of
+ * level l around it, and one of a coarser level l' in the 27 cells of level
+ * l' around it: each particle searches, for every level l', the particles of
+ * level l' in the cells of level min(l, l'), and finds each pair once.
+ * Reads X, V, M, H, RHO, P, CS; writes A and DUDT (FP32).  Errors:
+ * SPH_ESTATE (not in level mode, or inputs not current), SPH_ECUDA. */
+sph_status sph_force_levels(sph_ctx *ctx);
 
 /* Per level l (index l of both arrays, SPH_LEVEL_MAX + 1 entries each):
  * done[l] the particles whose density was computed at level l, promoted[l]

@@ -17,7 +17,7 @@ from ._capi import (AOS_F32, AOS_F64, BIT, ERR_HCAP, ERR_NEWTON, ERR_NONFINITE, 
                     F_A, F_CS, F_DUDT, F_H, F_M, F_P, F_RHO, F_U, F_V, F_X, FIELD_NAMES,
                     FIELDS_DENSITY, FIELDS_FORCE, FIELDS_KICK, FIELDS_OUTPUT, FLAG_PLAIN_SUM,
                     NCOMP, P_BF16, P_FP16, P_FP32, P_FP32_M10, P_FP32_M16, PREC, SPH_NFIELDS,
-                    BUFFER_MAX, BUFFER_MIN, LEVEL_MAX, LEVEL_MIN, SRC_AOS, SRC_SOA, WS_LEVELS, WS_REORDER,
+                    BUFFER_MAX, BUFFER_MIN, LEVEL_MAX, LEVEL_MIN, LEVELS_MAX, SRC_AOS, SRC_SOA, WS_LEVELS, WS_REORDER,
                     sph_aos_layout, sph_desc,
                     sph_params, sph_stats, sph_tuning)
 
@@ -129,6 +129,10 @@ def sph_bin_levels(ctx, level_min: int, level_max: int, h_margin: float) -> int:
 
 def sph_density_levels(ctx, newton_steps: int) -> int:
     return _lib.sph_density_levels(ctx, int(newton_steps))
+
+
+def sph_force_levels(ctx) -> int:
+    return _lib.sph_force_levels(ctx)
 
 
 def sph_level_counts(ctx):
@@ -412,6 +416,9 @@ class Sph:
 
     def density_levels(self, newton_steps: int = 0):
         _check(sph_density_levels(self.ctx, newton_steps), "sph_density_levels")
+
+    def force_levels(self):
+        _check(sph_force_levels(self.ctx), "sph_force_levels")
 
     def level_counts(self):
         """(done, promoted): per level l (index l), the particles computed

@@ -34,7 +34,7 @@ AOS_F64, AOS_F32 = 0, 1
 FLAG_PLAIN_SUM = 1
 WS_REORDER = 1
 WS_LEVELS = 2
-LEVEL_MIN, LEVEL_MAX = 2, 10
+LEVEL_MIN, LEVEL_MAX, LEVELS_MAX = 2, 10, 8
 ERR_NONFINITE, ERR_OUTSIDE, ERR_HCAP, ERR_NEWTON, ERR_TIMEOUT = 1, 2, 4, 8, 16
 SRC_AOS, SRC_SOA = 0, 1
 BUFFER_MIN, BUFFER_MAX = 32, 256
@@ -110,6 +110,7 @@ PROTOTYPES = {
     "sph_buffer_drift": (C.c_int, [_P, C.c_int32, C.c_double]),
     "sph_bin_levels": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_double]),
     "sph_density_levels": (C.c_int, [_P, C.c_int32]),
+    "sph_force_levels": (C.c_int, [_P]),
     "sph_level_counts": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "sph_destroy": (None, [_P]),
     "sph_status_str": (C.c_char_p, [C.c_int]),

@@ -470,6 +470,23 @@ __global__ void k_lvl_items(const int32_t *tcode, const int32_t *M, const int32_
     icount[o] = min(kItemTile, end - (int32_t)j);
 }
 
+// per-level lists: level l's slots in slot (Morton) order at
+// [lstart[l], lstart[l+1]) of plist, with their keys
+__global__ void k_lvl_list(const int8_t *level, const int32_t *pos, const int32_t *key, int64_t n, int l,
+                           const int32_t *lstart, int32_t *plist, int32_t *pkey)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n || level[k] != l) return;
+    const int32_t j = lstart[l] + pos[k];
+    plist[j] = (int32_t)k;
+    pkey[j] = key[k];
+}
+
+__global__ void k_lvl_list_next(int32_t *lstart, int l, const int32_t *M)
+{
+    if (threadIdx.x == 0) lstart[l + 1] = lstart[l] + *M;
+}
+
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
@@ -690,6 +707,26 @@ cudaError_t run_level_items(sph_ctx *c, int l)
                                   c->item_first, c->item_count, c->dstats);
     c->launches += 1;
     return cudaGetLastError();
+}
+
+cudaError_t run_level_lists(sph_ctx *c, int32_t *plist, int32_t *pkey)
+{
+    cudaStream_t s = c->stream;
+    cudaError_t e;
+    const int64_t n = c->n;
+    const unsigned g = blocks_for(n, 256);
+    if ((e = cudaMemsetAsync(c->lstart, 0, sizeof(int32_t) * (kLevelMax + 2), s)) != cudaSuccess) return e;
+    for (int l = c->lvl_min; l <= c->lvl_max; ++l) {
+        k_lvl_flags<<<g, 256, 0, s>>>(c->level, n, l, c->tscan);
+        c->launches += 1;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = scan_exclusive(c->tscan, c->tscan, n, c->scan_part, s, &c->launches)) != cudaSuccess) return e;
+        k_lvl_list<<<g, 256, 0, s>>>(c->level, c->tscan, c->slot_cell(), n, l, c->lstart, plist, pkey);
+        k_lvl_list_next<<<1, 32, 0, s>>>(c->lstart, l, c->tscan + n);
+        c->launches += 2;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t run_items(sph_ctx *c)

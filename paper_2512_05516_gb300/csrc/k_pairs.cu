@@ -70,6 +70,12 @@ struct Common {
     int fine_n;                      // cells per axis at the finest level
     float fine_edge[3];
     int32_t *defer;                  // slots of the targets gathered one by one (k_density_one)
+    // level force: the slots of every level in Morton order, one list after
+    // the other (level l at [lstart[l], lstart[l+1])), their keys, and the
+    // largest h of each level's particles
+    const int32_t *plist, *pkey, *lstart;
+    int lvl_min, lvl_max;
+    float lcap[kLevelMax + 1];
 };
 
 struct DensityArgs {
@@ -105,6 +111,7 @@ struct ForceArgs {
     const float4 *pA;                // (x, y, z, h), positions cell-relative
     const float4 *pB;                // (vx, vy, vz, m)
     const float4 *pC;                // (P / rho^2, rho, c, 0)
+    int lvl;                         // level force: the level of this launch's items
 };
 
 // The candidate stream of one warp: the kept (non-empty, within reach)
@@ -926,10 +933,94 @@ __global__ void __launch_bounds__(256) k_force_pack(ForceArgs a, const int32_t *
         pC[k] = make_float4(P / (rho * rho), rho, ld_val(a.cs.p[0], a.cs.fmt, k) * a.cs.dec, 0.0f);
         if (!(hv > 0.0f && hv <= 3.0e38f)) hv = a.h_cap;       // NaN / non-positive: assume h_max
     }
+    if (!key_hmax) return;           // level mode: no sub-cell table
     const unsigned peers = __match_any_sync(FULL, key);
     const unsigned mx = __reduce_max_sync(peers, __float_as_uint(hv));
     if (ok && (threadIdx.x & 31) == __ffs(peers) - 1)
         atomicMax(reinterpret_cast<unsigned *>(key_hmax) + key, mx);
+}
+
+// The level force's candidate streams for an item of level `lvl` whose cell
+// has Morton code `cell` at that level and finest-cell origin `org`: one per
+// level l' of the hierarchy, over the list of level-l' particles.  Pairs need
+// r < h_i + h_j; h_j <= h_l' and h_i <= h_lvl, so a partner of a finer or
+// equal level lies in the 27 cells of level lvl around the item's cell, and
+// one of a coarser level in the 27 cells of its own level l' around the
+// item's level-l' cell: stencil level s = min(l', lvl).  Entry (l', t) is
+// stencil cell t at level s, kept when its box comes within hw + h_l' of the
+// warp box; its run in list l' is found by binary search on the keys.
+// Entries go in (l', t) order, at most 8 x 27.
+__device__ int lvl_force_table(const Common &c, int cell, int lvl, int3 org, const Box &box, float hw, Tab &tab,
+                               int lane)
+{
+    const int K = c.lvl_max - c.lvl_min + 1;
+    const int nent = 27 * K;
+    const int E = (nent + 31) / 32;
+    constexpr int kE = (27 * 8 + 31) / 32;
+    int cnt[kE], st[kE];
+    int local = 0, kept = 0;
+#pragma unroll
+    for (int i = 0; i < kE; ++i) {
+        cnt[i] = 0;
+        st[i] = 0;
+        const int e = lane * E + i;
+        if (i < E && e < nent) {
+            const int lp = c.lvl_min + e / 27, t = e % 27;
+            const int sl = min(lp, lvl);                       // stencil level
+            const int dn = c.lvl_max - sl;                     // its cells in finest cells: 2^dn
+            const uint32_t cs = (uint32_t)cell >> (3 * (lvl - sl));
+            const int da[3] = {t % 3 - 1, (t / 3) % 3 - 1, t / 9 - 1};
+            const int oc[3] = {(int)morton_compact(cs), (int)morton_compact(cs >> 1), (int)morton_compact(cs >> 2)};
+            const int og[3] = {org.x, org.y, org.z};
+            const float reach = hw + c.lcap[lp];
+            float d2 = 0.0f;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                // the stencil cell's box in the item frame, in finest cells:
+                // (coordinate + d) 2^dn - org, one level-sl edge wide
+                const float fe = c.fine_edge[a];
+                const float lo = (float)((oc[a] + da[a]) * (1 << dn) - og[a]) * fe - fe * (1.0f / 512.0f);
+                const float hi = lo + (float)(1 << dn) * fe + fe * (1.0f / 256.0f);
+                const float g = fmaxf(0.0f, fmaxf(lo - box.hi[a], box.lo[a] - hi));
+                d2 = fmaf(g, g, d2);
+            }
+            if (d2 < reach * reach) {
+                const uint32_t m = (1u << sl) - 1u;
+                const int32_t code = (int32_t)morton_key((uint32_t)(oc[0] + da[0]) & m, (uint32_t)(oc[1] + da[1]) & m,
+                                                         (uint32_t)(oc[2] + da[2]) & m);
+                const int l0 = __ldg(c.lstart + lp), l1 = __ldg(c.lstart + lp + 1);
+                const int s0 = key_lower_bound(c.pkey, l0, l1, code << (3 * dn));
+                cnt[i] = key_lower_bound(c.pkey, s0, l1, (code + 1) << (3 * dn)) - s0;
+                st[i] = s0;
+            }
+        }
+        local += cnt[i];
+        kept += cnt[i] > 0 ? 1 : 0;
+    }
+    int inc = local, kinc = kept;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(FULL, inc, o);
+        const int w = __shfl_up_sync(FULL, kinc, o);
+        if (lane >= o) {
+            inc += v;
+            kinc += w;
+        }
+    }
+    int run = inc - local, pos = kinc - kept;
+#pragma unroll
+    for (int i = 0; i < kE; ++i) {
+        if (cnt[i] > 0) {
+            run += cnt[i];
+            tab.incl[pos] = run;
+            tab.base[pos] = st[i] - (run - cnt[i]);
+            tab.t[pos] = 0;
+            ++pos;
+        }
+    }
+    if (lane == 31) tab.nk = kinc;
+    __syncwarp();
+    return __shfl_sync(FULL, inc, 31);
 }
 
 // Stage the force candidates (those within h_max(warp) + h_j of the warp box)
@@ -939,8 +1030,9 @@ __global__ void __launch_bounds__(256) k_force_pack(ForceArgs a, const int32_t *
 // slot in sC.w.  Returns how many were staged and moves `cur` (as
 // stage_density).  The 27-cell grid covers pairs up to 2 h_max only; a
 // candidate with a larger h sets the h-cap error bit.
+template <bool kLvl>
 __device__ int stage_force(const ForceArgs &a, const Tab &tab, int total, const Box &box, float hw, float4 *sA,
-                           float4 *sB, float4 *sC, int cap, Cursor &cur, int lane, unsigned &err)
+                           float4 *sB, float4 *sC, int cap, Cursor &cur, int lane, unsigned &err, int3 org)
 {
     const Common &c = a.c;
     const unsigned lt = (1u << lane) - 1u;
@@ -959,11 +1051,15 @@ __device__ int stage_force(const ForceArgs &a, const Tab &tab, int total, const 
             qc[u] = make_float4(0.f, 1.f, 0.f, 0.f);
             if (g < total) {
                 e = advance(tab, nk, e, g);
-                const int j = tab.base[e] + g;
-                float sx, sy, sz;
-                stencil_shift(c, tab.t[e], sx, sy, sz);
+                const int j = kLvl ? __ldg(c.plist + tab.base[e] + g) : tab.base[e] + g;
                 const float4 p = __ldg(a.pA + j);
-                qa[u] = make_float4(p.x + sx, p.y + sy, p.z + sz, p.w);
+                if (kLvl) {
+                    qa[u] = lvl_frame(c, (uint32_t)__ldg(c.mkey + j), org, p);
+                } else {
+                    float sx, sy, sz;
+                    stencil_shift(c, tab.t[e], sx, sy, sz);
+                    qa[u] = make_float4(p.x + sx, p.y + sy, p.z + sz, p.w);
+                }
                 qb[u] = __ldg(a.pB + j);
                 qc[u] = __ldg(a.pC + j);
                 qc[u].w = __int_as_float(j);
@@ -1006,6 +1102,7 @@ __host__ __device__ inline size_t force_warp_bytes(int cap)
     return (size_t)cap * 3 * sizeof(float4) + (size_t)32 * kListSlots * sizeof(uint16_t) + sizeof(Tab);
 }
 
+template <bool kLvl>
 __global__ void __launch_bounds__(kMaxBlock, 1) k_force(ForceArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1026,11 +1123,20 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_force(ForceArgs a)
         const int first = c.ifirst[it];
         const int count = c.icount[it];
         const bool ok = lane < count;
-        const int k = first + lane;
+        int k = first + lane;
+        int3 org = make_int3(0, 0, 0);       // level mode: the item cell's origin in finest cells
+        if (kLvl) {
+            k = ok ? __ldg(c.tslot + first + lane) : 0;
+            const uint32_t cc = (uint32_t)cell;
+            org = make_int3((int)(morton_compact(cc) << c.lvl_dn), (int)(morton_compact(cc >> 1) << c.lvl_dn),
+                            (int)(morton_compact(cc >> 2) << c.lvl_dn));
+        }
         float xi = 0.f, yi = 0.f, zi = 0.f, hi = 0.f, vxi = 0.f, vyi = 0.f, vzi = 0.f;
         float rhoi = 1.f, Pr2i = 0.f, ci = 0.f;
         if (ok) {
-            const float4 qa = __ldg(a.pA + k), qb = __ldg(a.pB + k), qc = __ldg(a.pC + k);
+            float4 qa = __ldg(a.pA + k);
+            const float4 qb = __ldg(a.pB + k), qc = __ldg(a.pC + k);
+            if (kLvl) qa = lvl_frame(c, (uint32_t)__ldg(c.mkey + k), org, qa);
             xi = qa.x;
             yi = qa.y;
             zi = qa.z;
@@ -1044,13 +1150,14 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_force(ForceArgs a)
         }
         const Box box = warp_box(ok, xi, yi, zi);
         const float hw = warp_max(ok ? hi : 0.0f);
-        const int total = build_stream(c, cell, box, 0.0f, tab, lane, a.key_hmax, hw);
+        const int total = kLvl ? lvl_force_table(c, cell, a.lvl, org, box, hw, tab, lane)
+                               : build_stream(c, cell, box, 0.0f, tab, lane, a.key_hmax, hw);
         float ax = 0.f, ay = 0.f, az = 0.f, du = 0.f;
         int cnt = 0;
         if (hi > a.h_cap) my_err |= SPH_ERR_HCAP;
         Cursor cur{0, 0};
         do {
-            const int len = stage_force(a, tab, total, box, hw, sA, sB, sC, c.cap, cur, lane, my_err);
+            const int len = stage_force<kLvl>(a, tab, total, box, hw, sA, sB, sC, c.cap, cur, lane, my_err, org);
             if (ok) {
                 my_tests += (unsigned long long)len;
                 // phase 1 collects this lane's pairs among up to kLaneCap
@@ -1298,6 +1405,9 @@ Common make_common(sph_ctx *c, int cap)
     m.fine_n = 0;
     for (int k = 0; k < 3; ++k) m.fine_edge[k] = 0.0f;
     m.defer = nullptr;
+    m.plist = m.pkey = m.lstart = nullptr;
+    m.lvl_min = m.lvl_max = 0;
+    for (int l = 0; l <= kLevelMax; ++l) m.lcap[l] = 0.0f;
     m.st = c->dstats;
     auto ref = [&](int f) {
         FieldRef r;
@@ -1471,9 +1581,10 @@ cudaError_t run_density_levels(sph_ctx *c, int newton_steps)
     return cudaSuccess;
 }
 
-cudaError_t run_force(sph_ctx *c)
+namespace {
+
+ForceArgs force_args(sph_ctx *c)
 {
-    if (c->n == 0) return cudaSuccess;
     ForceArgs a;
     a.c = make_common(c, c->tuning.stage_force);
     auto ref = [&](int f) {
@@ -1494,14 +1605,25 @@ cudaError_t run_force(sph_ctx *c)
     for (int k = 0; k < 3; ++k) a.a[k] = (float *)c->soa[SPH_F_A][k];
     a.dudt = (float *)c->soa[SPH_F_DUDT][0];
     a.nngb = c->nngb_force;
+    a.pA = c->pack;
+    a.pB = c->pack + c->n;
+    a.pC = c->pack + 2 * c->n;
+    a.key_hmax = nullptr;
+    a.lvl = 0;
+    return a;
+}
+
+}  // namespace
+
+cudaError_t run_force(sph_ctx *c)
+{
+    if (c->n == 0) return cudaSuccess;
+    ForceArgs a = force_args(c);
     // the pack pass: FP32 inputs per slot, and the reach of every sub-cell
     // from the h the force will read
     cudaError_t e;
     const int64_t nkeys = c->ncell * c->sub * c->sub * c->sub;
     if ((e = cudaMemsetAsync(c->key_hmax, 0, sizeof(float) * nkeys, c->stream)) != cudaSuccess) return e;
-    a.pA = c->pack;
-    a.pB = c->pack + c->n;
-    a.pC = c->pack + 2 * c->n;
     k_force_pack<<<(unsigned)((c->n + 255) / 256), 256, 0, c->stream>>>(a, c->slot_cell(), c->key_hmax, c->pack,
                                                                        c->pack + c->n, c->pack + 2 * c->n);
     c->launches += 1;
@@ -1514,7 +1636,46 @@ cudaError_t run_force(sph_ctx *c)
     }
     // the pair kernel reads only the packed FP32 arrays: one instantiation
     const size_t smem = force_smem_bytes(c->tuning.block_threads, a.c.cap);
-    return launch_persistent(c, k_force, a, smem, c->lc_force);
+    return launch_persistent(c, k_force<false>, a, smem, c->lc_force);
+}
+
+// The force over the level hierarchy: one pack pass, the per-level lists,
+// then one launch per level over that level's work items.
+cudaError_t run_force_levels(sph_ctx *c)
+{
+    if (c->n == 0) return cudaSuccess;
+    ForceArgs a = force_args(c);
+    a.c.mkey = c->slot_cell();
+    a.c.tslot = c->tlist;
+    a.c.fine_n = 1 << c->lvl_max;
+    for (int k = 0; k < 3; ++k) a.c.fine_edge[k] = (float)c->edge[k];
+    int32_t *plist = c->keys[c->sorted_buf ^ 1], *pkey = c->vals[c->sorted_buf ^ 1];   // free after the sort
+    a.c.plist = plist;
+    a.c.pkey = pkey;
+    a.c.lstart = c->lstart;
+    a.c.lvl_min = c->lvl_min;
+    a.c.lvl_max = c->lvl_max;
+    for (int l = 0; l <= kLevelMax; ++l) {
+        double e_l = std::ldexp(c->params.box[0], -l);
+        for (int k = 1; k < 3; ++k) e_l = std::fmin(e_l, std::ldexp(c->params.box[k], -l));
+        a.c.lcap[l] = (float)std::fmin(0.5 * e_l, c->params.h_max);
+    }
+    cudaError_t e;
+    k_force_pack<<<(unsigned)((c->n + 255) / 256), 256, 0, c->stream>>>(a, c->slot_cell(), nullptr, c->pack,
+                                                                       c->pack + c->n, c->pack + 2 * c->n);
+    c->launches += 1;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = run_level_lists(c, plist, pkey)) != cudaSuccess) return e;
+    const size_t smem = force_smem_bytes(c->tuning.block_threads, a.c.cap);
+    for (int l = c->lvl_max; l >= c->lvl_min; --l) {
+        if ((e = run_level_items(c, l)) != cudaSuccess) return e;
+        for (int k = 0; k < 3; ++k) a.c.edge[k] = (float)std::ldexp(c->params.box[k], -l);
+        a.c.lvl_dn = c->lvl_max - l;
+        a.c.lvl_n = 1 << l;
+        a.lvl = l;
+        if ((e = launch_persistent(c, k_force<true>, a, smem, c->lc_force_lv)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace sph

@@ -120,6 +120,7 @@ bool make_plan(const sph_aos_layout &L, int64_t n, int64_t ncell_max, uint32_t w
         p->tcode = take(4 * N);
         p->tscan = take(4 * (N + 1));
         p->iscan = take(4 * (N + 1));
+        p->lstart = take(4 * (kLevelMax + 2));
     }
     p->stats = take(sizeof(DevStats));
     for (int f = 0; f < SPH_NFIELDS; ++f)
@@ -219,6 +220,7 @@ sph_status sph_create(const sph_aos_layout *layout, const sph_params *params, in
         c->tcode = (int32_t *)(w + plan.tcode);
         c->tscan = (int32_t *)(w + plan.tscan);
         c->iscan = (int32_t *)(w + plan.iscan);
+        c->lstart = (int32_t *)(w + plan.lstart);
     }
     c->dstats = (DevStats *)(w + plan.stats);
     for (int f = 0; f < SPH_NFIELDS; ++f) {
@@ -441,7 +443,9 @@ double level_cap(const sph_ctx *c, int l)
 sph_status sph_bin_levels(sph_ctx *c, int32_t level_min, int32_t level_max, double h_margin)
 {
     if (!c) return SPH_EINVAL;
-    if (level_min < SPH_LEVEL_MIN || level_max > SPH_LEVEL_MAX || level_min > level_max) return SPH_EINVAL;
+    if (level_min < SPH_LEVEL_MIN || level_max > SPH_LEVEL_MAX || level_min > level_max ||
+        level_max - level_min >= SPH_LEVELS_MAX)
+        return SPH_EINVAL;
     if (!std::isfinite(h_margin) || !(h_margin >= 0.0)) return SPH_EINVAL;
     if (c->layout.offset[SPH_F_H] < 0) return SPH_EINVAL;
     if (!(c->ws_flags & SPH_WS_LEVELS)) return SPH_ENOSPACE;
@@ -475,6 +479,20 @@ sph_status sph_density_levels(sph_ctx *c, int32_t newton_steps)
     if (run_density_levels(c, newton_steps) != cudaSuccess) return SPH_ECUDA;
     c->valid |= SPH_BIT(SPH_F_RHO) | SPH_BIT(SPH_F_H);
     if (c->valid & SPH_BIT(SPH_F_U)) c->valid |= SPH_BIT(SPH_F_P) | SPH_BIT(SPH_F_CS);
+    return SPH_OK;
+}
+
+sph_status sph_force_levels(sph_ctx *c)
+{
+    if (!c) return SPH_EINVAL;
+    if (!c->binned || !c->levels) return SPH_ESTATE;
+    const uint32_t need = SPH_BIT(SPH_F_X) | SPH_BIT(SPH_F_V) | SPH_BIT(SPH_F_M) | SPH_BIT(SPH_F_H) |
+                          SPH_BIT(SPH_F_RHO) | SPH_BIT(SPH_F_P) | SPH_BIT(SPH_F_CS);
+    if ((c->valid & need) != need) return SPH_ESTATE;
+    c->prec[SPH_F_A] = SPH_P_FP32;
+    c->prec[SPH_F_DUDT] = SPH_P_FP32;
+    if (run_force_levels(c) != cudaSuccess) return SPH_ECUDA;
+    c->valid |= SPH_BIT(SPH_F_A) | SPH_BIT(SPH_F_DUDT);
     return SPH_OK;
 }
 

@@ -83,7 +83,7 @@ struct Plan {
     size_t cell_count, cell_start, scan_part, ghist;
     size_t item_cell, item_first, item_count, item_tmp, item_sorted, item_class, class_hist;
     size_t nngb, nngb_force, stage, aos_tmp, stats, key_hmax, origin, pack, buf_origin;
-    size_t level, level_tmp, tlist, tcode, tscan, iscan;   // level hierarchy (SPH_WS_LEVELS)
+    size_t level, level_tmp, tlist, tcode, tscan, iscan, lstart;   // level hierarchy (SPH_WS_LEVELS)
     size_t soa[SPH_NFIELDS][3];
     size_t total;
     int64_t item_max, nblk_radix;
@@ -325,7 +325,7 @@ struct sph_ctx {
     bool levels = false;          // level mode: Morton order over a hierarchy of grids
     int32_t lvl_min = 0, lvl_max = 0;
     sph::LaunchCache lc_density, lc_force;   // launch shapes of the persistent pair kernels
-    sph::LaunchCache lc_density_lv, lc_density_one;   // ... and of the density over the level hierarchy
+    sph::LaunchCache lc_density_lv, lc_density_one, lc_force_lv;   // ... and of the kernels over the level hierarchy
     int sorted_buf = 0;          // which ping-pong buffer holds the sorted keys/values
 
     // workspace arrays
@@ -349,6 +349,7 @@ struct sph_ctx {
     // sort, and one level's target slots, their cell codes and two scans
     int8_t *level = nullptr, *level_tmp = nullptr;
     int32_t *tlist = nullptr, *tcode = nullptr, *tscan = nullptr, *iscan = nullptr;
+    int32_t *lstart = nullptr;    // start of every level's list (force), kLevelMax + 2 entries
     sph::DevStats *dstats = nullptr;
     void *soa[SPH_NFIELDS][3] = {};
     int prec[SPH_NFIELDS] = {};
@@ -374,6 +375,8 @@ cudaError_t run_kick_drift(sph_ctx *c, double dt_kick, double dt_drift, uint32_t
 // level hierarchy (k_bin.cu, k_pairs.cu)
 cudaError_t run_bin_levels(sph_ctx *c, double grow);
 cudaError_t run_level_items(sph_ctx *c, int level);
+cudaError_t run_level_lists(sph_ctx *c, int32_t *plist, int32_t *pkey);
+cudaError_t run_force_levels(sph_ctx *c);
 cudaError_t run_density_levels(sph_ctx *c, int newton_steps);
 // host-side conversion (host_convert.cu)
 size_t host_stage_bytes(const sph_ctx *c);

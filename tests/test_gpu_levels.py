@@ -8,9 +8,14 @@
   them; the level counters account for every particle.
 * One level: the hierarchy reproduces the single-grid density of the same
   cells bit for bit (same candidates in the same order, same frames).
+* Force with every particle's own h: acceleration and du/dt match the FP64
+  oracle's brute-force pairs r < h_i + h_j, given the same h, rho, P and c,
+  within 1e-5 of |a_i| + mean |a| per particle (a relative bound with the
+  paper's mean-based floor; accelerations span orders of magnitude here).
 """
 import numpy as np
 import pytest
+import torch
 
 import sph_inputs
 from gpu_util import make_sph
@@ -165,7 +170,8 @@ def test_level_calls_check_their_arguments_and_order():
     with pytest.raises(sph_mod.SphError) as e:         # not binned for levels
         s.density_levels(0)
     assert e.value.status == sph_mod._capi.ESTATE
-    for a, b, m in ((1, hi, 0.0), (lo, 11, 0.0), (hi, lo, 0.0), (lo, hi, -0.1), (lo, hi, float("nan"))):
+    for a, b, m in ((1, hi, 0.0), (lo, 11, 0.0), (hi, lo, 0.0), (lo, hi, -0.1), (lo, hi, float("nan")),
+                    (2, 2 + sph_mod.LEVELS_MAX, 0.0)):
         with pytest.raises(sph_mod.SphError) as e:
             s.bin_levels(a, b, m)
         assert e.value.status == sph_mod._capi.EINVAL, (a, b, m)
@@ -174,6 +180,9 @@ def test_level_calls_check_their_arguments_and_order():
     assert e.value.status == sph_mod._capi.ECAPACITY
     s.bin_levels(lo, hi, 0.0)
     s.aos_to_soa(sph_mod.FIELDS_FORCE)
+    with pytest.raises(sph_mod.SphError) as e:         # the force needs the density's outputs
+        s.force_levels()
+    assert e.value.status == sph_mod._capi.ESTATE
     for call in (lambda: s.density(0), s.force):       # single-grid kernels refuse level mode
         with pytest.raises(sph_mod.SphError) as e:
             call()
@@ -181,9 +190,53 @@ def test_level_calls_check_their_arguments_and_order():
     with pytest.raises(sph_mod.SphError):              # positions are not written back
         s.soa_to_aos(sph_mod.mask("x"))
     s.density_levels(2)
+    s.force_levels()
     # back to cells: the single-grid density runs again
     s.bin_cells(wl.cell_edge)
     s.aos_to_soa(sph_mod.FIELDS_DENSITY)
     s.density(0)
     assert s.stats()["error_bits"] & (sph_mod.ERR_NONFINITE | sph_mod.ERR_OUTSIDE) == 0
     s.close()
+
+
+# a 136-byte record that also carries the sound speed and du/dt
+OFFS_136 = {"x": 0, "v": 24, "a": 48, "m": 72, "h": 80, "rho": 88, "u": 96, "P": 104,
+            "cs": 112, "dudt": 120}
+
+
+@pytest.mark.parametrize("margin", [0.0, 0.1])
+def test_level_force_matches_oracle(orc, margin):
+    wl = _wl(262_144 - 77)
+    wl.col("v")[:] = np.random.default_rng(8).uniform(-0.5, 0.5, (wl.n, 3))
+    lo, hi = wl.meta["levels"]
+    rec = np.zeros((wl.n, 17))
+    rec[:, :14] = wl.aos
+    s = make_sph(wl, aos=torch.from_numpy(rec).cuda(), layout=sph_mod.make_layout(OFFS_136, 136),
+                 ws_flags=sph_mod.WS_LEVELS)
+    s.bin_levels(lo, hi, margin)
+    s.aos_to_soa(sph_mod.FIELDS_FORCE)
+    s.density_levels(5)
+    s.force_levels()
+    s.soa_to_aos(sph_mod.mask("h", "rho", "P", "cs", "a", "dudt"))
+    out = s.aos.cpu().numpy()
+    lev = np.empty(wl.n, np.int8)
+    lev[s.perm().cpu().numpy()] = s.levels().cpu().numpy()
+    st = s.stats()
+    s.close()
+    assert st["error_bits"] & (sph_mod.ERR_NONFINITE | sph_mod.ERR_OUTSIDE) == 0
+    h, rho, P, c = out[:, 10], out[:, 11], out[:, 13], out[:, 14]
+    rng = np.random.default_rng(9)
+    t = [rng.choice(wl.n, 300, replace=False)]
+    for l in np.unique(lev):
+        idx = np.flatnonzero(lev == l)
+        t.append(rng.choice(idx, min(40, idx.size), replace=False))
+    t = np.unique(np.concatenate(t))
+    f = orc.force(wl.col("x"), wl.col("v"), wl.col("m"), h, rho, P, c, wl.box, wl.alpha_av, wl.beta_av,
+                  wl.eps_av, brute=True, targets=t)
+    a_g, du_g = out[t, 6:9], out[t, 15]
+    na = np.linalg.norm(f["a"], axis=1)
+    err_a = np.linalg.norm(a_g - f["a"], axis=1)
+    assert np.all(err_a <= 1e-5 * (na + na.mean())), (err_a / (na + na.mean())).max()
+    err_u = np.abs(du_g - f["dudt"])
+    assert np.all(err_u <= 1e-5 * (np.abs(f["dudt"]) + np.abs(f["dudt"]).mean()))
+    assert st["pairs_force"] > 0
