@@ -1001,8 +1001,8 @@ def profile_buffers():
 
 def profile_levels():
     """'levels': the adaptive-h clustered set at 2,097,152 particles (AoS
-    235 MB > L2), levels from the set, margin 0.1: bin, convert, and the
-    density with 5 Newton steps over the hierarchy, twice."""
+    235 MB > L2), levels from the set, margin 0.1: bin, convert, the density
+    with 5 Newton steps and the force over the hierarchy, twice."""
     import torch
     import paper_2512_05516_gb300 as sph
     wl = sph_inputs.gaussian_mixture_adaptive(2_097_152)
@@ -1012,13 +1012,15 @@ def profile_levels():
     s = sph.Sph(aos, sph.layout_112(), params, 27, sph.WS_LEVELS)
     for _ in range(2):
         s.bin_levels(lo, hi, 0.1)
-        s.aos_to_soa(sph.FIELDS_DENSITY)
+        s.aos_to_soa(sph.FIELDS_FORCE)
         s.density_levels(5)
+        s.force_levels()
     torch.cuda.synchronize()
     st = s.stats()
     done, prom = s.level_counts()
     print(json.dumps({"profile_case": "levels", "n": wl.n, "levels": [lo, hi], "error_bits": st["error_bits"],
-                      "pairs_density": st["pairs_density"], "done": done[lo:hi + 1],
+                      "pairs_density": st["pairs_density"], "pairs_force": st["pairs_force"],
+                      "done": done[lo:hi + 1],
                       "promoted": prom[lo:hi + 1]}))
     if st["error_bits"] & (sph.ERR_NONFINITE | sph.ERR_OUTSIDE):
         raise SystemExit(1)
