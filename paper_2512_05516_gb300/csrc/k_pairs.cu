@@ -129,6 +129,9 @@ struct __align__(16) Tab {
 // float4 stage starts right after, so every part keeps 16-byte multiples.
 static_assert(sizeof(Tab) % 16 == 0, "stencil table size must keep 16-byte alignment");
 static_assert((32 * kListSlots * sizeof(uint16_t)) % 16 == 0, "list size must keep 16-byte alignment");
+// level force: an item whose candidate stream is longer than this is
+// gathered target by target (k_force_one)
+constexpr int kForceDefer = 8192;
 // the level kernel adds the 27 x 9 run boundaries of its item's stencil
 constexpr size_t kBndBytes = (27 * 9 * sizeof(int) + 15) / 16 * 16;
 
@@ -1152,6 +1155,18 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_force(ForceArgs a)
         const float hw = warp_max(ok ? hi : 0.0f);
         const int total = kLvl ? lvl_force_table(c, cell, a.lvl, org, box, hw, tab, lane)
                                : build_stream(c, cell, box, 0.0f, tab, lane, a.key_hmax, hw);
+        if (kLvl && total > kForceDefer) {
+            // A long stream: coarse targets spread over their cell next to a
+            // dense cluster, whose box takes in the cluster's fine lists.
+            // Each target goes to the per-target list instead and is gathered
+            // by a whole warp with its own reach (k_force_one).
+            const unsigned bal = __ballot_sync(FULL, ok);
+            unsigned base = 0;
+            if (lane == 0) base = atomicAdd(&c.st->defer_n, (unsigned)__popc(bal));
+            base = __shfl_sync(FULL, base, 0);
+            if (ok) c.defer[base + __popc(bal & ((1u << lane) - 1u))] = k;
+            continue;
+        }
         float ax = 0.f, ay = 0.f, az = 0.f, du = 0.f;
         int cnt = 0;
         if (hi > a.h_cap) my_err |= SPH_ERR_HCAP;
@@ -1214,6 +1229,83 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_force(ForceArgs a)
         }
     }
     my_pairs = warp_sum_u64(my_pairs);
+    my_tests = warp_sum_u64(my_tests);
+    if (lane == 0) {
+        if (my_pairs) atomicAdd(&c.st->pairs_force, my_pairs);
+        if (my_tests) atomicAdd(&c.st->tests_force, my_tests);
+    }
+    if (my_err) set_error(c.st, my_err);
+}
+
+// The level force's per-target pass: every target that k_force<true>
+// deferred is gathered by one whole warp.  Its K level streams are pruned to
+// its own reach (h_i + h_l'), the lanes evaluate its staged candidates in
+// turn, and the partial sums meet in a butterfly.  Lane 0 writes.
+__global__ void __launch_bounds__(kMaxBlock, 1) k_force_one(ForceArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Common &c = a.c;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float4 *sA = reinterpret_cast<float4 *>(smem + warp * force_warp_bytes(c.cap));
+    float4 *sB = sA + c.cap;
+    float4 *sC = sB + c.cap;
+    uint16_t *lst = reinterpret_cast<uint16_t *>(sC + c.cap);
+    Tab &tab = *reinterpret_cast<Tab *>(lst + 32 * kListSlots);
+    unsigned long long my_pairs = 0, my_tests = 0;
+    unsigned my_err = 0;
+    const unsigned nd = c.st->defer_n;
+    for (unsigned j = pop_deferred(c.st, lane); j < nd; j = pop_deferred(c.st, lane)) {
+        const int k = c.defer[j];
+        const uint32_t key = (uint32_t)__ldg(c.mkey + k);
+        const int cell = (int)(key >> (3 * c.lvl_dn));
+        const int3 org = make_int3((int)(morton_compact((uint32_t)cell) << c.lvl_dn),
+                                   (int)(morton_compact((uint32_t)cell >> 1) << c.lvl_dn),
+                                   (int)(morton_compact((uint32_t)cell >> 2) << c.lvl_dn));
+        const float4 qa = lvl_frame(c, key, org, __ldg(a.pA + k));
+        const float4 qb = __ldg(a.pB + k), qcv = __ldg(a.pC + k);
+        const float xi = qa.x, yi = qa.y, zi = qa.z, hi = qa.w;
+        const Box pb{{xi, yi, zi}, {xi, yi, zi}};
+        if (hi > a.h_cap && lane == 0) my_err |= SPH_ERR_HCAP;
+        const int total = lvl_force_table(c, cell, a.lvl, org, pb, hi, tab, lane);
+        float ax = 0.f, ay = 0.f, az = 0.f, du = 0.f;
+        int cnt = 0;
+        Cursor cur{0, 0};
+        do {
+            const int len = stage_force<true>(a, tab, total, pb, hi, sA, sB, sC, c.cap, cur, lane, my_err, org);
+            my_tests += (unsigned long long)max(0, (len - lane + 31) >> 5);
+            for (int p = lane; p < len; p += 32) {
+                const float4 qc = sC[p];
+                const float4 q = sA[p];
+                const float dx = xi - q.x, dy = yi - q.y, dz = zi - q.z;
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                const float hs = hi + q.w;
+                if (__float_as_int(qc.w) != k && r2 < hs * hs) {
+                    ++cnt;
+                    if (r2 > 0.0f)
+                        force_pair(ax, ay, az, du, qb.x, qb.y, qb.z, qcv.y, qcv.x, qcv.z, dx, dy, dz, r2, hs, sB[p], qc,
+                                   a.alpha, a.beta, a.eps);
+                }
+            }
+            __syncwarp();
+        } while (cur.g < total);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ax += __shfl_xor_sync(FULL, ax, o);
+            ay += __shfl_xor_sync(FULL, ay, o);
+            az += __shfl_xor_sync(FULL, az, o);
+            du += __shfl_xor_sync(FULL, du, o);
+            cnt += __shfl_xor_sync(FULL, cnt, o);
+        }
+        if (lane == 0) {
+            if (!isfinite(ax) || !isfinite(ay) || !isfinite(az) || !isfinite(du)) my_err |= SPH_ERR_NONFINITE;
+            a.a[0][k] = ax;
+            a.a[1][k] = ay;
+            a.a[2][k] = az;
+            a.dudt[k] = du;
+            a.nngb[k] = cnt;
+            my_pairs += (unsigned long long)cnt;
+        }
+    }
     my_tests = warp_sum_u64(my_tests);
     if (lane == 0) {
         if (my_pairs) atomicAdd(&c.st->pairs_force, my_pairs);
@@ -1655,6 +1747,7 @@ cudaError_t run_force_levels(sph_ctx *c)
     a.c.lstart = c->lstart;
     a.c.lvl_min = c->lvl_min;
     a.c.lvl_max = c->lvl_max;
+    a.c.defer = c->tcode;     // free while the level's kernels run (its items are built)
     for (int l = 0; l <= kLevelMax; ++l) {
         double e_l = std::ldexp(c->params.box[0], -l);
         for (int k = 1; k < 3; ++k) e_l = std::fmin(e_l, std::ldexp(c->params.box[k], -l));
@@ -1673,7 +1766,9 @@ cudaError_t run_force_levels(sph_ctx *c)
         a.c.lvl_dn = c->lvl_max - l;
         a.c.lvl_n = 1 << l;
         a.lvl = l;
+        if ((e = cudaMemsetAsync(&c->dstats->defer_n, 0, 2 * sizeof(unsigned), c->stream)) != cudaSuccess) return e;
         if ((e = launch_persistent(c, k_force<true>, a, smem, c->lc_force_lv)) != cudaSuccess) return e;
+        if ((e = launch_persistent(c, k_force_one, a, smem, c->lc_force_one)) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }

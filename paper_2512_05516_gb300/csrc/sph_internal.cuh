@@ -325,7 +325,7 @@ struct sph_ctx {
     bool levels = false;          // level mode: Morton order over a hierarchy of grids
     int32_t lvl_min = 0, lvl_max = 0;
     sph::LaunchCache lc_density, lc_force;   // launch shapes of the persistent pair kernels
-    sph::LaunchCache lc_density_lv, lc_density_one, lc_force_lv;   // ... and of the kernels over the level hierarchy
+    sph::LaunchCache lc_density_lv, lc_density_one, lc_force_lv, lc_force_one;   // ... and over the level hierarchy
     int sorted_buf = 0;          // which ping-pong buffer holds the sorted keys/values
 
     // workspace arrays
