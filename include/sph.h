@@ -318,10 +318,11 @@ sph_status sph_kick_drift(sph_ctx *ctx, double dt_kick, double dt_drift);
 
 /* S7, C^T o N^T o U^T (Section 4, the write-back epilogue): widen the SoA
  * fields in `fields` to the AoS element type and scatter them to their
- * records.  Positions are not written after sph_bin_cells (the AoS keeps
- * them in FP64; drift updates them in place).  After sph_bin_buffers they
- * may be: x = buffer origin + offset in FP64, wrapped into [0, box).
- * Errors: SPH_EINVAL (X requested after sph_bin_cells, or field absent from
+ * records.  Positions are not written after sph_bin_cells or sph_bin_levels
+ * (the AoS keeps them in FP64; drift updates them in place).  After
+ * sph_bin_buffers they may be: x = buffer origin + offset in FP64, wrapped
+ * into [0, box).
+ * Errors: SPH_EINVAL (X requested outside buffer mode, or field absent from
  * the layout), SPH_ESTATE (field not current), SPH_ECUDA. */
 sph_status sph_soa_to_aos(sph_ctx *ctx, uint32_t fields);
 
