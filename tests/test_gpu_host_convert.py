@@ -117,6 +117,25 @@ def test_host_conversion_buffer_mode_with_positions():
     s.close()
 
 
+def test_host_gather_equals_device_gather_levels():
+    # level mode: positions are offsets from the finest cell, whose
+    # coordinates the host decodes from the Morton key
+    wl = sph_inputs.gaussian_mixture_adaptive(40_003)
+    lo, hi = wl.meta["levels"]
+    fields = sph_mod.mask("x", "m", "h", "u")
+    prec = {"x": "fp16", "m": "bf16", "h": "m10"}
+    s = make_sph(wl, ws_flags=sph_mod.WS_LEVELS)
+    s.bin_levels(lo, hi, 0.1)
+    s.aos_to_soa(fields, prec)
+    dev = _raw_codes(s, fields)
+    s.aos_to_soa_host(torch.from_numpy(np.ascontiguousarray(wl.aos)), fields, prec, 3)
+    torch.cuda.synchronize()
+    got = _raw_codes(s, fields)
+    for key in dev:
+        assert np.array_equal(got[key], dev[key]), key
+    s.close()
+
+
 def test_host_conversion_argument_rules():
     wl = _workload(n=3000, seed=54)
     s = make_sph(wl)
