@@ -502,7 +502,7 @@ struct Cursor {
 // Returns how many were staged (<= cap) and moves `cur` to the first batch
 // not staged (cur.g == total when the stream is exhausted).  A chunk always
 // stages at least one batch, since a batch holds at most 32 <= cap.
-template <bool kLvl>
+template <bool kLvl, int kU = kStageUnroll>
 __device__ int stage_density(const Common &c, const float4 *pD, const Tab &tab, int total, const Box &box,
                              float R2, float4 *sj, int cap, Cursor &cur, int lane, int3 org)
 {
@@ -510,12 +510,12 @@ __device__ int stage_density(const Common &c, const float4 *pD, const Tab &tab, 
     const int nk = tab.nk;
     int found = 0;
     int ecur = cur.e;
-    for (int g0 = cur.g; g0 < total; g0 += 32 * kStageUnroll) {
-        float4 q[kStageUnroll];
-        int eu[kStageUnroll];
+    for (int g0 = cur.g; g0 < total; g0 += 32 * kU) {
+        float4 q[kU];
+        int eu[kU];
         int e = ecur;
 #pragma unroll
-        for (int u = 0; u < kStageUnroll; ++u) {
+        for (int u = 0; u < kU; ++u) {
             const int g = g0 + u * 32 + lane;
             q[u] = make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.0f);
             if (g < total) {
@@ -533,7 +533,7 @@ __device__ int stage_density(const Common &c, const float4 *pD, const Tab &tab, 
             eu[u] = e;
         }
 #pragma unroll
-        for (int u = 0; u < kStageUnroll; ++u) {
+        for (int u = 0; u < kU; ++u) {
             const bool keep = box_dist2(box, q[u].x, q[u].y, q[u].z) < R2;
             const unsigned b = __ballot_sync(FULL, keep);
             const int nb = __popc(b);
@@ -776,9 +776,11 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
 // (k_density deferred it) is gathered by one whole warp.  Its stream is pruned
 // to its own reach with the children of the stencil cells; the lanes take its
 // candidates in turn and the partial sums meet in a butterfly, so every lane
-// holds the same bits and runs the same Newton steps.  Persistent warps pop
-// targets from the list; the outputs, promotion and counters follow
-// k_density's epilogue.
+// holds the same bits and runs the same Newton steps.  Few warps are busy
+// here and their scans wait on global loads, so staging keeps 8 batches of
+// 32 candidates in flight (4 in k_density).  Persistent warps pop targets
+// from the list; the outputs, promotion and counters follow k_density's
+// epilogue.
 __global__ void __launch_bounds__(kMaxBlock, 1) k_density_one(DensityArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -824,7 +826,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density_one(DensityArgs a)
                 const float R2p = 4.0f * hs * hs;
                 const int tot = lvl_table(c, bnd, pb, R2p, tab, lane);
                 Cursor pc{0, 0};
-                Tt = stage_density<true>(c, a.pD, tab, tot, pb, R2p, sj, c.cap, pc, lane, org);
+                Tt = stage_density<true, 8>(c, a.pD, tab, tot, pb, R2p, sj, c.cap, pc, lane, org);
                 fit_t = pc.g >= tot;
             }
             const float h2x4 = 4.0f * ht * ht;
@@ -839,7 +841,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density_one(DensityArgs a)
                 const int tot = lvl_table(c, bnd, pb, h2x4, tab, lane);
                 Cursor sc{0, 0};
                 do {
-                    const int len = stage_density<true>(c, a.pD, tab, tot, pb, h2x4, sj, c.cap, sc, lane, org);
+                    const int len = stage_density<true, 8>(c, a.pD, tab, tot, pb, h2x4, sj, c.cap, sc, lane, org);
                     for (int e = lane; e < len; e += 32)
                         dens_pair(acc, xt, yt, zt, h2x4, hinv, a.plain_sum, deriv, sj[e]);
                     my_tests += (unsigned long long)max(0, (len - lane + 31) >> 5);
