@@ -242,7 +242,7 @@ sph_status sph_create(const sph_aos_layout *layout, const sph_params *params, in
                       size_t workspace_bytes, void *stream, sph_ctx **out);
 
 /* S1, cell binning (the paper works on 64-particle co-located buffers,
- * Section 6; the build generalises them to a uniform grid).  Cells per axis
+ * Section 6; this library generalises them to a uniform grid).  Cells per axis
  * nc_d = floor(box_d / max(cell_edge, 2 h_max)); each particle's cell is
  * k_d = clamp(floor(x_d * (nc_d / box_d)), 0, nc_d - 1) in FP64, linear id
  * kx + nc_x (ky + nc_y kz).  Each cell is split into s^3 sub-cells
