@@ -71,6 +71,11 @@ def test_workspace_query_and_bad_layouts(sph):
     assert ws > 0 and ws % 256 == 0
     assert sph.sph_workspace_bytes(L, n, 1000, sph.WS_REORDER) >= ws + 112 * n
     assert sph.sph_workspace_bytes(L, -1, 1000) == 0
+    # the level hierarchy's arrays: levels (2 B), one level's targets and codes
+    # (8 B), two per-slot scans (8 B) and work items for a tile per particle
+    lv = sph.sph_workspace_bytes(L, n, 1000, sph.WS_LEVELS)
+    assert lv >= ws + 18 * n
+    assert sph.sph_workspace_bytes(L, 0, 1000, sph.WS_LEVELS) > 0
     assert sph.sph_workspace_bytes(L, n, 5) == 0            # fewer than 27 cells
     bad = sph.layout_112()
     bad.record_bytes = 100                                  # not a multiple of 8
@@ -123,6 +128,10 @@ def test_calls_on_null_context_fail_cleanly(sph):
     assert sph.sph_describe(null)[0] == sph._capi.EINVAL
     assert sph.sph_set_field_scale(null, [0] * sph.SPH_NFIELDS) == sph._capi.EINVAL
     assert sph.sph_get_field_scale(null)[0] == sph._capi.EINVAL
+    assert sph.sph_bin_levels(null, 3, 6, 0.1) == sph._capi.EINVAL
+    assert sph.sph_density_levels(null, 0) == sph._capi.EINVAL
+    assert sph.sph_force_levels(null) == sph._capi.EINVAL
+    assert sph.sph_level_counts(null)[0] == sph._capi.EINVAL
     sph.sph_destroy(null)
     assert sph.sph_status_str(-5).startswith("cell grid")
 
