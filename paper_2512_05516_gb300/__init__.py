@@ -427,6 +427,17 @@ class Sph:
         _check(st, "sph_level_counts")
         return done, prom
 
+    def step_levels(self, dt: float, level_min: int, level_max: int, newton_steps: int = 5, prec=None,
+                    h_margin: float = 0.1, out_fields: int = FIELDS_OUTPUT):
+        """One time step with every particle's own h over the level hierarchy:
+        bin for the levels, convert, density (+h) and force over the levels,
+        kick/drift fused with the write-back.  Needs ws_flags=WS_LEVELS."""
+        self.bin_levels(level_min, level_max, h_margin)
+        self.aos_to_soa(FIELDS_FORCE, prec)
+        self.density_levels(newton_steps)
+        self.force_levels()
+        self.kick_drift_writeback(dt, dt, out_fields)
+
     def step(self, dt: float, newton_steps: int = 5, prec=None, cell_edge: float = 0.0,
              reorder: bool = False, out_fields: int = FIELDS_OUTPUT):
         """One SPH time step: bin, convert, density (+h), force, kick/drift

@@ -240,3 +240,29 @@ def test_level_force_matches_oracle(orc, margin):
     err_u = np.abs(du_g - f["dudt"])
     assert np.all(err_u <= 1e-5 * (np.abs(f["dudt"]) + np.abs(f["dudt"]).mean()))
     assert st["pairs_force"] > 0
+
+
+def test_adaptive_step_kicks_and_drifts_with_the_level_force():
+    # a whole step over the hierarchy: the fused kick/drift + write-back uses
+    # the level force's accelerations (v' = v + a dt in FP32, x' = x + v' dt in
+    # FP64, periodic), and the density's outputs reach the records
+    wl = _wl(65_536 + 5)
+    wl.col("v")[:] = np.random.default_rng(12).uniform(-0.5, 0.5, (wl.n, 3))
+    lo, hi = wl.meta["levels"]
+    dt = 1e-5
+    s = make_sph(wl, ws_flags=sph_mod.WS_LEVELS)
+    s.step_levels(dt, lo, hi, newton_steps=3)
+    st = s.stats()
+    assert st["error_bits"] & (sph_mod.ERR_NONFINITE | sph_mod.ERR_OUTSIDE) == 0
+    perm = s.perm().cpu().numpy()
+    a = np.empty((wl.n, 3))
+    for c in range(3):
+        a[perm, c] = s.soa_raw("a", c).cpu().numpy()
+    out = s.aos.cpu().numpy()
+    s.close()
+    v32 = wl.col("v").astype(np.float32) + (a.astype(np.float32) * np.float32(dt))
+    assert np.allclose(out[:, 3:6], v32, rtol=0, atol=4e-7 * np.abs(v32).max())
+    x = wl.col("x") + out[:, 3:6] * dt
+    x -= np.floor(x)
+    assert np.abs(out[:, 0:3] - x).max() <= 1e-12
+    assert np.all(out[:, 11] > 0) and np.all(out[:, 10] > 0)        # rho, h written back
