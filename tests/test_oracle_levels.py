@@ -81,3 +81,13 @@ def test_bad_levels_are_refused(orc):
     x = np.zeros((1, 3))
     with pytest.raises(ValueError):
         orc.levels(x, np.ones(1), (1, 1, 1), 5, 4)
+
+
+def test_positions_outside_the_box_clamp_into_the_edge_cells(orc):
+    # as the cell binning: floor(x F / L) clamped to [0, F - 1]; NaN -> 0
+    F = 2 ** 5
+    x = np.array([[-0.3, 0.5, 0.5], [1.0, 0.5, 0.5], [2.7, 0.5, 0.5], [np.nan, 0.5, 0.5]])
+    key, _, _ = orc.levels(x, np.full(4, 1e-3), (1.0, 1.0, 1.0), 2, 5)
+    f = _decode(key, 5)
+    assert f[:, 0].tolist() == [0, F - 1, F - 1, 0]
+    assert np.all(f[:, 1] == F // 2) and np.all(f[:, 2] == F // 2)
