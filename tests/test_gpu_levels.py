@@ -266,3 +266,24 @@ def test_adaptive_step_kicks_and_drifts_with_the_level_force():
     x -= np.floor(x)
     assert np.abs(out[:, 0:3] - x).max() <= 1e-12
     assert np.all(out[:, 11] > 0) and np.all(out[:, 10] > 0)        # rho, h written back
+
+
+def test_level_binning_flags_bad_positions_and_stays_exact(orc):
+    # NaN and out-of-box positions: flagged, clamped into the edge cells on
+    # both sides exactly as the oracle does, and the context stays usable
+    wl = _wl(20_000)
+    lo, hi = wl.meta["levels"]
+    bad = wl.aos.copy()
+    bad[3, 0] = np.nan
+    bad[5, 1] = 1.5
+    bad[8, 2] = -0.1
+    s = make_sph(wl, aos=torch.from_numpy(bad).cuda(), ws_flags=sph_mod.WS_LEVELS)
+    s.bin_levels(lo, hi, 0.1)
+    st = s.stats()
+    assert st["status"] == sph_mod._capi.ENUMERIC
+    assert st["error_bits"] & sph_mod.ERR_OUTSIDE and st["error_bits"] & sph_mod.ERR_NONFINITE
+    key, lev, perm = orc.levels(bad[:, 0:3], bad[:, 10], wl.box, lo, hi, 0.1)
+    assert np.array_equal(s.perm().cpu().numpy(), perm)
+    assert np.array_equal(s.slot_cell().cpu().numpy(), key[perm])
+    assert np.array_equal(s.levels().cpu().numpy(), lev[perm])
+    s.close()
