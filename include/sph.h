@@ -445,9 +445,11 @@ sph_status sph_buffer_drift(sph_ctx *ctx, int32_t source, double dt);
  * and h_max <= h_level_min (the coarsest cells hold the largest support).
  * Invalidates every SoA field; leaves cell and buffer mode (sph_density,
  * sph_force and the buffer calls return SPH_ESTATE until sph_bin_cells or
- * sph_bin_buffers).  Errors: SPH_EINVAL (levels,
- * margin), SPH_ENOSPACE (workspace without SPH_WS_LEVELS), SPH_ECAPACITY
- * (h_max > h_level_min), SPH_ECUDA. */
+ * sph_bin_buffers).  Positions outside [0, box) or not finite set
+ * SPH_ERR_OUTSIDE (and SPH_ERR_NONFINITE) in the error word, as in
+ * sph_bin_cells, and land in the edge cells.  Errors: SPH_EINVAL (levels,
+ * margin, or no H in the layout), SPH_ENOSPACE (workspace without
+ * SPH_WS_LEVELS), SPH_ECAPACITY (h_max > h_level_min), SPH_ECUDA. */
 sph_status sph_bin_levels(sph_ctx *ctx, int32_t level_min, int32_t level_max, double h_margin);
 
 /* S3+S4 over the hierarchy: the density of sph_density (same Newton steps,
