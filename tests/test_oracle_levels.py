@@ -91,3 +91,40 @@ def test_positions_outside_the_box_clamp_into_the_edge_cells(orc):
     f = _decode(key, 5)
     assert f[:, 0].tolist() == [0, F - 1, F - 1, 0]
     assert np.all(f[:, 1] == F // 2) and np.all(f[:, 2] == F // 2)
+
+
+def test_level_search_finds_every_force_pair_once(orc):
+    # R24 by brute force on a small clustered set: with every h within its
+    # level's cap, searching for each level l' the level-l' particles in the 27
+    # cells of level min(l_i, l') around particle i finds every pair with
+    # r < h_i + h_j exactly once (and the density's 27 cells of level l_i hold
+    # every r < 2 h_i)
+    rng = np.random.default_rng(11)
+    n = 3000
+    x = np.concatenate([rng.uniform(0, 1, (n // 3, 3)), 0.3 + 0.02 * rng.standard_normal((n - n // 3, 3))]) % 1.0
+    lo, hi = 2, 6
+    h = rng.uniform(0.004, 0.12, n)
+    _, lev, _ = orc.levels(x, h, (1.0, 1.0, 1.0), lo, hi, 0.0)
+    lev = lev.astype(int)
+    cap = 0.5 * 2.0 ** -lev.astype(float)
+    h = np.minimum(h, cap)                      # every h within its level's cap
+    d = x[:, None, :] - x[None, :, :]
+    d -= np.round(d)
+    r = np.sqrt((d * d).sum(-1))
+    for i in rng.choice(n, 200, replace=False):
+        found = []
+        for lp in range(lo, hi + 1):
+            s = min(lev[i], lp)
+            ci = np.floor(x[i] * 2 ** s).astype(int)
+            cj = np.floor(x * 2 ** s).astype(int)
+            dd = (cj - ci + 1) % 2 ** s            # neighbour cells -> 0, 1, 2
+            near = np.all(dd <= 2, axis=1)
+            found.extend(np.flatnonzero(near & (lev == lp)).tolist())
+        assert len(found) == len(set(found))    # each candidate once
+        pairs = set(np.flatnonzero((r[i] < h[i] + h) & (np.arange(n) != i)).tolist())
+        assert pairs <= set(found), sorted(pairs - set(found))[:5]
+        dens = set(np.flatnonzero(r[i] < 2 * h[i]).tolist())
+        s = lev[i]
+        cells = np.all((np.floor(x * 2 ** s).astype(int) - np.floor(x[i] * 2 ** s).astype(int) + 1) % 2 ** s <= 2,
+                       axis=1)
+        assert dens <= set(np.flatnonzero(cells).tolist())
