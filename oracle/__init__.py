@@ -168,9 +168,11 @@ def bin_cells(x, box, nc, sub=1):
 
 
 def levels(x, h, box, level_min, level_max, margin=0.0):
-    """The level hierarchy's binning: Morton key of every particle's finest
-    cell (2^level_max per axis), its level from h, and the stable order by
-    key.  Returns (key[n] int32, level[n] int8, perm[n] int64)."""
+    """The level hierarchy's binning (every particle has its own h, Section 2;
+    the cells of each level hold the support of its particles): Morton key of
+    every particle's finest cell (2^level_max per axis), its level from h, and
+    the stable order by key.  Returns (key[n] int32, level[n] int8,
+    perm[n] int64)."""
     x = _f64(x, (-1, 3))
     n = x.shape[0]
     key = np.zeros(n, np.int32)

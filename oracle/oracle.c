@@ -194,7 +194,10 @@ static int cmp_keyidx(const void *pa, const void *pb)
 }
 
 /*
- * Levels l = level_min..level_max: 2^l cells per axis, edge L_d / 2^l.  The
+ * Section 2 gives every particle its own h (adapted to a fixed neighbour
+ * number); the paper's SWIFT kernels search neighbours in a cell tree.  This
+ * is the hierarchy read from that, as a linear octree:
+ * levels l = level_min..level_max: 2^l cells per axis, edge L_d / 2^l.  The
  * key of a particle is the Morton code of its finest cell, f_d =
  * clamp(floor(x_d * (2^level_max / L_d)), 0, 2^level_max - 1).  Its level is
  * the largest l with h (1 + margin) <= h_l = min_d (L_d / 2^l) / 2, or
