@@ -473,8 +473,12 @@ sph_status sph_density_levels(sph_ctx *ctx, int32_t newton_steps);
  * level l around it, and one of a coarser level l' in the 27 cells of level
  * l' around it: each particle searches, for every level l', the particles of
  * level l' in the cells of level min(l, l'), and finds each pair once.
+ * The search relies on every h being within its level's cap, which
+ * sph_density_levels guarantees: it must have run since the last
+ * sph_bin_levels and since H was last converted from the records.
  * Reads X, V, M, H, RHO, P, CS; writes A and DUDT (FP32).  Errors:
- * SPH_ESTATE (not in level mode, or inputs not current), SPH_ECUDA. */
+ * SPH_ESTATE (not in level mode, no sph_density_levels since, or inputs not
+ * current), SPH_ECUDA. */
 sph_status sph_force_levels(sph_ctx *ctx);
 
 /* Per level l (index l of both arrays, SPH_LEVEL_MAX + 1 entries each):

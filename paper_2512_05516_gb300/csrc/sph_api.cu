@@ -283,6 +283,7 @@ sph_status sph_aos_to_soa(sph_ctx *c, uint32_t fields, const int32_t *prec)
         if (fields & SPH_BIT(f)) c->prec[f] = prec ? prec[f] : SPH_P_FP32;
     if (run_aos_to_soa(c, fields) != cudaSuccess) return SPH_ECUDA;
     c->valid |= fields;
+    if (fields & SPH_BIT(SPH_F_H)) c->levels_fixed = false;   // h no longer the density's
     return SPH_OK;
 }
 
@@ -319,6 +320,7 @@ sph_status sph_aos_to_soa_host(sph_ctx *c, const void *host_aos, uint32_t fields
     if (run_aos_to_soa_host(c, (const uint8_t *)host_aos, fields, (uint8_t *)host_stage, nthreads) != cudaSuccess)
         return SPH_ECUDA;
     c->valid |= fields;
+    if (fields & SPH_BIT(SPH_F_H)) c->levels_fixed = false;
     return SPH_OK;
 }
 
@@ -462,6 +464,7 @@ sph_status sph_bin_levels(sph_ctx *c, int32_t level_min, int32_t level_max, doub
     c->binned = false;
     c->buffer = 0;
     c->levels = true;
+    c->levels_fixed = false;
     c->lvl_min = level_min;
     c->lvl_max = level_max;
     c->items_by_class = false;
@@ -477,6 +480,7 @@ sph_status sph_density_levels(sph_ctx *c, int32_t newton_steps)
     const uint32_t need = SPH_BIT(SPH_F_X) | SPH_BIT(SPH_F_M) | SPH_BIT(SPH_F_H);
     if ((c->valid & need) != need) return SPH_ESTATE;
     if (run_density_levels(c, newton_steps) != cudaSuccess) return SPH_ECUDA;
+    c->levels_fixed = true;
     c->valid |= SPH_BIT(SPH_F_RHO) | SPH_BIT(SPH_F_H);
     if (c->valid & SPH_BIT(SPH_F_U)) c->valid |= SPH_BIT(SPH_F_P) | SPH_BIT(SPH_F_CS);
     return SPH_OK;
@@ -485,7 +489,7 @@ sph_status sph_density_levels(sph_ctx *c, int32_t newton_steps)
 sph_status sph_force_levels(sph_ctx *c)
 {
     if (!c) return SPH_EINVAL;
-    if (!c->binned || !c->levels) return SPH_ESTATE;
+    if (!c->binned || !c->levels || !c->levels_fixed) return SPH_ESTATE;
     const uint32_t need = SPH_BIT(SPH_F_X) | SPH_BIT(SPH_F_V) | SPH_BIT(SPH_F_M) | SPH_BIT(SPH_F_H) |
                           SPH_BIT(SPH_F_RHO) | SPH_BIT(SPH_F_P) | SPH_BIT(SPH_F_CS);
     if ((c->valid & need) != need) return SPH_ESTATE;

@@ -323,6 +323,7 @@ struct sph_ctx {
     bool binned = false;
     int32_t buffer = 0;           // buffer mode: records taken in buffers of this size (0: cell lists)
     bool levels = false;          // level mode: Morton order over a hierarchy of grids
+    bool levels_fixed = false;    // level mode: the density fixed the levels (every h within its cap)
     int32_t lvl_min = 0, lvl_max = 0;
     sph::LaunchCache lc_density, lc_force;   // launch shapes of the persistent pair kernels
     sph::LaunchCache lc_density_lv, lc_density_one, lc_force_lv, lc_force_one;   // ... and over the level hierarchy

@@ -191,6 +191,12 @@ def test_level_calls_check_their_arguments_and_order():
         s.soa_to_aos(sph_mod.mask("x"))
     s.density_levels(2)
     s.force_levels()
+    s.aos_to_soa(sph_mod.mask("h"))                    # h from the records again: levels not fixed
+    with pytest.raises(sph_mod.SphError) as e:
+        s.force_levels()
+    assert e.value.status == sph_mod._capi.ESTATE
+    s.density_levels(2)
+    s.force_levels()
     # back to cells: the single-grid density runs again
     s.bin_cells(wl.cell_edge)
     s.aos_to_soa(sph_mod.FIELDS_DENSITY)
