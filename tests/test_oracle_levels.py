@@ -128,3 +128,38 @@ def test_level_search_finds_every_force_pair_once(orc):
         cells = np.all((np.floor(x * 2 ** s).astype(int) - np.floor(x[i] * 2 ** s).astype(int) + 1) % 2 ** s <= 2,
                        axis=1)
         assert dens <= set(np.flatnonzero(cells).tolist())
+
+
+def test_promotion_reproduces_the_single_cap_density(orc):
+    # R23 on the oracle: Newton steps capped at each level's h_l, with every
+    # particle that meets its cap moved one level up and recomputed from its
+    # original h, end with exactly the h and density of the steps capped at
+    # h_max alone (the same FP64 arithmetic on the same neighbours)
+    rng = np.random.default_rng(13)
+    n = 1500
+    x = np.concatenate([rng.uniform(0, 1, (n // 2, 3)), 0.6 + 0.03 * rng.standard_normal((n - n // 2, 3))]) % 1.0
+    m = np.full(n, 1.0 / n)
+    eta = 0.5 * (3 * 48 / (4 * np.pi)) ** (1 / 3)
+    lo, hi = 2, 6
+    h0 = rng.uniform(0.01, 0.1, n)
+    h_max = 0.5 * 2.0 ** -lo
+    ref = orc.density(x, m, h0, (1.0, 1.0, 1.0), eta, h_max, 5, brute=True)
+    _, lev, _ = orc.levels(x, h0, (1.0, 1.0, 1.0), lo, hi, 0.0)
+    lev = lev.astype(int)
+    rho = np.full(n, np.nan)
+    hh = np.full(n, np.nan)
+    todo = np.arange(n)
+    promoted = 0
+    for l in range(hi, lo - 1, -1):
+        t = todo[lev[todo] == l]
+        if t.size == 0:
+            continue
+        cap = min(h_max, 0.5 * 2.0 ** -l)
+        o = orc.density(x, m, h0, (1.0, 1.0, 1.0), eta, cap, 5, brute=True, targets=t)
+        up = (o["flags"] & orc.FLAG_HCAP) != 0 if l > lo else np.zeros(t.size, bool)
+        rho[t[~up]] = o["rho"][~up]
+        hh[t[~up]] = o["h"][~up]
+        lev[t[up]] = l - 1
+        promoted += int(up.sum())
+    assert promoted > 0
+    assert np.array_equal(rho, ref["rho"]) and np.array_equal(hh, ref["h"])
