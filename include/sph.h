@@ -161,8 +161,9 @@ typedef struct {
 #define SPH_ERR_OUTSIDE   2      /* a position lay outside [0, box) at binning */
 #define SPH_ERR_HCAP      4      /* some h was clamped at h_max */
 #define SPH_ERR_NEWTON    8      /* a Newton step met a non-positive derivative */
-#define SPH_ERR_TIMEOUT   16     /* an asynchronous record copy did not complete within its bounded
-                                    wait; the records of that warp were skipped */
+#define SPH_ERR_TIMEOUT   16     /* an asynchronous record copy did not complete within its first
+                                    bounded wait; the warp waited once more, longer, and skipped
+                                    its records only if the copy had still not landed */
 
 /* Launch shapes of the pair kernels (an autotuner sets them; the defaults
  * after sph_create are block_threads 32, ctas_per_sm 0, stage_density 1024,
@@ -460,8 +461,9 @@ sph_status sph_bin_levels(sph_ctx *ctx, int32_t level_min, int32_t level_max, do
  * moves to level l - 1 and is computed again there from its original h, so
  * that every particle's result is the one a single grid of cells >= 2 h_max
  * gives (up to the order of the sums).  hcap_clamps counts the particles
- * clamped at level_min.  Reads X, M, H (and U); writes RHO, H (newton_steps
- * > 0), P and CS (U current) and the neighbour counts.  Requires
+ * clamped at level_min.  Reads X, M, H (and U); writes RHO, H (always, even
+ * with newton_steps = 0, so that an input h above the level_min cap reaches
+ * the force clamped), P and CS (U current) and the neighbour counts.  Requires
  * sph_bin_levels and sph_aos_to_soa of X, M, H.  Errors: SPH_EINVAL
  * (newton_steps < 0 or > 32), SPH_ESTATE, SPH_ECUDA. */
 sph_status sph_density_levels(sph_ctx *ctx, int32_t newton_steps);

@@ -74,6 +74,9 @@ def _declare(L):
     for name in ("orc_W", "orc_dWdr", "orc_dWdh"):
         getattr(L, name).restype = _d
         getattr(L, name).argtypes = [_d, _d]
+    for name in ("orc_trunc64", "orc_trunc_half"):
+        getattr(L, name).restype = None
+        getattr(L, name).argtypes = [_i64, _p, C.c_int, _p]
     L.orc_bin.restype = C.c_int
     L.orc_bin.argtypes = [_i64, _p, _p, _p, _p, _p, _p]
     L.orc_bin_sub.restype = C.c_int
@@ -308,6 +311,35 @@ def quantize(values, fmt, exp2=0):
     return np.ldexp(out, -int(exp2)), code
 
 
+def truncate_bits(values, total_bits):
+    """Values as stored in `total_bits` bits by Table 2's family: 64 bits keep
+    the double; 63..33 the double layout with total - 12 mantissa bits; 32
+    single (round to nearest even); 31..17 the single layout with total - 9
+    mantissa bits; 16 half; 15..10 the half layout with total - 6 mantissa
+    bits.  The truncated widths drop the low mantissa bits (toward zero).
+    Table 2 prints the mantissa ranges as 51..24 and 22..11, which do not add
+    up to its own total widths 33 and 17; the mantissa here is always the
+    total minus the sign and exponent bits."""
+    v = _f64(values).ravel()
+    out = np.empty_like(v)
+    t = int(total_bits)
+    if t == 64:
+        out[:] = v
+    elif 33 <= t <= 63:
+        lib().orc_trunc64(v.shape[0], _ptr(v), t - 12, _ptr(out))
+    elif t == 32:
+        out = quantize(v, "fp32")[0]
+    elif 17 <= t <= 31:
+        out = quantize(v, f"m{t - 9}")[0]
+    elif t == 16:
+        out = quantize(v, "fp16")[0]
+    elif 10 <= t <= 15:
+        lib().orc_trunc_half(v.shape[0], _ptr(v), t - 6, _ptr(out))
+    else:
+        raise ValueError(f"no storage format of {t} bits")
+    return out.reshape(np.shape(values))
+
+
 def pack_bits(codes, bits):
     c = np.ascontiguousarray(codes, dtype=np.uint32)
     words = np.zeros((c.shape[0] * bits + 31) // 32, np.uint32)
@@ -346,7 +378,9 @@ def step(wl, newton_steps=None, targets=None, dt=None, with_kick_drift=True):
     """One SPH step on an sph_inputs.Workload in FP64: density with h iteration,
     EOS, force, kick/drift.  With `targets`, density/EOS are evaluated on every
     particle within 2*h_cap of a target (all that the targets' forces need) and
-    the force on the targets only; kick/drift is then skipped."""
+    the force on the targets only; kick/drift is then skipped.  The sampled
+    result also carries ``h_all``: the h the force read for every particle (the
+    iterated h inside the targets' balls, the input h elsewhere)."""
     x = wl.col("x")
     v = wl.col("v")
     m = wl.col("m")
@@ -384,5 +418,6 @@ def step(wl, newton_steps=None, targets=None, dt=None, with_kick_drift=True):
               targets=targets)
     pos = np.searchsorted(sub, targets)
     out.update(rho=d["rho"][pos], h=d["h"][pos], nngb=d["nngb"][pos], flags=d["flags"][pos],
-               P=Ps[pos], c=cs[pos], a=f["a"], dudt=f["dudt"], nngb_force=f["nngb"])
+               P=Ps[pos], c=cs[pos], a=f["a"], dudt=f["dudt"], nngb_force=f["nngb"],
+               h_all=hh)
     return out

@@ -753,6 +753,35 @@ void orc_quantize(int64_t n, const double *in, int fmt, double *value, uint32_t 
     }
 }
 
+/* Table 2, total widths 63..33: the double layout (sign, 11 exponent bits)
+ * with its mantissa truncated toward zero to `mant` bits (0..52; 52 keeps
+ * every value).  Infinities and NaNs pass unchanged. */
+void orc_trunc64(int64_t n, const double *in, int mant, double *out)
+{
+    const uint64_t keep = mant >= 52 ? ~0ull : ~((1ull << (52 - mant)) - 1ull);
+    for (int64_t i = 0; i < n; ++i) {
+        uint64_t b;
+        memcpy(&b, &in[i], 8);
+        if (((b >> 52) & 0x7FFull) != 0x7FFull) b &= keep;
+        memcpy(&out[i], &b, 8);
+    }
+}
+
+/* Table 2, total widths 15 and below: the half layout (sign, 5 exponent
+ * bits) with its mantissa truncated toward zero to `mant` bits (0..10): the
+ * value is first rounded to half (through single, as ORC_FMT_FP16), then the
+ * low 10 - mant mantissa bits of the half are cleared.  Infinities and NaNs
+ * keep their class. */
+void orc_trunc_half(int64_t n, const double *in, int mant, double *out)
+{
+    const uint16_t keep = (uint16_t)(mant >= 10 ? 0xFFFFu : ~((1u << (10 - mant)) - 1u));
+    for (int64_t i = 0; i < n; ++i) {
+        uint16_t h = orc_f16_from_f32(orc_f32_bits(in[i]));
+        if ((h & 0x7C00u) != 0x7C00u) h &= keep;
+        out[i] = orc_f32_value(orc_f32_from_f16(h));
+    }
+}
+
 /* Sec. 3.2: value k occupies bits [k*B, (k+1)*B) of a little-endian stream of
  * 32-bit words.  `words` must hold ceil(n*B/32) entries and is overwritten. */
 void orc_pack_bits(int64_t n, const uint32_t *codes, int bits, uint32_t *words)

@@ -97,6 +97,8 @@ uint32_t orc_f32_from_f16(uint16_t hbits);
 uint16_t orc_bf16_from_f32(uint32_t fbits);
 uint32_t orc_f32_from_bf16(uint16_t bbits);
 uint32_t orc_trunc_code(uint32_t fbits, int mant_bits);
+void orc_trunc64(int64_t n, const double *in, int mant, double *out);
+void orc_trunc_half(int64_t n, const double *in, int mant, double *out);
 uint32_t orc_f32_from_trunc(uint32_t code, int mant_bits);
 int      orc_fmt_bits(int fmt);
 void     orc_quantize(int64_t n, const double *in, int fmt, double *value, uint32_t *code);

@@ -1648,6 +1648,9 @@ cudaError_t run_density_levels(sph_ctx *c, int newton_steps)
     for (int k = 0; k < 3; ++k) a.c.fine_edge[k] = (float)c->edge[k];
     a.level = c->level;
     a.c.defer = c->tcode;     // free while the level's kernels run (its items are built)
+    // h is written even without Newton steps: an input h above its level's cap
+    // is clamped, and the level force relies on every h being within its cap
+    a.write_h = true;
     k_density_pack<<<(unsigned)((c->n + 255) / 256), 256, 0, c->stream>>>(a.c, c->pack);
     c->launches += 1;
     cudaError_t e = cudaGetLastError();

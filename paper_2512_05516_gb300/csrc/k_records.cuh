@@ -193,8 +193,7 @@ __device__ __forceinline__ float buffer_offset_f32(double x, double o, double L)
 // the same way.  Fully scattered records (one run per lane) move as fast
 // this way as by per-lane chunk loads, and their write-back faster.  Every
 // wait is bounded: a copy that has not landed after kBulkPolls polls sets
-// SPH_ERR_TIMEOUT, and the warp waits once more (bounded) for it and skips
-// its records.
+// SPH_ERR_TIMEOUT (bulk_wait says what follows).
 constexpr uint32_t kBulkPolls = 1u << 22;
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -289,15 +288,24 @@ __device__ __forceinline__ void bulk_issue_runs(const uint8_t *aos, int64_t o, c
     if (w.start) bulk_g2s(rec + lane * U, aos + o * rb, (uint32_t)w.len * (uint32_t)rb, bar);
 }
 
-// Wait for them; false after a timeout (error bit set).  Every lane calls it.
+// Wait for them.  Every lane calls it.  A copy that has not landed within
+// the first bound sets SPH_ERR_TIMEOUT; then the whole warp keeps waiting,
+// up to kBulkFinal times as long, so that its shared memory (and with it the
+// CTA) stays allocated while the copy may still be landing there.  Returns
+// whether the copy landed: if it did in that second wait, the records are
+// processed as usual (the error bit still reports the slow copy); if not,
+// the caller skips its records and exits without issuing another copy into
+// that memory.
+constexpr uint32_t kBulkFinal = 16u;
+
 __device__ __forceinline__ bool bulk_wait(uint64_t *bar, unsigned int *err, int lane)
 {
     if (__all_sync(0xffffffffu, mbar_wait(bar, 0, kBulkPolls))) return true;
-    if (lane == 0) {
-        atomicOr(err, (unsigned)SPH_ERR_TIMEOUT);
-        mbar_wait(bar, 0, kBulkPolls);
-    }
-    return false;
+    if (lane == 0) atomicOr(err, (unsigned)SPH_ERR_TIMEOUT);
+    bool landed = false;
+    for (uint32_t r = 0; r < kBulkFinal && !landed; ++r)
+        landed = __all_sync(0xffffffffu, mbar_wait(bar, 0, kBulkPolls));
+    return landed;
 }
 
 __device__ __forceinline__ bool bulk_load_runs(const uint8_t *aos, int64_t o, const WarpRuns &w, int rb,

@@ -40,13 +40,38 @@ def read_aos(s):
     return s.aos.cpu().numpy()
 
 
-def count_band_ok(orc, wl, h_ref, counts_gpu, delta):
+def count_band_ok(orc, wl, h_ref, counts_gpu, delta, targets=None, m=None):
     """Every GPU neighbour count must lie between the oracle's counts at
     h (1 - delta) and h (1 + delta): only pairs whose separation is within
-    delta of the support radius may be classified differently by FP32."""
-    x, m = wl.col("x"), wl.col("m")
-    lo = orc.density(x, m, h_ref * (1 - delta), wl.box, wl.eta, wl.h_cap * 2, 0)["nngb"]
-    hi = orc.density(x, m, h_ref * (1 + delta), wl.box, wl.eta, wl.h_cap * 2, 0)["nngb"]
+    delta of the support radius may be classified differently by FP32.  With
+    `targets`, h_ref holds every particle's h and the counts are the targets'.
+    `m` replaces the workload's masses (e.g. by their storage-rounded values)."""
+    x = wl.col("x")
+    m = wl.col("m") if m is None else m
+    lo = orc.density(x, m, h_ref * (1 - delta), wl.box, wl.eta, wl.h_cap * 2, 0,
+                     targets=targets)["nngb"]
+    hi = orc.density(x, m, h_ref * (1 + delta), wl.box, wl.eta, wl.h_cap * 2, 0,
+                     targets=targets)["nngb"]
+    ok = (counts_gpu >= lo) & (counts_gpu <= hi)
+    return ok, lo, hi
+
+
+def force_count_band_ok(orc, x, m, h, box, counts_gpu, delta, targets=None):
+    """The force's rule (R7: a pair iff r < h_i + h_j) with the same band: every
+    GPU force-neighbour count must lie between the oracle's counts with every
+    h scaled by (1 - delta) and by (1 + delta), which scales each pair's
+    support h_i + h_j by the same factor.  Only pairs whose separation lies
+    within delta of h_i + h_j may be classified differently.  The counts do not
+    depend on rho, P, c or v, so neutral values are passed for them."""
+    n = x.shape[0]
+    ones, zeros = np.ones(n), np.zeros(n)
+    v0 = np.zeros((n, 3))
+
+    def cnt(scale):
+        return orc.force(x, v0, m, h * scale, ones, zeros, zeros, box, 1.0, 2.0, 0.01,
+                         targets=targets)["nngb"]
+
+    lo, hi = cnt(1.0 - delta), cnt(1.0 + delta)
     ok = (counts_gpu >= lo) & (counts_gpu <= hi)
     return ok, lo, hi
 

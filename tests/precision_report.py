@@ -20,7 +20,12 @@ L2 flushing (indicative; bench.py times the benchmark).
 With --sweep: the truncated family at every width instead, v, m, h, u stored
 with 23 down to 1 mantissa bits (32 down to 10 total bits), one Sod step.
 
+With --oracle-sweep (CPU only, no GPU): the paper's own study on the FP64
+oracle, one force call in FP64 arithmetic over inputs stored in 64 down to 10
+total bits of Table 2's family.
+
 Usage (GPU):  python tests/precision_report.py [--json out.json] [--quick | --sweep]
+Usage (CPU):  python tests/precision_report.py --oracle-sweep [--json out.json]
 """
 import argparse
 import json
@@ -144,6 +149,39 @@ def sweep_report(wl, torch, sph):
     return rows
 
 
+def oracle_sweep_report():
+    """The paper's error-against-bits study (Section 7, Fig. 5) on the FP64
+    oracle alone, CPU only: the Sod set at 62,208 particles (the paper's
+    ~65,000) with small random velocities, its FP64 density (5 Newton steps)
+    and EOS as the state; then one force call in FP64 arithmetic whose inputs
+    (x, v, m, h, rho, P, c) are stored in t bits of Table 2's family, for every
+    t from 64 down to 10, against the same call on the untruncated inputs.
+    Also with the positions kept in FP64 and only the other inputs truncated.
+    Error: relative RMSE of the acceleration (RMSE over the mean |a|) and the
+    maximum over the mean."""
+    wl = sph_inputs.sod(n_lattice=48, seed=sph_inputs.SEED_BASE + 40)
+    wl.col("v")[:] = np.random.default_rng(40).uniform(-0.1, 0.1, (wl.n, 3))
+    x, v, m, u = wl.col("x"), wl.col("v"), wl.col("m"), wl.col("u")
+    d = oracle.density(x, m, wl.col("h"), wl.box, wl.eta, wl.h_cap, wl.newton_steps)
+    P, c = oracle.eos(d["rho"], u, wl.gamma)
+    inputs = {"x": x, "v": v, "m": m, "h": d["h"], "rho": d["rho"], "P": P, "c": c}
+
+    def force(q):
+        return oracle.force(q["x"], q["v"], q["m"], q["h"], q["rho"], q["P"], q["c"], wl.box,
+                            wl.alpha_av, wl.beta_av, wl.eps_av)["a"]
+
+    ref = force(inputs)
+    rows = []
+    for t in range(64, 9, -1):
+        tr = {k: oracle.truncate_bits(a, t) for k, a in inputs.items()}
+        keep_x = dict(tr, x=x)
+        r = {"workload": "sod", "n": wl.n, "total_bits": t,
+             "a_all": errors(force(tr), ref, True), "a_x_fp64": errors(force(keep_x), ref, True)}
+        rows.append(r)
+        print(json.dumps(r), flush=True)
+    return rows
+
+
 def hundred_step_report(name, wl, torch, sph):
     path = os.path.join(ROOT, "tests", "golden", f"trajectory_{name}.npz")
     if not os.path.exists(path):
@@ -193,7 +231,26 @@ def main():
     ap.add_argument("--quick", action="store_true", help="1-step rows only")
     ap.add_argument("--sweep", action="store_true",
                     help="only the truncated-mantissa sweep (32 down to 10 total bits) on the Sod set")
+    ap.add_argument("--oracle-sweep", action="store_true",
+                    help="CPU only: the FP64 oracle's force error against total storage bits "
+                         "(64 down to 10, Table 2's family)")
     args = ap.parse_args()
+    if args.oracle_sweep:
+        rows = oracle_sweep_report()
+        print()
+        print("| total bits | layout | a: all inputs truncated | a: positions kept in FP64 |")
+        print("|---|---|---|---|")
+        for r in rows:
+            t = r["total_bits"]
+            lay = ("double" if t == 64 else f"double, {t - 12} mantissa bits" if t >= 33 else
+                   "single" if t == 32 else f"single, {t - 9} mantissa bits" if t >= 17 else
+                   "half" if t == 16 else f"half, {t - 6} mantissa bits")
+            print(f"| {t} | {lay} | " + " | ".join(
+                f"{r[f]['rel_rmse']:.2e} / {r[f]['max_rel']:.1e}" for f in ("a_all", "a_x_fp64")) + " |")
+        if args.json:
+            with open(args.json, "w") as f:
+                json.dump(rows, f, indent=1)
+        return
     import torch
     import paper_2512_05516_gb300 as sph
     if not torch.cuda.is_available():

@@ -11,7 +11,7 @@ import pytest
 import torch
 
 import sph_inputs
-from gpu_util import make_sph
+from gpu_util import count_band_ok, force_count_band_ok, make_sph
 
 pytestmark = pytest.mark.gpu
 
@@ -55,10 +55,24 @@ def test_sod_1072476_sampled(orc):
     # oracle's up to pairs at the edge of the support; all particles sit near
     # the ~48 the smoothing-length iteration aims for (the jittered lattice
     # and the contact spread it)
+    perm = s.perm().cpu().numpy()
     cnt = np.empty(wl.n, np.int32)
-    cnt[s.perm().cpu().numpy()] = s.nngb().cpu().numpy()
-    assert np.abs(cnt[targets] - o["nngb"]).max() <= 1
+    cnt[perm] = s.nngb().cpu().numpy()
+    # the sample's density counts: within the band of the oracle's counts at
+    # h (1 -+ 2e-5) around the oracle's own h (h itself is held to 1e-5)
+    h_ref = o["h_all"].copy()
+    ok, lo, hi = count_band_ok(orc, wl, h_ref, cnt[targets], 2e-5, targets=targets)
+    assert ok.all()
+    assert np.array_equal(cnt[targets][lo == hi], o["nngb"][lo == hi])
     assert 12 <= cnt.min() and cnt.max() <= 120
+    # the sample's force counts (r < h_i + h_j) by the same band rule, on
+    # the h the oracle's sampled force read
+    cntf = np.empty(wl.n, np.int32)
+    cntf[perm] = s.nngb(force=True).cpu().numpy()
+    ok, lo, hi = force_count_band_ok(orc, x, m, h_ref, wl.box, cntf[targets], 2e-5,
+                                     targets=targets)
+    assert ok.all()
+    assert np.array_equal(cntf[targets][lo == hi], o["nngb_force"][lo == hi])
 
 
 def test_long_run_33554432_sampled(orc):
@@ -113,7 +127,9 @@ def test_gaussian_mixture_uneven_cells(orc):
     assert o["nngb"].max() > 20000                  # some targets sit in the dense core
     cnt = np.empty(wl.n, np.int32)
     cnt[s.perm().cpu().numpy()] = s.nngb().cpu().numpy()
-    assert np.abs(cnt[targets] - o["nngb"]).max() <= 2
+    ok, lo, hi = count_band_ok(orc, wl, wl.col("h"), cnt[targets], 4e-6, targets=targets)
+    assert ok.all()
+    assert np.array_equal(cnt[targets][lo == hi], o["nngb"][lo == hi])
 
 
 def test_gaussian_mixture_16777216_bf16_sampled(orc):
@@ -147,5 +163,7 @@ def test_gaussian_mixture_16777216_bf16_sampled(orc):
     assert o["nngb"].max() > 50000                  # some targets sit in the dense core
     cnt = np.empty(wl.n, np.int32)
     cnt[s.perm().cpu().numpy()] = s.nngb().cpu().numpy()
-    assert np.abs(cnt[targets] - o["nngb"]).max() <= 2
+    ok, lo, hi = count_band_ok(orc, wl, hq, cnt[targets], 4e-6, targets=targets, m=mq)
+    assert ok.all()
+    assert np.array_equal(cnt[targets][lo == hi], o["nngb"][lo == hi])
     s.close()

@@ -293,3 +293,46 @@ def test_level_binning_flags_bad_positions_and_stays_exact(orc):
     assert np.array_equal(s.slot_cell().cpu().numpy(), key[perm])
     assert np.array_equal(s.levels().cpu().numpy(), lev[perm])
     s.close()
+
+
+def test_level_density_without_newton_clamps_h_for_the_force(orc):
+    # an input h above the coarsest level's cap (h_max): the density with no
+    # Newton step clamps it to h_max and writes the clamped h, so that the
+    # level force, which searches stencils sized for each level's cap, sees
+    # every pair r < h_i + h_j of the oracle fed the same h, rho, P and c
+    wl = _wl(65_536 + 9)
+    wl.col("v")[:] = np.random.default_rng(13).uniform(-0.5, 0.5, (wl.n, 3))
+    lo, hi = wl.meta["levels"]
+    big = np.random.default_rng(14).choice(wl.n, 24, replace=False)
+    wl.col("h")[big] = 1.5 * wl.h_cap
+    rec = np.zeros((wl.n, 17))
+    rec[:, :14] = wl.aos
+    s = make_sph(wl, aos=torch.from_numpy(rec).cuda(), layout=sph_mod.make_layout(OFFS_136, 136),
+                 ws_flags=sph_mod.WS_LEVELS)
+    s.bin_levels(lo, hi, 0.0)
+    s.aos_to_soa(sph_mod.FIELDS_FORCE)
+    s.density_levels(0)
+    s.force_levels()
+    s.soa_to_aos(sph_mod.mask("h", "rho", "P", "cs", "a", "dudt"))
+    out = s.aos.cpu().numpy()
+    st = s.stats()
+    s.close()
+    assert st["error_bits"] & sph_mod.ERR_HCAP
+    assert st["error_bits"] & (sph_mod.ERR_NONFINITE | sph_mod.ERR_OUTSIDE) == 0
+    h, rho, P, c = out[:, 10], out[:, 11], out[:, 13], out[:, 14]
+    assert np.all(h[big] == float(np.float32(wl.h_cap)))
+    assert np.all(h <= float(np.float32(wl.h_cap)))
+    o = orc.density(wl.col("x"), wl.col("m"), wl.col("h"), wl.box, wl.eta, wl.h_cap, 0, brute=True,
+                    targets=big)
+    assert np.all(o["h"] == wl.h_cap) and np.all(o["flags"] & orc.FLAG_HCAP)
+    assert (np.abs(rho[big] - o["rho"]) / o["rho"]).max() <= 1e-5
+    # targets: the clamped particles and their force partners
+    x = wl.col("x")
+    near = orc.ball_mark(x, wl.box, 2.0 * wl.h_cap, big)
+    rng = np.random.default_rng(15)
+    t = np.unique(np.concatenate([big, rng.choice(np.flatnonzero(near), 200, replace=False)]))
+    f = orc.force(x, wl.col("v"), wl.col("m"), h, rho, P, c, wl.box, wl.alpha_av, wl.beta_av,
+                  wl.eps_av, brute=True, targets=t)
+    na = np.linalg.norm(f["a"], axis=1)
+    err_a = np.linalg.norm(out[t, 6:9] - f["a"], axis=1)
+    assert np.all(err_a <= 1e-5 * (na + na.mean())), (err_a / (na + na.mean())).max()

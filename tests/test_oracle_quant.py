@@ -141,3 +141,56 @@ def test_truncated_family_matches_the_named_widths(orc):
         code = np.zeros(d.shape, np.uint32)
         L.orc_quantize(d.shape[0], orc._ptr(d), 100 + n, orc._ptr(out), orc._ptr(code))
         assert np.array_equal(code, c0) and np.array_equal(out, v0)
+
+
+def test_truncate_64_bits_and_52_mantissa_bits_are_the_identity(orc):
+    rng = np.random.default_rng(40)
+    v = np.concatenate([rng.standard_normal(1000) * 10.0 ** rng.integers(-300, 300, 1000),
+                        [0.0, -0.0, 5e-324, -2.2e-308, np.inf, -np.inf, 1.0 + 2.0 ** -52]])
+    for t in (64,):
+        assert np.array_equal(orc.truncate_bits(v, t).view(np.uint64), v.view(np.uint64))
+    out = np.empty_like(v)
+    orc.lib().orc_trunc64(v.shape[0], v.ctypes.data, 52, out.ctypes.data)
+    assert np.array_equal(out.view(np.uint64), v.view(np.uint64))
+    nan = np.array([np.nan])
+    assert np.isnan(orc.truncate_bits(nan, 40)[0])
+
+
+def test_truncate_bits_hand_values(orc):
+    # 1 + 2^-52 keeps its last bit only at 52 mantissa bits (64 total)
+    one = np.array([1.0 + 2.0 ** -52, -(1.0 + 2.0 ** -30 + 2.0 ** -52)])
+    assert np.array_equal(orc.truncate_bits(one, 63), [1.0, -(1.0 + 2.0 ** -30)])
+    assert np.array_equal(orc.truncate_bits(one, 42), [1.0, -(1.0 + 2.0 ** -30)])
+    assert np.array_equal(orc.truncate_bits(one, 41), [1.0, -1.0])
+    # 4/3 = 1.010101...b: 21 mantissa bits (33 total) keep 1.0101...010b,
+    # i.e. 1 + (1 - 2^-20)/3 = 1398101 / 2^20, toward zero for either sign
+    x = np.array([4.0 / 3.0, -4.0 / 3.0])
+    assert np.array_equal(orc.truncate_bits(x, 33), [1398101 / 2.0 ** 20, -1398101 / 2.0 ** 20])
+    # 32 bits: the nearest single; 31 bits: 22 mantissa bits of the single
+    # 1.01010101010101010101011b (rounded up at bit 23), cut to 22 bits
+    assert orc.truncate_bits(x, 32)[0] == 11184811 / 2.0 ** 23
+    assert orc.truncate_bits(x, 31)[0] == 5592405 / 2.0 ** 22
+    # 16 bits: half 1.0101010101b (rounded down); 10 bits: 4 mantissa bits 1.0101b
+    assert orc.truncate_bits(x, 16)[0] == 1365 / 1024.0
+    assert orc.truncate_bits(x, 10)[1] == -21 / 16.0
+    # the exponent range follows the layout: 1e-30 is a double and a single,
+    # but 0 in half (far below its subnormals), and 1e6 overflows half
+    tiny = np.array([1e-30, 1e6])
+    assert orc.truncate_bits(tiny, 40)[0] > 0 and orc.truncate_bits(tiny, 20)[0] > 0
+    assert orc.truncate_bits(tiny, 12)[0] == 0.0 and np.isinf(orc.truncate_bits(tiny, 12)[1])
+
+
+def test_truncation_error_shrinks_with_width(orc):
+    # truncation toward zero within one layout: each extra mantissa bit at
+    # most halves the relative error bound 2^-mant, and the error never grows
+    rng = np.random.default_rng(41)
+    v = rng.uniform(0.5, 4.0, 20000)
+    prev = np.inf
+    for t in range(33, 65):
+        e = np.max(np.abs(orc.truncate_bits(v, t) - v) / v)
+        assert e <= 2.0 ** -(t - 12) and e <= prev
+        prev = e
+    for t in range(17, 32):
+        e = np.max(np.abs(orc.truncate_bits(v, t) - v) / v)
+        # the single's own rounding (2^-24) plus the truncation
+        assert e <= 2.0 ** -(t - 9) + 2.0 ** -24

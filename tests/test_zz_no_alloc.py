@@ -45,7 +45,7 @@ def _grid(wl):
     return [int(math.floor(b / want)) for b in wl.box]
 
 
-def test_matches_regular_binning_on_two_calls_in_a_row():
+def test_matches_regular_binning_on_two_calls_in_a_row(orc):
     import torch
     # first a larger set with a 3-pass radix sort, then a smaller shuffled one:
     # the second call must not see anything the first left in the shared array
@@ -59,6 +59,12 @@ def test_matches_regular_binning_on_two_calls_in_a_row():
         got = _noalloc(wl, nc)
         for r, g in zip(ref, got):
             assert torch.equal(r, g)
+        # and directly against the FP64 oracle's stable sort by cell id
+        cell_of, perm, start = orc.bin_cells(wl.col("x"), wl.box, nc)
+        g_perm, g_cell, g_start = (t.cpu().numpy() for t in got)
+        assert np.array_equal(g_perm, perm)
+        assert np.array_equal(g_cell, cell_of[perm])
+        assert np.array_equal(g_start, start)
 
 
 def test_rejects_sizes_beyond_its_array():
