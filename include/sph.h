@@ -166,12 +166,15 @@ typedef struct {
                                     its records only if the copy had still not landed */
 
 /* Launch shapes of the pair kernels (an autotuner sets them; the defaults
- * after sph_create are block_threads 32, ctas_per_sm 0, stage_density 1024,
+ * after sph_create are block_threads 32, ctas_per_sm 0, stage_density 128,
  * stage_force 96, subcells 2, item_order 1, class_launches 0, pair_kernel 0). */
 typedef struct {
     int32_t block_threads;       /* threads per CTA of the pair kernels (32..256, multiple of 32); one warp per work item */
     int32_t ctas_per_sm;         /* persistent CTAs per SM (0: occupancy maximum) */
-    int32_t stage_density;       /* neighbour candidates staged per warp, density kernel (>= 32) */
+    int32_t stage_density;       /* density kernel: candidates staged per warp in one round of the
+                                    stream that fills the per-lane lists (>= 32); in level mode
+                                    an item whose box gathers more than 8 x stage_density
+                                    candidates is deferred to the per-target pass */
     int32_t stage_force;         /* neighbour candidates staged per warp, force kernel (>= 32) */
     int32_t subcells;            /* sub-cells per cell edge used to order particles, 1 or 2
                                     (default 2); takes effect at the next sph_bin_cells */

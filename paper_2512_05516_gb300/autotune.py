@@ -29,7 +29,7 @@ SPACE = {
     "subcells": (1, 2),
     "item_order": (0, 1),
     "block_threads": (32, 64, 128),
-    "stage_density": (512, 768, 1024, 1536),
+    "stage_density": (64, 128, 256, 512),
     "stage_force": (96, 128, 192, 256, 384, 512),
 }
 

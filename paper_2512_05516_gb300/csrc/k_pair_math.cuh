@@ -8,17 +8,40 @@
 
 namespace sph {
 
-// M4 spline w(q) and w'(q), branch-free, for any q >= 0: with
-// t = max(2 - q, 0) and u = max(1 - q, 0),
-//   w = t^3 / 4 - u^3,   w' = -3 t^2 / 4 + 3 u^2,
+// M4 spline w(q) and w'(q), branch-free, for any q >= 0: with the clamped
+// linear terms p = sat(1 - q/2) = max(2 - q, 0) / 2 and u = sat(1 - q)
+// (sat clamps to [0, 1], so both run on the FMA pipe),
+//   w = 2 p^3 - u^3,   w' = 3 (u^2 - p^2),
 // which is 1 - 3q^2/2 + 3q^3/4 on [0, 1), (2 - q)^3 / 4 on [1, 2) and 0 beyond.
+struct SplineTerms {
+    float p, u, p2, u2;
+};
+
+__device__ __forceinline__ SplineTerms spline_terms(float q)
+{
+    SplineTerms s;
+    s.p = __saturatef(fmaf(q, -0.5f, 1.0f));
+    s.u = __saturatef(1.0f - q);
+    s.p2 = s.p * s.p;
+    s.u2 = s.u * s.u;
+    return s;
+}
+
 __device__ __forceinline__ void spline(float q, float &w, float &dw)
 {
-    const float t = fmaxf(2.0f - q, 0.0f);
-    const float u = fmaxf(1.0f - q, 0.0f);
-    const float t2 = t * t, u2 = u * u;
-    w = fmaf(0.25f * t2, t, -(u2 * u));
-    dw = fmaf(3.0f, u2, -0.75f * t2);
+    const SplineTerms s = spline_terms(q);
+    w = fmaf(s.p2 + s.p2, s.p, -(s.u2 * s.u));
+    dw = 3.0f * (s.u2 - s.p2);
+}
+
+// 1 / sqrt(x) for x >= 1e-30 (a normal number), the approximate hardware
+// reciprocal square root (the same result as rsqrtf for such x, without the
+// handling of subnormal inputs)
+__device__ __forceinline__ float rsqrt_normal(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 
 // Kahan compensated accumulation: s - c carries the running sum; c holds the
@@ -38,10 +61,10 @@ __device__ __forceinline__ void force_pair(float &ax, float &ay, float &az, floa
                                            float dz, float r2, float hs, const float4 qb, const float4 qc,
                                            float alpha, float beta, float eps)
 {
-    const float rinv = rsqrtf(r2);
+    const float rinv = rsqrt_normal(fmaxf(r2, 1.0e-30f));
     const float r = r2 * rinv;
     const float hb = 0.5f * hs;
-    const float hbinv = 2.0f / hs;
+    const float hbinv = __fdividef(2.0f, hs);
     const float qq = r * hbinv;
     float w, dw;
     spline(qq, w, dw);
@@ -51,10 +74,10 @@ __device__ __forceinline__ void force_pair(float &ax, float &ay, float &az, floa
     const float vdotr = fmaf(vx, dx, fmaf(vy, dy, vz * dz));
     float visc = 0.0f;
     if (vdotr < 0.0f) {
-        const float mu = hb * vdotr / fmaf(eps * hb, hb, r2);
+        const float mu = __fdividef(hb * vdotr, fmaf(eps * hb, hb, r2));
         const float cbar = 0.5f * (ci + qc.z);
         const float rbar = 0.5f * (rhoi + qc.y);
-        visc = fmaf(-alpha * cbar, mu, beta * mu * mu) / rbar;
+        visc = __fdividef(fmaf(-alpha * cbar, mu, beta * mu * mu), rbar);
     }
     const float fac = qb.w * (Pr2i + qc.x + visc) * gw;
     ax = fmaf(-fac, dx, ax);

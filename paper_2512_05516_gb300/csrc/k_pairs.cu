@@ -37,10 +37,14 @@ cudaError_t run_pack(sph_ctx *c, const float *src, int f);
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int kLaneCap = 96;                                 // per-lane pair list entries
-constexpr int kListSlots = kLaneCap + 1;                     // plus one scratch slot per lane
+constexpr int kForceCap = 96;                                // force: per-lane pair list entries
+constexpr int kForceSlots = kForceCap + 1;                   // plus one scratch slot per lane
+constexpr int kDensCapUni = 96;                              // density: list entries r
+constexpr int kDensCapPair = 48;                             // density: list entries (r, m)
+constexpr int kDensSlots = 98;                               // words per lane, scratch entry included
+static_assert(kDensCapUni < kDensSlots && 2 * kDensCapPair + 1 < kDensSlots, "density list scratch entry");
 #ifndef SPH_LIST_SKIN
-#define SPH_LIST_SKIN 0.09f
+#define SPH_LIST_SKIN 0.03f
 #endif
 constexpr float kSkin = SPH_LIST_SKIN;                       // list radius = 2 h (1 + skin)
 constexpr float kStageSkin = 0.12f;                          // stage radius = 2 max h (1 + skin)
@@ -53,6 +57,7 @@ struct Common {
     int64_t n;
     int32_t nc[3];
     float edge[3];
+    float4 shift[27];                // offset of stencil cell t in the item cell's frame (from edge)
     int sub, s3;                     // sub-cells per cell edge, per cell
     int lg_sub, lg_s3;               // their base-2 logarithms (sub is 1 or 2)
     const int32_t *cell_start;       // indexed by key = cell * s3 + sub-cell
@@ -60,7 +65,8 @@ struct Common {
     const int32_t *range;            // [first, last) item of this launch in device memory, or null: all
     DevStats *st;
     FieldRef x, m, h;
-    int cap;                         // staged candidates per warp
+    int cap;                         // staged candidates per warp (one streaming round)
+    int defer_cap;                   // level density: staged candidates beyond which an item is deferred
     // level hierarchy: cells of one level, particles in Morton order of
     // their finest cell, positions offsets from that cell's origin
     const int32_t *tslot;            // item entry -> slot (null: entry = slot)
@@ -128,7 +134,8 @@ struct __align__(16) Tab {
 // Each warp's shared-memory region is stage | lists | table; the next warp's
 // float4 stage starts right after, so every part keeps 16-byte multiples.
 static_assert(sizeof(Tab) % 16 == 0, "stencil table size must keep 16-byte alignment");
-static_assert((32 * kListSlots * sizeof(uint16_t)) % 16 == 0, "list size must keep 16-byte alignment");
+static_assert((32 * kForceSlots * sizeof(uint16_t)) % 16 == 0, "list size must keep 16-byte alignment");
+static_assert((32 * kDensSlots * sizeof(float)) % 16 == 0, "list size must keep 16-byte alignment");
 // level force: an item whose candidate stream is longer than this is
 // gathered target by target (k_force_one)
 constexpr int kForceDefer = 8192;
@@ -193,9 +200,10 @@ __device__ __forceinline__ float box_dist2(const Box &b, float x, float y, float
 // offset of stencil cell t (0..26) in the item cell's frame
 __device__ __forceinline__ void stencil_shift(const Common &c, int t, float &sx, float &sy, float &sz)
 {
-    sx = (float)(t % 3 - 1) * c.edge[0];
-    sy = (float)((t / 3) % 3 - 1) * c.edge[1];
-    sz = (float)(t / 9 - 1) * c.edge[2];
+    const float4 v = c.shift[t];
+    sx = v.x;
+    sy = v.y;
+    sz = v.z;
 }
 
 // List the stencil sub-cells of `cell` whose box comes within reach of the
@@ -441,55 +449,49 @@ __device__ int lvl_table(const Common &c, const int *bnd, const Box &box, float 
 
 // density pass accumulators of one lane
 struct DAcc {
-    float s, c, d;   // compensated sum of m w (s - c), and sum of m (3w + q w')
-    int n;           // pairs with r < 2h (self included)
+    float s, c;      // compensated sum of m w (s - c)
+    float d;         // sum of m (3w + q w') / 3
+    float n;         // pairs with r < 2h, self included (exact: far below 2^24)
 };
 
-// one candidate of a density pass; `deriv` adds the dh term (Newton passes)
-__device__ __forceinline__ void dens_pair(DAcc &a, float xi, float yi, float zi, float h2x4,
-                                          float hinv, bool plain, bool deriv, const float4 q)
+// The separation of a candidate from (xi, yi, zi), as every density path
+// forms it: r = r^2 rsqrt(r^2), 0 for the self pair.
+__device__ __forceinline__ float pair_r(float xi, float yi, float zi, const float4 q)
 {
     const float dx = xi - q.x, dy = yi - q.y, dz = zi - q.z;
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    const bool in = r2 < h2x4;                           // the neighbour test (counts)
-    const float r = r2 * rsqrtf(fmaxf(r2, 1.0e-30f));    // 0 for the self pair
-    const float qq = r * hinv;
-    float w, dw;
-    spline(qq, w, dw);                                   // w = w' = 0 beyond the support
-    const float mw = q.w * w;
-    if (plain) a.s += mw;
-    else kahan_add(a.s, a.c, mw);
-    if (deriv) a.d = fmaf(q.w, fmaf(qq, dw, 3.0f * w), a.d);
-    a.n += in ? 1 : 0;
+    return r2 * rsqrt_normal(r2 + 1.0e-30f);
 }
 
-// This lane's list of the staged candidates with r^2 < R2 (indices into the
-// stage, at lst[l * 32 + lane]); returns how many there are (only the first
-// kLaneCap are stored).  Candidates go in batches whose shared-memory loads
-// are all issued before the batch's list stores.
-__device__ __forceinline__ int build_list(const float4 *sj, int T, float xi, float yi, float zi, float R2,
-                                          uint16_t *lst, int lane)
+// One pair of a density pass from its separation r: the spline at q = r/h,
+// m_j w into the (compensated) sum, on Newton passes the dh term
+// m_j (3w + q w') / 3 = m_j (w + q (u^2 - p^2)), and the neighbour count
+// (q < 2, i.e. p > 0: the pairs the spline gives weight; sat(p 2^100) is 1
+// for every p > 0, as p >= 2^-24 then).  With one mass for every pair (mj = 1
+// here and the sums scaled by m afterwards) the multiplications by m fold
+// away.
+template <bool kPlain, bool kDeriv>
+__device__ __forceinline__ void dens_acc(DAcc &a, float r, float hinv, float mj)
 {
-    constexpr int LB = 8;
-    int n = 0;
-    for (int e0 = 0; e0 < T; e0 += LB) {
-        float r2[LB];
-#pragma unroll
-        for (int u = 0; u < LB; ++u) {
-            const float4 q = sj[min(e0 + u, T - 1)];
-            const float dx = xi - q.x, dy = yi - q.y, dz = zi - q.z;
-            r2[u] = e0 + u < T ? fmaf(dx, dx, fmaf(dy, dy, dz * dz)) : R2;
-        }
-        // branch-free append: every candidate is written at the next free
-        // slot (slot kLaneCap is scratch once the list is full) and the
-        // count advances only for the kept ones
-#pragma unroll
-        for (int u = 0; u < LB; ++u) {
-            lst[min(n, kLaneCap) * 32 + lane] = (uint16_t)(e0 + u);
-            n += r2[u] < R2 ? 1 : 0;
-        }
+    const float qq = r * hinv;
+    const SplineTerms t = spline_terms(qq);
+    const float w = fmaf(t.p2 + t.p2, t.p, -(t.u2 * t.u));
+    const float mw = mj * w;
+    if (kPlain) a.s += mw;
+    else kahan_add(a.s, a.c, mw);
+    if (kDeriv) a.d = fmaf(mj, fmaf(qq, t.u2 - t.p2, w), a.d);
+    a.n += __saturatef(t.p * 1.2676506e30f);
+}
+
+__device__ __forceinline__ void dens_acc_rt(DAcc &a, float r, float hinv, float mj, bool plain, bool deriv)
+{
+    if (plain) {
+        if (deriv) dens_acc<true, true>(a, r, hinv, mj);
+        else dens_acc<true, false>(a, r, hinv, mj);
+    } else {
+        if (deriv) dens_acc<false, true>(a, r, hinv, mj);
+        else dens_acc<false, false>(a, r, hinv, mj);
     }
-    return n;
 }
 
 // A position in the candidate stream and the table entry holding it.
@@ -504,7 +506,8 @@ struct Cursor {
 // stages at least one batch, since a batch holds at most 32 <= cap.
 template <bool kLvl, int kU = kStageUnroll>
 __device__ int stage_density(const Common &c, const float4 *pD, const Tab &tab, int total, const Box &box,
-                             float R2, float4 *sj, int cap, Cursor &cur, int lane, int3 org)
+                             float R2, float4 *sj, int cap, Cursor &cur, int lane, int3 org, float mref = 0.0f,
+                             bool *mixed = nullptr)
 {
     const unsigned lt = (1u << lane) - 1u;
     const int nk = tab.nk;
@@ -543,7 +546,10 @@ __device__ int stage_density(const Common &c, const float4 *pD, const Tab &tab, 
                 __syncwarp();
                 return found;
             }
-            if (keep) sj[found + __popc(b & lt)] = q[u];
+            if (keep) {
+                sj[found + __popc(b & lt)] = q[u];
+                if (mixed && q[u].w != mref) *mixed = true;
+            }
             found += nb;
         }
         ecur = __shfl_sync(FULL, e, 31);
@@ -565,17 +571,157 @@ __global__ void __launch_bounds__(256) k_density_pack(Common c, float4 *pD)
                         ld_val(c.x.p[2], c.x.fmt, k) * c.x.dec, ld_val(c.m.p[0], c.m.fmt, k) * c.m.dec);
 }
 
+// Shared memory of one density warp: the streaming stage (cap candidates),
+// the per-lane lists of separations and the stencil table (plus, in level
+// mode, the run boundaries of the item's stencil).
+__host__ __device__ inline size_t density_warp_bytes(int cap, bool levels)
+{
+    return (size_t)cap * sizeof(float4) + (size_t)32 * kDensSlots * sizeof(float) + sizeof(Tab) +
+           (levels ? kBndBytes : 0);
+}
+
+// A lane's list of separations.  With one mass for every staged candidate
+// (`uni`) entry e is r at lr[e * 32 + lane], up to kDensCapUni entries;
+// otherwise entry e is the pair (r, m_j) at lr[2e * 32 + lane],
+// lr[(2e + 1) * 32 + lane], up to kDensCapPair.  Appends past the capacity
+// land in the scratch entry (the count keeps growing, so an overflow is seen).
+
+// Append the staged candidates sj[0, len) with r^2 < R2l to a lane's list.
+template <bool kUni>
+__device__ __forceinline__ int append_list(const float4 *sj, int len, float xi, float yi, float zi, float R2l,
+                                           float *lr, int n, int lane)
+{
+    constexpr int lcap = kUni ? kDensCapUni : kDensCapPair;
+    constexpr int LB = 4;
+    int e0 = 0;
+    for (; e0 + LB <= len; e0 += LB) {
+        float4 q[LB];
+#pragma unroll
+        for (int u = 0; u < LB; ++u) q[u] = sj[e0 + u];
+#pragma unroll
+        for (int u = 0; u < LB; ++u) {
+            const float r = pair_r(xi, yi, zi, q[u]);
+            const float dx = xi - q[u].x, dy = yi - q[u].y, dz = zi - q[u].z;
+            const bool keep = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < R2l;
+            const int s = min(n, lcap);
+            if (kUni) {
+                lr[s * 32 + lane] = r;
+            } else {
+                lr[(2 * s) * 32 + lane] = r;
+                lr[(2 * s + 1) * 32 + lane] = q[u].w;
+            }
+            n += keep ? 1 : 0;
+        }
+    }
+    for (; e0 < len; ++e0) {
+        const float4 q = sj[e0];
+        const float r = pair_r(xi, yi, zi, q);
+        const float dx = xi - q.x, dy = yi - q.y, dz = zi - q.z;
+        const bool keep = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < R2l;
+        const int s = min(n, lcap);
+        if (kUni) {
+            lr[s * 32 + lane] = r;
+        } else {
+            lr[(2 * s) * 32 + lane] = r;
+            lr[(2 * s + 1) * 32 + lane] = q.w;
+        }
+        n += keep ? 1 : 0;
+    }
+    return n;
+}
+
+// Stream the item's candidates within 2 h_list of the lanes with `bld` and
+// append each of those lanes' candidates with r < 2 h_list to its list, in
+// stream order.  `box` and R2s (the squared reach of the building lanes)
+// prune the stream.  `mixed` is set when a staged candidate's mass differs
+// from mref (then the lists cannot share one mass).  Returns the staged
+// candidate count of the warp, or -1 in level mode once it exceeds
+// `defer_at` (the item is deferred).  `stop_at` ends the stream early once
+// every building lane has found more entries than that (their lists
+// overflow whatever follows).
+template <bool kLvl>
+__device__ int build_lists(const Common &c, const float4 *pD, Tab &tab, const int *bnd, int cell, const Box &box,
+                           float R2s, float4 *sj, int cap, float *lr, bool uni, bool bld, float xi, float yi, float zi,
+                           float mref, float R2l, int &n, bool &mixed, int stop_at, int defer_at,
+                           unsigned long long &tests, int lane, int3 org)
+{
+    const int total = kLvl ? lvl_table(c, bnd, box, R2s, tab, lane) : build_stream(c, cell, box, R2s, tab, lane);
+    if (bld) n = 0;
+    bool mix = false;
+    int staged = 0;
+    Cursor cur{0, 0};
+    do {
+        const int len = stage_density<kLvl>(c, pD, tab, total, box, R2s, sj, cap, cur, lane, org, mref, &mix);
+        staged += len;
+        if (kLvl && staged > defer_at) return -1;
+        if (bld) {
+            tests += (unsigned long long)len;
+            n = uni ? append_list<true>(sj, len, xi, yi, zi, R2l, lr, n, lane)
+                    : append_list<false>(sj, len, xi, yi, zi, R2l, lr, n, lane);
+        }
+        __syncwarp();
+        if (__all_sync(FULL, !bld || n > stop_at)) break;
+    } while (cur.g < total);
+    mixed = __any_sync(FULL, mix);
+    return staged;
+}
+
+// One pass over a lane's list.
+template <bool kPlain, bool kDeriv, bool kUni>
+__device__ __forceinline__ void list_pass(DAcc &acc, const float *lr, int n, float hinv, int lane)
+{
+    if (kUni) {
+#pragma unroll 4
+        for (int e = 0; e < n; ++e) dens_acc<kPlain, kDeriv>(acc, lr[e * 32 + lane], hinv, 1.0f);
+    } else {
+#pragma unroll 4
+        for (int e = 0; e < n; ++e)
+            dens_acc<kPlain, kDeriv>(acc, lr[(2 * e) * 32 + lane], hinv, lr[(2 * e + 1) * 32 + lane]);
+    }
+}
+
+__device__ __forceinline__ void list_pass_rt(DAcc &acc, const float *lr, int n, float hinv, bool plain, bool deriv,
+                                             bool uni, int lane)
+{
+    if (uni) {
+        if (plain) {
+            if (deriv) list_pass<true, true, true>(acc, lr, n, hinv, lane);
+            else list_pass<true, false, true>(acc, lr, n, hinv, lane);
+        } else {
+            if (deriv) list_pass<false, true, true>(acc, lr, n, hinv, lane);
+            else list_pass<false, false, true>(acc, lr, n, hinv, lane);
+        }
+    } else {
+        if (plain) {
+            if (deriv) list_pass<true, true, false>(acc, lr, n, hinv, lane);
+            else list_pass<true, false, false>(acc, lr, n, hinv, lane);
+        } else {
+            if (deriv) list_pass<false, true, false>(acc, lr, n, hinv, lane);
+            else list_pass<false, false, false>(acc, lr, n, hinv, lane);
+        }
+    }
+}
+
+// Density over the warp work items.  Per item, every lane keeps the list of
+// its candidates within 2 h (1 + skin) as separations r (the passes need
+// nothing else: the positions do not move during the Newton steps), built by
+// streaming the stencil's candidates through a small stage; a lane rebuilds
+// its list only when its h outgrows the list radius.  While every listed
+// candidate of the item has the mass of the lane that lists it (`uni`, the
+// usual case) the lists hold r alone and the sums are scaled by that mass;
+// otherwise the item's lists hold (r, m_j) pairs at half the capacity.  A
+// lane whose list overflows even at the tight skin sums every pass straight
+// from the stream.  Level mode defers an item whose box gathers more than
+// `defer_at` staged candidates to the per-target pass (k_density_one).
 template <bool kLvl>
 __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const Common &c = a.c;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const size_t per_warp = (size_t)c.cap * sizeof(float4) + (size_t)32 * kListSlots * sizeof(uint16_t) + sizeof(Tab) +
-                            (kLvl ? kBndBytes : 0);
-    float4 *sj = reinterpret_cast<float4 *>(smem + warp * per_warp);
-    uint16_t *lst = reinterpret_cast<uint16_t *>(sj + c.cap);
-    Tab &tab = *reinterpret_cast<Tab *>(lst + 32 * kListSlots);
+    float4 *sj = reinterpret_cast<float4 *>(smem + warp * density_warp_bytes(c.cap, kLvl));
+    float *lr = reinterpret_cast<float *>(sj + c.cap);
+    Tab &tab = *reinterpret_cast<Tab *>(lr + 32 * kDensSlots);
     int *bnd = reinterpret_cast<int *>(&tab + 1);          // level kernel: the item's stencil runs
 
     unsigned long long my_pairs = 0, my_tests = 0, my_done = 0, my_prom = 0;
@@ -611,100 +757,98 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
             if (!(hi > 0.0f) || !isfinite(hi)) { hi = a.h_cap; my_err |= SPH_ERR_NONFINITE; }
             if (hi > a.h_cap) { hi = a.h_cap; clamped = true; }
         }
-        const Box box = warp_box(ok, xi, yi, zi);
 
-        // stage everything within 2 h_stage of the box, h_stage = max h (1 + skin)
-        float h_stage = fminf(warp_max(ok ? hi : 0.0f) * (1.0f + kStageSkin), a.h_cap);
-        float R2s = 4.0f * h_stage * h_stage;
-        int total = kLvl ? lvl_table(c, bnd, box, R2s, tab, lane) : build_stream(c, cell, box, R2s, tab, lane);
-        Cursor cur{0, 0};
-        int T = stage_density<kLvl>(c, a.pD, tab, total, box, R2s, sj, c.cap, cur, lane, org);
-        bool fits = cur.g >= total;
-        float h_list = 0.0f;       // this lane's list holds every staged candidate within 2 h_list
-        int nlist = 0;
-
+        float h_list = 0.0f;       // this lane's list holds every candidate within 2 h_list
+        int nl = 0;                // entries in this lane's list (may exceed the capacity)
+        bool direct = false;       // list overflowed: every pass sums straight from the stream
+        bool uni = true;           // warp-uniform list layout (see build_lists)
+        bool per_target = false;
+        const float mref = __shfl_sync(FULL, mi, 0);
         float rho = 0.f, drdh = 0.f;
         int cnt = 0;
         unsigned long long lane_pairs = 0;
-        bool per_target = kLvl && !fits;
-        if (!per_target)
         for (int pass = 0; pass < a.npass; ++pass) {
-            const float h2x4 = 4.0f * hi * hi;
             const float hinv = 1.0f / hi;
             const bool deriv = pass + 1 < a.npass;     // the last pass needs no dh term
-            DAcc acc{0.f, 0.f, 0.f, 0};
-            if (fits && __any_sync(FULL, ok && hi > h_stage)) {
-                // h outgrew the stage: re-stage with the current h
-                h_stage = fminf(warp_max(ok ? hi : 0.0f) * (1.0f + kStageSkin), a.h_cap);
-                R2s = 4.0f * h_stage * h_stage;
-                total = kLvl ? lvl_table(c, bnd, box, R2s, tab, lane) : build_stream(c, cell, box, R2s, tab, lane);
-                Cursor rc{0, 0};
-                T = stage_density<kLvl>(c, a.pD, tab, total, box, R2s, sj, c.cap, rc, lane, org);
-                fits = rc.g >= total;
-                h_list = 0.0f;
-                if (kLvl && !fits) {
-                    // the grown neighbourhood no longer fits: the level
-                    // kernel starts the item over, target by target
-                    per_target = true;
+            // (re)build the lists of the lanes whose h outgrew their list radius
+            bool need = ok && !direct && hi > h_list;
+            if (__any_sync(FULL, need)) {
+                if (need) h_list = fminf(hi * (1.0f + kSkin), a.h_cap);
+                for (int round = 0; round < 2; ++round) {
+                    const Box bb = warp_box(need, xi, yi, zi);
+                    const float hb = 2.0f * warp_max(need ? h_list : 0.0f);
+                    const int lc = uni ? kDensCapUni : kDensCapPair;
+                    bool mixed = false;
+                    const int st = build_lists<kLvl>(c, a.pD, tab, bnd, cell, bb, hb * hb, sj, c.cap, lr, uni, need, xi,
+                                                     yi, zi, mref, 4.0f * h_list * h_list, nl, mixed, lc + lc / 4,
+                                                     c.defer_cap, my_tests, lane, org);
+                    if (kLvl && st < 0) {
+                        per_target = true;
+                        break;
+                    }
+                    // a staged candidate of another mass: every list of the
+                    // item is rebuilt as (r, m) pairs
+                    if (uni && mixed) {
+                        uni = false;
+                        need = ok && !direct;
+                        continue;
+                    }
                     break;
                 }
+                if (per_target) break;
+                // overflowing lists: once more with the tight skin, then the stream
+                const int lcap = uni ? kDensCapUni : kDensCapPair;
+                const bool over = need && nl > lcap;
+                if (__any_sync(FULL, over)) {
+                    // far above the capacity the tight skin cannot help
+                    const bool retry = over && nl <= lcap + lcap / 4;
+                    if (over && !retry) direct = true;
+                    if (__any_sync(FULL, retry)) {
+                        if (retry) h_list = fminf(hi * (1.0f + kSkinTight), a.h_cap);
+                        const Box bb = warp_box(retry, xi, yi, zi);
+                        const float hb = 2.0f * warp_max(retry ? h_list : 0.0f);
+                        bool mixed = false;
+                        const int st = build_lists<kLvl>(c, a.pD, tab, bnd, cell, bb, hb * hb, sj, c.cap, lr, uni, retry,
+                                                         xi, yi, zi, mref, 4.0f * h_list * h_list, nl, mixed, lcap,
+                                                         c.defer_cap, my_tests, lane, org);
+                        if (kLvl && st < 0) {
+                            per_target = true;
+                            break;
+                        }
+                        if (retry && nl > lcap) direct = true;
+                    }
+                }
             }
-            if (fits) {
-                // rebuild when some lane's h outgrew its list radius (always on pass 0)
-                // (only the lanes whose h outgrew their list rebuild it)
-                if (__any_sync(FULL, ok && hi > h_list)) {
-                    if (ok && hi > h_list) {
-                        h_list = fminf(hi * (1.0f + kSkin), h_stage);
-                        my_tests += (unsigned long long)T;
-                        nlist = build_list(sj, T, xi, yi, zi, 4.0f * h_list * h_list, lst, lane);
-                        if (nlist > kLaneCap) {
-                            // too many within the skin: a tighter radius (more
-                            // rebuilds for this lane, but no walk of the whole stage)
-                            h_list = fminf(hi * (1.0f + kSkinTight), h_stage);
-                            nlist = build_list(sj, T, xi, yi, zi, 4.0f * h_list * h_list, lst, lane);
-                        }
-                    }
-                    __syncwarp();
-                }
-                if (ok) {
-                    my_tests += (unsigned long long)(nlist <= kLaneCap ? nlist : T);
-                    if (nlist <= kLaneCap) {
-                        // the summation mode is fixed per call: one loop body
-                        // each, so that the unrolled iterations overlap
-                        if (a.plain_sum) {
-#pragma unroll 4
-                            for (int e = 0; e < nlist; ++e)
-                                dens_pair(acc, xi, yi, zi, h2x4, hinv, true, true, sj[lst[e * 32 + lane]]);
-                        } else {
-#pragma unroll 4
-                            for (int e = 0; e < nlist; ++e)
-                                dens_pair(acc, xi, yi, zi, h2x4, hinv, false, true, sj[lst[e * 32 + lane]]);
-                        }
-                    } else {
-                        // this lane's list overflowed: walk the whole stage
-                        for (int e = 0; e < T; ++e) dens_pair(acc, xi, yi, zi, h2x4, hinv, a.plain_sum, deriv, sj[e]);
-                    }
-                }
-            } else {
-                // the neighbourhood does not fit: stream it through the stage
-                const float hw = warp_max(ok ? hi : 0.0f);
-                const float R2 = 4.0f * hw * hw;
-                const int tot = kLvl ? lvl_table(c, bnd, box, R2, tab, lane) : build_stream(c, cell, box, R2, tab, lane);
+            DAcc acc{0.f, 0.f, 0.f, 0.f};
+            if (ok && !direct) {
+                my_tests += (unsigned long long)nl;
+                list_pass_rt(acc, lr, nl, hinv, a.plain_sum, deriv, uni, lane);
+            }
+            const bool dl = ok && direct;
+            if (__any_sync(FULL, dl)) {
+                // lists that overflow: stream the candidates within reach of
+                // those lanes through the stage, every pass
+                const Box bb = warp_box(dl, xi, yi, zi);
+                const float hw = 2.0f * warp_max(dl ? hi : 0.0f);
+                const float R2 = hw * hw;
+                const int tot = kLvl ? lvl_table(c, bnd, bb, R2, tab, lane) : build_stream(c, cell, bb, R2, tab, lane);
                 Cursor sc{0, 0};
                 do {
-                    const int len = stage_density<kLvl>(c, a.pD, tab, tot, box, R2, sj, c.cap, sc, lane, org);
-                    if (ok) {
+                    const int len = stage_density<kLvl>(c, a.pD, tab, tot, bb, R2, sj, c.cap, sc, lane, org);
+                    if (dl) {
                         my_tests += (unsigned long long)len;
-                        for (int e = 0; e < len; ++e) dens_pair(acc, xi, yi, zi, h2x4, hinv, a.plain_sum, deriv, sj[e]);
+                        for (int e = 0; e < len; ++e)
+                            dens_acc_rt(acc, pair_r(xi, yi, zi, sj[e]), hinv, sj[e].w, a.plain_sum, deriv);
                     }
                     __syncwarp();
                 } while (sc.g < tot);
             }
             if (ok) {
                 const float h3inv = hinv * hinv * hinv;
-                rho = kSigma * h3inv * (acc.s - acc.c);
-                drdh = -kSigma * h3inv * hinv * acc.d;
-                cnt = acc.n - 1;           // the self term is in rho, not in the count
+                const float ms = (uni && !direct) ? mi : 1.0f;    // the lists' common mass
+                rho = kSigma * h3inv * ((acc.s - acc.c) * ms);
+                drdh = -3.0f * kSigma * h3inv * hinv * (acc.d * ms);
+                cnt = (int)acc.n - 1;      // the self term is in rho, not in the count
                 lane_pairs += (unsigned long long)cnt;
                 if (pass + 1 < a.npass) {
                     // Newton step on f(h) = rho(h) - m (eta/h)^3
@@ -718,10 +862,10 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
                     hi = hn;
                 }
             }
-                }
+        }
         if (kLvl && per_target) {
             // The item's box gathers (or, as h grows, comes to gather) more
-            // than the stage holds: coarse-level targets spread over their
+            // candidates than defer_at: coarse-level targets spread over their
             // cell next to a dense cluster, or started from an h far too large
             // for what surrounds them.  Its targets go to the per-target list
             // and are gathered one by one, each by a whole warp, in the
@@ -786,11 +930,9 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density_one(DensityArgs a)
     extern __shared__ __align__(16) unsigned char smem[];
     const Common &c = a.c;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const size_t per_warp = (size_t)c.cap * sizeof(float4) + (size_t)32 * kListSlots * sizeof(uint16_t) + sizeof(Tab) +
-                            kBndBytes;
-    float4 *sj = reinterpret_cast<float4 *>(smem + warp * per_warp);
-    uint16_t *lst = reinterpret_cast<uint16_t *>(sj + c.cap);
-    Tab &tab = *reinterpret_cast<Tab *>(lst + 32 * kListSlots);
+    float4 *sj = reinterpret_cast<float4 *>(smem + warp * density_warp_bytes(c.cap, true));
+    float *lr = reinterpret_cast<float *>(sj + c.cap);
+    Tab &tab = *reinterpret_cast<Tab *>(lr + 32 * kDensSlots);
     int *bnd = reinterpret_cast<int *>(&tab + 1);
     unsigned long long my_pairs = 0, my_tests = 0, my_done = 0, my_prom = 0;
     unsigned my_err = 0;
@@ -832,9 +974,10 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density_one(DensityArgs a)
             const float h2x4 = 4.0f * ht * ht;
             const float hinv = 1.0f / ht;
             const bool deriv = pass + 1 < a.npass;
-            DAcc acc{0.f, 0.f, 0.f, 0};
+            DAcc acc{0.f, 0.f, 0.f, 0.f};
             if (fit_t) {
-                for (int e = lane; e < Tt; e += 32) dens_pair(acc, xt, yt, zt, h2x4, hinv, a.plain_sum, deriv, sj[e]);
+                for (int e = lane; e < Tt; e += 32)
+                    dens_acc_rt(acc, pair_r(xt, yt, zt, sj[e]), hinv, sj[e].w, a.plain_sum, deriv);
                 my_tests += (unsigned long long)max(0, (Tt - lane + 31) >> 5);
             } else {
                 // more than the stage within the target's own reach: stream it
@@ -843,13 +986,13 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density_one(DensityArgs a)
                 do {
                     const int len = stage_density<true, 8>(c, a.pD, tab, tot, pb, h2x4, sj, c.cap, sc, lane, org);
                     for (int e = lane; e < len; e += 32)
-                        dens_pair(acc, xt, yt, zt, h2x4, hinv, a.plain_sum, deriv, sj[e]);
+                        dens_acc_rt(acc, pair_r(xt, yt, zt, sj[e]), hinv, sj[e].w, a.plain_sum, deriv);
                     my_tests += (unsigned long long)max(0, (len - lane + 31) >> 5);
                     __syncwarp();
                 } while (sc.g < tot);
             }
             float sum = acc.s - acc.c, dsum = acc.d;
-            int nn = acc.n;
+            int nn = (int)acc.n;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 sum += __shfl_xor_sync(FULL, sum, o);
@@ -858,7 +1001,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density_one(DensityArgs a)
             }
             const float h3inv = hinv * hinv * hinv;
             rt = kSigma * h3inv * sum;
-            dt = -kSigma * h3inv * hinv * dsum;
+            dt = -3.0f * kSigma * h3inv * hinv * dsum;
             nt = nn - 1;
             pt += (unsigned long long)nt;
             if (pass + 1 < a.npass) {
@@ -1104,7 +1247,7 @@ __device__ int stage_force(const ForceArgs &a, const Tab &tab, int total, const 
 // (P/rho^2, rho, c, slot), the per-lane pair lists and the stencil table
 __host__ __device__ inline size_t force_warp_bytes(int cap)
 {
-    return (size_t)cap * 3 * sizeof(float4) + (size_t)32 * kListSlots * sizeof(uint16_t) + sizeof(Tab);
+    return (size_t)cap * 3 * sizeof(float4) + (size_t)32 * kForceSlots * sizeof(uint16_t) + sizeof(Tab);
 }
 
 template <bool kLvl>
@@ -1117,7 +1260,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_force(ForceArgs a)
     float4 *sB = sA + c.cap;                                                             // vx, vy, vz, m
     float4 *sC = sB + c.cap;                                                             // P/rho^2, rho, c, slot
     uint16_t *lst = reinterpret_cast<uint16_t *>(sC + c.cap);                            // per-lane pair lists
-    Tab &tab = *reinterpret_cast<Tab *>(lst + 32 * kListSlots);
+    Tab &tab = *reinterpret_cast<Tab *>(lst + 32 * kForceSlots);
     unsigned long long my_pairs = 0, my_tests = 0;
     unsigned my_err = 0;
     const int lo = c.range ? c.range[0] : 0;
@@ -1177,13 +1320,13 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_force(ForceArgs a)
             const int len = stage_force<kLvl>(a, tab, total, box, hw, sA, sB, sC, c.cap, cur, lane, my_err, org);
             if (ok) {
                 my_tests += (unsigned long long)len;
-                // phase 1 collects this lane's pairs among up to kLaneCap
+                // phase 1 collects this lane's pairs among up to kForceCap
                 // staged candidates into its list (branch-free appends in
-                // batches: loads first, then the stores; a range of kLaneCap
+                // batches: loads first, then the stores; a range of kForceCap
                 // candidates cannot overflow the list), phase 2 evaluates
                 // them; repeated over the stage
-                for (int s0 = 0; s0 < len; s0 += kLaneCap) {
-                    const int s1 = min(s0 + kLaneCap, len);
+                for (int s0 = 0; s0 < len; s0 += kForceCap) {
+                    const int s1 = min(s0 + kForceCap, len);
                     int nl = 0;
                     constexpr int LB = 8;
                     for (int e0 = s0; e0 < s1; e0 += LB) {
@@ -1198,7 +1341,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_force(ForceArgs a)
                         }
 #pragma unroll
                         for (int u = 0; u < LB; ++u) {
-                            lst[nl * 32 + lane] = (uint16_t)(e0 + u);     // nl <= kLaneCap: slot kLaneCap is scratch
+                            lst[nl * 32 + lane] = (uint16_t)(e0 + u);     // nl <= kForceCap: slot kForceCap is scratch
                             nl += in[u] ? 1 : 0;
                         }
                     }
@@ -1252,7 +1395,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_force_one(ForceArgs a)
     float4 *sB = sA + c.cap;
     float4 *sC = sB + c.cap;
     uint16_t *lst = reinterpret_cast<uint16_t *>(sC + c.cap);
-    Tab &tab = *reinterpret_cast<Tab *>(lst + 32 * kListSlots);
+    Tab &tab = *reinterpret_cast<Tab *>(lst + 32 * kForceSlots);
     unsigned long long my_pairs = 0, my_tests = 0;
     unsigned my_err = 0;
     const unsigned nd = c.st->defer_n;
@@ -1362,10 +1505,9 @@ __global__ void __launch_bounds__(128) k_density_plain(DensityArgs a, const int3
     int cnt = 0;
     unsigned long long tests = 0, pairs = 0;
     for (int pass = 0; pass < a.npass; ++pass) {
-        const float h2x4 = 4.0f * hi * hi;
         const float hinv = 1.0f / hi;
         const bool deriv = pass + 1 < a.npass;
-        DAcc acc{0.f, 0.f, 0.f, 0};
+        DAcc acc{0.f, 0.f, 0.f, 0.f};
         for (int t = 0; t < 27; ++t) {
             float sx, sy, sz;
             stencil_shift(c, t, sx, sy, sz);
@@ -1377,13 +1519,13 @@ __global__ void __launch_bounds__(128) k_density_plain(DensityArgs a, const int3
                                              fmaf(ld_val(c.x.p[1], c.x.fmt, j), c.x.dec, sy),
                                              fmaf(ld_val(c.x.p[2], c.x.fmt, j), c.x.dec, sz),
                                              ld_val(c.m.p[0], c.m.fmt, j) * c.m.dec);
-                dens_pair(acc, xi, yi, zi, h2x4, hinv, a.plain_sum, deriv, q);
+                dens_acc_rt(acc, pair_r(xi, yi, zi, q), hinv, q.w, a.plain_sum, deriv);
             }
         }
         const float h3inv = hinv * hinv * hinv;
         rho = kSigma * h3inv * (acc.s - acc.c);
-        const float drdh = -kSigma * h3inv * hinv * acc.d;
-        cnt = acc.n - 1;
+        const float drdh = -3.0f * kSigma * h3inv * hinv * acc.d;
+        cnt = (int)acc.n - 1;
         pairs += (unsigned long long)cnt;      // every pass's pairs, as the batched kernel counts them
         if (pass + 1 < a.npass) {
             const float f = rho - mi * a.eta3 * h3inv;
@@ -1483,6 +1625,9 @@ Common make_common(sph_ctx *c, int cap)
         m.nc[k] = c->nc[k];
         m.edge[k] = (float)c->edge[k];
     }
+    for (int t = 0; t < 27; ++t)
+        m.shift[t] = make_float4((float)(t % 3 - 1) * m.edge[0], (float)((t / 3) % 3 - 1) * m.edge[1],
+                                 (float)(t / 9 - 1) * m.edge[2], 0.0f);
     m.sub = c->sub;
     m.s3 = c->sub * c->sub * c->sub;
     m.lg_sub = c->sub == 2 ? 1 : 0;
@@ -1514,6 +1659,7 @@ Common make_common(sph_ctx *c, int cap)
     m.m = ref(SPH_F_M);
     m.h = ref(SPH_F_H);
     m.cap = cap;
+    m.defer_cap = 8 * cap;
     return m;
 }
 
@@ -1559,8 +1705,7 @@ cudaError_t launch_persistent(sph_ctx *c, K kernel, const A &args, size_t smem, 
 
 size_t density_smem_bytes(int block_threads, int cap, bool levels)
 {
-    return (size_t)(block_threads / 32) * ((size_t)cap * sizeof(float4) + (size_t)32 * kListSlots * sizeof(uint16_t) +
-                                           sizeof(Tab) + (levels ? kBndBytes : 0));
+    return (size_t)(block_threads / 32) * density_warp_bytes(cap, levels);
 }
 
 size_t force_smem_bytes(int block_threads, int cap)

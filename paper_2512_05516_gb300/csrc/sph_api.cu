@@ -57,7 +57,7 @@ void default_tuning(sph_tuning *t)
     // warps, and the costliest work items go first
     t->block_threads = 32;
     t->ctas_per_sm = 0;
-    t->stage_density = 1024;
+    t->stage_density = 128;
     t->stage_force = 96;
     t->subcells = 2;
     t->item_order = 1;
