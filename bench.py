@@ -850,6 +850,10 @@ def _levels_density(sph, wl, dev, stream, margin, reps, force=True):
                 ms_frc.append(ev[2].elapsed_time(ev[3]))
         st = s.stats()
         done, prom = s.level_counts()
+        fl = s.density_flags()
+        flags = {"newton": int(((fl & sph.PFLAG_NEWTON) != 0).sum().item()),
+                 "hcap": int(((fl & sph.PFLAG_HCAP) != 0).sum().item()),
+                 "nonfinite": int(((fl & sph.PFLAG_NONFINITE) != 0).sum().item())}
     s.close()
     del aos
     torch.cuda.empty_cache()
@@ -859,7 +863,10 @@ def _levels_density(sph, wl, dev, stream, margin, reps, force=True):
             "tests_per_pair": st["tests_density"] / max(st["pairs_density"], 1),
             "particles_per_level": {str(l): done[l] for l in range(lo, hi + 1)},
             "promoted_per_level": {str(l): prom[l] for l in range(lo, hi + 1)},
-            "error_bits": st["error_bits"]}
+            "error_bits": st["error_bits"],
+            # particles whose Newton step met f'(h) <= 0 and kept their h (the
+            # FP64 oracle flags the same ones: tests/test_gpu_levels.py)
+            "particles_flagged": flags}
     if force:
         out.update({"force_ms": statistics.median(ms_frc),
                     "force_pairs_per_s": st["pairs_force"] / (ms_frc[-1] / 1e3),

@@ -161,6 +161,12 @@ typedef struct {
 #define SPH_ERR_OUTSIDE   2      /* a position lay outside [0, box) at binning */
 #define SPH_ERR_HCAP      4      /* some h was clamped at h_max */
 #define SPH_ERR_NEWTON    8      /* a Newton step met a non-positive derivative */
+/* Per-particle flags of a density call (sph_desc.off_density_flags, slot
+ * order): which particles set the error word's HCAP, NEWTON and NONFINITE
+ * bits.  The FP64 oracle reports the same three conditions per particle. */
+#define SPH_PFLAG_HCAP      1    /* h was clamped at its cap */
+#define SPH_PFLAG_NEWTON    2    /* a Newton step met f'(h) <= 0 or a non-finite f: h kept */
+#define SPH_PFLAG_NONFINITE 4    /* the input h or the resulting density was not finite */
 #define SPH_ERR_TIMEOUT   16     /* an asynchronous record copy did not complete within its first
                                     bounded wait; the warp waited once more, longer, and skipped
                                     its records only if the copy had still not landed */
@@ -213,6 +219,8 @@ typedef struct {
     int64_t off_level;           /* int8[n]: level of every slot (sph_bin_levels; -1 without
                                     SPH_WS_LEVELS); after sph_density_levels, the level each
                                     particle's density was computed at */
+    int64_t off_density_flags;   /* uint8[n]: per-slot flags of the last density call,
+                                    SPH_PFLAG_* bits */
 } sph_desc;
 
 typedef struct sph_ctx sph_ctx;

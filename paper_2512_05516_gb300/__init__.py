@@ -14,6 +14,7 @@ import ctypes as C
 
 from . import _capi
 from ._capi import (AOS_F32, AOS_F64, BIT, ERR_HCAP, ERR_NEWTON, ERR_NONFINITE, ERR_OUTSIDE, ERR_TIMEOUT,
+                    PFLAG_HCAP, PFLAG_NEWTON, PFLAG_NONFINITE,
                     F_A, F_CS, F_DUDT, F_H, F_M, F_P, F_RHO, F_U, F_V, F_X, FIELD_NAMES,
                     FIELDS_DENSITY, FIELDS_FORCE, FIELDS_KICK, FIELDS_OUTPUT, FLAG_PLAIN_SUM,
                     NCOMP, P_BF16, P_FP16, P_FP32, P_FP32_M10, P_FP32_M16, PREC, SPH_NFIELDS,
@@ -509,6 +510,11 @@ class Sph:
     def nngb(self, force: bool = False):
         d = self.describe()
         return self._ws_view(d.off_nngb_force if force else d.off_nngb, self.n, self.torch.int32)
+
+    def density_flags(self):
+        """Per-slot flags of the last density call (uint8, PFLAG_* bits)."""
+        d = self.describe()
+        return self._ws_view(d.off_density_flags, self.n, self.torch.uint8)
 
     def soa_raw(self, field: str, comp: int = 0):
         """The stored words of one SoA component (float32, 16-bit codes, or the

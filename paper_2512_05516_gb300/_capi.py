@@ -36,6 +36,7 @@ WS_REORDER = 1
 WS_LEVELS = 2
 LEVEL_MIN, LEVEL_MAX, LEVELS_MAX = 2, 10, 8
 ERR_NONFINITE, ERR_OUTSIDE, ERR_HCAP, ERR_NEWTON, ERR_TIMEOUT = 1, 2, 4, 8, 16
+PFLAG_HCAP, PFLAG_NEWTON, PFLAG_NONFINITE = 1, 2, 4
 SRC_AOS, SRC_SOA = 0, 1
 BUFFER_MIN, BUFFER_MAX = 32, 256
 
@@ -73,7 +74,7 @@ class sph_desc(C.Structure):
                 ("off_cell_start", C.c_int64), ("off_nngb", C.c_int64),
                 ("off_nngb_force", C.c_int64), ("off_soa", (C.c_int64 * 3) * SPH_NFIELDS),
                 ("prec", C.c_int32 * SPH_NFIELDS), ("valid", C.c_uint32), ("subcells", C.c_int32),
-                ("off_level", C.c_int64)]
+                ("off_level", C.c_int64), ("off_density_flags", C.c_int64)]
 
 
 # every symbol the header declares, with its prototype

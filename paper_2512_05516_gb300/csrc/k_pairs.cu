@@ -44,7 +44,7 @@ constexpr int kDensCapPair = 48;                             // density: list en
 constexpr int kDensSlots = 98;                               // words per lane, scratch entry included
 static_assert(kDensCapUni < kDensSlots && 2 * kDensCapPair + 1 < kDensSlots, "density list scratch entry");
 #ifndef SPH_LIST_SKIN
-#define SPH_LIST_SKIN 0.03f
+#define SPH_LIST_SKIN 0.01f
 #endif
 constexpr float kSkin = SPH_LIST_SKIN;                       // list radius = 2 h (1 + skin)
 constexpr float kStageSkin = 0.12f;                          // stage radius = 2 max h (1 + skin)
@@ -99,6 +99,7 @@ struct DensityArgs {
     float rho_enc, h_enc, P_enc, cs_enc;   // storage scales of the outputs
     const float4 *pD;                // every slot's (x, y, z, m) in FP32, from the pack pass
     int32_t *nngb;
+    uint8_t *pflags;                 // per-slot SPH_PFLAG_* of this call
     // level hierarchy: this level, and whether a clamped particle moves up
     int8_t *level;
     int lvl;
@@ -744,6 +745,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
             lvl_bounds(c, cell, bnd, lane);
         }
         bool clamped = false;
+        unsigned lf = 0;           // this particle's SPH_PFLAG_* bits
         float xi = 0.f, yi = 0.f, zi = 0.f, mi = 0.f, hi = 0.f, ui = 0.f;
         if (ok) {
             float4 p = __ldg(a.pD + k);
@@ -754,7 +756,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
             mi = p.w;
             hi = ld_val(c.h.p[0], c.h.fmt, k) * c.h.dec;
             if (a.has_u) ui = ld_val(a.u.p[0], a.u.fmt, k) * a.u.dec;
-            if (!(hi > 0.0f) || !isfinite(hi)) { hi = a.h_cap; my_err |= SPH_ERR_NONFINITE; }
+            if (!(hi > 0.0f) || !isfinite(hi)) { hi = a.h_cap; lf |= SPH_PFLAG_NONFINITE; }
             if (hi > a.h_cap) { hi = a.h_cap; clamped = true; }
         }
 
@@ -856,7 +858,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
                     const float fp = drdh + 3.0f * mi * a.eta3 * h3inv * hinv;
                     float hn = hi;
                     if (fp > 0.0f && isfinite(f) && isfinite(fp)) hn = hi - f / fp;
-                    else my_err |= SPH_ERR_NEWTON;
+                    else lf |= SPH_PFLAG_NEWTON;
                     hn = fminf(fmaxf(hn, 0.5f * hi), 2.0f * hi);
                     if (hn > a.h_cap) { hn = a.h_cap; clamped = true; }
                     hi = hn;
@@ -886,7 +888,11 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
         } else if (ok) {
             my_pairs += lane_pairs;
             if (kLvl) ++my_done;
-            if (!isfinite(rho)) my_err |= SPH_ERR_NONFINITE;
+            if (!isfinite(rho)) lf |= SPH_PFLAG_NONFINITE;
+            if (clamped) lf |= SPH_PFLAG_HCAP;
+            a.pflags[k] = (uint8_t)lf;
+            if (lf & SPH_PFLAG_NONFINITE) my_err |= SPH_ERR_NONFINITE;
+            if (lf & SPH_PFLAG_NEWTON) my_err |= SPH_ERR_NEWTON;
             st_val(a.rho_out, a.rho_fmt, k, rho * a.rho_enc);
             if (a.write_h) st_val(a.h_out, a.h_fmt, k, hi * a.h_enc);
             a.nngb[k] = cnt;
@@ -949,9 +955,10 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density_one(DensityArgs a)
         const float xt = p.x, yt = p.y, zt = p.z, mt = p.w;
         float ht = ld_val(c.h.p[0], c.h.fmt, k) * c.h.dec;
         bool clamped = false;
+        unsigned lf = 0;           // the target's SPH_PFLAG_* bits (the same in every lane)
         if (!(ht > 0.0f) || !isfinite(ht)) {
             ht = a.h_cap;
-            if (lane == 0) my_err |= SPH_ERR_NONFINITE;
+            lf |= SPH_PFLAG_NONFINITE;
         }
         if (ht > a.h_cap) {
             ht = a.h_cap;
@@ -1010,7 +1017,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density_one(DensityArgs a)
                 const float fp = dt + 3.0f * mt * a.eta3 * h3inv * hinv;
                 float hn = ht;
                 if (fp > 0.0f && isfinite(f) && isfinite(fp)) hn = ht - f / fp;
-                else if (lane == 0) my_err |= SPH_ERR_NEWTON;
+                else lf |= SPH_PFLAG_NEWTON;
                 hn = fminf(fmaxf(hn, 0.5f * ht), 2.0f * ht);
                 if (hn > a.h_cap) {
                     hn = a.h_cap;
@@ -1027,7 +1034,11 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density_one(DensityArgs a)
         }
         my_pairs += pt;
         ++my_done;
-        if (!isfinite(rt)) my_err |= SPH_ERR_NONFINITE;
+        if (!isfinite(rt)) lf |= SPH_PFLAG_NONFINITE;
+        if (clamped) lf |= SPH_PFLAG_HCAP;
+        a.pflags[k] = (uint8_t)lf;
+        if (lf & SPH_PFLAG_NONFINITE) my_err |= SPH_ERR_NONFINITE;
+        if (lf & SPH_PFLAG_NEWTON) my_err |= SPH_ERR_NEWTON;
         st_val(a.rho_out, a.rho_fmt, k, rt * a.rho_enc);
         if (a.write_h) st_val(a.h_out, a.h_fmt, k, ht * a.h_enc);
         a.nngb[k] = nt;
@@ -1497,9 +1508,9 @@ __global__ void __launch_bounds__(128) k_density_plain(DensityArgs a, const int3
     const float mi = ld_val(c.m.p[0], c.m.fmt, k) * c.m.dec;
     float hi = ld_val(c.h.p[0], c.h.fmt, k) * c.h.dec;
     const float ui = a.has_u ? ld_val(a.u.p[0], a.u.fmt, k) * a.u.dec : 0.0f;
-    unsigned err = 0;
+    unsigned err = 0, lf = 0;
     bool clamped = false;
-    if (!(hi > 0.0f) || !isfinite(hi)) { hi = a.h_cap; err |= SPH_ERR_NONFINITE; }
+    if (!(hi > 0.0f) || !isfinite(hi)) { hi = a.h_cap; lf |= SPH_PFLAG_NONFINITE; }
     if (hi > a.h_cap) { hi = a.h_cap; clamped = true; }
     float rho = 0.f;
     int cnt = 0;
@@ -1532,13 +1543,17 @@ __global__ void __launch_bounds__(128) k_density_plain(DensityArgs a, const int3
             const float fp = drdh + 3.0f * mi * a.eta3 * h3inv * hinv;
             float hn = hi;
             if (fp > 0.0f && isfinite(f) && isfinite(fp)) hn = hi - f / fp;
-            else err |= SPH_ERR_NEWTON;
+            else lf |= SPH_PFLAG_NEWTON;
             hn = fminf(fmaxf(hn, 0.5f * hi), 2.0f * hi);
             if (hn > a.h_cap) { hn = a.h_cap; clamped = true; }
             hi = hn;
         }
     }
-    if (!isfinite(rho)) err |= SPH_ERR_NONFINITE;
+    if (!isfinite(rho)) lf |= SPH_PFLAG_NONFINITE;
+    if (clamped) lf |= SPH_PFLAG_HCAP;
+    a.pflags[k] = (uint8_t)lf;
+    if (lf & SPH_PFLAG_NONFINITE) err |= SPH_ERR_NONFINITE;
+    if (lf & SPH_PFLAG_NEWTON) err |= SPH_ERR_NEWTON;
     st_val(a.rho_out, a.rho_fmt, k, rho * a.rho_enc);
     if (a.write_h) st_val(a.h_out, a.h_fmt, k, hi * a.h_enc);
     a.nngb[k] = cnt;
@@ -1745,6 +1760,7 @@ DensityArgs density_args(sph_ctx *c, int newton_steps)
     a.P_enc = c->enc(SPH_F_P);
     a.cs_enc = c->enc(SPH_F_CS);
     a.nngb = c->nngb;
+    a.pflags = c->dflags;
     a.level = nullptr;
     a.lvl = 0;
     a.promote = false;

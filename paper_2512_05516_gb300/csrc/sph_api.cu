@@ -107,6 +107,7 @@ bool make_plan(const sph_aos_layout &L, int64_t n, int64_t ncell_max, uint32_t w
     p->class_hist = take(4 * 3 * (kItemClasses + 1));
     p->nngb = take(4 * N);
     p->nngb_force = take(4 * N);
+    p->dflags = take(N);
     p->stage = take(4 * N);
     p->key_hmax = take(4 * (size_t)nkeys);
     p->origin = take(sizeof(double) * 3 * kMaxCellsPerAxis);
@@ -207,6 +208,7 @@ sph_status sph_create(const sph_aos_layout *layout, const sph_params *params, in
     c->class_hist = (int32_t *)(w + plan.class_hist);
     c->nngb = (int32_t *)(w + plan.nngb);
     c->nngb_force = (int32_t *)(w + plan.nngb_force);
+    c->dflags = (uint8_t *)(w + plan.dflags);
     c->stage = (float *)(w + plan.stage);
     c->key_hmax = (float *)(w + plan.key_hmax);
     c->origin = (double *)(w + plan.origin);
@@ -695,6 +697,7 @@ sph_status sph_describe(const sph_ctx *c, sph_desc *out)
     out->valid = c->valid;
     out->subcells = c->sub;
     out->off_level = rel(c->level);
+    out->off_density_flags = rel(c->dflags);
     return SPH_OK;
 }
 

@@ -82,7 +82,7 @@ struct Plan {
     size_t keys[2], vals[2];
     size_t cell_count, cell_start, scan_part, ghist;
     size_t item_cell, item_first, item_count, item_tmp, item_sorted, item_class, class_hist;
-    size_t nngb, nngb_force, stage, aos_tmp, stats, key_hmax, origin, pack, buf_origin;
+    size_t nngb, nngb_force, dflags, stage, aos_tmp, stats, key_hmax, origin, pack, buf_origin;
     size_t level, level_tmp, tlist, tcode, tscan, iscan, lstart;   // level hierarchy (SPH_WS_LEVELS)
     size_t soa[SPH_NFIELDS][3];
     size_t total;
@@ -340,6 +340,7 @@ struct sph_ctx {
     int32_t *class_hist = nullptr;    // per class: count, start (kItemClasses + 1), cursor
     bool items_by_class = false;      // the last binning grouped the items by cost class
     int32_t *nngb = nullptr, *nngb_force = nullptr;
+    uint8_t *dflags = nullptr;    // per-slot flags of the last density call (SPH_PFLAG_*)
     float *stage = nullptr;
     float *key_hmax = nullptr;    // largest h of every sub-cell (force pruning)
     double *origin = nullptr;     // cell origins k * (L_d / nc_d), kMaxCellsPerAxis per axis

@@ -336,3 +336,44 @@ def test_level_density_without_newton_clamps_h_for_the_force(orc):
     na = np.linalg.norm(f["a"], axis=1)
     err_a = np.linalg.norm(out[t, 6:9] - f["a"], axis=1)
     assert np.all(err_a <= 1e-5 * (na + na.mean())), (err_a / (na + na.mean())).max()
+
+
+def test_level_density_16777216_newton_flags_sampled(orc):
+    # The full-size clustered set as bench.py runs it (levels from the set,
+    # margin 0.1, 5 Newton steps, FP32 storage).  A Newton step that meets
+    # f'(h) <= 0 keeps h (R5) and flags the particle; the per-particle flags
+    # show which.  Targets: every flagged particle (a random 3,000 of them if
+    # there are more) and 300 others; the FP64 oracle with the single cap
+    # must flag the same ones and give the same h and rho within 1e-5.
+    wl = sph_inputs.gaussian_mixture_adaptive(16_777_216)
+    lo, hi = wl.meta["levels"]
+    s = make_sph(wl, ws_flags=sph_mod.WS_LEVELS)
+    s.bin_levels(lo, hi, 0.1)
+    s.aos_to_soa(sph_mod.FIELDS_DENSITY)
+    s.density_levels(5)
+    s.soa_to_aos(sph_mod.mask("rho", "h"))
+    perm = s.perm().cpu().numpy()
+    fl = np.empty(wl.n, np.uint8)
+    fl[perm] = s.density_flags().cpu().numpy()
+    out = s.aos.cpu().numpy()
+    st = s.stats()
+    done, prom = s.level_counts()
+    s.close()
+    assert sum(done) == wl.n
+    assert st["error_bits"] & (sph_mod.ERR_NONFINITE | sph_mod.ERR_OUTSIDE) == 0
+    newt = np.flatnonzero(fl & sph_mod.PFLAG_NEWTON)
+    # the error word's NEWTON bit is exactly the union of the per-particle flags
+    assert bool(st["error_bits"] & sph_mod.ERR_NEWTON) == (newt.size > 0)
+    assert np.all((fl & sph_mod.PFLAG_NONFINITE) == 0)
+    rng = np.random.default_rng(17)
+    pick = newt if newt.size <= 3000 else rng.choice(newt, 3000, replace=False)
+    others = rng.choice(np.flatnonzero((fl & sph_mod.PFLAG_NEWTON) == 0), 300, replace=False)
+    t = np.unique(np.concatenate([pick, others]))
+    o = orc.density(wl.col("x"), wl.col("m"), wl.col("h"), wl.box, wl.eta, wl.h_cap, 5, targets=t)
+    assert (np.abs(out[t, 10] - o["h"]) / o["h"]).max() <= 1e-5
+    assert (np.abs(out[t, 11] - o["rho"]) / o["rho"]).max() <= 1e-5
+    g_new = (fl[t] & sph_mod.PFLAG_NEWTON) != 0
+    o_new = (o["flags"] & orc.FLAG_NEWTON) != 0
+    # the sign of f' is decided in FP32 on the GPU and in FP64 in the oracle:
+    # only particles with f' within rounding of 0 may differ
+    assert np.count_nonzero(g_new != o_new) <= max(2, t.size // 1000)
