@@ -54,8 +54,10 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x)
     s = t;
 }
 
-// One interacting force pair (r2 > 0, j != i): separation d = x_i - x_j,
-// hs = h_i + h_j, qb = (v_j, m_j), qc = (P_j / rho_j^2, rho_j, c_j, -).
+// One interacting force pair: separation d = x_i - x_j, hs = h_i + h_j,
+// qb = (v_j, m_j), qc = (P_j / rho_j^2, rho_j, c_j, -).  A pair at r = 0 (the
+// particle itself, or a coincident one) adds exactly zero: w'(0) = 0 and
+// v_ij . d = 0.
 __device__ __forceinline__ void force_pair(float &ax, float &ay, float &az, float &du, float vxi, float vyi,
                                            float vzi, float rhoi, float Pr2i, float ci, float dx, float dy,
                                            float dz, float r2, float hs, const float4 qb, const float4 qc,

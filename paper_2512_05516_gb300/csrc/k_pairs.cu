@@ -135,7 +135,11 @@ struct __align__(16) Tab {
 // Each warp's shared-memory region is stage | lists | table; the next warp's
 // float4 stage starts right after, so every part keeps 16-byte multiples.
 static_assert(sizeof(Tab) % 16 == 0, "stencil table size must keep 16-byte alignment");
-static_assert((32 * kForceSlots * sizeof(uint16_t)) % 16 == 0, "list size must keep 16-byte alignment");
+static_assert((32 * kForceSlots * sizeof(uint8_t)) % 16 == 0, "list size must keep 16-byte alignment");
+static_assert(kForceCap <= 256, "force list entries are byte offsets into a range of kForceCap candidates");
+// staged force candidates are followed by kForcePad far-away entries, so the
+// pair tests run whole batches of 8 without bounds checks
+constexpr int kForcePad = 8;
 static_assert((32 * kDensSlots * sizeof(float)) % 16 == 0, "list size must keep 16-byte alignment");
 // level force: an item whose candidate stream is longer than this is
 // gathered target by target (k_force_one)
@@ -1258,7 +1262,7 @@ __device__ int stage_force(const ForceArgs &a, const Tab &tab, int total, const 
 // (P/rho^2, rho, c, slot), the per-lane pair lists and the stencil table
 __host__ __device__ inline size_t force_warp_bytes(int cap)
 {
-    return (size_t)cap * 3 * sizeof(float4) + (size_t)32 * kForceSlots * sizeof(uint16_t) + sizeof(Tab);
+    return (size_t)(cap + kForcePad) * 3 * sizeof(float4) + (size_t)32 * kForceSlots * sizeof(uint8_t) + sizeof(Tab);
 }
 
 template <bool kLvl>
@@ -1268,9 +1272,9 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_force(ForceArgs a)
     const Common &c = a.c;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float4 *sA = reinterpret_cast<float4 *>(smem + warp * force_warp_bytes(c.cap));   // x, y, z, h
-    float4 *sB = sA + c.cap;                                                             // vx, vy, vz, m
-    float4 *sC = sB + c.cap;                                                             // P/rho^2, rho, c, slot
-    uint16_t *lst = reinterpret_cast<uint16_t *>(sC + c.cap);                            // per-lane pair lists
+    float4 *sB = sA + c.cap + kForcePad;                                                 // vx, vy, vz, m
+    float4 *sC = sB + c.cap + kForcePad;                                                 // P/rho^2, rho, c, slot
+    uint8_t *lst = reinterpret_cast<uint8_t *>(sC + c.cap + kForcePad);                  // per-lane pair lists
     Tab &tab = *reinterpret_cast<Tab *>(lst + 32 * kForceSlots);
     unsigned long long my_pairs = 0, my_tests = 0;
     unsigned my_err = 0;
@@ -1329,46 +1333,51 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_force(ForceArgs a)
         Cursor cur{0, 0};
         do {
             const int len = stage_force<kLvl>(a, tab, total, box, hw, sA, sB, sC, c.cap, cur, lane, my_err, org);
+            if (lane < kForcePad) sA[len + lane] = make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.0f);   // far away
+            __syncwarp();
             if (ok) {
                 my_tests += (unsigned long long)len;
                 // phase 1 collects this lane's pairs among up to kForceCap
                 // staged candidates into its list (branch-free appends in
-                // batches: loads first, then the stores; a range of kForceCap
-                // candidates cannot overflow the list), phase 2 evaluates
-                // them; repeated over the stage
+                // batches of 8: loads first, then the stores; the far-away
+                // entries after the stage fail every test; a range of
+                // kForceCap candidates cannot overflow the list), phase 2
+                // evaluates them; repeated over the stage
                 for (int s0 = 0; s0 < len; s0 += kForceCap) {
                     const int s1 = min(s0 + kForceCap, len);
                     int nl = 0;
                     constexpr int LB = 8;
+                    static_assert(kForceCap % LB == 0 && LB <= kForcePad, "force test batches");
                     for (int e0 = s0; e0 < s1; e0 += LB) {
                         bool in[LB];
 #pragma unroll
                         for (int u = 0; u < LB; ++u) {
-                            const float4 q = sA[min(e0 + u, s1 - 1)];
+                            const float4 q = sA[e0 + u];
                             const float dx = xi - q.x, dy = yi - q.y, dz = zi - q.z;
                             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                             const float hs = hi + q.w;
-                            in[u] = e0 + u < s1 && r2 < hs * hs;
+                            in[u] = r2 < hs * hs;
                         }
 #pragma unroll
                         for (int u = 0; u < LB; ++u) {
-                            lst[nl * 32 + lane] = (uint16_t)(e0 + u);     // nl <= kForceCap: slot kForceCap is scratch
+                            lst[nl * 32 + lane] = (uint8_t)(e0 + u - s0); // nl <= kForceCap: slot kForceCap is scratch
                             nl += in[u] ? 1 : 0;
                         }
                     }
+                    // every listed pair is evaluated: the self pair and
+                    // coincident pairs (r = 0) contribute exactly zero (the
+                    // spline derivative vanishes at q = 0 and v_ij . d = 0), so
+                    // only the count excludes the particle itself
 #pragma unroll 2
                     for (int l = 0; l < nl; ++l) {
-                        const int p = lst[l * 32 + lane];
+                        const int p = s0 + lst[l * 32 + lane];
                         const float4 qc = sC[p];
-                        if (__float_as_int(qc.w) != k) {
-                            const float4 q = sA[p];
-                            const float dx = xi - q.x, dy = yi - q.y, dz = zi - q.z;
-                            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                            ++cnt;
-                            if (r2 > 0.0f)
-                                force_pair(ax, ay, az, du, vxi, vyi, vzi, rhoi, Pr2i, ci, dx, dy, dz, r2,
-                                           hi + q.w, sB[p], qc, a.alpha, a.beta, a.eps);
-                        }
+                        const float4 q = sA[p];
+                        const float dx = xi - q.x, dy = yi - q.y, dz = zi - q.z;
+                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        cnt += __float_as_int(qc.w) != k ? 1 : 0;
+                        force_pair(ax, ay, az, du, vxi, vyi, vzi, rhoi, Pr2i, ci, dx, dy, dz, r2, hi + q.w, sB[p], qc,
+                                   a.alpha, a.beta, a.eps);
                     }
                 }
             }
@@ -1403,9 +1412,9 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_force_one(ForceArgs a)
     const Common &c = a.c;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float4 *sA = reinterpret_cast<float4 *>(smem + warp * force_warp_bytes(c.cap));
-    float4 *sB = sA + c.cap;
-    float4 *sC = sB + c.cap;
-    uint16_t *lst = reinterpret_cast<uint16_t *>(sC + c.cap);
+    float4 *sB = sA + c.cap + kForcePad;
+    float4 *sC = sB + c.cap + kForcePad;
+    uint8_t *lst = reinterpret_cast<uint8_t *>(sC + c.cap + kForcePad);
     Tab &tab = *reinterpret_cast<Tab *>(lst + 32 * kForceSlots);
     unsigned long long my_pairs = 0, my_tests = 0;
     unsigned my_err = 0;
