@@ -39,16 +39,19 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kForceCap = 96;                                // force: per-lane pair list entries
 constexpr int kForceSlots = kForceCap + 1;                   // plus one scratch slot per lane
-constexpr int kDensCapUni = 96;                              // density: list entries r
-constexpr int kDensCapPair = 48;                             // density: list entries (r, m)
-constexpr int kDensSlots = 98;                               // words per lane, scratch entry included
+#ifndef SPH_DENS_CAP
+#define SPH_DENS_CAP 96
+#endif
+constexpr int kDensCapUni = SPH_DENS_CAP;                    // density: list entries r
+constexpr int kDensCapPair = SPH_DENS_CAP / 2;               // density: list entries (r, m)
+constexpr int kDensSlots = SPH_DENS_CAP + 2;                 // words per lane, scratch entry included
 static_assert(kDensCapUni < kDensSlots && 2 * kDensCapPair + 1 < kDensSlots, "density list scratch entry");
 #ifndef SPH_LIST_SKIN
 #define SPH_LIST_SKIN 0.01f
 #endif
 constexpr float kSkin = SPH_LIST_SKIN;                       // list radius = 2 h (1 + skin)
 constexpr float kStageSkin = 0.12f;                          // stage radius = 2 max h (1 + skin)
-constexpr float kSkinTight = 0.02f;                          // list skin of a lane whose list overflowed
+constexpr float kSkinTight = 0.0f;                           // list skin of a lane whose list overflowed
 constexpr int kMaxEnt = 27 * kMaxSub * kMaxSub * kMaxSub;    // stencil sub-cells
 constexpr int kEntPerLane = (kMaxEnt + 31) / 32;
 constexpr int kStageUnroll = 4;                              // 32-candidate batches in flight
