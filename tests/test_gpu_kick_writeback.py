@@ -95,3 +95,32 @@ def test_fused_leaves_soa_v_u_stale_and_rejects_x():
     with pytest.raises(sph_mod.SphError):
         s.soa_to_aos(sph_mod.mask("v"))
     s.close()
+
+
+def test_fused_equals_separate_many_batches_per_warp():
+    # the memory-bound long-run lattice at 1/8 of its size (4,194,304
+    # particles), cell-ordered records as the long run keeps them: the fused
+    # kernel's persistent warps take ~36 record blocks each, reusing their two
+    # block buffers and barriers, and must still give the separate calls'
+    # bytes with no copy timing out
+    wl = sph_inputs.long_run(nx=256, ny=128, nz=128)
+    prec = {"x": "fp16", "v": "fp16", "m": "fp16", "h": "fp16", "u": "fp16"}
+    out_fields = sph_mod.mask("v", "a", "h", "rho", "u", "P")
+    results = []
+    for fused in (False, True):
+        s = make_sph(wl, ws_flags=sph_mod.WS_REORDER)
+        s.bin_cells(wl.cell_edge, reorder=True)
+        s.aos_to_soa(sph_mod.FIELDS_FORCE, prec)
+        s.density(0)
+        s.force()
+        dt = 1e-4
+        if fused:
+            s.kick_drift_writeback(dt, dt, out_fields)
+        else:
+            s.kick_drift(dt, dt)
+            s.soa_to_aos(out_fields)
+        torch.cuda.synchronize()
+        assert s.stats()["error_bits"] == 0
+        results.append(s.aos.cpu().numpy().view(np.uint8).copy())
+        s.close()
+    assert np.array_equal(results[0], results[1])
