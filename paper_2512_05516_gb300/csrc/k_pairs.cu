@@ -944,8 +944,9 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density_one(DensityArgs a)
     const Common &c = a.c;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float4 *sj = reinterpret_cast<float4 *>(smem + warp * density_warp_bytes(c.cap, true));
-    float *lr = reinterpret_cast<float *>(sj + c.cap);
-    Tab &tab = *reinterpret_cast<Tab *>(lr + 32 * kDensSlots);
+    // no per-lane lists here: the stage extends over their space
+    const int cap1 = c.cap + 32 * kDensSlots * (int)sizeof(float) / (int)sizeof(float4);
+    Tab &tab = *reinterpret_cast<Tab *>(sj + cap1);
     int *bnd = reinterpret_cast<int *>(&tab + 1);
     unsigned long long my_pairs = 0, my_tests = 0, my_done = 0, my_prom = 0;
     unsigned my_err = 0;
@@ -982,7 +983,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density_one(DensityArgs a)
                 const float R2p = 4.0f * hs * hs;
                 const int tot = lvl_table(c, bnd, pb, R2p, tab, lane);
                 Cursor pc{0, 0};
-                Tt = stage_density<true, 8>(c, a.pD, tab, tot, pb, R2p, sj, c.cap, pc, lane, org);
+                Tt = stage_density<true, 8>(c, a.pD, tab, tot, pb, R2p, sj, cap1, pc, lane, org);
                 fit_t = pc.g >= tot;
             }
             const float h2x4 = 4.0f * ht * ht;
@@ -998,7 +999,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density_one(DensityArgs a)
                 const int tot = lvl_table(c, bnd, pb, h2x4, tab, lane);
                 Cursor sc{0, 0};
                 do {
-                    const int len = stage_density<true, 8>(c, a.pD, tab, tot, pb, h2x4, sj, c.cap, sc, lane, org);
+                    const int len = stage_density<true, 8>(c, a.pD, tab, tot, pb, h2x4, sj, cap1, sc, lane, org);
                     for (int e = lane; e < len; e += 32)
                         dens_acc_rt(acc, pair_r(xt, yt, zt, sj[e]), hinv, sj[e].w, a.plain_sum, deriv);
                     my_tests += (unsigned long long)max(0, (len - lane + 31) >> 5);
