@@ -826,6 +826,13 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
                         }
                         if (retry && nl > lcap) direct = true;
                     }
+                    // level mode: a lane that would stream every pass (its
+                    // frames cost a Morton decode per candidate) sends the
+                    // item to the per-target pass instead
+                    if (kLvl && __any_sync(FULL, direct)) {
+                        per_target = true;
+                        break;
+                    }
                 }
             }
             DAcc acc{0.f, 0.f, 0.f, 0.f};

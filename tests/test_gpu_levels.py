@@ -123,10 +123,12 @@ def test_level_density_reduced_storage(orc):
 
 def test_one_level_equals_the_single_grid():
     # levels l..l over 2^l cells per axis and sph_density over the same
-    # cells (one sub-cell): identical candidates, order and frames.  The
-    # stage holds every item's neighbourhood, so both kernels take their list
-    # path (a level item that does not fit is gathered target by target, a
-    # cell item is streamed: the same pairs, summed in another order).
+    # cells (one sub-cell): identical candidates, order and frames, so every
+    # particle whose list holds its neighbourhood gets the same bits from
+    # both kernels.  A particle whose list overflows (a sparse one whose h
+    # overshoots in a Newton step) is summed from the stream by the cell
+    # kernel and gathered target by target by the level kernel: the same
+    # pairs in another order, equal to rounding.
     wl = sph_inputs.uniform_density(131_072, seed=sph_inputs.SEED_BASE + 21)
     h = float(wl.col("h").max())
     l = int(np.floor(np.log2(1.0 / (4.0 * h))))
@@ -146,14 +148,19 @@ def test_one_level_equals_the_single_grid():
     b.density(4)
     b.soa_to_aos(sph_mod.mask("rho", "h", "P"))
     ra, rb = a.aos.cpu().numpy(), b.aos.cpu().numpy()
+    same = np.ones(wl.n, bool)
     for col in (10, 11, 13):
-        assert np.array_equal(ra[:, col], rb[:, col]), col
+        same &= ra[:, col] == rb[:, col]
+        assert np.all(np.abs(ra[:, col] - rb[:, col]) <= 1e-6 * np.abs(rb[:, col])), col
+    assert same.mean() >= 0.995, same.mean()
     pa = np.empty(wl.n, np.int32)
     pa[a.perm().cpu().numpy()] = a.nngb().cpu().numpy()
     pb = np.empty(wl.n, np.int32)
     pb[b.perm().cpu().numpy()] = b.nngb().cpu().numpy()
-    assert np.array_equal(pa, pb)
-    assert a.stats()["pairs_density"] == b.stats()["pairs_density"]
+    assert np.array_equal(pa[same], pb[same])
+    assert np.abs(pa - pb).max() <= 1
+    ta, tb = a.stats()["pairs_density"], b.stats()["pairs_density"]
+    assert abs(ta - tb) <= 1e-4 * tb
     a.close()
     b.close()
 
