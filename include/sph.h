@@ -173,7 +173,7 @@ typedef struct {
 
 /* Launch shapes of the pair kernels (an autotuner sets them; the defaults
  * after sph_create are block_threads 32, ctas_per_sm 0, stage_density 128,
- * stage_force 160, subcells 2, item_order 1, class_launches 0, pair_kernel 0). */
+ * stage_force 128, subcells 2, item_order 1, class_launches 0, pair_kernel 0). */
 typedef struct {
     int32_t block_threads;       /* threads per CTA of the pair kernels (32..256, multiple of 32); one warp per work item */
     int32_t ctas_per_sm;         /* persistent CTAs per SM (0: occupancy maximum) */

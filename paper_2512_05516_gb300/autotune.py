@@ -30,7 +30,7 @@ SPACE = {
     "item_order": (0, 1),
     "block_threads": (32, 64, 128),
     "stage_density": (64, 128, 256, 512),
-    "stage_force": (96, 128, 160, 192, 256),
+    "stage_force": (96, 128, 160, 192),
 }
 
 

@@ -37,7 +37,10 @@ cudaError_t run_pack(sph_ctx *c, const float *src, int f);
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int kForceCap = 96;                                // force: per-lane pair list entries
+#ifndef SPH_FORCE_CAP
+#define SPH_FORCE_CAP 128
+#endif
+constexpr int kForceCap = SPH_FORCE_CAP;                     // force: per-lane pair list entries
 constexpr int kForceSlots = kForceCap + 1;                   // plus one scratch slot per lane
 #ifndef SPH_DENS_CAP
 #define SPH_DENS_CAP 96

@@ -58,7 +58,7 @@ void default_tuning(sph_tuning *t)
     t->block_threads = 32;
     t->ctas_per_sm = 0;
     t->stage_density = 128;
-    t->stage_force = 160;
+    t->stage_force = 128;
     t->subcells = 2;
     t->item_order = 1;
     t->class_launches = 0;
