@@ -173,9 +173,12 @@ typedef struct {
 
 /* Launch shapes of the pair kernels (an autotuner sets them; the defaults
  * after sph_create are block_threads 32, ctas_per_sm 0, stage_density 128,
- * stage_force 128, subcells 2, item_order 1, class_launches 0, pair_kernel 0). */
+ * stage_force 128, subcells 2, item_order 1, class_launches 0, pair_kernel 0,
+ * block_threads_force 32). */
 typedef struct {
-    int32_t block_threads;       /* threads per CTA of the pair kernels (32..256, multiple of 32); one warp per work item */
+    int32_t block_threads;       /* threads per CTA of the density kernels (32..256, multiple of 32), one
+                                    warp per work item; sph_set_tuning also gives it to the force
+                                    kernels unless block_threads_force is set */
     int32_t ctas_per_sm;         /* persistent CTAs per SM (0: occupancy maximum) */
     int32_t stage_density;       /* density kernel: candidates staged per warp in one round of the
                                     stream that fills the per-lane lists (>= 32); in level mode
@@ -198,6 +201,9 @@ typedef struct {
                                     kernels, 0 stages each buffer in shared memory and
                                     1 reads every partner from global memory (the
                                     paper's kernel structure); -1 keeps the current */
+    int32_t block_threads_force; /* threads per CTA of the force kernels (32..256, multiple of 32);
+                                    0 in sph_set_tuning: block_threads if that is set, else
+                                    the current */
 } sph_tuning;
 
 /* Where the library's arrays live inside the workspace (byte offsets from the

@@ -464,9 +464,9 @@ class Sph:
         _check(sph_reset_stats(self.ctx), "sph_reset_stats")
 
     def set_tuning(self, block_threads=0, ctas_per_sm=0, stage_density=0, stage_force=0,
-                   subcells=0, item_order=-1, class_launches=-1, pair_kernel=-1):
+                   subcells=0, item_order=-1, class_launches=-1, pair_kernel=-1, block_threads_force=0):
         t = sph_tuning(block_threads, ctas_per_sm, stage_density, stage_force, subcells,
-                       item_order, class_launches, pair_kernel)
+                       item_order, class_launches, pair_kernel, block_threads_force)
         _check(sph_set_tuning(self.ctx, t), "sph_set_tuning")
 
     def tuning(self) -> dict:
@@ -475,7 +475,8 @@ class Sph:
         return {"block_threads": t.block_threads, "ctas_per_sm": t.ctas_per_sm,
                 "stage_density": t.stage_density, "stage_force": t.stage_force,
                 "subcells": t.subcells, "item_order": t.item_order,
-                "class_launches": t.class_launches, "pair_kernel": t.pair_kernel}
+                "class_launches": t.class_launches, "pair_kernel": t.pair_kernel,
+                "block_threads_force": t.block_threads_force}
 
     def describe(self) -> sph_desc:
         st, d = sph_describe(self.ctx)

@@ -65,7 +65,8 @@ class sph_stats(C.Structure):
 class sph_tuning(C.Structure):
     _fields_ = [("block_threads", C.c_int32), ("ctas_per_sm", C.c_int32),
                 ("stage_density", C.c_int32), ("stage_force", C.c_int32), ("subcells", C.c_int32),
-                ("item_order", C.c_int32), ("class_launches", C.c_int32), ("pair_kernel", C.c_int32)]
+                ("item_order", C.c_int32), ("class_launches", C.c_int32), ("pair_kernel", C.c_int32),
+                ("block_threads_force", C.c_int32)]
 
 
 class sph_desc(C.Structure):

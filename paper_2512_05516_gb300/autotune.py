@@ -11,9 +11,9 @@ the fastest shape:
 
   1. the binning choices (sub-cells per cell edge, queue order), each timed
      as density + force at the current launch shapes;
-  2. with those fixed, the block size and stage sizes, density and force
-     measured separately; the block size is shared, so the one with the
-     smallest density + force time wins.
+  2. with those fixed, the block size and stage size of each kernel,
+     density and force measured separately (each kernel launches with its
+     own block size).
 
 Results are cached in a JSON file keyed by the device and a signature of the
 workload (particle count, cell grid, occupancy, storage formats, Newton
@@ -135,8 +135,9 @@ def tune(s, cell_edge: float, prec: dict | None = None, newton_steps: int = 5, r
         s.set_tuning(subcells=best_bin[0], item_order=best_bin[1], class_launches=0)
         prepare()
 
-        # 2. block size and stages, per kernel
-        dens, forc = {}, {}
+        # 2. block size and stage, per kernel (each kernel takes its own
+        # block size)
+        dens, forc = None, None
         for bt in SPACE["block_threads"]:
             for sd in SPACE["stage_density"]:
                 try:
@@ -145,22 +146,21 @@ def tune(s, cell_edge: float, prec: dict | None = None, newton_steps: int = 5, r
                     continue                         # does not fit in shared memory
                 t = measure("density")
                 trials.append({"block_threads": bt, "stage_density": sd, "density_ms": t})
-                if t < dens.get(bt, (float("inf"), 0))[0]:
-                    dens[bt] = (t, sd)
+                if dens is None or t < dens[0]:
+                    dens = (t, bt, sd)
+        for bt in SPACE["block_threads"]:
             for sf in SPACE["stage_force"]:
                 try:
-                    s.set_tuning(block_threads=bt, stage_force=sf)
+                    s.set_tuning(block_threads_force=bt, stage_force=sf)
                 except SphError:
                     continue
                 t = measure("force")
-                trials.append({"block_threads": bt, "stage_force": sf, "force_ms": t})
-                if t < forc.get(bt, (float("inf"), 0))[0]:
-                    forc[bt] = (t, sf)
-        blocks = [bt for bt in SPACE["block_threads"] if bt in dens and bt in forc]
-        bt = min(blocks, key=lambda b: dens[b][0] + forc[b][0])
-        best = {"block_threads": bt, "stage_density": dens[bt][1], "stage_force": forc[bt][1],
-                "subcells": best_bin[0], "item_order": best_bin[1], "class_launches": 0}
-        ms = {"density": dens[bt][0], "force": forc[bt][0]}
+                trials.append({"block_threads_force": bt, "stage_force": sf, "force_ms": t})
+                if forc is None or t < forc[0]:
+                    forc = (t, bt, sf)
+        best = {"block_threads": dens[1], "stage_density": dens[2], "block_threads_force": forc[1],
+                "stage_force": forc[2], "subcells": best_bin[0], "item_order": best_bin[1], "class_launches": 0}
+        ms = {"density": dens[0], "force": forc[0]}
         s.set_tuning(**best)
         prepare()
     if use_cache:

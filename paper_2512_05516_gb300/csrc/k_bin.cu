@@ -1,8 +1,10 @@
 // S1 cell binning: FP64 cell index per particle, cell histogram, exclusive
-// scan, and a stable LSD radix sort of (cell id, particle index) pairs, so
-// that particles end up cell by cell in ascending original index.  Also
-// builds the pair-kernel work items (cell, first slot, count) and optionally
-// rewrites the AoS records in cell order.
+// scan, then the particles placed cell by cell in ascending original index
+// (the result of a stable sort by cell): on the uniform grid by counting
+// placement and an ordering pass over each cell's range, for the level
+// hierarchy and the allocation-free entry point by a stable LSD radix sort of
+// (key, particle index) pairs.  Also builds the pair-kernel work items (cell,
+// first slot, count) and optionally rewrites the AoS records in cell order.
 #include "sph_internal.cuh"
 
 namespace sph {
@@ -16,6 +18,7 @@ struct CellArgs {
     int64_t n;
     int32_t stride, xoff;
     double inv[3], box[3];
+    float invh[3], invl[3];      // inv as an FP32 pair: inv = invh + invl to a relative 2^-48
     int32_t nc[3];
     int32_t sub;                 // sub-cells per cell edge
     int32_t *keys, *vals, *count;
@@ -32,6 +35,46 @@ __device__ __forceinline__ int32_t cell_coord(double x, double inv, int32_t nc)
     return min(max(f, 0), nc - 1);
 }
 
+// cell_coord's result computed on the FP32 pipe for almost every particle
+// (the FP64 pipe of this GPU runs at a small fraction of the FP32 rate).  x is
+// split from its bits into FP32 parts, x = hi + lo up to a relative 2^-47
+// (hi: the leading 24 significant bits, lo: the other 29 rounded to 24), and
+// the product x * inv is formed as the unevaluated FP32 pair p + t, where
+// p + fma(hi, ih, -p) = hi * ih exactly; the pair is within 2^-44 of the
+// exact product, relatively, so within 2^-31 absolutely below 8192.  The
+// floor of the pair then equals the floor of the rounded FP64 product unless
+// the pair's fractional part lies within 2^-20 of 0 or 1, and those
+// particles (on or next to a face), like x outside [2^-74, 2^100), negative
+// or not finite, take the FP64 product.
+__device__ __forceinline__ int32_t cell_coord_fast(double x, float ih, float il, double inv, int32_t nc)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    if (b == 0ull) return 0;                                // +0
+    const int e = (int)(b >> 52);                          // biased exponent (sign bit set: >= 2048)
+    bool exact = e < 949 || e >= 1123;
+    int32_t f = 0;
+    if (!exact) {
+        const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+        const float hi = __int_as_float(((e - 896) << 23) | (int)(m >> 29));
+        const float lo = __uint2float_rn((unsigned)(m & 0x1FFFFFFFu)) * __int_as_float((e - 948) << 23);
+        const float p = hi * ih;
+        const float t = fmaf(hi, ih, -p) + fmaf(hi, il, lo * ih);
+        float fl = floorf(p);
+        float d = (p - fl) + t;
+        if (d < 0.0f) {
+            fl -= 1.0f;
+            d += 1.0f;
+        } else if (d >= 1.0f) {
+            fl += 1.0f;
+            d -= 1.0f;
+        }
+        exact = d < 0x1p-20f || d > 1.0f - 0x1p-20f;
+        f = min(max(__float2int_rz(fl), 0), nc - 1);
+    }
+    if (exact) f = cell_coord(x, inv, nc);
+    return f;
+}
+
 // x in [0, L) compared on bit patterns (FP64 compares are slow on this GPU):
 // non-negative doubles order like their bits; -0 counts as inside
 __device__ __forceinline__ bool in_box(double x, double L)
@@ -42,23 +85,196 @@ __device__ __forceinline__ bool in_box(double x, double L)
 
 __global__ void k_cell_ids(CellArgs a)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
-    const double *x = (const double *)(a.aos + i * a.stride + a.xoff);
-    double x0 = x[0], x1 = x[1], x2 = x[2];
-    const bool outside = !(in_box(x0, a.box[0]) && in_box(x1, a.box[1]) && in_box(x2, a.box[2]));
-    if (outside) set_error(a.st, SPH_ERR_OUTSIDE | ((isfinite(x0) && isfinite(x1) && isfinite(x2)) ? 0u : SPH_ERR_NONFINITE));
-    // fine coordinates on the grid of sub-cells (inv = sub * nc / L); the cell
-    // is f / sub, the sub-cell f % sub
-    const int32_t S = a.sub;
-    int32_t fx = cell_coord(x0, a.inv[0], a.nc[0] * S);
-    int32_t fy = cell_coord(x1, a.inv[1], a.nc[1] * S);
-    int32_t fz = cell_coord(x2, a.inv[2], a.nc[2] * S);
-    int32_t cell = fx / S + a.nc[0] * (fy / S + a.nc[1] * (fz / S));
-    int32_t c = cell * S * S * S + (fx % S + S * (fy % S + S * (fz % S)));
-    a.keys[i] = c;
-    a.vals[i] = (int32_t)i;
-    atomicAdd(&a.count[c], 1);
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool ok = i < a.n;
+    int32_t c = -1;
+    if (ok) {
+        const double *x = (const double *)(a.aos + i * a.stride + a.xoff);
+        double x0 = x[0], x1 = x[1], x2 = x[2];
+        const bool outside = !(in_box(x0, a.box[0]) && in_box(x1, a.box[1]) && in_box(x2, a.box[2]));
+        if (outside)
+            set_error(a.st, SPH_ERR_OUTSIDE | ((isfinite(x0) && isfinite(x1) && isfinite(x2)) ? 0u : SPH_ERR_NONFINITE));
+        // fine coordinates on the grid of sub-cells (inv = sub * nc / L); the
+        // cell is f / sub, the sub-cell f % sub
+        const int32_t S = a.sub;
+        int32_t fx = cell_coord_fast(x0, a.invh[0], a.invl[0], a.inv[0], a.nc[0] * S);
+        int32_t fy = cell_coord_fast(x1, a.invh[1], a.invl[1], a.inv[1], a.nc[1] * S);
+        int32_t fz = cell_coord_fast(x2, a.invh[2], a.invl[2], a.inv[2], a.nc[2] * S);
+        int32_t cell = fx / S + a.nc[0] * (fy / S + a.nc[1] * (fz / S));
+        c = cell * S * S * S + (fx % S + S * (fy % S + S * (fz % S)));
+        a.keys[i] = c;
+        if (a.vals) a.vals[i] = (int32_t)i;
+    }
+    // one atomic per key present in the warp (neighbouring records often
+    // share their cell)
+    const unsigned peers = __match_any_sync(0xffffffffu, c);
+    if (ok && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&a.count[c], __popc(peers));
+}
+
+// ---------------------------------------------------------------------------
+// counting placement (the context's binning): the histogram and its scan
+// give every key its range of slots; each particle takes a slot in its
+// key's range, and k_seg_order then puts every range in ascending particle
+// index, which makes the result that of a stable sort by key
+// ---------------------------------------------------------------------------
+// cursor[K] holds K's count on entry and 0 on exit.  A warp claims, per key
+// present in it, the next block of its range (one atomic), its lanes in
+// index order.  Blocks of different warps follow the order of their atomics.
+__global__ void k_place(const int32_t *key, int64_t n, const int32_t *start, int32_t *cursor, int32_t *perm,
+                        int32_t *skey)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const bool ok = i < n;
+    const int32_t K = ok ? key[i] : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, K);
+    const int leader = __ffs(peers) - 1;
+    const int m = __popc(peers);
+    int left = 0;
+    if (ok && lane == leader) left = atomicSub(&cursor[K], m);
+    left = __shfl_sync(0xffffffffu, left, leader);
+    if (!ok) return;
+    const int32_t s = start[K];
+    const int32_t pos = s + (start[K + 1] - s - left) + __popc(peers & ((1u << lane) - 1u));
+    perm[pos] = (int32_t)i;
+    skey[pos] = K;
+}
+
+// A slot whose successor in the same key range holds a smaller particle
+// index marks that key (plain stores: every writer stores 1).  mark[] is zero
+// on entry (the cursors after k_place).
+__global__ void k_inversions(const int32_t *perm, const int32_t *skey, int64_t n, int32_t *mark)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p + 1 >= n) return;
+    const int32_t K = skey[p];
+    if (K == skey[p + 1] && perm[p] > perm[p + 1]) mark[K] = 1;
+}
+
+// ascending bitonic sort of one value per lane
+__device__ __forceinline__ int32_t warp_bitonic32(int32_t v, int lane)
+{
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1)
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const int32_t o = __shfl_xor_sync(0xffffffffu, v, j);
+            const bool up = (lane & k) == 0;          // this block of k lanes ascends
+            const bool low = (lane & j) == 0;         // this lane keeps the smaller of the pair
+            v = (low == up) ? min(v, o) : max(v, o);
+        }
+    return v;
+}
+
+constexpr int kSegSmem = 1024;        // particle indices one warp sorts in shared memory
+constexpr int kSegWarps = 8;          // warps per k_seg_order block
+
+// One key range put in ascending order by one warp: up to 32 indices in
+// registers, up to kSegSmem by a bitonic network in shared memory, longer
+// ranges by a stable LSD radix sort on the index bits (8 per pass) through
+// the same range of `scratch`.
+__device__ void warp_order_range(int32_t *seg, int32_t *scratch, int32_t len, int64_t n, int32_t *buf, int lane)
+{
+    const unsigned lt = (1u << lane) - 1u;
+    if (len <= 32) {
+        const int32_t v = warp_bitonic32(lane < len ? seg[lane] : INT32_MAX, lane);
+        if (lane < len) seg[lane] = v;
+        return;
+    }
+    if (len <= kSegSmem) {
+        int P = 64;
+        while (P < len) P <<= 1;
+        for (int i = lane; i < P; i += 32) buf[i] = i < len ? seg[i] : INT32_MAX;
+        __syncwarp();
+        for (int k = 2; k <= P; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = lane; i < P; i += 32) {
+                    const int l = i ^ j;
+                    if (l > i) {
+                        const int32_t x = buf[i], y = buf[l];
+                        if ((x > y) == ((i & k) == 0)) {
+                            buf[i] = y;
+                            buf[l] = x;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        for (int i = lane; i < len; i += 32) seg[i] = buf[i];
+        __syncwarp();
+        return;
+    }
+    int bits = 1;
+    while (bits < 31 && ((int64_t)1 << bits) < n) ++bits;
+    int32_t *src = seg, *dst = scratch;
+    for (int shift = 0; shift < bits; shift += 8) {
+        for (int d = lane; d < 256; d += 32) buf[d] = 0;
+        __syncwarp();
+        for (int i = lane; i < len; i += 32) atomicAdd(&buf[((uint32_t)src[i] >> shift) & 255u], 1);
+        __syncwarp();
+        {   // exclusive scan of the 256 digit counts, 8 per lane
+            int32_t cnt[8], sum = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                cnt[q] = buf[lane * 8 + q];
+                sum += cnt[q];
+            }
+            int32_t inc = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            int32_t e = inc - sum;
+            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                buf[lane * 8 + q] = e;
+                e += cnt[q];
+            }
+        }
+        __syncwarp();
+        // stable scatter, 32 indices per round in index order
+        for (int b0 = 0; b0 < len; b0 += 32) {
+            const int i = b0 + lane;
+            const bool ok = i < len;
+            const int32_t v = ok ? src[i] : 0;
+            const uint32_t d = ok ? (((uint32_t)v >> shift) & 255u) : 256u;
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            const int r = __popc(peers & lt);
+            if (ok) dst[buf[d] + r] = v;
+            __syncwarp();
+            if (ok && r == 0) buf[d] += __popc(peers);
+            __syncwarp();
+        }
+        int32_t *tmp = src;
+        src = dst;
+        dst = tmp;
+    }
+    if (src != seg)
+        for (int i = lane; i < len; i += 32) seg[i] = src[i];
+    __syncwarp();
+}
+
+// Every marked key range put in ascending order.  A warp task is 32
+// consecutive keys; the warp orders its marked keys' ranges one after the
+// other.
+__global__ void __launch_bounds__(32 * kSegWarps) k_seg_order(const int32_t *start, const int32_t *mark, int64_t nkeys,
+                                                             int32_t *perm, int32_t *scratch, int64_t n)
+{
+    __shared__ int32_t sm[kSegWarps][kSegSmem];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t nw = (int64_t)gridDim.x * kSegWarps;
+    for (int64_t t = (int64_t)blockIdx.x * kSegWarps + w; t * 32 < nkeys; t += nw) {
+        const int64_t k0 = t * 32;
+        unsigned todo = __ballot_sync(0xffffffffu, k0 + lane < nkeys && mark[k0 + lane] != 0);
+        while (todo) {
+            const int64_t K = k0 + __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int32_t s = start[K];
+            warp_order_range(perm + s, scratch + s, start[K + 1] - s, n, sm[w], lane);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -557,11 +773,13 @@ cudaError_t run_binning(sph_ctx *c, int reorder)
         a.sub = S;
         for (int k = 0; k < 3; ++k) {
             a.inv[k] = (double)(c->nc[k] * S) / c->params.box[k];
+            a.invh[k] = (float)a.inv[k];
+            a.invl[k] = (float)(a.inv[k] - (double)a.invh[k]);
             a.box[k] = c->params.box[k];
             a.nc[k] = c->nc[k];
         }
         a.keys = c->keys[0];
-        a.vals = c->vals[0];
+        a.vals = nullptr;
         a.count = c->cell_count;
         a.st = c->dstats;
         k_cell_ids<<<blocks_for(n, 256), 256, 0, s>>>(a);
@@ -570,9 +788,17 @@ cudaError_t run_binning(sph_ctx *c, int reorder)
     }
     if ((e = scan_exclusive(c->cell_count, c->cell_start, nkeys, c->scan_part, s, &c->launches)) != cudaSuccess) return e;
     if (n > 0) {
-        int bits = 0;
-        while (bits < 31 && ((int64_t)1 << bits) < nkeys) ++bits;
-        if ((e = radix_sort(c, bits)) != cudaSuccess) return e;
+        // keys[0] (the particles' keys) -> keys[1] / vals[1] (sorted keys and
+        // permutation); cell_count (the cursors, zero after k_place) marks the
+        // ranges to order and vals[0] is the radix scratch of long ranges
+        k_place<<<blocks_for(n, 256), 256, 0, s>>>(c->keys[0], n, c->cell_start, c->cell_count, c->vals[1],
+                                                   c->keys[1]);
+        k_inversions<<<blocks_for(n, 256), 256, 0, s>>>(c->vals[1], c->keys[1], n, c->cell_count);
+        k_seg_order<<<(unsigned)(c->sm_count * 4), 32 * kSegWarps, 0, s>>>(c->cell_start, c->cell_count, nkeys,
+                                                                          c->vals[1], c->vals[0], n);
+        c->launches += 3;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        c->sorted_buf = 1;
         if (reorder) {
             k_gather_records<<<blocks_for(n * 32, 256), 256, 0, s>>>(c->aos, c->aos_tmp, c->perm(), n,
                                                                      c->layout.record_bytes);
@@ -608,6 +834,8 @@ cudaError_t bin_raw(const BinRaw &b, cudaStream_t s)
         a.sub = 1;                   // plain cells: b.ncell keys
         for (int k = 0; k < 3; ++k) {
             a.inv[k] = b.inv[k];
+            a.invh[k] = (float)b.inv[k];
+            a.invl[k] = (float)(b.inv[k] - (double)a.invh[k]);
             a.box[k] = b.box[k];
             a.nc[k] = b.nc[k];
         }

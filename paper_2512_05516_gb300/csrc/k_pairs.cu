@@ -1702,10 +1702,9 @@ Common make_common(sph_ctx *c, int cap)
 }
 
 template <typename K, typename A>
-cudaError_t launch_persistent(sph_ctx *c, K kernel, const A &args, size_t smem, LaunchCache &lc)
+cudaError_t launch_persistent(sph_ctx *c, K kernel, const A &args, size_t smem, LaunchCache &lc, int block)
 {
     cudaError_t e;
-    const int block = c->tuning.block_threads;
     if (lc.smem != smem || lc.block != block || lc.per_sm_req != c->tuning.ctas_per_sm) {
         if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
             return e;
@@ -1812,7 +1811,7 @@ cudaError_t run_density(sph_ctx *c, int newton_steps)
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t smem = density_smem_bytes(c->tuning.block_threads, a.c.cap);
-    if ((e = launch_persistent(c, k_density<false>, a, smem, c->lc_density)) != cudaSuccess) return e;
+    if ((e = launch_persistent(c, k_density<false>, a, smem, c->lc_density, c->tuning.block_threads)) != cudaSuccess) return e;
     if (a.write_h && h_packed) return run_pack(c, c->stage, SPH_F_H);
     return cudaSuccess;
 }
@@ -1855,8 +1854,8 @@ cudaError_t run_density_levels(sph_ctx *c, int newton_steps)
         a.lvl = l;
         a.promote = l > c->lvl_min;
         if ((e = cudaMemsetAsync(&c->dstats->defer_n, 0, 2 * sizeof(unsigned), c->stream)) != cudaSuccess) return e;
-        if ((e = launch_persistent(c, k_density<true>, a, smem, c->lc_density_lv)) != cudaSuccess) return e;
-        if ((e = launch_persistent(c, k_density_one, a, smem, c->lc_density_one)) != cudaSuccess) return e;
+        if ((e = launch_persistent(c, k_density<true>, a, smem, c->lc_density_lv, c->tuning.block_threads)) != cudaSuccess) return e;
+        if ((e = launch_persistent(c, k_density_one, a, smem, c->lc_density_one, c->tuning.block_threads)) != cudaSuccess) return e;
     }
     if (a.write_h && h_packed) return run_pack(c, c->stage, SPH_F_H);
     return cudaSuccess;
@@ -1916,8 +1915,8 @@ cudaError_t run_force(sph_ctx *c)
         return cudaGetLastError();
     }
     // the pair kernel reads only the packed FP32 arrays: one instantiation
-    const size_t smem = force_smem_bytes(c->tuning.block_threads, a.c.cap);
-    return launch_persistent(c, k_force<false>, a, smem, c->lc_force);
+    const size_t smem = force_smem_bytes(c->tuning.block_threads_force, a.c.cap);
+    return launch_persistent(c, k_force<false>, a, smem, c->lc_force, c->tuning.block_threads_force);
 }
 
 // The force over the level hierarchy: one pack pass, the per-level lists,
@@ -1948,7 +1947,7 @@ cudaError_t run_force_levels(sph_ctx *c)
     c->launches += 1;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = run_level_lists(c, plist, pkey)) != cudaSuccess) return e;
-    const size_t smem = force_smem_bytes(c->tuning.block_threads, a.c.cap);
+    const size_t smem = force_smem_bytes(c->tuning.block_threads_force, a.c.cap);
     for (int l = c->lvl_max; l >= c->lvl_min; --l) {
         if ((e = run_level_items(c, l)) != cudaSuccess) return e;
         for (int k = 0; k < 3; ++k) a.c.edge[k] = (float)std::ldexp(c->params.box[k], -l);
@@ -1956,8 +1955,8 @@ cudaError_t run_force_levels(sph_ctx *c)
         a.c.lvl_n = 1 << l;
         a.lvl = l;
         if ((e = cudaMemsetAsync(&c->dstats->defer_n, 0, 2 * sizeof(unsigned), c->stream)) != cudaSuccess) return e;
-        if ((e = launch_persistent(c, k_force<true>, a, smem, c->lc_force_lv)) != cudaSuccess) return e;
-        if ((e = launch_persistent(c, k_force_one, a, smem, c->lc_force_one)) != cudaSuccess) return e;
+        if ((e = launch_persistent(c, k_force<true>, a, smem, c->lc_force_lv, c->tuning.block_threads_force)) != cudaSuccess) return e;
+        if ((e = launch_persistent(c, k_force_one, a, smem, c->lc_force_one, c->tuning.block_threads_force)) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }

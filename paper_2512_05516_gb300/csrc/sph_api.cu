@@ -56,6 +56,7 @@ void default_tuning(sph_tuning *t)
     // prefers a stage that holds a whole neighbourhood, force more resident
     // warps, and the costliest work items go first
     t->block_threads = 32;
+    t->block_threads_force = 32;
     t->ctas_per_sm = 0;
     t->stage_density = 128;
     t->stage_force = 128;
@@ -639,6 +640,11 @@ sph_status sph_set_tuning(sph_ctx *c, const sph_tuning *t)
         if (t->block_threads % 32 != 0 || t->block_threads < 32 || t->block_threads > kMaxBlock)
             return SPH_EINVAL;
         n.block_threads = t->block_threads;
+        n.block_threads_force = t->block_threads;
+    }
+    if (t->block_threads_force > 0) {
+        if (t->block_threads_force % 32 != 0 || t->block_threads_force > kMaxBlock) return SPH_EINVAL;
+        n.block_threads_force = t->block_threads_force;
     }
     if (t->ctas_per_sm > 0) n.ctas_per_sm = t->ctas_per_sm;
     if (t->stage_density > 0) n.stage_density = t->stage_density;
@@ -663,7 +669,7 @@ sph_status sph_set_tuning(sph_ctx *c, const sph_tuning *t)
     if (n.stage_density > 65535 || n.stage_force > 65535) return SPH_EINVAL;
     if (density_smem_bytes(n.block_threads, n.stage_density, (c->ws_flags & SPH_WS_LEVELS) != 0) > c->smem_optin)
         return SPH_EINVAL;
-    if (force_smem_bytes(n.block_threads, n.stage_force) > c->smem_optin) return SPH_EINVAL;
+    if (force_smem_bytes(n.block_threads_force, n.stage_force) > c->smem_optin) return SPH_EINVAL;
     c->tuning = n;
     return SPH_OK;
 }

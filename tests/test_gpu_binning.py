@@ -71,3 +71,48 @@ def test_small_and_ragged_sizes(orc, n):
     wl.h_cap = 0.05
     wl.cell_edge = 0.1
     _check(orc, wl)
+
+
+def _clustered(n, seed, blobs):
+    """Uniform cloud with some particles squeezed into single sub-cells:
+    blobs = [(count, corner, extent)], each blob inside one sub-cell of the
+    0.1-cell grid with 2 sub-cells per edge (edge 0.05)."""
+    wl = sph_inputs.random_cloud(n, seed=seed)
+    x = wl.col("x")
+    o = 0
+    for cnt, corner, ext in blobs:
+        x[o:o + cnt] = corner + ext * x[o:o + cnt]
+        o += cnt
+    wl.h_cap = 0.05
+    wl.cell_edge = 0.1
+    return wl
+
+
+def test_long_cell_ranges(orc):
+    # key ranges of every length class: ~5 particles (registers), 600
+    # (shared memory), 10,000 and 150,000 (radix over the index bits, 18-bit
+    # indices: three passes)
+    wl = _clustered(200_000, 7, [(150_000, 0.0, 0.01), (10_000, 0.5, 0.02), (600, 0.3, 0.04)])
+    _check(orc, wl)
+
+
+def test_long_cell_range_four_radix_passes(orc):
+    # more than 2^24 particles: 25-bit indices, four radix passes over a
+    # 100,000-particle range
+    wl = _clustered(16_777_300, 8, [(100_000, 0.7, 0.02)])
+    _check(orc, wl)
+
+
+def test_particles_on_cell_faces(orc):
+    # a lattice whose points lie exactly on sub-cell faces (k / 24 with 12
+    # cells of 2 sub-cells per axis) and on the faces' neighbouring doubles:
+    # the cases where the cell index depends on the rounding of x * (n_c / L)
+    k = np.arange(24, dtype=np.float64) / 24.0
+    g = np.stack(np.meshgrid(k, k, k, indexing="ij"), -1).reshape(-1, 3)
+    pts = np.concatenate([g, np.nextafter(g, 0.0), np.nextafter(g, 1.0)])
+    wl = sph_inputs.random_cloud(pts.shape[0], seed=9)
+    wl.col("x")[:] = np.clip(pts, 0.0, np.nextafter(1.0, 0.0))
+    wl.h_cap = 1.0 / 24.0
+    wl.cell_edge = 1.0 / 12.0
+    s = _check(orc, wl)
+    assert tuple(s.nc) == (12, 12, 12)
