@@ -189,7 +189,7 @@ def run_ours(args, rank, world):
     names = ["bin", "aos_to_soa", "density", "force", "kick_drift_writeback"]
 
     def step(ev=None):
-        calls = [lambda: s.bin_cells(wl.cell_edge),
+        calls = [lambda: s.bin_cells(wl.cell_edge, drift_keys=True),
                  lambda: s.aos_to_soa(sph.FIELDS_FORCE, prec),
                  lambda: s.density(wl.newton_steps),
                  lambda: s.force(),
@@ -389,7 +389,7 @@ def run_long_run(steps: int = 3, graph_steps: int = 100):
     with torch.cuda.stream(stream):
         tuned = autotune.tune(s, wl.cell_edge, prec, 0)
     names = ["bin", "aos_to_soa", "density", "force", "kick_drift_writeback"]
-    calls = [lambda: s.bin_cells(wl.cell_edge), lambda: s.aos_to_soa(sph.FIELDS_FORCE, prec),
+    calls = [lambda: s.bin_cells(wl.cell_edge, drift_keys=True), lambda: s.aos_to_soa(sph.FIELDS_FORCE, prec),
              lambda: s.density(0), lambda: s.force(),
              lambda: s.kick_drift_writeback(wl.dt, wl.dt, sph.FIELDS_OUTPUT)]
     ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in names]
@@ -449,7 +449,7 @@ def run_long_run(steps: int = 3, graph_steps: int = 100):
             for _ in range(steps)]
     with torch.cuda.stream(stream):
         for k in range(steps + 1):
-            for i, fn in enumerate([lambda: s.bin_cells(wl.cell_edge), None, lambda: s.density(0),
+            for i, fn in enumerate([lambda: s.bin_cells(wl.cell_edge, drift_keys=True), None, lambda: s.density(0),
                                     lambda: s.force(), lambda: s.kick_drift(wl.dt, wl.dt)]):
                 if fn is None:
                     s.aos_to_soa(sph.FIELDS_FORCE)          # FP32, untimed
@@ -560,7 +560,7 @@ def run_streaming(steps: int = 5):
         t = torch.from_numpy(wl.aos.copy())
         aos = t.to(dev) if where == "in_place" else t.pin_memory()
         s = sph.Sph(aos, sph.layout_112(), params, int(np.prod(nc)), 0, stream=stream)
-        calls = [lambda: s.bin_cells(wl.cell_edge), lambda: s.aos_to_soa(sph.FIELDS_FORCE),
+        calls = [lambda: s.bin_cells(wl.cell_edge, drift_keys=True), lambda: s.aos_to_soa(sph.FIELDS_FORCE),
                  lambda: s.density(wl.newton_steps), lambda: s.force(),
                  lambda: s.kick_drift_writeback(wl.dt, wl.dt, sph.FIELDS_OUTPUT)]
         ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in names]

@@ -269,12 +269,33 @@ sph_status sph_create(const sph_aos_layout *layout, const sph_params *params, in
  * cell s^3 + (s_x + s (s_y + s s_z)).  The permutation lists particles by key,
  * ascending original index among equal keys (a stable sort), so every cell
  * stays contiguous and spatially compact inside; the pair-kernel work items
- * are rebuilt.  reorder_aos = 1 also rewrites the AoS records in
- * that order (the permutation then becomes the identity); it needs a
- * workspace created with SPH_WS_REORDER.  Invalidates every SoA field.
- * Errors: SPH_ECAPACITY (< 3 cells on an axis), SPH_ENOSPACE (more than
- * ncell_max cells, or reorder without room), SPH_ECUDA. */
-sph_status sph_bin_cells(sph_ctx *ctx, double cell_edge, int32_t reorder_aos);
+ * are rebuilt.  flags (SPH_BIN_*, or-ed; 0 for neither):
+ *   SPH_BIN_REORDER    also rewrite the AoS records in that order (the
+ *                      permutation then becomes the identity); needs a
+ *                      workspace created with SPH_WS_REORDER;
+ *   SPH_BIN_DRIFT_KEYS the caller vouches that no position in the AoS changed
+ *                      since this context's last sph_kick_drift or
+ *                      sph_kick_drift_writeback: the keys that call computed
+ *                      for the positions it wrote are used instead of reading
+ *                      the records again (the same keys, bit for bit).  The
+ *                      flag is ignored, and the records read, when there are
+ *                      no such keys: no kick/drift since the last binning, a
+ *                      binning on another grid (cell_edge, subcells), the
+ *                      level hierarchy or buffers, or a call that wrote
+ *                      positions since (sph_aos_upload; sph_soa_to_aos and
+ *                      sph_soa_to_aos_host of X).  The library cannot see writes made
+ *                      to the records by other code: a caller who moves
+ *                      particles between the two calls must not set it.
+ *                      A kick/drift that computes the keys reports a
+ *                      non-finite position as SPH_ERR_OUTSIDE too, as the
+ *                      binning would.
+ * Invalidates every SoA field.
+ * Errors: SPH_EINVAL (unknown flags), SPH_ECAPACITY (< 3 cells on an axis),
+ * SPH_ENOSPACE (more than ncell_max cells, or reorder without room),
+ * SPH_ECUDA. */
+#define SPH_BIN_REORDER 1
+#define SPH_BIN_DRIFT_KEYS 2
+sph_status sph_bin_cells(sph_ctx *ctx, double cell_edge, int32_t flags);
 
 /* S2, U o N o C (Section 4, Eq. 12): gather the fields in `fields` from the AoS
  * in cell order, round them to their storage formats and write them as SoA.

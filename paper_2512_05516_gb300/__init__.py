@@ -13,7 +13,7 @@ from __future__ import annotations
 import ctypes as C
 
 from . import _capi
-from ._capi import (AOS_F32, AOS_F64, BIT, ERR_HCAP, ERR_NEWTON, ERR_NONFINITE, ERR_OUTSIDE, ERR_TIMEOUT,
+from ._capi import (AOS_F32, AOS_F64, BIN_DRIFT_KEYS, BIN_REORDER, BIT, ERR_HCAP, ERR_NEWTON, ERR_NONFINITE, ERR_OUTSIDE, ERR_TIMEOUT,
                     PFLAG_HCAP, PFLAG_NEWTON, PFLAG_NONFINITE,
                     F_A, F_CS, F_DUDT, F_H, F_M, F_P, F_RHO, F_U, F_V, F_X, FIELD_NAMES,
                     FIELDS_DENSITY, FIELDS_FORCE, FIELDS_KICK, FIELDS_OUTPUT, FLAG_PLAIN_SUM,
@@ -335,8 +335,11 @@ class Sph:
         self.ctx = ctx
 
     # --- the path
-    def bin_cells(self, cell_edge: float = 0.0, reorder: bool = False):
-        _check(sph_bin_cells(self.ctx, cell_edge, 1 if reorder else 0), "sph_bin_cells")
+    def bin_cells(self, cell_edge: float = 0.0, reorder: bool = False, drift_keys: bool = False):
+        """drift_keys: the caller vouches that the records' positions are those
+        the last kick/drift wrote (see SPH_BIN_DRIFT_KEYS)."""
+        flags = (BIN_REORDER if reorder else 0) | (BIN_DRIFT_KEYS if drift_keys else 0)
+        _check(sph_bin_cells(self.ctx, cell_edge, flags), "sph_bin_cells")
 
     def aos_to_soa(self, fields: int, prec=None):
         arr = prec if isinstance(prec, list) else (prec_array(prec) if prec is not None else None)

@@ -33,6 +33,7 @@ for _n in range(1, 23):
 AOS_F64, AOS_F32 = 0, 1
 FLAG_PLAIN_SUM = 1
 WS_REORDER = 1
+BIN_REORDER, BIN_DRIFT_KEYS = 1, 2
 WS_LEVELS = 2
 LEVEL_MIN, LEVEL_MAX, LEVELS_MAX = 2, 10, 8
 ERR_NONFINITE, ERR_OUTSIDE, ERR_HCAP, ERR_NEWTON, ERR_TIMEOUT = 1, 2, 4, 8, 16

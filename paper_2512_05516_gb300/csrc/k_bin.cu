@@ -5,7 +5,7 @@
 // hierarchy and the allocation-free entry point by a stable LSD radix sort of
 // (key, particle index) pairs.  Also builds the pair-kernel work items (cell,
 // first slot, count) and optionally rewrites the AoS records in cell order.
-#include "sph_internal.cuh"
+#include "k_cellkey.cuh"
 
 namespace sph {
 namespace {
@@ -17,63 +17,11 @@ struct CellArgs {
     const uint8_t *aos;
     int64_t n;
     int32_t stride, xoff;
-    double inv[3], box[3];
-    float invh[3], invl[3];      // inv as an FP32 pair: inv = invh + invl to a relative 2^-48
-    int32_t nc[3];
-    int32_t sub;                 // sub-cells per cell edge
+    double box[3];
+    CellGrid g;
     int32_t *keys, *vals, *count;
     DevStats *st;
 };
-
-// floor(x * inv) clamped to [0, nc-1]: one FP64 multiply (the product must
-// round exactly as the definition says) and one round-down conversion, which
-// maps NaN to INT_MIN and overflows to INT_MAX, so the integer clamp gives
-// 0 for NaN and negatives and nc-1 above the grid.
-__device__ __forceinline__ int32_t cell_coord(double x, double inv, int32_t nc)
-{
-    const int f = __double2int_rd(__dmul_rn(x, inv));
-    return min(max(f, 0), nc - 1);
-}
-
-// cell_coord's result computed on the FP32 pipe for almost every particle
-// (the FP64 pipe of this GPU runs at a small fraction of the FP32 rate).  x is
-// split from its bits into FP32 parts, x = hi + lo up to a relative 2^-47
-// (hi: the leading 24 significant bits, lo: the other 29 rounded to 24), and
-// the product x * inv is formed as the unevaluated FP32 pair p + t, where
-// p + fma(hi, ih, -p) = hi * ih exactly; the pair is within 2^-44 of the
-// exact product, relatively, so within 2^-31 absolutely below 8192.  The
-// floor of the pair then equals the floor of the rounded FP64 product unless
-// the pair's fractional part lies within 2^-20 of 0 or 1, and those
-// particles (on or next to a face), like x outside [2^-74, 2^100), negative
-// or not finite, take the FP64 product.
-__device__ __forceinline__ int32_t cell_coord_fast(double x, float ih, float il, double inv, int32_t nc)
-{
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    if (b == 0ull) return 0;                                // +0
-    const int e = (int)(b >> 52);                          // biased exponent (sign bit set: >= 2048)
-    bool exact = e < 949 || e >= 1123;
-    int32_t f = 0;
-    if (!exact) {
-        const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
-        const float hi = __int_as_float(((e - 896) << 23) | (int)(m >> 29));
-        const float lo = __uint2float_rn((unsigned)(m & 0x1FFFFFFFu)) * __int_as_float((e - 948) << 23);
-        const float p = hi * ih;
-        const float t = fmaf(hi, ih, -p) + fmaf(hi, il, lo * ih);
-        float fl = floorf(p);
-        float d = (p - fl) + t;
-        if (d < 0.0f) {
-            fl -= 1.0f;
-            d += 1.0f;
-        } else if (d >= 1.0f) {
-            fl += 1.0f;
-            d -= 1.0f;
-        }
-        exact = d < 0x1p-20f || d > 1.0f - 0x1p-20f;
-        f = min(max(__float2int_rz(fl), 0), nc - 1);
-    }
-    if (exact) f = cell_coord(x, inv, nc);
-    return f;
-}
 
 // x in [0, L) compared on bit patterns (FP64 compares are slow on this GPU):
 // non-negative doubles order like their bits; -0 counts as inside
@@ -83,32 +31,64 @@ __device__ __forceinline__ bool in_box(double x, double L)
     return (b >= 0 && b < __double_as_longlong(L)) || b == (long long)0x8000000000000000ull;
 }
 
-__global__ void k_cell_ids(CellArgs a)
+// Each thread takes kBinU particles, kBinThreads apart, their loads issued
+// together (a thread per particle leaves too few loads in flight).
+constexpr int kBinThreads = 256;
+constexpr int kBinU = 4;
+
+__global__ void __launch_bounds__(kBinThreads) k_cell_ids(CellArgs a)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool ok = i < a.n;
-    int32_t c = -1;
-    if (ok) {
-        const double *x = (const double *)(a.aos + i * a.stride + a.xoff);
-        double x0 = x[0], x1 = x[1], x2 = x[2];
-        const bool outside = !(in_box(x0, a.box[0]) && in_box(x1, a.box[1]) && in_box(x2, a.box[2]));
-        if (outside)
-            set_error(a.st, SPH_ERR_OUTSIDE | ((isfinite(x0) && isfinite(x1) && isfinite(x2)) ? 0u : SPH_ERR_NONFINITE));
-        // fine coordinates on the grid of sub-cells (inv = sub * nc / L); the
-        // cell is f / sub, the sub-cell f % sub
-        const int32_t S = a.sub;
-        int32_t fx = cell_coord_fast(x0, a.invh[0], a.invl[0], a.inv[0], a.nc[0] * S);
-        int32_t fy = cell_coord_fast(x1, a.invh[1], a.invl[1], a.inv[1], a.nc[1] * S);
-        int32_t fz = cell_coord_fast(x2, a.invh[2], a.invl[2], a.inv[2], a.nc[2] * S);
-        int32_t cell = fx / S + a.nc[0] * (fy / S + a.nc[1] * (fz / S));
-        c = cell * S * S * S + (fx % S + S * (fy % S + S * (fz % S)));
-        a.keys[i] = c;
-        if (a.vals) a.vals[i] = (int32_t)i;
+    const int64_t i0 = (int64_t)blockIdx.x * (kBinThreads * kBinU) + threadIdx.x;
+    double x[kBinU][3];
+#pragma unroll
+    for (int u = 0; u < kBinU; ++u) {
+        const int64_t i = i0 + u * kBinThreads;
+        if (i < a.n) {
+            const double *p = (const double *)(a.aos + i * a.stride + a.xoff);
+            x[u][0] = p[0];
+            x[u][1] = p[1];
+            x[u][2] = p[2];
+        }
     }
-    // one atomic per key present in the warp (neighbouring records often
-    // share their cell)
-    const unsigned peers = __match_any_sync(0xffffffffu, c);
-    if (ok && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&a.count[c], __popc(peers));
+#pragma unroll
+    for (int u = 0; u < kBinU; ++u) {
+        const int64_t i = i0 + u * kBinThreads;
+        const bool ok = i < a.n;
+        int32_t c = -1;
+        if (ok) {
+            const double x0 = x[u][0], x1 = x[u][1], x2 = x[u][2];
+            const bool outside = !(in_box(x0, a.box[0]) && in_box(x1, a.box[1]) && in_box(x2, a.box[2]));
+            if (outside)
+                set_error(a.st, SPH_ERR_OUTSIDE |
+                                    ((isfinite(x0) && isfinite(x1) && isfinite(x2)) ? 0u : SPH_ERR_NONFINITE));
+            c = cell_key(a.g, x0, x1, x2);
+            a.keys[i] = c;
+            if (a.vals) a.vals[i] = (int32_t)i;
+        }
+        // one atomic per key present in the warp (neighbouring records often
+        // share their cell)
+        const unsigned peers = __match_any_sync(0xffffffffu, c);
+        if (ok && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&a.count[c], __popc(peers));
+    }
+}
+
+// The histogram alone, over the keys the drift computed for the positions it
+// wrote (k_kick_drift), when the caller vouches that the records have not
+// changed since.
+__global__ void __launch_bounds__(kBinThreads) k_key_hist(const int32_t *keys, int64_t n, int32_t *count)
+{
+    const int64_t i0 = (int64_t)blockIdx.x * (kBinThreads * kBinU) + threadIdx.x;
+    int32_t c[kBinU];
+#pragma unroll
+    for (int u = 0; u < kBinU; ++u) {
+        const int64_t i = i0 + u * kBinThreads;
+        c[u] = i < n ? keys[i] : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < kBinU; ++u) {
+        const unsigned peers = __match_any_sync(0xffffffffu, c[u]);
+        if (c[u] >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&count[c[u]], __popc(peers));
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -120,35 +100,54 @@ __global__ void k_cell_ids(CellArgs a)
 // cursor[K] holds K's count on entry and 0 on exit.  A warp claims, per key
 // present in it, the next block of its range (one atomic), its lanes in
 // index order.  Blocks of different warps follow the order of their atomics.
-__global__ void k_place(const int32_t *key, int64_t n, const int32_t *start, int32_t *cursor, int32_t *perm,
-                        int32_t *skey)
+__global__ void __launch_bounds__(kBinThreads) k_place(const int32_t *key, int64_t n, const int32_t *start,
+                                                     int32_t *cursor, int32_t *perm, int32_t *skey)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i0 = (int64_t)blockIdx.x * (kBinThreads * kBinU) + threadIdx.x;
     const int lane = threadIdx.x & 31;
-    const bool ok = i < n;
-    const int32_t K = ok ? key[i] : -1;
-    const unsigned peers = __match_any_sync(0xffffffffu, K);
-    const int leader = __ffs(peers) - 1;
-    const int m = __popc(peers);
-    int left = 0;
-    if (ok && lane == leader) left = atomicSub(&cursor[K], m);
-    left = __shfl_sync(0xffffffffu, left, leader);
-    if (!ok) return;
-    const int32_t s = start[K];
-    const int32_t pos = s + (start[K + 1] - s - left) + __popc(peers & ((1u << lane) - 1u));
-    perm[pos] = (int32_t)i;
-    skey[pos] = K;
+    const unsigned lt = (1u << lane) - 1u;
+    int32_t K[kBinU], s0[kBinU], s1[kBinU], left[kBinU];
+    unsigned peers[kBinU];
+#pragma unroll
+    for (int u = 0; u < kBinU; ++u) {
+        const int64_t i = i0 + u * kBinThreads;
+        K[u] = i < n ? key[i] : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < kBinU; ++u) {
+        s0[u] = K[u] >= 0 ? start[K[u]] : 0;
+        s1[u] = K[u] >= 0 ? start[K[u] + 1] : 0;
+        peers[u] = __match_any_sync(0xffffffffu, K[u]);
+        left[u] = 0;
+        if (K[u] >= 0 && lane == __ffs(peers[u]) - 1) left[u] = atomicSub(&cursor[K[u]], __popc(peers[u]));
+    }
+#pragma unroll
+    for (int u = 0; u < kBinU; ++u) {
+        const int64_t i = i0 + u * kBinThreads;
+        const int l = __shfl_sync(0xffffffffu, left[u], __ffs(peers[u]) - 1);
+        if (i < n) {
+            const int32_t pos = s0[u] + (s1[u] - s0[u] - l) + __popc(peers[u] & lt);
+            perm[pos] = (int32_t)i;
+            skey[pos] = K[u];
+        }
+    }
 }
 
 // A slot whose successor in the same key range holds a smaller particle
 // index marks that key (plain stores: every writer stores 1).  mark[] is zero
 // on entry (the cursors after k_place).
-__global__ void k_inversions(const int32_t *perm, const int32_t *skey, int64_t n, int32_t *mark)
+__global__ void __launch_bounds__(kBinThreads) k_inversions(const int32_t *perm, const int32_t *skey, int64_t n,
+                                                          int32_t *mark)
 {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p + 1 >= n) return;
-    const int32_t K = skey[p];
-    if (K == skey[p + 1] && perm[p] > perm[p + 1]) mark[K] = 1;
+    const int64_t p0 = (int64_t)blockIdx.x * (kBinThreads * kBinU) + threadIdx.x;
+#pragma unroll
+    for (int u = 0; u < kBinU; ++u) {
+        const int64_t p = p0 + u * kBinThreads;
+        if (p + 1 < n) {
+            const int32_t k = skey[p];
+            if (k == skey[p + 1] && perm[p] > perm[p + 1]) mark[k] = 1;
+        }
+    }
 }
 
 // ascending bitonic sort of one value per lane
@@ -257,8 +256,9 @@ __device__ void warp_order_range(int32_t *seg, int32_t *scratch, int32_t len, in
 }
 
 // Every marked key range put in ascending order.  A warp task is 32
-// consecutive keys; the warp orders its marked keys' ranges one after the
-// other.
+// consecutive keys.  Its marked ranges of up to 32 indices are sorted four at
+// a time in registers (four independent loads and bitonic networks keep the
+// warp busy while one range waits on memory), longer ones one by one.
 __global__ void __launch_bounds__(32 * kSegWarps) k_seg_order(const int32_t *start, const int32_t *mark, int64_t nkeys,
                                                              int32_t *perm, int32_t *scratch, int64_t n)
 {
@@ -267,12 +267,41 @@ __global__ void __launch_bounds__(32 * kSegWarps) k_seg_order(const int32_t *sta
     const int64_t nw = (int64_t)gridDim.x * kSegWarps;
     for (int64_t t = (int64_t)blockIdx.x * kSegWarps + w; t * 32 < nkeys; t += nw) {
         const int64_t k0 = t * 32;
-        unsigned todo = __ballot_sync(0xffffffffu, k0 + lane < nkeys && mark[k0 + lane] != 0);
-        while (todo) {
-            const int64_t K = k0 + __ffs(todo) - 1;
-            todo &= todo - 1;
-            const int32_t s = start[K];
-            warp_order_range(perm + s, scratch + s, start[K + 1] - s, n, sm[w], lane);
+        const bool in = k0 + lane < nkeys && mark[k0 + lane] != 0;
+        const int32_t my_s = in ? start[k0 + lane] : 0;
+        const int32_t my_len = in ? start[k0 + lane + 1] - my_s : 0;
+        unsigned small = __ballot_sync(0xffffffffu, in && my_len <= 32);
+        unsigned big = __ballot_sync(0xffffffffu, in && my_len > 32);
+        while (small) {
+            int32_t v[4], sq[4], lq[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int src = small ? __ffs(small) - 1 : 0;
+                lq[q] = small ? __shfl_sync(0xffffffffu, my_len, src) : 0;
+                sq[q] = __shfl_sync(0xffffffffu, my_s, src);
+                small &= small - 1;
+                v[q] = lane < lq[q] ? perm[sq[q] + lane] : INT32_MAX;
+            }
+#pragma unroll
+            for (int k = 2; k <= 32; k <<= 1)
+#pragma unroll
+                for (int j = k >> 1; j > 0; j >>= 1) {
+                    const bool keep_min = ((lane & j) == 0) == ((lane & k) == 0);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int32_t o = __shfl_xor_sync(0xffffffffu, v[q], j);
+                        v[q] = keep_min ? min(v[q], o) : max(v[q], o);
+                    }
+                }
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (lane < lq[q]) perm[sq[q] + lane] = v[q];
+        }
+        while (big) {
+            const int src = __ffs(big) - 1;
+            big &= big - 1;
+            const int32_t s0 = __shfl_sync(0xffffffffu, my_s, src), len = __shfl_sync(0xffffffffu, my_len, src);
+            warp_order_range(perm + s0, scratch + s0, len, n, sm[w], lane);
         }
     }
 }
@@ -441,10 +470,15 @@ __global__ void k_items_count(const int32_t *cell_start, int64_t ncell, int s3, 
                               DevStats *st)
 {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncell) return;
-    int32_t cnt = cell_start[(c + 1) * s3] - cell_start[c * s3];
-    tmp[c] = (cnt + block - 1) / block;
-    if (cnt > 0) atomicMax(&st->max_occ, cnt);
+    int32_t cnt = 0;
+    if (c < ncell) {
+        cnt = cell_start[(c + 1) * s3] - cell_start[c * s3];
+        tmp[c] = (cnt + block - 1) / block;
+    }
+    // one atomic per warp
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt = max(cnt, __shfl_xor_sync(0xffffffffu, cnt, o));
+    if ((threadIdx.x & 31) == 0 && cnt > 0) atomicMax(&st->max_occ, cnt);
 }
 
 __global__ void k_items_fill(const int32_t *cell_start, const int32_t *item_off, int64_t ncell, int s3, int block,
@@ -750,7 +784,7 @@ cudaError_t radix_sort(sph_ctx *c, int bits)
 
 }  // namespace
 
-cudaError_t run_binning(sph_ctx *c, int reorder)
+cudaError_t run_binning(sph_ctx *c, int reorder, bool drift_keys)
 {
     cudaStream_t s = c->stream;
     cudaError_t e;
@@ -764,25 +798,24 @@ cudaError_t run_binning(sph_ctx *c, int reorder)
                                                      make_double3(c->edge[0], c->edge[1], c->edge[2]));
     c->launches += 1;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (n > 0) {
+    if (n > 0 && drift_keys) {
+        // keys[0] holds the keys of the drifted positions
+        k_key_hist<<<blocks_for(n, kBinThreads * kBinU), kBinThreads, 0, s>>>(c->keys[0], n, c->cell_count);
+        c->launches += 1;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    } else if (n > 0) {
         CellArgs a;
         a.aos = c->aos;
         a.n = n;
         a.stride = c->layout.record_bytes;
         a.xoff = c->layout.offset[SPH_F_X];
-        a.sub = S;
-        for (int k = 0; k < 3; ++k) {
-            a.inv[k] = (double)(c->nc[k] * S) / c->params.box[k];
-            a.invh[k] = (float)a.inv[k];
-            a.invl[k] = (float)(a.inv[k] - (double)a.invh[k]);
-            a.box[k] = c->params.box[k];
-            a.nc[k] = c->nc[k];
-        }
+        a.g = cell_grid(c->nc, S, c->params.box);
+        for (int k = 0; k < 3; ++k) a.box[k] = c->params.box[k];
         a.keys = c->keys[0];
         a.vals = nullptr;
         a.count = c->cell_count;
         a.st = c->dstats;
-        k_cell_ids<<<blocks_for(n, 256), 256, 0, s>>>(a);
+        k_cell_ids<<<blocks_for(n, kBinThreads * kBinU), kBinThreads, 0, s>>>(a);
         c->launches += 1;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
@@ -791,9 +824,9 @@ cudaError_t run_binning(sph_ctx *c, int reorder)
         // keys[0] (the particles' keys) -> keys[1] / vals[1] (sorted keys and
         // permutation); cell_count (the cursors, zero after k_place) marks the
         // ranges to order and vals[0] is the radix scratch of long ranges
-        k_place<<<blocks_for(n, 256), 256, 0, s>>>(c->keys[0], n, c->cell_start, c->cell_count, c->vals[1],
+        k_place<<<blocks_for(n, kBinThreads * kBinU), kBinThreads, 0, s>>>(c->keys[0], n, c->cell_start, c->cell_count, c->vals[1],
                                                    c->keys[1]);
-        k_inversions<<<blocks_for(n, 256), 256, 0, s>>>(c->vals[1], c->keys[1], n, c->cell_count);
+        k_inversions<<<blocks_for(n, kBinThreads * kBinU), kBinThreads, 0, s>>>(c->vals[1], c->keys[1], n, c->cell_count);
         k_seg_order<<<(unsigned)(c->sm_count * 4), 32 * kSegWarps, 0, s>>>(c->cell_start, c->cell_count, nkeys,
                                                                           c->vals[1], c->vals[0], n);
         c->launches += 3;
@@ -831,19 +864,19 @@ cudaError_t bin_raw(const BinRaw &b, cudaStream_t s)
         a.n = b.n;
         a.stride = b.stride;
         a.xoff = b.xoff;
-        a.sub = 1;                   // plain cells: b.ncell keys
+        a.g.sub = 1;                 // plain cells: b.ncell keys
         for (int k = 0; k < 3; ++k) {
-            a.inv[k] = b.inv[k];
-            a.invh[k] = (float)b.inv[k];
-            a.invl[k] = (float)(b.inv[k] - (double)a.invh[k]);
+            a.g.inv[k] = b.inv[k];
+            a.g.invh[k] = (float)b.inv[k];
+            a.g.invl[k] = (float)(b.inv[k] - (double)a.g.invh[k]);
+            a.g.nc[k] = b.nc[k];
             a.box[k] = b.box[k];
-            a.nc[k] = b.nc[k];
         }
         a.keys = b.keys[0];
         a.vals = b.vals[0];
         a.count = b.count;
         a.st = b.st;
-        k_cell_ids<<<blocks_for(b.n, 256), 256, 0, s>>>(a);
+        k_cell_ids<<<blocks_for(b.n, kBinThreads * kBinU), kBinThreads, 0, s>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if ((e = scan_exclusive(b.count, b.out_start, b.ncell, b.scan_part, s, &launches)) != cudaSuccess) return e;

@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <cstring>
 
+#include "k_cellkey.cuh"
 #include "k_records.cuh"
 
 namespace sph {
@@ -58,6 +59,8 @@ struct KDArgs {
     int32_t rb;                  // record bytes
     int nwb;
     WbComp wb[kMaxWb];
+    int32_t *keys_out;           // the next binning's cell key of every record (by record index), or null
+    CellGrid kg;                 // ... on this grid
     DevStats *st;
 };
 
@@ -134,6 +137,12 @@ __global__ void __launch_bounds__(kKDThreads, 10) k_kick_drift(KDArgs a)
             xs[c] = y;
         }
         if (bad || !isfinite(un)) set_error(a.st, SPH_ERR_NONFINITE);
+        // the cell key of the new position, as the next binning computes it
+        // from the record (a non-finite position: outside the box, as there)
+        if (a.keys_out) {
+            a.keys_out[o] = cell_key(a.kg, xs[0], xs[1], xs[2]);
+            if (bad) set_error(a.st, SPH_ERR_OUTSIDE);
+        }
         // the write-back: v and u as the storage format holds them after the
         // kick, the other fields as stored
 #pragma unroll
@@ -240,6 +249,10 @@ cudaError_t run_kick_drift(sph_ctx *c, double dt_kick, double dt_drift, uint32_t
     a.wrun = chunk_run(chunks_of_units(a.umask, cb));
     a.rb = c->layout.record_bytes;
     a.bulk = bulk_plan(cb == 16 && a.g.Up == a.g.U && c->aos_device, a.g.U, xm, a.umask);
+    if (c->binned && !c->levels && c->buffer == 0) {
+        a.keys_out = c->keys[0];     // free between binnings on the cell grid
+        a.kg = cell_grid(c->nc, c->sub, c->params.box);
+    }
     a.st = c->dstats;
     return cb == 16 ? launch_kd<uint4>(c, a) : launch_kd<uint2>(c, a);
 }

@@ -238,9 +238,11 @@ sph_status sph_create(const sph_aos_layout *layout, const sph_params *params, in
     return SPH_OK;
 }
 
-sph_status sph_bin_cells(sph_ctx *c, double cell_edge, int32_t reorder_aos)
+sph_status sph_bin_cells(sph_ctx *c, double cell_edge, int32_t flags)
 {
     if (!c || !(std::isfinite(cell_edge) || cell_edge <= 0.0)) return SPH_EINVAL;
+    if (flags & ~(SPH_BIN_REORDER | SPH_BIN_DRIFT_KEYS)) return SPH_EINVAL;
+    const bool reorder_aos = (flags & SPH_BIN_REORDER) != 0;
     if (reorder_aos && !c->aos_tmp) return SPH_ENOSPACE;
     double want = 2.0 * c->params.h_max;
     if (cell_edge > want) want = cell_edge;
@@ -265,7 +267,12 @@ sph_status sph_bin_cells(sph_ctx *c, double cell_edge, int32_t reorder_aos)
     c->binned = false;
     c->buffer = 0;
     c->levels = false;
-    if (run_binning(c, reorder_aos ? 1 : 0) != cudaSuccess) return SPH_ECUDA;
+    // the drift's keys serve when the caller vouches for the records and the
+    // grid is the one they were computed on
+    const bool dk = (flags & SPH_BIN_DRIFT_KEYS) && c->drift_keys && c->dk_sub == c->sub && c->dk_nc[0] == nc[0] &&
+                    c->dk_nc[1] == nc[1] && c->dk_nc[2] == nc[2];
+    c->drift_keys = false;
+    if (run_binning(c, reorder_aos ? 1 : 0, dk) != cudaSuccess) return SPH_ECUDA;
     if (run_items(c) != cudaSuccess) return SPH_ECUDA;
     c->binned = true;
     return SPH_OK;
@@ -338,6 +345,7 @@ sph_status sph_soa_to_aos_host(sph_ctx *c, void *host_aos, uint32_t fields, void
     if (stage_bytes < host_stage_bytes(c)) return SPH_ENOSPACE;
     if (!c->binned) return SPH_ESTATE;
     if ((c->valid & fields) != fields) return SPH_ESTATE;
+    if (fields & SPH_BIT(SPH_F_X)) c->drift_keys = false;
     if (run_soa_to_aos_host(c, (uint8_t *)host_aos, fields, (uint8_t *)host_stage, nthreads) != cudaSuccess)
         return SPH_ECUDA;
     return SPH_OK;
@@ -379,6 +387,20 @@ sph_status sph_force(sph_ctx *c)
     return SPH_OK;
 }
 
+namespace {
+
+// after a kick/drift on the cell grid: keys[0] holds the keys of the new
+// positions (run_kick_drift writes them there on that grid)
+void note_drift_keys(sph_ctx *c)
+{
+    if (!c->binned || c->levels || c->buffer != 0) return;
+    c->drift_keys = true;
+    for (int k = 0; k < 3; ++k) c->dk_nc[k] = c->nc[k];
+    c->dk_sub = c->sub;
+}
+
+}  // namespace
+
 sph_status sph_kick_drift(sph_ctx *c, double dt_kick, double dt_drift)
 {
     if (!c || !std::isfinite(dt_kick) || !std::isfinite(dt_drift)) return SPH_EINVAL;
@@ -386,7 +408,9 @@ sph_status sph_kick_drift(sph_ctx *c, double dt_kick, double dt_drift)
     const uint32_t need = SPH_BIT(SPH_F_V) | SPH_BIT(SPH_F_A) | SPH_BIT(SPH_F_U) |
                           SPH_BIT(SPH_F_DUDT);
     if ((c->valid & need) != need) return SPH_ESTATE;
+    c->drift_keys = false;
     if (run_kick_drift(c, dt_kick, dt_drift, 0) != cudaSuccess) return SPH_ECUDA;
+    note_drift_keys(c);
     c->valid &= ~SPH_BIT(SPH_F_X);   // SoA positions are stale after the drift
     return SPH_OK;
 }
@@ -400,7 +424,9 @@ sph_status sph_kick_drift_writeback(sph_ctx *c, double dt_kick, double dt_drift,
     if (!c->binned) return SPH_ESTATE;
     const uint32_t need = SPH_BIT(SPH_F_V) | SPH_BIT(SPH_F_A) | SPH_BIT(SPH_F_U) | SPH_BIT(SPH_F_DUDT) | fields;
     if ((c->valid & need) != need) return SPH_ESTATE;
+    c->drift_keys = false;
     if (run_kick_drift(c, dt_kick, dt_drift, fields) != cudaSuccess) return SPH_ECUDA;
+    note_drift_keys(c);
     c->valid &= ~(SPH_BIT(SPH_F_X) | SPH_BIT(SPH_F_V) | SPH_BIT(SPH_F_U));   // kicked values went to the AoS only
     return SPH_OK;
 }
@@ -414,6 +440,7 @@ sph_status sph_soa_to_aos(sph_ctx *c, uint32_t fields)
         if ((fields & SPH_BIT(f)) && c->layout.offset[f] < 0) return SPH_EINVAL;
     if (!c->binned) return SPH_ESTATE;
     if ((c->valid & fields) != fields) return SPH_ESTATE;
+    if (fields & SPH_BIT(SPH_F_X)) c->drift_keys = false;
     if (run_soa_to_aos(c, fields) != cudaSuccess) return SPH_ECUDA;
     return SPH_OK;
 }
@@ -425,6 +452,7 @@ sph_status sph_bin_buffers(sph_ctx *c, int32_t buffer_size)
         return SPH_EINVAL;
     c->valid = 0;
     c->binned = false;
+    c->drift_keys = false;
     c->buffer = buffer_size;
     c->levels = false;
     if (run_bin_buffers(c) != cudaSuccess) return SPH_ECUDA;
@@ -464,6 +492,7 @@ sph_status sph_bin_levels(sph_ctx *c, int32_t level_min, int32_t level_max, doub
     c->ncell = (int64_t)F * F * F;
     c->sub = 1;
     c->valid = 0;
+    c->drift_keys = false;
     c->binned = false;
     c->buffer = 0;
     c->levels = true;
@@ -710,6 +739,7 @@ sph_status sph_describe(const sph_ctx *c, sph_desc *out)
 sph_status sph_aos_upload(sph_ctx *c, const void *host, size_t bytes)
 {
     if (!c || !host || bytes > (size_t)c->n * (size_t)c->layout.record_bytes) return SPH_EINVAL;
+    c->drift_keys = false;
     if (cudaMemcpyAsync(c->aos, host, bytes, cudaMemcpyDefault, c->stream) != cudaSuccess)
         return SPH_ECUDA;
     return SPH_OK;

@@ -321,6 +321,12 @@ struct sph_ctx {
     int64_t ncell = 0;
     int sub = 1;                  // sub-cells per cell edge of the last binning
     bool binned = false;
+    // keys[0] holds the cell key of every record's position as the last
+    // kick/drift wrote it, on the grid dk_nc / dk_sub (sph_bin_cells may
+    // use them when the caller asks)
+    bool drift_keys = false;
+    int32_t dk_nc[3] = {0, 0, 0};
+    int32_t dk_sub = 0;
     int32_t buffer = 0;           // buffer mode: records taken in buffers of this size (0: cell lists)
     bool levels = false;          // level mode: Morton order over a hierarchy of grids
     bool levels_fixed = false;    // level mode: the density fixed the levels (every h within its cap)
@@ -367,7 +373,7 @@ struct sph_ctx {
 
 namespace sph {
 // launch wrappers (each returns the first CUDA error, or cudaSuccess)
-cudaError_t run_binning(sph_ctx *c, int reorder);
+cudaError_t run_binning(sph_ctx *c, int reorder, bool drift_keys);
 cudaError_t run_items(sph_ctx *c);
 cudaError_t run_aos_to_soa(sph_ctx *c, uint32_t fields);
 cudaError_t run_soa_to_aos(sph_ctx *c, uint32_t fields);
