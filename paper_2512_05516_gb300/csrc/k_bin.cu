@@ -135,19 +135,31 @@ __global__ void __launch_bounds__(kBinThreads) k_place(const int32_t *key, int64
 
 // A slot whose successor in the same key range holds a smaller particle
 // index marks that key (plain stores: every writer stores 1).  mark[] is zero
-// on entry (the cursors after k_place).
+// on entry (the cursors after k_place).  A thread checks four slots, loaded
+// as one 16-byte vector per array.
 __global__ void __launch_bounds__(kBinThreads) k_inversions(const int32_t *perm, const int32_t *skey, int64_t n,
                                                           int32_t *mark)
 {
-    const int64_t p0 = (int64_t)blockIdx.x * (kBinThreads * kBinU) + threadIdx.x;
-#pragma unroll
-    for (int u = 0; u < kBinU; ++u) {
-        const int64_t p = p0 + u * kBinThreads;
-        if (p + 1 < n) {
-            const int32_t k = skey[p];
-            if (k == skey[p + 1] && perm[p] > perm[p + 1]) mark[k] = 1;
+    const int64_t p = 4 * ((int64_t)blockIdx.x * kBinThreads + threadIdx.x);
+    if (p + 1 >= n) return;
+    int32_t pv[5], kv[5];
+    int m;
+    if (p + 4 < n) {
+        const int4 a = *reinterpret_cast<const int4 *>(perm + p);
+        const int4 b = *reinterpret_cast<const int4 *>(skey + p);
+        pv[0] = a.x, pv[1] = a.y, pv[2] = a.z, pv[3] = a.w, pv[4] = perm[p + 4];
+        kv[0] = b.x, kv[1] = b.y, kv[2] = b.z, kv[3] = b.w, kv[4] = skey[p + 4];
+        m = 4;
+    } else {
+        m = (int)(n - 1 - p);
+        for (int j = 0; j <= m; ++j) {
+            pv[j] = perm[p + j];
+            kv[j] = skey[p + j];
         }
     }
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        if (j < m && kv[j] == kv[j + 1] && pv[j] > pv[j + 1]) mark[kv[j]] = 1;
 }
 
 // ascending bitonic sort of one value per lane
@@ -475,10 +487,16 @@ __global__ void k_items_count(const int32_t *cell_start, int64_t ncell, int s3, 
         cnt = cell_start[(c + 1) * s3] - cell_start[c * s3];
         tmp[c] = (cnt + block - 1) / block;
     }
-    // one atomic per warp
+    // one atomic per block
+    __shared__ int32_t wmax[8];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) cnt = max(cnt, __shfl_xor_sync(0xffffffffu, cnt, o));
-    if ((threadIdx.x & 31) == 0 && cnt > 0) atomicMax(&st->max_occ, cnt);
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) cnt = max(cnt, wmax[w]);
+        if (cnt > 0) atomicMax(&st->max_occ, cnt);
+    }
 }
 
 __global__ void k_items_fill(const int32_t *cell_start, const int32_t *item_off, int64_t ncell, int s3, int block,
@@ -826,7 +844,7 @@ cudaError_t run_binning(sph_ctx *c, int reorder, bool drift_keys)
         // ranges to order and vals[0] is the radix scratch of long ranges
         k_place<<<blocks_for(n, kBinThreads * kBinU), kBinThreads, 0, s>>>(c->keys[0], n, c->cell_start, c->cell_count, c->vals[1],
                                                    c->keys[1]);
-        k_inversions<<<blocks_for(n, kBinThreads * kBinU), kBinThreads, 0, s>>>(c->vals[1], c->keys[1], n, c->cell_count);
+        k_inversions<<<blocks_for((n + 3) / 4, kBinThreads), kBinThreads, 0, s>>>(c->vals[1], c->keys[1], n, c->cell_count);
         k_seg_order<<<(unsigned)(c->sm_count * 4), 32 * kSegWarps, 0, s>>>(c->cell_start, c->cell_count, nkeys,
                                                                           c->vals[1], c->vals[0], n);
         c->launches += 3;
