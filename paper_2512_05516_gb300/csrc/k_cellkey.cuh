@@ -83,14 +83,16 @@ __device__ __forceinline__ int32_t cell_coord_fast(double x, float ih, float il,
 
 // The key of position (x0, x1, x2): fine coordinates f_d on the grid of
 // sub-cells, cell f / s, sub-cell f % s, key cell s^3 + (s_x + s (s_y + s s_z)).
+// s is 1 or 2, so the divisions are shifts.
+static_assert(kMaxSub <= 2, "cell_key takes s = 1 or 2");
 __device__ __forceinline__ int32_t cell_key(const CellGrid &g, double x0, double x1, double x2)
 {
-    const int32_t S = g.sub;
+    const int32_t S = g.sub, lg = S - 1;
     const int32_t fx = cell_coord_fast(x0, g.invh[0], g.invl[0], g.inv[0], g.nc[0] * S);
     const int32_t fy = cell_coord_fast(x1, g.invh[1], g.invl[1], g.inv[1], g.nc[1] * S);
     const int32_t fz = cell_coord_fast(x2, g.invh[2], g.invl[2], g.inv[2], g.nc[2] * S);
-    const int32_t cell = fx / S + g.nc[0] * (fy / S + g.nc[1] * (fz / S));
-    return cell * S * S * S + (fx % S + S * (fy % S + S * (fz % S)));
+    const int32_t cell = (fx >> lg) + g.nc[0] * ((fy >> lg) + g.nc[1] * (fz >> lg));
+    return (cell << (3 * lg)) + ((fx & lg) + ((fy & lg) << lg) + ((fz & lg) << (2 * lg)));
 }
 
 }  // namespace sph
