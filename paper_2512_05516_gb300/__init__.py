@@ -54,8 +54,8 @@ def sph_create(layout, params, n, ncell_max, ws_flags, d_aos, d_workspace, works
     return st, out
 
 
-def sph_bin_cells(ctx, cell_edge: float, reorder_aos: int) -> int:
-    return _lib.sph_bin_cells(ctx, float(cell_edge), int(reorder_aos))
+def sph_bin_cells(ctx, cell_edge: float, flags: int) -> int:
+    return _lib.sph_bin_cells(ctx, float(cell_edge), int(flags))
 
 
 def sph_aos_to_soa(ctx, fields: int, prec) -> int:

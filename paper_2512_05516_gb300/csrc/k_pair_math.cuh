@@ -74,13 +74,13 @@ __device__ __forceinline__ void force_pair(float &ax, float &ay, float &az, floa
     const float gw = kSigma * hb2 * hb2 * dw * rinv;   // grad_i W = d * gw
     const float vx = vxi - qb.x, vy = vyi - qb.y, vz = vzi - qb.z;
     const float vdotr = fmaf(vx, dx, fmaf(vy, dy, vz * dz));
-    float visc = 0.0f;
-    if (vdotr < 0.0f) {
-        const float mu = __fdividef(hb * vdotr, fmaf(eps * hb, hb, r2));
-        const float cbar = 0.5f * (ci + qc.z);
-        const float rbar = 0.5f * (rhoi + qc.y);
-        visc = __fdividef(fmaf(-alpha * cbar, mu, beta * mu * mu), rbar);
-    }
+    // Monaghan viscosity, branch-free: a receding pair (v_ij . d >= 0) gets
+    // mu = 0 and so visc = 0 exactly (a branch costs more here: the lanes of
+    // a warp disagree on it)
+    const float mu = __fdividef(hb * fminf(vdotr, 0.0f), fmaf(eps * hb, hb, r2));
+    const float cbar = 0.5f * (ci + qc.z);
+    const float rbar = 0.5f * (rhoi + qc.y);
+    const float visc = __fdividef(fmaf(-alpha * cbar, mu, beta * mu * mu), rbar);
     const float fac = qb.w * (Pr2i + qc.x + visc) * gw;
     ax = fmaf(-fac, dx, ax);
     ay = fmaf(-fac, dy, ay);
