@@ -140,7 +140,7 @@ typedef struct {
 #define SPH_FLAG_PLAIN_SUM 1   /* density sum without compensation (default: Neumaier) */
 
 /* workspace options */
-#define SPH_WS_REORDER 1       /* reserve room for sph_bin_cells(reorder_aos = 1) */
+#define SPH_WS_REORDER 1       /* reserve room for sph_bin_cells(SPH_BIN_REORDER) */
 #define SPH_WS_LEVELS 2        /* reserve room for the level hierarchy (sph_bin_levels) */
 
 /* Counters accumulated on the device since creation or sph_reset_stats. */
