@@ -148,3 +148,14 @@ def test_suggest_scale_puts_fp16_values_in_range(sph):
     assert sph.suggest_scale(0.0, "fp16") == 0
     assert sph.suggest_scale(1e-300, "fp16") == sph.SCALE_MAX_EXP
     assert sph.scale_array({"m": 5, "u": -3}) == [0, 0, 0, 5, 0, 0, -3, 0, 0, 0]
+
+
+def test_binding_constants_match_the_header(sph):
+    src = open(HEADER).read()
+    defs = dict((k, int(v)) for k, v in re.findall(r"#define (SPH_[A-Z_0-9]+)\s+(-?\d+)\b", src))
+    from paper_2512_05516_gb300 import _capi
+    assert defs["SPH_BIN_REORDER"] == _capi.BIN_REORDER
+    assert defs["SPH_BIN_DRIFT_KEYS"] == _capi.BIN_DRIFT_KEYS
+    assert defs["SPH_WS_REORDER"] == _capi.WS_REORDER
+    assert defs["SPH_WS_LEVELS"] == _capi.WS_LEVELS
+    assert _capi.sph_tuning.block_threads_force.offset == C.sizeof(_capi.sph_tuning) - 4
