@@ -1359,7 +1359,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_force(ForceArgs a)
                 // evaluates them; repeated over the stage
                 for (int s0 = 0; s0 < len; s0 += kForceCap) {
                     const int s1 = min(s0 + kForceCap, len);
-                    int nl = 0;
+                    uint8_t *lp = lst + lane;
                     constexpr int LB = 8;
                     static_assert(kForceCap % LB == 0 && LB <= kForcePad, "force test batches");
                     for (int e0 = s0; e0 < s1; e0 += LB) {
@@ -1374,10 +1374,13 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_force(ForceArgs a)
                         }
 #pragma unroll
                         for (int u = 0; u < LB; ++u) {
-                            lst[nl * 32 + lane] = (uint8_t)(e0 + u - s0); // nl <= kForceCap: slot kForceCap is scratch
-                            nl += in[u] ? 1 : 0;
+                            // a range of kForceCap candidates advances lp at
+                            // most kForceCap rows: row kForceCap is scratch
+                            *lp = (uint8_t)(e0 + u - s0);
+                            lp += in[u] ? 32 : 0;
                         }
                     }
+                    const int nl = (int)(lp - (lst + lane)) >> 5;
                     // every listed pair is evaluated: the self pair and
                     // coincident pairs (r = 0) contribute exactly zero (the
                     // spline derivative vanishes at q = 0 and v_ij . d = 0), so
