@@ -184,7 +184,10 @@ typedef struct {
                                     stream that fills the per-lane lists (>= 32); in level mode
                                     an item whose box gathers more than 8 x stage_density
                                     candidates is deferred to the per-target pass */
-    int32_t stage_force;         /* neighbour candidates staged per warp, force kernel (>= 32) */
+    int32_t stage_force;         /* neighbour candidates staged per warp, force kernel (>= 32); in
+                                    level mode an item whose candidate streams hold more than
+                                    64 x stage_force candidates is deferred to the per-target
+                                    pass */
     int32_t subcells;            /* sub-cells per cell edge used to order particles, 1 or 2
                                     (default 2); takes effect at the next sph_bin_cells */
     int32_t item_order;          /* order of the pair-kernel work queue, set at sph_bin_cells:

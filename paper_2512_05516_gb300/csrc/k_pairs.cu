@@ -82,6 +82,13 @@ struct Common {
     int fine_n;                      // cells per axis at the finest level
     float fine_edge[3];
     int32_t *defer;                  // slots of the targets gathered one by one (k_density_one)
+    // the per-target passes run twice: one warp per target over `defer`,
+    // sending a target whose stream holds more than heavy_at candidates on
+    // to `heavy` (phase 0); then a block of warps per target over `heavy`
+    // (phase 1)
+    int32_t *heavy;
+    int heavy_at;
+    int one_phase;
     // level force: the slots of every level in Morton order, one list after
     // the other (level l at [lstart[l], lstart[l+1])), their keys, and the
     // largest h of each level's particles
@@ -147,24 +154,32 @@ static_assert(kForceCap <= 256, "force list entries are byte offsets into a rang
 // pair tests run whole batches of 8 without bounds checks
 constexpr int kForcePad = 8;
 static_assert((32 * kDensSlots * sizeof(float)) % 16 == 0, "list size must keep 16-byte alignment");
-// level force: an item whose candidate stream is longer than this is
-// gathered target by target (k_force_one)
-constexpr int kForceDefer = 8192;
+// level force: an item whose candidate stream is longer than this many
+// stages (8192 candidates at the default stage of 128) is gathered target by
+// target (k_force_one)
+constexpr int kForceDeferStages = 64;
 // the level kernel adds the 27 x 9 run boundaries of its item's stencil
 constexpr size_t kBndBytes = (27 * 9 * sizeof(int) + 15) / 16 * 16;
+// warps per block of the level hierarchy's per-target passes (one target per
+// block), fewer when their stages do not fit the shared memory
+#ifndef SPH_ONE_WARPS
+#define SPH_ONE_WARPS 4
+#endif
+constexpr int kOneWarps = SPH_ONE_WARPS;
+// a target goes from the one-warp pass to the block-wide one when its stream
+// holds more candidates than one warp's stage (density) or than this many
+// force stages
+#ifndef SPH_FORCE_HEAVY_STAGES
+#define SPH_FORCE_HEAVY_STAGES 64
+#endif
+constexpr int kForceHeavyStages = SPH_FORCE_HEAVY_STAGES;
+static_assert(kOneWarps >= 1 && kOneWarps * 32 <= kMaxBlock, "per-target block");
 
 __device__ __forceinline__ int pop_item(DevStats *st, int lane)
 {
     int it = 0;
     if (lane == 0) it = (int)atomicAdd(&st->queue, 1u);
     return __shfl_sync(FULL, it, 0);
-}
-
-__device__ __forceinline__ unsigned pop_deferred(DevStats *st, int lane)
-{
-    unsigned j = 0;
-    if (lane == 0) j = atomicAdd(&st->defer_q, 1u);
-    return __shfl_sync(FULL, j, 0);
 }
 
 __device__ __forceinline__ float warp_max(float v)
@@ -939,20 +954,44 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
     if (my_err) set_error(c.st, my_err);
 }
 
+// A warp's share of a candidate stream of `total` positions when the W warps
+// of a block split it: [g0, g1), contiguous, in stream order.
+__device__ __forceinline__ void stream_slice(int total, int warp, int W, int &g0, int &g1)
+{
+    g0 = (int)(((long long)total * warp) / W);
+    g1 = (int)(((long long)total * (warp + 1)) / W);
+}
+
+// Sum of the W warps' partials v[w] (in w order, so every thread gets the
+// same bits); `red` is block-shared scratch of kMaxBlock / 32 entries.
+__device__ __forceinline__ float block_sum_ordered(float v, float *red, int warp, int lane, int W)
+{
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    float t = 0.0f;
+    for (int w = 0; w < W; ++w) t += red[w];
+    __syncthreads();
+    return t;
+}
+
 // The level kernel's per-target pass: every target of the per-target list
-// (k_density deferred it) is gathered by one whole warp.  Its stream is pruned
-// to its own reach with the children of the stencil cells; the lanes take its
-// candidates in turn and the partial sums meet in a butterfly, so every lane
-// holds the same bits and runs the same Newton steps.  Few warps are busy
-// here and their scans wait on global loads, so staging keeps 8 batches of
-// 32 candidates in flight (4 in k_density).  Persistent warps pop targets
-// from the list; the outputs, promotion and counters follow k_density's
-// epilogue.
+// (k_density deferred it) is gathered by one whole block of W warps.  Its
+// stream is pruned to its own reach with the children of the stencil cells
+// and split into W contiguous slices, one per warp; a warp's lanes take its
+// slice's candidates in turn, the lanes' partial sums meet in a butterfly and
+// the warps' in stream order, so every thread holds the same bits and runs
+// the same Newton steps.  Heavy targets (thousands of candidates: coarse
+// particles next to a cluster) are what this pass gathers, and few are left
+// at its end, so each gets W warps.  Staging keeps 8 batches of 32
+// candidates in flight (4 in k_density).  Persistent blocks pop targets from
+// the list; the outputs, promotion and counters follow k_density's epilogue.
 __global__ void __launch_bounds__(kMaxBlock, 1) k_density_one(DensityArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ float red[kMaxBlock / 32];
+    __shared__ unsigned next;
     const Common &c = a.c;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
     float4 *sj = reinterpret_cast<float4 *>(smem + warp * density_warp_bytes(c.cap, true));
     // no per-lane lists here: the stage extends over their space
     const int cap1 = c.cap + 32 * kDensSlots * (int)sizeof(float) / (int)sizeof(float4);
@@ -960,9 +999,16 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density_one(DensityArgs a)
     int *bnd = reinterpret_cast<int *>(&tab + 1);
     unsigned long long my_pairs = 0, my_tests = 0, my_done = 0, my_prom = 0;
     unsigned my_err = 0;
-    const unsigned nd = c.st->defer_n;
-    for (unsigned j = pop_deferred(c.st, lane); j < nd; j = pop_deferred(c.st, lane)) {
-        const int64_t k = c.defer[j];
+    const int32_t *list = c.one_phase ? c.heavy : c.defer;
+    unsigned *head = c.one_phase ? &c.st->heavy_q : &c.st->defer_q;
+    const unsigned nd = c.one_phase ? c.st->heavy_n : c.st->defer_n;
+    for (;;) {
+        if (threadIdx.x == 0) next = atomicAdd(head, 1u);
+        __syncthreads();
+        const unsigned j = next;
+        __syncthreads();
+        if (j >= nd) break;
+        const int64_t k = list[j];
         const uint32_t key = (uint32_t)__ldg(c.mkey + k);
         const int cell = (int)(key >> (3 * c.lvl_dn));
         const int3 org = make_int3((int)(morton_compact((uint32_t)cell) << c.lvl_dn),
@@ -973,7 +1019,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density_one(DensityArgs a)
         const float xt = p.x, yt = p.y, zt = p.z, mt = p.w;
         float ht = ld_val(c.h.p[0], c.h.fmt, k) * c.h.dec;
         bool clamped = false;
-        unsigned lf = 0;           // the target's SPH_PFLAG_* bits (the same in every lane)
+        unsigned lf = 0;           // the target's SPH_PFLAG_* bits (the same in every thread)
         if (!(ht > 0.0f) || !isfinite(ht)) {
             ht = a.h_cap;
             lf |= SPH_PFLAG_NONFINITE;
@@ -985,16 +1031,24 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density_one(DensityArgs a)
         const Box pb{{xt, yt, zt}, {xt, yt, zt}};
         float hs = 0.0f, rt = 0.0f, dt = 0.0f;
         int Tt = 0, nt = 0;
-        bool fit_t = false;
+        bool fit_t = false;        // every warp's slice of the stream sits in its stage
+        bool sent = false;         // passed on to the block-wide pass
         unsigned long long pt = 0;
         for (int pass = 0; pass < a.npass; ++pass) {
             if (pass == 0 || (fit_t && ht > hs)) {
                 hs = fminf(ht * (1.0f + kStageSkin), a.h_cap);
                 const float R2p = 4.0f * hs * hs;
                 const int tot = lvl_table(c, bnd, pb, R2p, tab, lane);
-                Cursor pc{0, 0};
-                Tt = stage_density<true, 8>(c, a.pD, tab, tot, pb, R2p, sj, cap1, pc, lane, org);
-                fit_t = pc.g >= tot;
+                if (pass == 0 && c.heavy_at > 0 && tot > c.heavy_at) {
+                    if (threadIdx.x == 0) c.heavy[atomicAdd(&c.st->heavy_n, 1u)] = (int32_t)k;
+                    sent = true;
+                    break;
+                }
+                int g0, g1;
+                stream_slice(tot, warp, W, g0, g1);
+                Cursor pc{g0, g0 < g1 ? advance(tab, tab.nk, 0, g0) : 0};
+                Tt = stage_density<true, 8>(c, a.pD, tab, g1, pb, R2p, sj, cap1, pc, lane, org);
+                fit_t = __syncthreads_and(pc.g >= g1) != 0;
             }
             const float h2x4 = 4.0f * ht * ht;
             const float hinv = 1.0f / ht;
@@ -1005,16 +1059,18 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density_one(DensityArgs a)
                     dens_acc_rt(acc, pair_r(xt, yt, zt, sj[e]), hinv, sj[e].w, a.plain_sum, deriv);
                 my_tests += (unsigned long long)max(0, (Tt - lane + 31) >> 5);
             } else {
-                // more than the stage within the target's own reach: stream it
+                // more than the stages within the target's own reach: stream it
                 const int tot = lvl_table(c, bnd, pb, h2x4, tab, lane);
-                Cursor sc{0, 0};
-                do {
-                    const int len = stage_density<true, 8>(c, a.pD, tab, tot, pb, h2x4, sj, cap1, sc, lane, org);
+                int g0, g1;
+                stream_slice(tot, warp, W, g0, g1);
+                Cursor sc{g0, g0 < g1 ? advance(tab, tab.nk, 0, g0) : 0};
+                while (sc.g < g1) {
+                    const int len = stage_density<true, 8>(c, a.pD, tab, g1, pb, h2x4, sj, cap1, sc, lane, org);
                     for (int e = lane; e < len; e += 32)
                         dens_acc_rt(acc, pair_r(xt, yt, zt, sj[e]), hinv, sj[e].w, a.plain_sum, deriv);
                     my_tests += (unsigned long long)max(0, (len - lane + 31) >> 5);
                     __syncwarp();
-                } while (sc.g < tot);
+                }
             }
             float sum = acc.s - acc.c, dsum = acc.d;
             int nn = (int)acc.n;
@@ -1023,6 +1079,11 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density_one(DensityArgs a)
                 sum += __shfl_xor_sync(FULL, sum, o);
                 dsum += __shfl_xor_sync(FULL, dsum, o);
                 nn += __shfl_xor_sync(FULL, nn, o);
+            }
+            if (W > 1) {
+                sum = block_sum_ordered(sum, red, warp, lane, W);
+                dsum = block_sum_ordered(dsum, red, warp, lane, W);
+                nn = (int)block_sum_ordered((float)nn, red, warp, lane, W);   // exact: far below 2^24
             }
             const float h3inv = hinv * hinv * hinv;
             rt = kSigma * h3inv * sum;
@@ -1044,7 +1105,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density_one(DensityArgs a)
                 ht = hn;
             }
         }
-        if (lane != 0) continue;
+        if (sent || threadIdx.x != 0) continue;
         if (clamped && a.promote) {
             a.level[k] = (int8_t)(a.lvl - 1);
             ++my_prom;
@@ -1329,7 +1390,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_force(ForceArgs a)
         const float hw = warp_max(ok ? hi : 0.0f);
         const int total = kLvl ? lvl_force_table(c, cell, a.lvl, org, box, hw, tab, lane)
                                : build_stream(c, cell, box, 0.0f, tab, lane, a.key_hmax, hw);
-        if (kLvl && total > kForceDefer) {
+        if (kLvl && total > kForceDeferStages * c.cap) {
             // A long stream: coarse targets spread over their cell next to a
             // dense cluster, whose box takes in the cluster's fine lists.
             // Each target goes to the per-target list instead and is gathered
@@ -1420,14 +1481,18 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_force(ForceArgs a)
 }
 
 // The level force's per-target pass: every target that k_force<true>
-// deferred is gathered by one whole warp.  Its K level streams are pruned to
-// its own reach (h_i + h_l'), the lanes evaluate its staged candidates in
-// turn, and the partial sums meet in a butterfly.  Lane 0 writes.
+// deferred is gathered by one whole block of W warps.  Its K level streams
+// are pruned to its own reach (h_i + h_l') and split into W contiguous
+// slices, one per warp; a warp's lanes evaluate its slice's staged
+// candidates in turn, the lanes' partial sums meet in a butterfly and the
+// warps' in stream order.  Thread 0 writes.
 __global__ void __launch_bounds__(kMaxBlock, 1) k_force_one(ForceArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ float red[kMaxBlock / 32];
+    __shared__ unsigned next;
     const Common &c = a.c;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
     float4 *sA = reinterpret_cast<float4 *>(smem + warp * force_warp_bytes(c.cap));
     float4 *sB = sA + c.cap + kForcePad;
     float4 *sC = sB + c.cap + kForcePad;
@@ -1435,9 +1500,16 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_force_one(ForceArgs a)
     Tab &tab = *reinterpret_cast<Tab *>(lst + 32 * kForceSlots);
     unsigned long long my_pairs = 0, my_tests = 0;
     unsigned my_err = 0;
-    const unsigned nd = c.st->defer_n;
-    for (unsigned j = pop_deferred(c.st, lane); j < nd; j = pop_deferred(c.st, lane)) {
-        const int k = c.defer[j];
+    const int32_t *list = c.one_phase ? c.heavy : c.defer;
+    unsigned *head = c.one_phase ? &c.st->heavy_q : &c.st->defer_q;
+    const unsigned nd = c.one_phase ? c.st->heavy_n : c.st->defer_n;
+    for (;;) {
+        if (threadIdx.x == 0) next = atomicAdd(head, 1u);
+        __syncthreads();
+        const unsigned j = next;
+        __syncthreads();
+        if (j >= nd) break;
+        const int k = list[j];
         const uint32_t key = (uint32_t)__ldg(c.mkey + k);
         const int cell = (int)(key >> (3 * c.lvl_dn));
         const int3 org = make_int3((int)(morton_compact((uint32_t)cell) << c.lvl_dn),
@@ -1447,13 +1519,19 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_force_one(ForceArgs a)
         const float4 qb = __ldg(a.pB + k), qcv = __ldg(a.pC + k);
         const float xi = qa.x, yi = qa.y, zi = qa.z, hi = qa.w;
         const Box pb{{xi, yi, zi}, {xi, yi, zi}};
-        if (hi > a.h_cap && lane == 0) my_err |= SPH_ERR_HCAP;
         const int total = lvl_force_table(c, cell, a.lvl, org, pb, hi, tab, lane);
+        if (c.heavy_at > 0 && total > c.heavy_at) {
+            if (threadIdx.x == 0) c.heavy[atomicAdd(&c.st->heavy_n, 1u)] = k;
+            continue;
+        }
+        if (hi > a.h_cap && threadIdx.x == 0) my_err |= SPH_ERR_HCAP;
+        int g0, g1;
+        stream_slice(total, warp, W, g0, g1);
         float ax = 0.f, ay = 0.f, az = 0.f, du = 0.f;
         int cnt = 0;
-        Cursor cur{0, 0};
-        do {
-            const int len = stage_force<true>(a, tab, total, pb, hi, sA, sB, sC, c.cap, cur, lane, my_err, org);
+        Cursor cur{g0, g0 < g1 ? advance(tab, tab.nk, 0, g0) : 0};
+        while (cur.g < g1) {
+            const int len = stage_force<true>(a, tab, g1, pb, hi, sA, sB, sC, c.cap, cur, lane, my_err, org);
             my_tests += (unsigned long long)max(0, (len - lane + 31) >> 5);
             for (int p = lane; p < len; p += 32) {
                 const float4 qc = sC[p];
@@ -1469,7 +1547,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_force_one(ForceArgs a)
                 }
             }
             __syncwarp();
-        } while (cur.g < total);
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             ax += __shfl_xor_sync(FULL, ax, o);
@@ -1478,7 +1556,14 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_force_one(ForceArgs a)
             du += __shfl_xor_sync(FULL, du, o);
             cnt += __shfl_xor_sync(FULL, cnt, o);
         }
-        if (lane == 0) {
+        if (W > 1) {
+            ax = block_sum_ordered(ax, red, warp, lane, W);
+            ay = block_sum_ordered(ay, red, warp, lane, W);
+            az = block_sum_ordered(az, red, warp, lane, W);
+            du = block_sum_ordered(du, red, warp, lane, W);
+            cnt = (int)block_sum_ordered((float)cnt, red, warp, lane, W);   // exact: far below 2^24
+        }
+        if (threadIdx.x == 0) {
             if (!isfinite(ax) || !isfinite(ay) || !isfinite(az) || !isfinite(du)) my_err |= SPH_ERR_NONFINITE;
             a.a[0][k] = ax;
             a.a[1][k] = ay;
@@ -1686,6 +1771,9 @@ Common make_common(sph_ctx *c, int cap)
     for (int k = 0; k < 3; ++k) m.fine_edge[k] = 0.0f;
     m.defer = nullptr;
     m.plist = m.pkey = m.lstart = nullptr;
+    m.heavy = nullptr;
+    m.heavy_at = 0;
+    m.one_phase = 0;
     m.lvl_min = m.lvl_max = 0;
     for (int l = 0; l <= kLevelMax; ++l) m.lcap[l] = 0.0f;
     m.st = c->dstats;
@@ -1739,6 +1827,24 @@ cudaError_t launch_persistent(sph_ctx *c, K kernel, const A &args, size_t smem, 
     kernel<<<(unsigned)lc.grid, block, smem, c->stream>>>(args);
     c->launches += 1;
     return cudaGetLastError();
+}
+
+// The level hierarchy's per-target passes of one level: one warp per target
+// over the deferred list, passing targets whose stream holds more than
+// heavy_at candidates on to a block of w warps per target.
+template <typename K, typename A>
+cudaError_t run_per_target(sph_ctx *c, K kernel, const A &args, size_t smem_1, size_t smem_w, int w, int heavy_at,
+                           LaunchCache &lc_1, LaunchCache &lc_w)
+{
+    A a = args;
+    a.c.heavy = c->tscan;      // scan scratch, free while a level's kernels run
+    a.c.one_phase = 0;
+    a.c.heavy_at = w > 1 ? heavy_at : 0;
+    cudaError_t e = launch_persistent(c, kernel, a, smem_1, lc_1, 32);
+    if (e != cudaSuccess || w == 1) return e;
+    a.c.one_phase = 1;
+    a.c.heavy_at = 0;
+    return launch_persistent(c, kernel, a, smem_w, lc_w, 32 * w);
 }
 
 }  // namespace
@@ -1842,6 +1948,12 @@ cudaError_t run_density_levels(sph_ctx *c, int newton_steps)
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t smem = density_smem_bytes(c->tuning.block_threads, a.c.cap, true);
+    int w_one = kOneWarps;
+    while (w_one > 1 && density_smem_bytes(32 * w_one, a.c.cap, true) + 256 > c->smem_optin) --w_one;
+    const size_t smem_one = density_smem_bytes(32 * w_one, a.c.cap, true);
+    const size_t smem_1 = density_smem_bytes(32, a.c.cap, true);
+    // one warp's stage holds cap + the per-lane list space (k_density_one)
+    const int heavy_dens = a.c.cap + 32 * kDensSlots * (int)sizeof(float) / (int)sizeof(float4);
     for (int l = c->lvl_max; l >= c->lvl_min; --l) {
         if ((e = run_level_items(c, l)) != cudaSuccess) return e;
         double cap = std::ldexp(c->params.box[0], -l);
@@ -1856,9 +1968,11 @@ cudaError_t run_density_levels(sph_ctx *c, int newton_steps)
         a.h_cap = (float)cap;
         a.lvl = l;
         a.promote = l > c->lvl_min;
-        if ((e = cudaMemsetAsync(&c->dstats->defer_n, 0, 2 * sizeof(unsigned), c->stream)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(&c->dstats->defer_n, 0, 4 * sizeof(unsigned), c->stream)) != cudaSuccess) return e;
         if ((e = launch_persistent(c, k_density<true>, a, smem, c->lc_density_lv, c->tuning.block_threads)) != cudaSuccess) return e;
-        if ((e = launch_persistent(c, k_density_one, a, smem, c->lc_density_one, c->tuning.block_threads)) != cudaSuccess) return e;
+        if ((e = run_per_target(c, k_density_one, a, smem_1, smem_one, w_one, heavy_dens, c->lc_density_one,
+                                c->lc_density_blk)) != cudaSuccess)
+            return e;
     }
     if (a.write_h && h_packed) return run_pack(c, c->stage, SPH_F_H);
     return cudaSuccess;
@@ -1951,15 +2065,21 @@ cudaError_t run_force_levels(sph_ctx *c)
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = run_level_lists(c, plist, pkey)) != cudaSuccess) return e;
     const size_t smem = force_smem_bytes(c->tuning.block_threads_force, a.c.cap);
+    int w_one = kOneWarps;
+    while (w_one > 1 && force_smem_bytes(32 * w_one, a.c.cap) + 256 > c->smem_optin) --w_one;
+    const size_t smem_one = force_smem_bytes(32 * w_one, a.c.cap);
+    const size_t smem_1 = force_smem_bytes(32, a.c.cap);
     for (int l = c->lvl_max; l >= c->lvl_min; --l) {
         if ((e = run_level_items(c, l)) != cudaSuccess) return e;
         for (int k = 0; k < 3; ++k) a.c.edge[k] = (float)std::ldexp(c->params.box[k], -l);
         a.c.lvl_dn = c->lvl_max - l;
         a.c.lvl_n = 1 << l;
         a.lvl = l;
-        if ((e = cudaMemsetAsync(&c->dstats->defer_n, 0, 2 * sizeof(unsigned), c->stream)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(&c->dstats->defer_n, 0, 4 * sizeof(unsigned), c->stream)) != cudaSuccess) return e;
         if ((e = launch_persistent(c, k_force<true>, a, smem, c->lc_force_lv, c->tuning.block_threads_force)) != cudaSuccess) return e;
-        if ((e = launch_persistent(c, k_force_one, a, smem, c->lc_force_one, c->tuning.block_threads_force)) != cudaSuccess) return e;
+        if ((e = run_per_target(c, k_force_one, a, smem_1, smem_one, w_one, kForceHeavyStages * a.c.cap,
+                                c->lc_force_one, c->lc_force_blk)) != cudaSuccess)
+            return e;
     }
     return cudaSuccess;
 }

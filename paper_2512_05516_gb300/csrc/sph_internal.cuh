@@ -70,7 +70,9 @@ struct DevStats {
     int max_occ;                 // particles in the fullest cell
     unsigned int defer_n;        // level hierarchy: targets gathered one by one, and their queue head
     unsigned int defer_q;
-    int pad[4];
+    unsigned int heavy_n;        // ... and those of them sent on to the block-wide pass
+    unsigned int heavy_q;
+    int pad[2];
     // level hierarchy: per level, the particles computed there (final) and
     // those moved from it to the next coarser level
     unsigned long long lvl_done[kLevelMax + 1];
@@ -333,6 +335,7 @@ struct sph_ctx {
     int32_t lvl_min = 0, lvl_max = 0;
     sph::LaunchCache lc_density, lc_force;   // launch shapes of the persistent pair kernels
     sph::LaunchCache lc_density_lv, lc_density_one, lc_force_lv, lc_force_one;   // ... and over the level hierarchy
+    sph::LaunchCache lc_density_blk, lc_force_blk;   // ... the block-wide per-target passes
     int sorted_buf = 0;          // which ping-pong buffer holds the sorted keys/values
 
     // workspace arrays
