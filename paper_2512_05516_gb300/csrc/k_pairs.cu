@@ -89,10 +89,10 @@ struct Common {
     int32_t *heavy;
     int heavy_at;
     int one_phase;
-    // level force: the slots of every level in Morton order, one list after
-    // the other (level l at [lstart[l], lstart[l+1])), their keys, and the
-    // largest h of each level's particles
-    const int32_t *plist, *pkey, *lstart;
+    // level force: the finest-cell keys of the per-level lists (every
+    // level's slots in Morton order, one list after the other: level l at
+    // [lstart[l], lstart[l+1])), and the largest h of each level's particles
+    const int32_t *pkey, *lstart;
     int lvl_min, lvl_max;
     float lcap[kLevelMax + 1];
 };
@@ -131,6 +131,10 @@ struct ForceArgs {
     const float4 *pA;                // (x, y, z, h), positions cell-relative
     const float4 *pB;                // (vx, vy, vz, m)
     const float4 *pC;                // (P / rho^2, rho, c, 0)
+    // level force: the same three arrays in the order of the per-level
+    // lists (entry i holds slot plist[i]; lC's w is that slot), so that a
+    // candidate run is read contiguously
+    const float4 *lA, *lB, *lC;
     int lvl;                         // level force: the level of this launch's items
 };
 
@@ -1178,6 +1182,22 @@ __global__ void __launch_bounds__(256) k_force_pack(ForceArgs a, const int32_t *
         atomicMax(reinterpret_cast<unsigned *>(key_hmax) + key, mx);
 }
 
+// The level force's pack arrays copied into the order of the per-level lists
+// (every slot appears once in them), each entry's slot in lC's w.
+__global__ void __launch_bounds__(256) k_lvl_gather_pack(const int32_t *plist, int64_t n, const float4 *pA,
+                                                         const float4 *pB, const float4 *pC, float4 *lA, float4 *lB,
+                                                         float4 *lC)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int j = __ldg(plist + i);
+    lA[i] = __ldg(pA + j);
+    lB[i] = __ldg(pB + j);
+    float4 q = __ldg(pC + j);
+    q.w = __int_as_float(j);
+    lC[i] = q;
+}
+
 // The level force's candidate streams for an item of level `lvl` whose cell
 // has Morton code `cell` at that level and finest-cell origin `org`: one per
 // level l' of the hierarchy, over the list of level-l' particles.  Pairs need
@@ -1289,18 +1309,20 @@ __device__ int stage_force(const ForceArgs &a, const Tab &tab, int total, const 
             qc[u] = make_float4(0.f, 1.f, 0.f, 0.f);
             if (g < total) {
                 e = advance(tab, nk, e, g);
-                const int j = kLvl ? __ldg(c.plist + tab.base[e] + g) : tab.base[e] + g;
-                const float4 p = __ldg(a.pA + j);
+                const int j = tab.base[e] + g;      // level mode: an entry of the level lists
                 if (kLvl) {
-                    qa[u] = lvl_frame(c, (uint32_t)__ldg(c.mkey + j), org, p);
+                    qa[u] = lvl_frame(c, (uint32_t)__ldg(c.pkey + j), org, __ldg(a.lA + j));
+                    qb[u] = __ldg(a.lB + j);
+                    qc[u] = __ldg(a.lC + j);
                 } else {
+                    const float4 p = __ldg(a.pA + j);
                     float sx, sy, sz;
                     stencil_shift(c, tab.t[e], sx, sy, sz);
                     qa[u] = make_float4(p.x + sx, p.y + sy, p.z + sz, p.w);
+                    qb[u] = __ldg(a.pB + j);
+                    qc[u] = __ldg(a.pC + j);
+                    qc[u].w = __int_as_float(j);
                 }
-                qb[u] = __ldg(a.pB + j);
-                qc[u] = __ldg(a.pC + j);
-                qc[u].w = __int_as_float(j);
             }
             eu[u] = e;
         }
@@ -1770,7 +1792,7 @@ Common make_common(sph_ctx *c, int cap)
     m.fine_n = 0;
     for (int k = 0; k < 3; ++k) m.fine_edge[k] = 0.0f;
     m.defer = nullptr;
-    m.plist = m.pkey = m.lstart = nullptr;
+    m.pkey = m.lstart = nullptr;
     m.heavy = nullptr;
     m.heavy_at = 0;
     m.one_phase = 0;
@@ -2006,6 +2028,7 @@ ForceArgs force_args(sph_ctx *c)
     a.pB = c->pack + c->n;
     a.pC = c->pack + 2 * c->n;
     a.key_hmax = nullptr;
+    a.lA = a.lB = a.lC = nullptr;
     a.lvl = 0;
     return a;
 }
@@ -2047,7 +2070,6 @@ cudaError_t run_force_levels(sph_ctx *c)
     a.c.fine_n = 1 << c->lvl_max;
     for (int k = 0; k < 3; ++k) a.c.fine_edge[k] = (float)c->edge[k];
     int32_t *plist = c->keys[c->sorted_buf ^ 1], *pkey = c->vals[c->sorted_buf ^ 1];   // free after the sort
-    a.c.plist = plist;
     a.c.pkey = pkey;
     a.c.lstart = c->lstart;
     a.c.lvl_min = c->lvl_min;
@@ -2064,6 +2086,14 @@ cudaError_t run_force_levels(sph_ctx *c)
     c->launches += 1;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = run_level_lists(c, plist, pkey)) != cudaSuccess) return e;
+    a.lA = c->lpack;
+    a.lB = c->lpack + c->n;
+    a.lC = c->lpack + 2 * c->n;
+    k_lvl_gather_pack<<<(unsigned)((c->n + 255) / 256), 256, 0, c->stream>>>(plist, c->n, a.pA, a.pB, a.pC,
+                                                                             c->lpack, c->lpack + c->n,
+                                                                             c->lpack + 2 * c->n);
+    c->launches += 1;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const size_t smem = force_smem_bytes(c->tuning.block_threads_force, a.c.cap);
     int w_one = kOneWarps;
     while (w_one > 1 && force_smem_bytes(32 * w_one, a.c.cap) + 256 > c->smem_optin) --w_one;

@@ -123,6 +123,7 @@ bool make_plan(const sph_aos_layout &L, int64_t n, int64_t ncell_max, uint32_t w
         p->tscan = take(4 * (N + 1));
         p->iscan = take(4 * (N + 1));
         p->lstart = take(4 * (kLevelMax + 2));
+        p->lpack = take(3 * 16 * N);
     }
     p->stats = take(sizeof(DevStats));
     for (int f = 0; f < SPH_NFIELDS; ++f)
@@ -223,6 +224,7 @@ sph_status sph_create(const sph_aos_layout *layout, const sph_params *params, in
         c->tcode = (int32_t *)(w + plan.tcode);
         c->tscan = (int32_t *)(w + plan.tscan);
         c->iscan = (int32_t *)(w + plan.iscan);
+        c->lpack = (float4 *)(w + plan.lpack);
         c->lstart = (int32_t *)(w + plan.lstart);
     }
     c->dstats = (DevStats *)(w + plan.stats);

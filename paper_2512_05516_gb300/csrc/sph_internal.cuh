@@ -85,7 +85,7 @@ struct Plan {
     size_t cell_count, cell_start, scan_part, ghist;
     size_t item_cell, item_first, item_count, item_tmp, item_sorted, item_class, class_hist;
     size_t nngb, nngb_force, dflags, stage, aos_tmp, stats, key_hmax, origin, pack, buf_origin;
-    size_t level, level_tmp, tlist, tcode, tscan, iscan, lstart;   // level hierarchy (SPH_WS_LEVELS)
+    size_t level, level_tmp, tlist, tcode, tscan, iscan, lstart, lpack;   // level hierarchy (SPH_WS_LEVELS)
     size_t soa[SPH_NFIELDS][3];
     size_t total;
     int64_t item_max, nblk_radix;
@@ -361,6 +361,7 @@ struct sph_ctx {
     int8_t *level = nullptr, *level_tmp = nullptr;
     int32_t *tlist = nullptr, *tcode = nullptr, *tscan = nullptr, *iscan = nullptr;
     int32_t *lstart = nullptr;    // start of every level's list (force), kLevelMax + 2 entries
+    float4 *lpack = nullptr;      // 3 x n: the force's pack arrays in the order of the level lists
     sph::DevStats *dstats = nullptr;
     void *soa[SPH_NFIELDS][3] = {};
     int prec[SPH_NFIELDS] = {};
