@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--no-placement", action="store_true", help="skip the host-vs-GPU conversion placement rows")
     ap.add_argument("--no-levels", action="store_true", help="skip the per-particle-h level hierarchy rows")
     ap.add_argument("--levels-only", action="store_true", help="print only the level hierarchy rows")
+    ap.add_argument("--profile-n", type=int, default=2_097_152,
+                    help="particles of the levels profile case")
     ap.add_argument("--profile-case", choices=["pairs", "memory", "buffers", "levels"], default=None,
                     help="run one small fixed workload for an ncu capture and exit")
     return ap.parse_args()
@@ -1006,13 +1008,13 @@ def profile_buffers():
         raise SystemExit(1)
 
 
-def profile_levels():
-    """'levels': the adaptive-h clustered set at 2,097,152 particles (AoS
-    235 MB > L2), levels from the set, margin 0.1: bin, convert, the density
-    with 5 Newton steps and the force over the hierarchy, twice."""
+def profile_levels(n: int = 2_097_152):
+    """'levels': the adaptive-h clustered set at n particles (2,097,152 by
+    default: AoS 235 MB > L2), levels from the set, margin 0.1: bin, convert,
+    the density with 5 Newton steps and the force over the hierarchy, twice."""
     import torch
     import paper_2512_05516_gb300 as sph
-    wl = sph_inputs.gaussian_mixture_adaptive(2_097_152)
+    wl = sph_inputs.gaussian_mixture_adaptive(n)
     lo, hi = wl.meta["levels"]
     params = sph.make_params(wl.box, eta=wl.eta, h_max=wl.h_cap)
     aos = torch.from_numpy(wl.aos).cuda()
@@ -1033,7 +1035,7 @@ def profile_levels():
         raise SystemExit(1)
 
 
-def profile_case(which: str):
+def profile_case(which: str, n_levels: int = 2_097_152):
     """Small fixed workloads for ncu captures (profiles/ summaries name the
     command).  'pairs': the 1,072,476-particle Sod step twice (the second is
     the one to capture), default launch shapes.  'memory': the long-run
@@ -1046,7 +1048,7 @@ def profile_case(which: str):
         profile_buffers()
         return
     if which == "levels":
-        profile_levels()
+        profile_levels(n_levels)
         return
     if which == "pairs":
         wl = sph_inputs.sod()
@@ -1081,7 +1083,7 @@ def profile_case(which: str):
 def main():
     args = parse()
     if args.profile_case:
-        profile_case(args.profile_case)
+        profile_case(args.profile_case, args.profile_n)
         return
     if args.levels_only:
         print(json.dumps({"adaptive_h_levels": run_levels()}))
