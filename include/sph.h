@@ -551,6 +551,19 @@ sph_status sph_get_stats(sph_ctx *ctx, sph_stats *out);
 /* Zero the device counters and the sticky error word (asynchronous). */
 sph_status sph_reset_stats(sph_ctx *ctx);
 
+/* Timing hooks around the pair kernels themselves (measurement only; the
+ * paper has no counterpart).  With a pair set, sph_density records ev_begin
+ * on the context's stream right before its pair kernel (after its pack
+ * pass) and ev_end right after it; with SPH_KEV_FORCE, sph_force does the
+ * same around its pair kernel.  ev_begin and ev_end are cudaEvent_t handles
+ * owned by the caller, who must keep them alive while they are set; NULL
+ * for both clears the hook.  Only the cell-list kernels record (not the
+ * level hierarchy's or the plain form's).  Errors: SPH_EINVAL (unknown
+ * `which`, or one handle NULL and the other not). */
+#define SPH_KEV_DENSITY 0
+#define SPH_KEV_FORCE   1
+sph_status sph_set_kernel_events(sph_ctx *ctx, int32_t which, void *ev_begin, void *ev_end);
+
 /* Set launch shapes; values <= 0 keep the defaults.  Takes effect at the next
  * pair-kernel call.  Errors: SPH_EINVAL (block_threads not a multiple of 32 in
  * [32, 256], or stage sizes outside [32, 65535] or above the shared-memory limit). */

@@ -13,7 +13,7 @@ from __future__ import annotations
 import ctypes as C
 
 from . import _capi
-from ._capi import (AOS_F32, AOS_F64, BIN_DRIFT_KEYS, BIN_REORDER, BIT, ERR_HCAP, ERR_NEWTON, ERR_NONFINITE, ERR_OUTSIDE, ERR_TIMEOUT,
+from ._capi import (KEV_DENSITY, KEV_FORCE, AOS_F32, AOS_F64, BIN_DRIFT_KEYS, BIN_REORDER, BIT, ERR_HCAP, ERR_NEWTON, ERR_NONFINITE, ERR_OUTSIDE, ERR_TIMEOUT,
                     PFLAG_HCAP, PFLAG_NEWTON, PFLAG_NONFINITE,
                     F_A, F_CS, F_DUDT, F_H, F_M, F_P, F_RHO, F_U, F_V, F_X, FIELD_NAMES,
                     FIELDS_DENSITY, FIELDS_FORCE, FIELDS_KICK, FIELDS_OUTPUT, FLAG_PLAIN_SUM,
@@ -162,6 +162,10 @@ def sph_get_stats(ctx):
 
 def sph_reset_stats(ctx) -> int:
     return _lib.sph_reset_stats(ctx)
+
+
+def sph_set_kernel_events(ctx, which: int, ev_begin, ev_end) -> int:
+    return _lib.sph_set_kernel_events(ctx, which, ev_begin, ev_end)
 
 
 def sph_set_tuning(ctx, tuning: sph_tuning) -> int:
@@ -465,6 +469,20 @@ class Sph:
 
     def reset_stats(self):
         _check(sph_reset_stats(self.ctx), "sph_reset_stats")
+
+    def set_kernel_events(self, which: int, ev_begin=None, ev_end=None):
+        """Record two torch.cuda.Events (enable_timing=True) around the
+        density (KEV_DENSITY) or force (KEV_FORCE) pair kernel of every later
+        call; None for both clears.  The events must stay alive while set."""
+        handles = []
+        for ev in (ev_begin, ev_end):
+            if ev is None:
+                handles.append(None)
+                continue
+            if not ev.cuda_event:            # torch creates the event at its first record
+                ev.record(self.stream)
+            handles.append(ev.cuda_event)
+        _check(sph_set_kernel_events(self.ctx, which, handles[0], handles[1]), "sph_set_kernel_events")
 
     def set_tuning(self, block_threads=0, ctas_per_sm=0, stage_density=0, stage_force=0,
                    subcells=0, item_order=-1, class_launches=-1, pair_kernel=-1, block_threads_force=0):

@@ -35,6 +35,7 @@ FLAG_PLAIN_SUM = 1
 WS_REORDER = 1
 BIN_REORDER, BIN_DRIFT_KEYS = 1, 2
 WS_LEVELS = 2
+KEV_DENSITY, KEV_FORCE = 0, 1
 LEVEL_MIN, LEVEL_MAX, LEVELS_MAX = 2, 10, 8
 ERR_NONFINITE, ERR_OUTSIDE, ERR_HCAP, ERR_NEWTON, ERR_TIMEOUT = 1, 2, 4, 8, 16
 PFLAG_HCAP, PFLAG_NEWTON, PFLAG_NONFINITE = 1, 2, 4
@@ -96,6 +97,7 @@ PROTOTYPES = {
     "sph_get_field_scale": (C.c_int, [_P, C.POINTER(C.c_int32)]),
     "sph_get_stats": (C.c_int, [_P, C.POINTER(sph_stats)]),
     "sph_reset_stats": (C.c_int, [_P]),
+    "sph_set_kernel_events": (C.c_int, [_P, C.c_int32, _P, _P]),
     "sph_set_tuning": (C.c_int, [_P, C.POINTER(sph_tuning)]),
     "sph_get_tuning": (C.c_int, [_P, C.POINTER(sph_tuning)]),
     "sph_describe": (C.c_int, [_P, C.POINTER(sph_desc)]),

@@ -1942,7 +1942,11 @@ cudaError_t run_density(sph_ctx *c, int newton_steps)
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t smem = density_smem_bytes(c->tuning.block_threads, a.c.cap);
+    if (c->kev[SPH_KEV_DENSITY][0] && (e = cudaEventRecord(c->kev[SPH_KEV_DENSITY][0], c->stream)) != cudaSuccess)
+        return e;
     if ((e = launch_persistent(c, k_density<false>, a, smem, c->lc_density, c->tuning.block_threads)) != cudaSuccess) return e;
+    if (c->kev[SPH_KEV_DENSITY][1] && (e = cudaEventRecord(c->kev[SPH_KEV_DENSITY][1], c->stream)) != cudaSuccess)
+        return e;
     if (a.write_h && h_packed) return run_pack(c, c->stage, SPH_F_H);
     return cudaSuccess;
 }
@@ -2056,7 +2060,12 @@ cudaError_t run_force(sph_ctx *c)
     }
     // the pair kernel reads only the packed FP32 arrays: one instantiation
     const size_t smem = force_smem_bytes(c->tuning.block_threads_force, a.c.cap);
-    return launch_persistent(c, k_force<false>, a, smem, c->lc_force, c->tuning.block_threads_force);
+    if (c->kev[SPH_KEV_FORCE][0] && (e = cudaEventRecord(c->kev[SPH_KEV_FORCE][0], c->stream)) != cudaSuccess)
+        return e;
+    if ((e = launch_persistent(c, k_force<false>, a, smem, c->lc_force, c->tuning.block_threads_force)) != cudaSuccess)
+        return e;
+    if (c->kev[SPH_KEV_FORCE][1]) return cudaEventRecord(c->kev[SPH_KEV_FORCE][1], c->stream);
+    return cudaSuccess;
 }
 
 // The force over the level hierarchy: one pack pass, the per-level lists,

@@ -650,6 +650,15 @@ sph_status sph_get_stats(sph_ctx *c, sph_stats *out)
     return SPH_OK;
 }
 
+sph_status sph_set_kernel_events(sph_ctx *c, int32_t which, void *ev_begin, void *ev_end)
+{
+    if (!c || (which != SPH_KEV_DENSITY && which != SPH_KEV_FORCE)) return SPH_EINVAL;
+    if ((ev_begin == nullptr) != (ev_end == nullptr)) return SPH_EINVAL;
+    c->kev[which][0] = (cudaEvent_t)ev_begin;
+    c->kev[which][1] = (cudaEvent_t)ev_end;
+    return SPH_OK;
+}
+
 sph_status sph_reset_stats(sph_ctx *c)
 {
     if (!c) return SPH_EINVAL;

@@ -368,6 +368,7 @@ struct sph_ctx {
     int32_t scale_exp[SPH_NFIELDS] = {};   // storage scale 2^e of every field
     uint32_t valid = 0;
     uint64_t launches = 0;        // kernels launched through this context
+    cudaEvent_t kev[2][2] = {};   // timing hooks around the density and force pair kernels
 
     int32_t *perm() const { return vals[sorted_buf]; }
     float enc(int f) const { return ldexpf(1.0f, scale_exp[f]); }     // value -> stored

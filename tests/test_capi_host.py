@@ -132,6 +132,7 @@ def test_calls_on_null_context_fail_cleanly(sph):
     assert sph.sph_density_levels(null, 0) == sph._capi.EINVAL
     assert sph.sph_force_levels(null) == sph._capi.EINVAL
     assert sph.sph_level_counts(null)[0] == sph._capi.EINVAL
+    assert sph.sph_set_kernel_events(null, sph.KEV_DENSITY, None, None) == sph._capi.EINVAL
     sph.sph_destroy(null)
     assert sph.sph_status_str(-5).startswith("cell grid")
 
@@ -158,4 +159,5 @@ def test_binding_constants_match_the_header(sph):
     assert defs["SPH_BIN_DRIFT_KEYS"] == _capi.BIN_DRIFT_KEYS
     assert defs["SPH_WS_REORDER"] == _capi.WS_REORDER
     assert defs["SPH_WS_LEVELS"] == _capi.WS_LEVELS
+    assert (defs["SPH_KEV_DENSITY"], defs["SPH_KEV_FORCE"]) == (_capi.KEV_DENSITY, _capi.KEV_FORCE)
     assert _capi.sph_tuning.block_threads_force.offset == C.sizeof(_capi.sph_tuning) - 4
