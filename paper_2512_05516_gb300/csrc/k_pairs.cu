@@ -906,8 +906,9 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
             // candidates than defer_at: coarse-level targets spread over their
             // cell next to a dense cluster, or started from an h far too large
             // for what surrounds them.  Its targets go to the per-target list
-            // and are gathered one by one, each by a whole warp, in the
-            // launch that follows (k_density_one); nothing is written here.
+            // and are gathered one by one, each by a warp (a block of warps
+            // when its stream outgrows a warp's stage), in the launches that
+            // follow (k_density_one); nothing is written here.
             const unsigned bal = __ballot_sync(FULL, ok);
             unsigned base = 0;
             if (lane == 0) base = atomicAdd(&c.st->defer_n, (unsigned)__popc(bal));
@@ -1416,7 +1417,8 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_force(ForceArgs a)
             // A long stream: coarse targets spread over their cell next to a
             // dense cluster, whose box takes in the cluster's fine lists.
             // Each target goes to the per-target list instead and is gathered
-            // by a whole warp with its own reach (k_force_one).
+            // with its own reach by a warp, or by a block of warps when its
+            // stream is long (k_force_one).
             const unsigned bal = __ballot_sync(FULL, ok);
             unsigned base = 0;
             if (lane == 0) base = atomicAdd(&c.st->defer_n, (unsigned)__popc(bal));
