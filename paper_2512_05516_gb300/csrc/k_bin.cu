@@ -966,6 +966,37 @@ cudaError_t run_bin_levels(sph_ctx *c, double grow)
     return cudaGetLastError();
 }
 
+// Coarse index of the sorted keys of list j (blockIdx.y): entry q of its
+// table is the first index of the list whose key >> shift is >= q, for q in
+// [0, C]; one thread per entry, each a binary search over the list.
+__global__ void k_coarse_index(const int32_t *keys, const int32_t *bounds, int64_t n, int shift, int C,
+                               int64_t stride, int32_t *tables)
+{
+    const int j = blockIdx.y;
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q > C) return;
+    int64_t lo = bounds ? bounds[j] : 0, hi = bounds ? bounds[j + 1] : n;
+    const int64_t v = q << shift;           // keys are below 2^31, so v never wraps them
+    while (lo < hi) {
+        const int64_t mid = lo + ((hi - lo) >> 1);
+        if ((int64_t)__ldg(keys + mid) < v) lo = mid + 1;
+        else hi = mid;
+    }
+    tables[j * stride + q] = (int32_t)lo;
+}
+
+cudaError_t run_coarse_index(sph_ctx *c, const int32_t *keys, const int32_t *bounds, int nlist, int lc,
+                             int32_t *tables)
+{
+    if (nlist <= 0) return cudaSuccess;
+    const int shift = 3 * (c->lvl_max - lc);
+    const int C = 1 << (3 * lc);
+    const dim3 grid(blocks_for((int64_t)C + 1, 256), (unsigned)nlist);
+    k_coarse_index<<<grid, 256, 0, c->stream>>>(keys, bounds, c->n, shift, C, c->cs_stride, tables);
+    c->launches += 1;
+    return cudaGetLastError();
+}
+
 cudaError_t run_level_items(sph_ctx *c, int l)
 {
     cudaStream_t s = c->stream;

@@ -94,6 +94,13 @@ struct Common {
     // [lstart[l], lstart[l+1])), and the largest h of each level's particles
     const int32_t *pkey, *lstart;
     int lvl_min, lvl_max;
+    // coarse indexes of the sorted keys (cs[q]: the first index in coarse
+    // cell q or later, q in [0, cs_C]), for the slots and for each level's
+    // force list (table lp - lvl_min), cs_stride apart
+    const int32_t *cs_slot, *cs_list;
+    int cs_shift, cs_C;              // the slots' table
+    int cl_shift, cl_C;              // the lists' tables
+    int64_t cs_stride;
     float lcap[kLevelMax + 1];
 };
 
@@ -361,6 +368,20 @@ __device__ __forceinline__ int key_lower_bound(const int32_t *key, int lo, int h
     return lo;
 }
 
+// The same, within a sub-range [lo, hi) of a sorted list whose coarse index
+// is cs: the answer over the whole list lies in [cs[q], cs[q + 1]] for v's
+// coarse cell q, so the search runs over that bracket only (none at all when
+// v opens a coarse cell) and the answer is then clamped to [lo, hi).
+__device__ __forceinline__ int key_lower_bound_cs(const int32_t *key, int lo, int hi, int32_t v, const int32_t *cs,
+                                                  int shift, int C)
+{
+    const int q = min(C, (int)((uint32_t)v >> shift));
+    const int A = __ldg(cs + q), B = __ldg(cs + min(q + 1, C));
+    const int a = max(A, lo), b = min(B, hi);
+    if (a >= b) return min(max(A, lo), hi);
+    return key_lower_bound(key, a, b, v);
+}
+
 // Slot runs of the 27 cells of the item's level around `cell` (its Morton
 // code at that level), periodic, and of their 8 children at the next level:
 // a cell of level l is the run of keys with its code as prefix, found by
@@ -379,15 +400,16 @@ __device__ void lvl_bounds(const Common &c, int cell, int *bnd, int lane)
         const uint32_t nz = (morton_compact(cc >> 2) + (uint32_t)da[2]) & m;
         const int sh = 3 * c.lvl_dn;
         const int32_t code = (int32_t)morton_key(nx, ny, nz);
-        const int s0 = key_lower_bound(c.mkey, 0, (int)c.n, code << sh);
-        const int e0 = key_lower_bound(c.mkey, s0, (int)c.n, (code + 1) << sh);
+        const int s0 = key_lower_bound_cs(c.mkey, 0, (int)c.n, code << sh, c.cs_slot, c.cs_shift, c.cs_C);
+        const int e0 = key_lower_bound_cs(c.mkey, s0, (int)c.n, (code + 1) << sh, c.cs_slot, c.cs_shift, c.cs_C);
         int *b = bnd + 9 * lane;
         b[0] = s0;
         b[8] = e0;
         int lo = s0;
 #pragma unroll
         for (int q = 1; q < 8; ++q) {
-            if (c.lvl_dn > 0 && lo < e0) lo = key_lower_bound(c.mkey, lo, e0, ((code << 3) + q) << (sh - 3));
+            if (c.lvl_dn > 0 && lo < e0)
+                lo = key_lower_bound_cs(c.mkey, lo, e0, ((code << 3) + q) << (sh - 3), c.cs_slot, c.cs_shift, c.cs_C);
             else lo = c.lvl_dn > 0 ? lo : e0;
             b[q] = lo;
         }
@@ -1248,8 +1270,9 @@ __device__ int lvl_force_table(const Common &c, int cell, int lvl, int3 org, con
                 const int32_t code = (int32_t)morton_key((uint32_t)(oc[0] + da[0]) & m, (uint32_t)(oc[1] + da[1]) & m,
                                                          (uint32_t)(oc[2] + da[2]) & m);
                 const int l0 = __ldg(c.lstart + lp), l1 = __ldg(c.lstart + lp + 1);
-                const int s0 = key_lower_bound(c.pkey, l0, l1, code << (3 * dn));
-                cnt[i] = key_lower_bound(c.pkey, s0, l1, (code + 1) << (3 * dn)) - s0;
+                const int32_t *cs = c.cs_list + (lp - c.lvl_min) * c.cs_stride;
+                const int s0 = key_lower_bound_cs(c.pkey, l0, l1, code << (3 * dn), cs, c.cl_shift, c.cl_C);
+                cnt[i] = key_lower_bound_cs(c.pkey, s0, l1, (code + 1) << (3 * dn), cs, c.cl_shift, c.cl_C) - s0;
                 st[i] = s0;
             }
         }
@@ -1795,6 +1818,19 @@ Common make_common(sph_ctx *c, int cap)
     for (int k = 0; k < 3; ++k) m.fine_edge[k] = 0.0f;
     m.defer = nullptr;
     m.pkey = m.lstart = nullptr;
+    m.cs_slot = m.cs_list = nullptr;
+    m.cs_shift = m.cl_shift = 0;
+    m.cs_C = m.cl_C = 0;
+    m.cs_stride = 0;
+    if (c->cidx) {
+        m.cs_slot = c->cidx;
+        m.cs_list = c->cidx + c->cs_stride;
+        m.cs_shift = 3 * (c->lvl_max - c->cs_lc);
+        m.cs_C = 1 << (3 * c->cs_lc);
+        m.cl_shift = 3 * (c->lvl_max - c->cl_lc);
+        m.cl_C = 1 << (3 * c->cl_lc);
+        m.cs_stride = c->cs_stride;
+    }
     m.heavy = nullptr;
     m.heavy_at = 0;
     m.one_phase = 0;
@@ -2097,6 +2133,9 @@ cudaError_t run_force_levels(sph_ctx *c)
     c->launches += 1;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = run_level_lists(c, plist, pkey)) != cudaSuccess) return e;
+    if ((e = run_coarse_index(c, pkey, c->lstart + c->lvl_min, c->lvl_max - c->lvl_min + 1, c->cl_lc,
+                              c->cidx + c->cs_stride)) != cudaSuccess)
+        return e;
     a.lA = c->lpack;
     a.lB = c->lpack + c->n;
     a.lC = c->lpack + 2 * c->n;

@@ -1,6 +1,7 @@
 // C-ABI entry points of libsph: argument validation, the workspace plan, and
 // dispatch to the kernels.  Every argument error is caught here, before any
 // device work is issued.
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -124,6 +125,10 @@ bool make_plan(const sph_aos_layout &L, int64_t n, int64_t ncell_max, uint32_t w
         p->iscan = take(4 * (N + 1));
         p->lstart = take(4 * (kLevelMax + 2));
         p->lpack = take(3 * 16 * N);
+        // coarse indexes: at most 8^7 cells, and no more cells than particles
+        p->cidx_lc = 1;
+        while (p->cidx_lc < 7 && ((int64_t)1 << (3 * (p->cidx_lc + 1))) <= n) ++p->cidx_lc;
+        p->cidx = take(4 * (size_t)(1 + SPH_LEVELS_MAX) * (((size_t)1 << (3 * p->cidx_lc)) + 1));
     }
     p->stats = take(sizeof(DevStats));
     for (int f = 0; f < SPH_NFIELDS; ++f)
@@ -225,6 +230,8 @@ sph_status sph_create(const sph_aos_layout *layout, const sph_params *params, in
         c->tscan = (int32_t *)(w + plan.tscan);
         c->iscan = (int32_t *)(w + plan.iscan);
         c->lpack = (float4 *)(w + plan.lpack);
+        c->cidx = (int32_t *)(w + plan.cidx);
+        c->cs_stride = ((int64_t)1 << (3 * plan.cidx_lc)) + 1;
         c->lstart = (int32_t *)(w + plan.lstart);
     }
     c->dstats = (DevStats *)(w + plan.stats);
@@ -503,6 +510,9 @@ sph_status sph_bin_levels(sph_ctx *c, int32_t level_min, int32_t level_max, doub
     c->lvl_max = level_max;
     c->items_by_class = false;
     if (run_bin_levels(c, 1.0 + h_margin) != cudaSuccess) return SPH_ECUDA;
+    c->cs_lc = std::min((int32_t)c->plan.cidx_lc, level_max);
+    c->cl_lc = std::min(c->cs_lc, (int32_t)6);
+    if (run_coarse_index(c, c->slot_cell(), nullptr, 1, c->cs_lc, c->cidx) != cudaSuccess) return SPH_ECUDA;
     c->binned = true;
     return SPH_OK;
 }

@@ -86,6 +86,8 @@ struct Plan {
     size_t item_cell, item_first, item_count, item_tmp, item_sorted, item_class, class_hist;
     size_t nngb, nngb_force, dflags, stage, aos_tmp, stats, key_hmax, origin, pack, buf_origin;
     size_t level, level_tmp, tlist, tcode, tscan, iscan, lstart, lpack;   // level hierarchy (SPH_WS_LEVELS)
+    size_t cidx;                 // level hierarchy: coarse indexes of the sorted keys
+    int32_t cidx_lc;             // ... over the cells of this level (8^cidx_lc of them)
     size_t soa[SPH_NFIELDS][3];
     size_t total;
     int64_t item_max, nblk_radix;
@@ -362,6 +364,15 @@ struct sph_ctx {
     int32_t *tlist = nullptr, *tcode = nullptr, *tscan = nullptr, *iscan = nullptr;
     int32_t *lstart = nullptr;    // start of every level's list (force), kLevelMax + 2 entries
     float4 *lpack = nullptr;      // 3 x n: the force's pack arrays in the order of the level lists
+    // coarse indexes of sorted finest-cell keys: entry q of a table is the
+    // first index whose key lies in coarse cell q or later (8^cs_lc + 1
+    // entries, a table every cs_stride): table 0 over all slots (after
+    // sph_bin_levels), table 1 + j over the force's list of level
+    // lvl_min + j.  They bound the binary searches of the level kernels.
+    int32_t *cidx = nullptr;
+    int32_t cs_lc = 0;            // coarse level of the slots' table (<= the plan's, <= lvl_max)
+    int32_t cl_lc = 0;            // ... of the force lists' tables (at most 6: they are rebuilt every force)
+    int64_t cs_stride = 0;
     sph::DevStats *dstats = nullptr;
     void *soa[SPH_NFIELDS][3] = {};
     int prec[SPH_NFIELDS] = {};
@@ -389,6 +400,11 @@ cudaError_t run_kick_drift(sph_ctx *c, double dt_kick, double dt_drift, uint32_t
 cudaError_t run_bin_levels(sph_ctx *c, double grow);
 cudaError_t run_level_items(sph_ctx *c, int level);
 cudaError_t run_level_lists(sph_ctx *c, int32_t *plist, int32_t *pkey);
+// coarse index tables (sph_ctx::cidx) of `nlist` sorted key lists over the
+// 8^lc cells of level lc: with bounds == null one list [0, n); else list j
+// is [bounds[j], bounds[j + 1])
+cudaError_t run_coarse_index(sph_ctx *c, const int32_t *keys, const int32_t *bounds, int nlist, int lc,
+                             int32_t *tables);
 cudaError_t run_force_levels(sph_ctx *c);
 cudaError_t run_density_levels(sph_ctx *c, int newton_steps);
 // host-side conversion (host_convert.cu)
