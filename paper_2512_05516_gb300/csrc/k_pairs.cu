@@ -718,17 +718,59 @@ __device__ int build_lists(const Common &c, const float4 *pD, Tab &tab, const in
     return staged;
 }
 
-// One pass over a lane's list.
+// Two consecutive list entries of a density pass, their spline terms in
+// packed FP32 pairs (one instruction for both entries; each component rounds
+// as the scalar code does), then accumulated one after the other, entry e
+// before e + 1, exactly as two calls of dens_acc would.
+template <bool kPlain, bool kDeriv, bool kUni>
+__device__ __forceinline__ void dens_acc2(DAcc &a, float2 r, float2 hinv, float2 mj)
+{
+    const float2 qq = __fmul2_rn(r, hinv);
+    const float2 p = make_float2(__saturatef(fmaf(qq.x, -0.5f, 1.0f)), __saturatef(fmaf(qq.y, -0.5f, 1.0f)));
+    const float2 u = make_float2(__saturatef(1.0f - qq.x), __saturatef(1.0f - qq.y));
+    const float2 p2 = __fmul2_rn(p, p), u2 = __fmul2_rn(u, u);
+    const float2 nu3 = __fmul2_rn(u2, make_float2(-u.x, -u.y));           // -(u^2 u), exactly
+    const float2 w = __ffma2_rn(__fadd2_rn(p2, p2), p, nu3);
+    const float2 mw = kUni ? w : __fmul2_rn(mj, w);
+    if (kPlain) {
+        a.s += mw.x;
+        a.s += mw.y;
+    } else {
+        kahan_add(a.s, a.c, mw.x);
+        kahan_add(a.s, a.c, mw.y);
+    }
+    if (kDeriv) {
+        const float2 g = __ffma2_rn(qq, __fadd2_rn(u2, make_float2(-p2.x, -p2.y)), w);
+        if (kUni) {
+            a.d = a.d + g.x;
+            a.d = a.d + g.y;
+        } else {
+            a.d = fmaf(mj.x, g.x, a.d);
+            a.d = fmaf(mj.y, g.y, a.d);
+        }
+    }
+    a.n += __saturatef(p.x * 1.2676506e30f);
+    a.n += __saturatef(p.y * 1.2676506e30f);
+}
+
+// One pass over a lane's list, two entries at a time.
 template <bool kPlain, bool kDeriv, bool kUni>
 __device__ __forceinline__ void list_pass(DAcc &acc, const float *lr, int n, float hinv, int lane)
 {
+    const float2 hv = make_float2(hinv, hinv);
+    int e = 0;
     if (kUni) {
-#pragma unroll 4
-        for (int e = 0; e < n; ++e) dens_acc<kPlain, kDeriv>(acc, lr[e * 32 + lane], hinv, 1.0f);
+#pragma unroll 2
+        for (; e + 2 <= n; e += 2)
+            dens_acc2<kPlain, kDeriv, true>(acc, make_float2(lr[e * 32 + lane], lr[(e + 1) * 32 + lane]), hv,
+                                            make_float2(1.0f, 1.0f));
+        if (e < n) dens_acc<kPlain, kDeriv>(acc, lr[e * 32 + lane], hinv, 1.0f);
     } else {
-#pragma unroll 4
-        for (int e = 0; e < n; ++e)
-            dens_acc<kPlain, kDeriv>(acc, lr[(2 * e) * 32 + lane], hinv, lr[(2 * e + 1) * 32 + lane]);
+#pragma unroll 2
+        for (; e + 2 <= n; e += 2)
+            dens_acc2<kPlain, kDeriv, false>(acc, make_float2(lr[(2 * e) * 32 + lane], lr[(2 * e + 2) * 32 + lane]),
+                                             hv, make_float2(lr[(2 * e + 1) * 32 + lane], lr[(2 * e + 3) * 32 + lane]));
+        if (e < n) dens_acc<kPlain, kDeriv>(acc, lr[(2 * e) * 32 + lane], hinv, lr[(2 * e + 1) * 32 + lane]);
     }
 }
 
