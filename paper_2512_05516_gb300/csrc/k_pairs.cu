@@ -551,6 +551,25 @@ struct Cursor {
     int g, e;
 };
 
+// The density's stage holds its candidates in pairs: candidate e's (x, y, z,
+// m) are the floats 8 (e / 2) + (e % 2) + {0, 2, 4, 6}, so that candidates 2k
+// and 2k + 1 load as packed pairs (x0, x1, y0, y1), (z0, z1, m0, m1) with two
+// 16-byte loads.  A stage of cap float4 holds cap candidates (cap even).
+__device__ __forceinline__ void stage_put(float4 *sj, int e, float4 v)
+{
+    float *f = reinterpret_cast<float *>(sj) + 8 * (e >> 1) + (e & 1);
+    f[0] = v.x;
+    f[2] = v.y;
+    f[4] = v.z;
+    f[6] = v.w;
+}
+
+__device__ __forceinline__ float4 stage_get(const float4 *sj, int e)
+{
+    const float *f = reinterpret_cast<const float *>(sj) + 8 * (e >> 1) + (e & 1);
+    return make_float4(f[0], f[2], f[4], f[6]);
+}
+
 // Stage the stream's candidates within distance sqrt(R2) of the warp box, in
 // stream order, starting at `cur`, until the stage is full or the stream ends.
 // Returns how many were staged (<= cap) and moves `cur` to the first batch
@@ -563,6 +582,7 @@ __device__ int stage_density(const Common &c, const float4 *pD, const Tab &tab, 
 {
     const unsigned lt = (1u << lane) - 1u;
     const int nk = tab.nk;
+    cap &= ~1;                       // the paired layout holds an even count
     int found = 0;
     int ecur = cur.e;
     for (int g0 = cur.g; g0 < total; g0 += 32 * kU) {
@@ -599,7 +619,7 @@ __device__ int stage_density(const Common &c, const float4 *pD, const Tab &tab, 
                 return found;
             }
             if (keep) {
-                sj[found + __popc(b & lt)] = q[u];
+                stage_put(sj, found + __popc(b & lt), q[u]);
                 if (mixed && q[u].w != mref) *mixed = true;
             }
             found += nb;
@@ -638,46 +658,55 @@ __host__ __device__ inline size_t density_warp_bytes(int cap, bool levels)
 // lr[(2e + 1) * 32 + lane], up to kDensCapPair.  Appends past the capacity
 // land in the scratch entry (the count keeps growing, so an overflow is seen).
 
-// Append the staged candidates sj[0, len) with r^2 < R2l to a lane's list.
+// One candidate onto a lane's list (branch-free: a candidate that is not
+// kept is written to the next entry and overwritten by the next append).
+template <bool kUni>
+__device__ __forceinline__ void append_one(float *lr, int &n, float r, float m, bool keep, int lane)
+{
+    constexpr int lcap = kUni ? kDensCapUni : kDensCapPair;
+    const int s = min(n, lcap);
+    if (kUni) {
+        lr[s * 32 + lane] = r;
+    } else {
+        lr[(2 * s) * 32 + lane] = r;
+        lr[(2 * s + 1) * 32 + lane] = m;
+    }
+    n += keep ? 1 : 0;
+}
+
+// Append the staged candidates 0..len-1 with r^2 < R2l to a lane's list, in
+// stage order.  Two candidates at a time: their separations in packed FP32
+// pairs, each component rounding as pair_r does.
 template <bool kUni>
 __device__ __forceinline__ int append_list(const float4 *sj, int len, float xi, float yi, float zi, float R2l,
                                            float *lr, int n, int lane)
 {
-    constexpr int lcap = kUni ? kDensCapUni : kDensCapPair;
-    constexpr int LB = 4;
+    const float2 XI = make_float2(xi, xi), YI = make_float2(yi, yi), ZI = make_float2(zi, zi);
     int e0 = 0;
-    for (; e0 + LB <= len; e0 += LB) {
-        float4 q[LB];
+    for (; e0 + 4 <= len; e0 += 4) {
+        float4 a[2], b[2];
 #pragma unroll
-        for (int u = 0; u < LB; ++u) q[u] = sj[e0 + u];
+        for (int u = 0; u < 2; ++u) {
+            a[u] = sj[e0 + 2 * u];          // (x, x', y, y') of candidates e0 + 2u, e0 + 2u + 1
+            b[u] = sj[e0 + 2 * u + 1];      // (z, z', m, m')
+        }
 #pragma unroll
-        for (int u = 0; u < LB; ++u) {
-            const float r = pair_r(xi, yi, zi, q[u]);
-            const float dx = xi - q[u].x, dy = yi - q[u].y, dz = zi - q[u].z;
-            const bool keep = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < R2l;
-            const int s = min(n, lcap);
-            if (kUni) {
-                lr[s * 32 + lane] = r;
-            } else {
-                lr[(2 * s) * 32 + lane] = r;
-                lr[(2 * s + 1) * 32 + lane] = q[u].w;
-            }
-            n += keep ? 1 : 0;
+        for (int u = 0; u < 2; ++u) {
+            const float2 dx = __fadd2_rn(XI, make_float2(-a[u].x, -a[u].y));
+            const float2 dy = __fadd2_rn(YI, make_float2(-a[u].z, -a[u].w));
+            const float2 dz = __fadd2_rn(ZI, make_float2(-b[u].x, -b[u].y));
+            const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+            const float2 t = __fadd2_rn(r2, make_float2(1.0e-30f, 1.0e-30f));
+            const float2 r = __fmul2_rn(r2, make_float2(rsqrt_normal(t.x), rsqrt_normal(t.y)));
+            append_one<kUni>(lr, n, r.x, b[u].z, r2.x < R2l, lane);
+            append_one<kUni>(lr, n, r.y, b[u].w, r2.y < R2l, lane);
         }
     }
     for (; e0 < len; ++e0) {
-        const float4 q = sj[e0];
+        const float4 q = stage_get(sj, e0);
         const float r = pair_r(xi, yi, zi, q);
         const float dx = xi - q.x, dy = yi - q.y, dz = zi - q.z;
-        const bool keep = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < R2l;
-        const int s = min(n, lcap);
-        if (kUni) {
-            lr[s * 32 + lane] = r;
-        } else {
-            lr[(2 * s) * 32 + lane] = r;
-            lr[(2 * s + 1) * 32 + lane] = q.w;
-        }
-        n += keep ? 1 : 0;
+        append_one<kUni>(lr, n, r, q.w, fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < R2l, lane);
     }
     return n;
 }
@@ -939,8 +968,10 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density(DensityArgs a)
                     const int len = stage_density<kLvl>(c, a.pD, tab, tot, bb, R2, sj, c.cap, sc, lane, org);
                     if (dl) {
                         my_tests += (unsigned long long)len;
-                        for (int e = 0; e < len; ++e)
-                            dens_acc_rt(acc, pair_r(xi, yi, zi, sj[e]), hinv, sj[e].w, a.plain_sum, deriv);
+                        for (int e = 0; e < len; ++e) {
+                            const float4 q = stage_get(sj, e);
+                            dens_acc_rt(acc, pair_r(xi, yi, zi, q), hinv, q.w, a.plain_sum, deriv);
+                        }
                     }
                     __syncwarp();
                 } while (sc.g < tot);
@@ -1124,8 +1155,10 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density_one(DensityArgs a)
             const bool deriv = pass + 1 < a.npass;
             DAcc acc{0.f, 0.f, 0.f, 0.f};
             if (fit_t) {
-                for (int e = lane; e < Tt; e += 32)
-                    dens_acc_rt(acc, pair_r(xt, yt, zt, sj[e]), hinv, sj[e].w, a.plain_sum, deriv);
+                for (int e = lane; e < Tt; e += 32) {
+                    const float4 q = stage_get(sj, e);
+                    dens_acc_rt(acc, pair_r(xt, yt, zt, q), hinv, q.w, a.plain_sum, deriv);
+                }
                 my_tests += (unsigned long long)max(0, (Tt - lane + 31) >> 5);
             } else {
                 // more than the stages within the target's own reach: stream it
@@ -1135,8 +1168,10 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_density_one(DensityArgs a)
                 Cursor sc{g0, g0 < g1 ? advance(tab, tab.nk, 0, g0) : 0};
                 while (sc.g < g1) {
                     const int len = stage_density<true, 8>(c, a.pD, tab, g1, pb, h2x4, sj, cap1, sc, lane, org);
-                    for (int e = lane; e < len; e += 32)
-                        dens_acc_rt(acc, pair_r(xt, yt, zt, sj[e]), hinv, sj[e].w, a.plain_sum, deriv);
+                    for (int e = lane; e < len; e += 32) {
+                        const float4 q = stage_get(sj, e);
+                        dens_acc_rt(acc, pair_r(xt, yt, zt, q), hinv, q.w, a.plain_sum, deriv);
+                    }
                     my_tests += (unsigned long long)max(0, (len - lane + 31) >> 5);
                     __syncwarp();
                 }
