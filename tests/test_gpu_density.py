@@ -5,7 +5,9 @@ Tolerances: density and h within 1e-5 relative (FP32 arithmetic on FP32
 storage).  Neighbour counts are integers decided by an FP32 distance test
 against the FP64 one: each GPU count must lie between the oracle's counts at
 h (1 -+ delta), i.e. only pairs within delta of the support radius may differ,
-and the counts must be identical for every particle without such a pair."""
+and the counts must be identical for every particle without such a pair.
+Unequal masses take the lists' (r, m) pair layout and, where a lane's
+neighbourhood outgrows it, the streamed sums; both are checked too."""
 import numpy as np
 import pytest
 
@@ -93,3 +95,26 @@ def test_h_clamp_is_counted(orc):
     clamped = int(np.count_nonzero(o["flags"] & orc.FLAG_HCAP))
     assert abs(int(g["stats"]["hcap_clamps"]) - clamped) <= max(2, clamped // 100)
     assert (np.abs(g["rho"] - o["rho"]) / o["rho"]).max() <= 1e-5
+
+
+@pytest.mark.parametrize("case", ["uniform_fixed_h", "sod_newton"])
+def test_unequal_masses(orc, case):
+    # masses that differ between particles: the density's lists hold (r, m)
+    # pairs at half the capacity (lanes whose neighbourhood outgrows that sum
+    # straight from the stream); rho, h and the counts still match the oracle
+    rng = np.random.default_rng(13)
+    if case == "uniform_fixed_h":
+        wl = sph_inputs.uniform_density()
+        wl.col("h")[:] *= 0.8             # ~25 neighbours: every list fits the pair layout
+        newton = 0
+    else:
+        wl = sph_inputs.sod(n_lattice=24, seed=13)
+        newton = 5
+    wl.col("m")[:] = wl.col("m") * rng.uniform(0.5, 1.5, wl.n)
+    g = _run_density(wl, newton)
+    o = orc.density(wl.col("x"), wl.col("m"), wl.col("h"), wl.box, wl.eta, wl.h_cap, newton)
+    assert (np.abs(g["h"] - o["h"]) / o["h"]).max() <= 1e-5
+    assert (np.abs(g["rho"] - o["rho"]) / o["rho"]).max() <= 1e-5
+    ok, lo, hi = count_band_ok(orc, wl, o["h"], g["nngb"], 2e-5)
+    assert ok.all()
+    assert g["stats"]["error_bits"] & sph_mod.ERR_NONFINITE == 0
