@@ -35,10 +35,13 @@ def _mean_abs(a):
     return float(np.mean(np.linalg.norm(a, axis=1)))
 
 
-def test_force_isolated(orc):
+@pytest.mark.parametrize("masses", ["equal", "unequal"])
+def test_force_isolated(orc, masses):
     # h, rho, P, c come from the oracle's density and are handed to both sides
     wl = sph_inputs.sod(n_lattice=24, seed=21)
     wl.col("v")[:] = np.random.default_rng(1).uniform(-0.5, 0.5, (wl.n, 3))
+    if masses == "unequal":
+        wl.col("m")[:] = wl.col("m") * np.random.default_rng(2).uniform(0.5, 1.5, wl.n)
     x, v, m, u = wl.col("x"), wl.col("v"), wl.col("m"), wl.col("u")
     d = orc.density(x, m, wl.col("h"), wl.box, wl.eta, wl.h_cap, 5)
     P, c = orc.eos(d["rho"], u, wl.gamma)
